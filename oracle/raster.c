@@ -1,0 +1,190 @@
+/*
+ * Oracle visibility: vertex transform, fixed-point snapping, scanline coverage
+ * with the top-left fill rule, and packed depth|triangle-id keys.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is part of the CPU oracle that checks the
+ * CUDA path; only the tests, the smoke check and the bench's CPU-baseline leg
+ * may load it. It shares no code with the CUDA kernels.
+ *
+ * The paper rasterizes with the primitives of Laine et al. 2020 (Sec. 5.2,
+ * "Differentiable Renderer") and states no fill rule, precision or depth
+ * encoding; this file fixes one reading bit for bit:
+ *   - clip_r = ((M[r][0] x + M[r][1] y) + M[r][2] z) + M[r][3] in float32,
+ *     every operation rounded to nearest (build with -ffp-contract=off);
+ *   - sx = (clip.x / clip.w) * (W/2) + W/2, sy = H/2 - (clip.y / clip.w) * (H/2),
+ *     X = rint(sx * 256), Y = rint(sy * 256) (8 sub-pixel bits, ties to even);
+ *   - a vertex is unusable when clip.w <= 1e-6 or |sx*256|, |sy*256| > 2^27;
+ *   - pixel (i, j) samples S = (256 i + 128, 256 j + 128);
+ *     E_ab(S) = (X_b - X_a)(S_y - Y_a) - (Y_b - Y_a)(S_x - X_a) in int64;
+ *   - both windings are drawn; a sample is covered when every edge of the
+ *     positively wound triangle has E > 0, or E == 0 on a top or left edge;
+ *   - depth d = (z0 + b1 (z1 - z0)) + b2 (z2 - z0), b1 = (float)E_20 / (float)A,
+ *     b2 = (float)E_01 / (float)A in the triangle's own vertex order;
+ *     samples with d outside [0, 1] are dropped;
+ *   - key = (float_bits(d) << 32) | triangle id, minimum per pixel (equal depth:
+ *     lower id wins), empty pixel = all ones.
+ * Coverage here is computed per row as an interval of pixels solved from each
+ * edge inequality (a scanline), not by testing pixels one at a time.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#define GUARD 134217728.0f /* 2^27 sub-pixel units */
+
+static int64_t floor_div(int64_t a, int64_t b) /* b > 0 */
+{
+    int64_t q = a / b;
+    if ((a % b != 0) && (a < 0)) q -= 1;
+    return q;
+}
+
+static int64_t ceil_div(int64_t a, int64_t b) /* b > 0 */
+{
+    return -floor_div(-a, b);
+}
+
+/* Transform V vertices by one view. Outputs (all caller-owned):
+ * clip[V*4], XY[V*2] snapped sub-pixel coordinates, z01[V], ok[V]. */
+void oracle_transform(const float* mvp, const float* pos, int V, int W, int H,
+                      float* clip, int32_t* XY, float* z01, int8_t* ok)
+{
+    const float hW = 0.5f * (float)W, hH = 0.5f * (float)H;
+    for (int v = 0; v < V; ++v) {
+        const float x = pos[3 * v], y = pos[3 * v + 1], z = pos[3 * v + 2];
+        float c[4];
+        for (int r = 0; r < 4; ++r) {
+            const float* m = mvp + 4 * r;
+            float a = m[0] * x;
+            float b = m[1] * y;
+            float s = a + b;
+            float t = m[2] * z;
+            s = s + t;
+            c[r] = s + m[3];
+        }
+        clip[4 * v + 0] = c[0];
+        clip[4 * v + 1] = c[1];
+        clip[4 * v + 2] = c[2];
+        clip[4 * v + 3] = c[3];
+        XY[2 * v] = 0;
+        XY[2 * v + 1] = 0;
+        z01[v] = 0.0f;
+        ok[v] = 0;
+        if (!(c[3] > 1e-6f)) continue;
+        float qx = c[0] / c[3];
+        float qy = c[1] / c[3];
+        float sx = qx * hW;
+        sx = sx + hW;
+        float sy = qy * hH;
+        sy = hH - sy;
+        float fx = sx * 256.0f, fy = sy * 256.0f;
+        if (!(fabsf(fx) <= GUARD) || !(fabsf(fy) <= GUARD)) continue;
+        XY[2 * v] = (int32_t)rintf(fx);
+        XY[2 * v + 1] = (int32_t)rintf(fy);
+        float qz = c[2] / c[3];
+        float zz = qz * 0.5f;
+        z01[v] = zz + 0.5f;
+        ok[v] = 1;
+    }
+}
+
+static int64_t edge_fn(int64_t xa, int64_t ya, int64_t xb, int64_t yb, int64_t sx, int64_t sy)
+{
+    return (xb - xa) * (sy - ya) - (yb - ya) * (sx - xa);
+}
+
+/* Rasterize F triangles of one view into keys[H*W] (caller initialises to all
+ * ones; keys already present are min-merged). area_sign[F] receives the sign
+ * of the snapped signed area (0 for unusable or degenerate triangles). */
+void oracle_raster(const int32_t* XY, const float* z01, const int8_t* ok,
+                   const int32_t* tri, int F, int W, int H,
+                   uint64_t* keys, int8_t* area_sign)
+{
+    for (int f = 0; f < F; ++f) {
+        const int32_t i0 = tri[3 * f], i1 = tri[3 * f + 1], i2 = tri[3 * f + 2];
+        area_sign[f] = 0;
+        if (!ok[i0] || !ok[i1] || !ok[i2]) continue;
+        const int64_t X0 = XY[2 * i0], Y0 = XY[2 * i0 + 1];
+        const int64_t X1 = XY[2 * i1], Y1 = XY[2 * i1 + 1];
+        const int64_t X2 = XY[2 * i2], Y2 = XY[2 * i2 + 1];
+        const int64_t A = edge_fn(X0, Y0, X1, Y1, X2, Y2);
+        if (A == 0) continue;
+        area_sign[f] = (int8_t)(A > 0 ? 1 : -1);
+
+        /* positively wound vertex order for the coverage test */
+        int64_t px[3] = {X0, X1, X2}, py[3] = {Y0, Y1, Y2};
+        if (A < 0) {
+            px[1] = X2; py[1] = Y2;
+            px[2] = X1; py[2] = Y1;
+        }
+        int64_t ex[3], ey[3], dx[3], dy[3];
+        int incl[3];
+        for (int k = 0; k < 3; ++k) {
+            /* edge k runs from vertex (k+1)%3 to (k+2)%3 */
+            const int a = (k + 1) % 3, b = (k + 2) % 3;
+            ex[k] = px[a];
+            ey[k] = py[a];
+            dx[k] = px[b] - px[a];
+            dy[k] = py[b] - py[a];
+            /* top edge: horizontal, interior below; left edge: going up */
+            incl[k] = (dy[k] < 0) || (dy[k] == 0 && dx[k] > 0);
+        }
+        int64_t minX = X0, maxX = X0, minY = Y0, maxY = Y0;
+        if (X1 < minX) minX = X1;
+        if (X2 < minX) minX = X2;
+        if (X1 > maxX) maxX = X1;
+        if (X2 > maxX) maxX = X2;
+        if (Y1 < minY) minY = Y1;
+        if (Y2 < minY) minY = Y2;
+        if (Y1 > maxY) maxY = Y1;
+        if (Y2 > maxY) maxY = Y2;
+        int64_t ilo = ceil_div(minX - 128, 256), ihi = floor_div(maxX - 128, 256);
+        int64_t jlo = ceil_div(minY - 128, 256), jhi = floor_div(maxY - 128, 256);
+        if (ilo < 0) ilo = 0;
+        if (jlo < 0) jlo = 0;
+        if (ihi > W - 1) ihi = W - 1;
+        if (jhi > H - 1) jhi = H - 1;
+
+        const float z0 = z01[i0], z1 = z01[i1], z2 = z01[i2];
+        const float fA = (float)A;
+        const float dz1 = z1 - z0, dz2 = z2 - z0;
+
+        for (int64_t j = jlo; j <= jhi; ++j) {
+            const int64_t Sy = 256 * j + 128;
+            int64_t lo = ilo, hi = ihi;
+            for (int k = 0; k < 3 && lo <= hi; ++k) {
+                /* E(i) = K - D i with S_x = 256 i + 128; need E(i) >= t */
+                const int64_t K = dx[k] * (Sy - ey[k]) - dy[k] * (128 - ex[k]);
+                const int64_t D = 256 * dy[k];
+                const int64_t t = incl[k] ? 0 : 1;
+                if (D == 0) {
+                    if (K < t) hi = lo - 1;
+                } else if (D > 0) {
+                    const int64_t m = floor_div(K - t, D);
+                    if (m < hi) hi = m;
+                } else {
+                    const int64_t m = ceil_div(t - K, -D);
+                    if (m > lo) lo = m;
+                }
+            }
+            for (int64_t i = lo; i <= hi; ++i) {
+                const int64_t Sx = 256 * i + 128;
+                const int64_t e20 = edge_fn(X2, Y2, X0, Y0, Sx, Sy);
+                const int64_t e01 = edge_fn(X0, Y0, X1, Y1, Sx, Sy);
+                const float b1 = (float)e20 / fA;
+                const float b2 = (float)e01 / fA;
+                float u = b1 * dz1;
+                float s = z0 + u;
+                float w = b2 * dz2;
+                float d = s + w;
+                if (!(d >= 0.0f && d <= 1.0f)) continue;
+                if (d == 0.0f) d = 0.0f; /* canonical +0 */
+                uint32_t bits;
+                memcpy(&bits, &d, 4);
+                const uint64_t key = ((uint64_t)bits << 32) | (uint32_t)f;
+                uint64_t* kp = keys + j * (int64_t)W + i;
+                if (key < *kp) *kp = key;
+            }
+        }
+    }
+}

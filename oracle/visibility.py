@@ -1,0 +1,73 @@
+"""ctypes front of the oracle's C visibility code (TEST INFRASTRUCTURE ONLY).
+
+See raster.c for the exact float32 / int64 contract (transform, 8-bit
+sub-pixel snapping, top-left fill rule, packed depth|id keys).
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _build
+
+EMPTY_KEY = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(_build.build())
+        P = ctypes.c_void_p
+        lib.oracle_transform.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P]
+        lib.oracle_transform.restype = None
+        lib.oracle_raster.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+        lib.oracle_raster.restype = None
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def transform(mvp, pos, width, height):
+    """float32 transform + snap of (V, 3) positions by one 4x4 row-major MVP.
+
+    Returns dict(clip (V,4) f32, XY (V,2) i32, z01 (V,) f32, ok (V,) i8)."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    mvp = np.ascontiguousarray(np.asarray(mvp, dtype=np.float32).reshape(16))
+    V = pos.shape[0]
+    clip = np.zeros((V, 4), np.float32)
+    XY = np.zeros((V, 2), np.int32)
+    z01 = np.zeros(V, np.float32)
+    ok = np.zeros(V, np.int8)
+    lib.oracle_transform(_ptr(mvp), _ptr(pos), V, int(width), int(height), _ptr(clip), _ptr(XY), _ptr(z01), _ptr(ok))
+    return dict(clip=clip, XY=XY, z01=z01, ok=ok)
+
+
+def raster(mvp, pos, tri, width, height):
+    """Visibility of one view: (keys (H, W) uint64, area_sign (F,) int8, transform dict)."""
+    lib = _load()
+    t = transform(mvp, pos, width, height)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    F = tri.shape[0]
+    keys = np.full((height, width), EMPTY_KEY, dtype=np.uint64)
+    asign = np.zeros(F, np.int8)
+    lib.oracle_raster(_ptr(t["XY"]), _ptr(t["z01"]), _ptr(t["ok"]), _ptr(tri), F, int(width), int(height),
+                      _ptr(keys), _ptr(asign))
+    return keys, asign, t
+
+
+def raster_views(views, pos, tri, width, height):
+    """Visibility for a batch of views: keys (B, H, W) uint64, area_sign (B, F) int8."""
+    keys, signs = [], []
+    for v in views:
+        k, s, _ = raster(v["mvp"], pos, tri, width, height)
+        keys.append(k)
+        signs.append(s)
+    return np.stack(keys), np.stack(signs)
