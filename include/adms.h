@@ -1,0 +1,209 @@
+/*
+ * adms.h — C ABI of the GB300 (sm_103a) render-and-compare library for
+ * appearance-driven mesh simplification (Hasselgren et al., "Appearance-Driven
+ * Automatic 3D Model Simplification").
+ *
+ * The calls follow the paper's statement of the problem (Sec. 3, Eq. 1):
+ * a latent mesh with textures is rendered under random cameras and lights,
+ * compared with renders of a reference, differentiated, and updated by Adam.
+ *
+ *   adms_render_reference  — forward render of a (frozen) job        (Sec. 3, reference renderer)
+ *   adms_forward_loss      — render + silhouette AA + image loss      (Sec. 5.1, 5.2, 5.3)
+ *   adms_backward          — gradients w.r.t. every latent            (Sec. 3: dL/dtheta)
+ *   adms_optimizer_step    — Laplacian term, lambda/lr schedules, Adam (Eq. 4, Eq. 5, Sec. 5.3)
+ *
+ * Conventions
+ *   - Every call returns an adms_status; nothing throws across the ABI.
+ *     adms_last_error() describes the latest failure of a context.
+ *   - Pointers: "device" = CUDA device memory of the context's GPU; "any" =
+ *     host or device memory (copied with cudaMemcpyDefault). The caller owns
+ *     every buffer it passes; the library owns each job's resident state
+ *     (mesh, textures with mip chains, gradients, Adam moments, scratch).
+ *   - All GPU work is ordered on the context's CUDA stream and asynchronous
+ *     unless stated otherwise. Inputs passed to adms_forward_loss (reference
+ *     images) must stay valid until the matching adms_backward has been
+ *     enqueued; views are copied in.
+ *   - A context is used by one host thread at a time.
+ *
+ * Layouts
+ *   - positions: float32 [V][3]; UV corners: float32 [T][2];
+ *     triangles: int32 [F][3] position indices and int32 [F][3] UV indices
+ *     (separate index buffers, so UV seams do not split positions).
+ *   - textures: float32 [h][w][4] (row = v, column = u), level 0 only;
+ *     h and w powers of two. Base colour (r, g, b, alpha); specular
+ *     (gamma, r, m, unused); tangent-space normal (x, y, z, unused).
+ *     displacement: float32 [h][w] (tessellated jobs only).
+ *   - images: float32 [B][H][W][3], row 0 at the top.
+ *   - keys: uint64 [B][H][W]; (float_bits(depth) << 32) | triangle id, all
+ *     ones for an empty pixel.
+ */
+#ifndef ADMS_H
+#define ADMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ADMS_OK = 0,
+    ADMS_ERR_ARG = -1,       /* invalid argument (null pointer, size, handle) */
+    ADMS_ERR_BUDGET = -2,    /* allocation would exceed the context's HBM budget */
+    ADMS_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+    ADMS_ERR_TIMEOUT = -4,   /* a bounded device wait gave up */
+    ADMS_ERR_NONFINITE = -5, /* a loss or gradient was NaN/Inf; the job is quarantined */
+    ADMS_ERR_STATE = -6      /* call out of order (e.g. backward before forward) */
+} adms_status;
+
+typedef struct adms_ctx adms_ctx;
+typedef int32_t adms_job;
+
+/* One camera and its lights, 112 bytes. clip = mvp * [x y z 1]^T (row-major,
+ * OpenGL conventions); screen x = (clip.x/clip.w)(W/2) + W/2,
+ * y = H/2 - (clip.y/clip.w)(H/2). A light with zero strength is off. */
+typedef struct {
+    float mvp[16];
+    float eye[3];
+    float pad0;
+    float light_pos[3]; /* point light position */
+    float light_I;      /* point light intensity; irradiance I / d^2 */
+    float light_dir[3]; /* unit vector towards the directional light */
+    float light_E;      /* directional irradiance */
+} adms_view;
+
+typedef struct {
+    int32_t n_verts, n_uv, n_tris;
+    const float* pos;       /* any, [n_verts][3] */
+    const float* uv;        /* any, [n_uv][2] */
+    const int32_t* tri_pos; /* any, [n_tris][3] */
+    const int32_t* tri_uv;  /* any, [n_tris][3] */
+} adms_mesh_desc;
+
+typedef struct {
+    const float* kd;   /* any, [kd_h][kd_w][4] */
+    const float* orm;  /* any, [orm_h][orm_w][4] */
+    const float* nrm;  /* any, [nrm_h][nrm_w][4] */
+    const float* disp; /* any, [disp_h][disp_w] or NULL */
+    int32_t kd_h, kd_w, orm_h, orm_w, nrm_h, nrm_w, disp_h, disp_w;
+    int32_t mips;      /* 1: full mip chains and trilinear filtering; 0: level 0 only */
+} adms_material_desc;
+
+enum { ADMS_LOSS_L1 = 0, ADMS_LOSS_LOGL1 = 1, ADMS_LOSS_L2 = 2 };
+
+typedef struct {
+    int32_t optimize_pos, optimize_kd, optimize_orm, optimize_nrm, optimize_disp; /* 0/1 */
+    int32_t loss;            /* ADMS_LOSS_* */
+    int32_t tess_levels;     /* edge-midpoint subdivisions of the base mesh (0 = none) */
+    int32_t batch_views;     /* views per optimizer step for the loss mean (0 = views of each call) */
+    int32_t relative_laplacian; /* 1: delta' = delta of the initial mesh; 0: absolute (delta' = 0) */
+    int32_t aa;              /* 1: silhouette antialiasing (default), 0: off */
+    float lr0;               /* initial learning rate (Sec. 5.3), e.g. 0.01 */
+    float lambda0;           /* initial Laplacian weight; <= 0 selects 0.25 L_image / L_delta at t = 0 */
+} adms_opt_params;
+
+/* Device pointers into a job's resident state (owned by the library, valid
+ * until adms_job_destroy). Texture and texture-gradient pointers address the
+ * whole mip chain, level after level (level k is [max(h>>k,1)][max(w>>k,1)][4]);
+ * gradients hold the latest backward's result per level until the next
+ * optimizer step folds the coarser levels into level 0 (the adjoint of the
+ * box filter) and zeroes them. */
+typedef struct {
+    float *pos, *kd, *orm, *nrm, *disp;
+    float *g_pos, *g_kd, *g_orm, *g_nrm, *g_disp;
+    int32_t n_verts, n_tris_render, kd_h, kd_w, orm_h, orm_w, nrm_h, nrm_w, disp_h, disp_w;
+    int32_t kd_levels, orm_levels, nrm_levels; /* mip levels held per texture (1 = level 0 only) */
+    int32_t t;            /* optimizer steps taken */
+} adms_param_view;
+
+/* Job state scalars, read back with adms_job_stats (synchronises the stream). */
+typedef struct {
+    float image_loss;     /* L_image of the latest step's forward calls (summed over calls) */
+    float laplacian;      /* L_delta at the latest optimizer step */
+    float lambda;         /* lambda_t used at the latest optimizer step */
+    float lr;             /* lr_t used at the latest optimizer step */
+    int32_t t;            /* optimizer steps taken */
+    int32_t status;       /* 0, or an adms_status latched on the device */
+    int64_t tile_overflows; /* raster tiles that fell back to a full triangle scan */
+} adms_stats;
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Create a context on the current CUDA device. hbm_budget_bytes bounds the
+ * library's own allocations (0 = no bound). cuda_stream: a cudaStream_t or
+ * NULL for the legacy default stream. */
+adms_status adms_ctx_create(adms_ctx** out, size_t hbm_budget_bytes, void* cuda_stream);
+adms_status adms_ctx_destroy(adms_ctx* ctx);
+adms_status adms_ctx_set_stream(adms_ctx* ctx, void* cuda_stream);
+/* Block until the context's stream is idle; surfaces latched device errors. */
+adms_status adms_sync(adms_ctx* ctx);
+const char* adms_last_error(adms_ctx* ctx);
+/* Bytes of HBM currently held by the context's jobs and scratch. */
+size_t adms_bytes_in_use(adms_ctx* ctx);
+
+/* ---- jobs ------------------------------------------------------------------ */
+
+/* Copy a mesh and its textures in and allocate the job's resident state
+ * (Sec. 3: the latent representation; Sec. 5.1: topology fixed, tessellation
+ * precomputed). opt may be NULL for a frozen job (e.g. a reference model).
+ * seed is kept with the job (checkpointed). Synchronises the stream. */
+adms_status adms_job_create(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
+                            const adms_opt_params* opt, uint64_t seed, adms_job* out);
+adms_status adms_job_destroy(adms_ctx* ctx, adms_job job);
+adms_status adms_job_params(adms_ctx* ctx, adms_job job, adms_param_view* out);
+adms_status adms_job_stats(adms_ctx* ctx, adms_job job, adms_stats* out);
+
+/* ---- the step (Sec. 3, Eq. 1) --------------------------------------------- */
+
+/* Forward render of n_views views at H x W with silhouette AA (Sec. 3: the
+ * reference renderer is a black box that only sees camera and light; here it
+ * is this library's own forward path applied to a frozen job).
+ * views: any, [n_views]; out_rgb: device, [n_views][H][W][3]. */
+adms_status adms_render_reference(adms_ctx* ctx, adms_job job, const adms_view* views, int32_t n_views,
+                                  int32_t H, int32_t W, float* out_rgb);
+
+/* Render each job under its views, antialias silhouettes, and take the image
+ * loss against its reference images (Sec. 5.3: L1 on Gamma(log(x + 1))).
+ *   jobs: host, [n_jobs]; views: any, all jobs' views back to back;
+ *   views_per_job, hw: host, [n_jobs] and [n_jobs][2] (H, W);
+ *   ref_rgb: host array of n_jobs device pointers, each [B_j][H_j][W_j][3];
+ *   out_loss: device, [n_jobs] (L_image of this call); out_img: NULL, or a
+ *   host array of n_jobs device pointers (NULL entries allowed) receiving the
+ *   antialiased images [B_j][H_j][W_j][3].
+ * Keeps what backward needs in the job's scratch. */
+adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, const adms_view* views,
+                              const int32_t* views_per_job, const int32_t* hw, const float* const* ref_rgb,
+                              float* out_loss, float* const* out_img);
+
+/* Accumulate dL_image/dtheta for every latent of each job from its latest
+ * forward_loss (Sec. 3, Sec. 5.1-5.2 chained backward: AA, shading, texture,
+ * interpolation, transform, tangent frame, tessellation). recompute_raster:
+ * 1 re-rasterizes and re-shades instead of reading the forward's buffers. */
+adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, int32_t recompute_raster);
+
+/* Per job: L_delta and its gradient (Eq. 4), lambda_t (Eq. 5, with the
+ * lambda_0 heuristic at t = 0), lr_t = lr0 10^(-0.0002 t) and one Adam step
+ * (beta = 0.9, 0.999, eps = 1e-8) on every optimized latent, fused with the
+ * adjoint of the mip chain and followed by clamping and a mip rebuild; zeroes
+ * the gradients and advances t. */
+adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs);
+
+/* Raw visibility of the latest forward_loss / render_reference of a job:
+ * copies [B][H][W] keys into out_keys (device). */
+adms_status adms_job_keys(adms_ctx* ctx, adms_job job, uint64_t* out_keys, size_t capacity);
+
+/* ---- checkpoint / resume --------------------------------------------------- */
+
+/* Serialise a job (latents, Adam moments, t, lambda, seed) into host memory.
+ * With host_buf == NULL only *bytes is set. Synchronises the stream. */
+adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t* bytes);
+/* Recreate a job from adms_job_export output; mesh and material give the
+ * topology and texture sizes (their latent values are overwritten). */
+adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
+                            const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADMS_H */

@@ -289,7 +289,33 @@ def perspective_barycentrics(s, w, q):
     return beta, dbeta
 
 
-def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True, lod_store=None):
+def texel_margin(levels, uv, lod):
+    """Distance (in texels) of each lookup's texel coordinates to the nearest
+    cell boundary, over the mip levels the trilinear filter actually uses.
+
+    At a cell boundary piecewise-bilinear filtering has a kink: its value is
+    continuous but its uv-derivative is one-sided, so a float32 evaluation may
+    legitimately take the other side. Tests use this to tell such lookups apart."""
+    L = len(levels) - 1
+    lod = lod.detach()
+    l0 = torch.floor(lod).long()
+    fr = lod - l0.to(F64)
+    l1 = torch.clamp(l0 + 1, max=L)
+    out = torch.full_like(lod, float("inf"))
+    for k in range(L + 1):
+        used = (l0 == k) | ((l1 == k) & (fr > 0))
+        h, w = levels[k].shape[0], levels[k].shape[1]
+        for c, n in ((uv[:, 0], w), (uv[:, 1], h)):
+            if n == 1:   # one texel across: both taps read it, no kink
+                continue
+            x = c * n - 0.5
+            f = x - torch.floor(x)
+            m = torch.minimum(f, 1 - f)
+            out = torch.where(used, torch.minimum(out, m), out)
+    return out
+
+
+def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True, lod_store=None, diag=None):
     """Pre-AA and AA images (H, W, 3) of one view with fixed visibility keys.
 
     geo: dict pos (V,3), nrm (V,3), tan (V,3), uv (T,2), tri (F,3), tri_uv (F,3)
@@ -297,7 +323,10 @@ def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True,
     keys: (H, W) uint64 visibility from raster.c; asign: (F,) int8 area signs.
     lod_store: optional dict; texture LODs and the antialiasing edge choices
     are read from it when present and stored into it otherwise (finite
-    differences hold them fixed, like the visibility keys)."""
+    differences hold them fixed, like the visibility keys).
+    diag: optional dict filled with per-pixel margins to the discrete
+    decisions inside the differentiable path (texel cells, n.l = 0, AA tau
+    and crossing tests), for tests that must tell kinks apart."""
     pos, tri, tri_uv = geo["pos"], geo["tri"], geo["tri_uv"]
     M = t64(np.asarray(view["mvp"], dtype=np.float32).astype(np.float64).reshape(4, 4))
     clip = torch.cat([pos, torch.ones_like(pos[:, :1])], dim=1) @ M.T
@@ -327,6 +356,8 @@ def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True,
     uv = interp(geo["uv"], ui)
     duv = [sum(db[k][:, None] * geo["uv"][ui[:, k]] for k in range(3)) for db in dbeta]
 
+    margins = []
+
     def fetch(name):
         lv = tex_levels[name]
         if lod_store is not None and name in lod_store:
@@ -335,16 +366,25 @@ def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True,
             lod = texture_lod(duv[0], duv[1], lv[0].shape[0], lv[0].shape[1], len(lv))
             if lod_store is not None:
                 lod_store[name] = lod
+        if diag is not None:
+            margins.append(texel_margin(lv, uv.detach(), lod))
         return trilinear(lv, uv[:, 0], uv[:, 1], lod)
 
-    col = shade(p, n_i, t_i, fetch("kd"), fetch("orm"), fetch("nrm"), view)
+    kd_s, orm_s, nrm_s = fetch("kd"), fetch("orm"), fetch("nrm")
+    col = shade(p, n_i, t_i, kd_s, orm_s, nrm_s, view)
+    if diag is not None:
+        with torch.no_grad():
+            ns = shading_frame(n_i, t_i, nrm_s)
+            nl = torch.stack([dot(ns, l)[:, 0].abs() for l, _ in view_lights(view, p)], 1).min(1).values
+        diag.update(pix=pix, tri=fid.numpy(), texel_margin=torch.stack(margins, 1).min(1).values.numpy(),
+                    nl_margin=nl.numpy())
     img = torch.zeros((height * width, 3), dtype=F64).index_copy(0, pixt, col)
     pre = img.reshape(height, width, 3)
     if not aa:
         return pre, pre
     sil = silhouette_flags(asign, adj)
     aa_store = None if lod_store is None else lod_store.setdefault("aa", {})
-    return pre, antialias(pre, keys, scr, tri, sil, width, height, aa_store=aa_store)
+    return pre, antialias(pre, keys, scr, tri, sil, width, height, aa_store=aa_store, diag=diag)
 
 
 # ----------------------------------------------------------------------------- antialiasing
@@ -358,7 +398,7 @@ def silhouette_flags(asign, adj):
     return (adj < 0) | (nb != asign[:, None])
 
 
-def antialias(pre, keys, scr, tri, sil, width, height, aa_store=None):
+def antialias(pre, keys, scr, tri, sil, width, height, aa_store=None, diag=None):
     """Silhouette antialiasing (reading of Laine et al. 2020's analytic AA).
 
     For each horizontally or vertically adjacent pixel pair with different
@@ -408,6 +448,19 @@ def antialias(pre, keys, scr, tri, sil, width, height, aa_store=None):
             xc = a[:, x_ax] + sp * (b[:, x_ax] - a[:, x_ax])
             return sigma * (xc - o_c[:, x_ax]), sp, den
 
+        if diag is not None:
+            with torch.no_grad():
+                sil_o = torch.as_tensor(sil[tid[oj, oi]])
+                margin = torch.full((pj.size,), float("inf"), dtype=F64)
+                for e in range(3):
+                    tau_e, sp, den = crossing(e)
+                    m = torch.minimum(torch.minimum(sp.abs(), (1 - sp).abs()),
+                                      torch.minimum(tau_e.abs(), (1 - tau_e).abs()))
+                    m = torch.minimum(m, (tau_e - 0.5).abs())
+                    margin = torch.where(sil_o[:, e] & (den != 0), torch.minimum(margin, m), margin)
+            prev = diag.get("aa_pairs", [])
+            prev.append((oj * W + oi, sj * W + si, margin.numpy()))
+            diag["aa_pairs"] = prev
         if aa_store is not None and axis in aa_store:
             choice = aa_store[axis]
         else:

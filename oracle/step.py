@@ -82,9 +82,10 @@ def texture_levels(job, params):
     return out
 
 
-def render(job, params, views, height, width, aa=True, vis=None, lods=None):
+def render(job, params, views, height, width, aa=True, vis=None, lods=None, diags=None):
     """Images of a batch of views. vis = (keys, asign) holds visibility fixed;
-    lods = a dict filled on first use and reused after it holds the LOD fixed."""
+    lods = a dict filled on first use and reused after it holds the LOD fixed;
+    diags = a list that receives each view's decision margins (render_view)."""
     geo = geometry(job, params)
     tex = texture_levels(job, params)
     if vis is None:
@@ -94,8 +95,11 @@ def render(job, params, views, height, width, aa=True, vis=None, lods=None):
     pres, imgs = [], []
     for b in range(len(views)):
         store = None if lods is None else lods.setdefault(b, {})
+        dg = None if diags is None else {}
         pre, img = R.render_view(geo, tex, views[b], keys[b], asign[b], job.adj, width, height, aa=aa,
-                                 lod_store=store)
+                                 lod_store=store, diag=dg)
+        if diags is not None:
+            diags.append(dg)
         pres.append(pre)
         imgs.append(img)
     return dict(pre=torch.stack(pres), img=torch.stack(imgs), keys=keys, asign=asign, geo=geo)
@@ -109,9 +113,9 @@ def render_reference(scene, views, height, width):
     return out["img"], out["keys"]
 
 
-def objective(job, params, views, refs, height, width, vis=None, lam=None, lods=None):
+def objective(job, params, views, refs, height, width, vis=None, lam=None, lods=None, diags=None):
     """L_opt = L_image + lambda_t L_delta (Eq. 5) for one batch; returns parts."""
-    out = render(job, params, views, height, width, vis=vis, lods=lods)
+    out = render(job, params, views, height, width, vis=vis, lods=lods, diags=diags)
     l_img = R.image_loss(out["img"], refs, job.loss)
     total = l_img
     l_lap = torch.zeros((), dtype=F64)

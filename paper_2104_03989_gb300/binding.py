@@ -1,0 +1,246 @@
+"""ctypes binding of libadms.so (argument marshalling only).
+
+Every function named adms_* here calls the C entry point of the same name and
+raises AdmsError on a non-zero status. All computation runs in the CUDA
+library; this module only converts numpy arrays / torch tensors into the
+pointers and structs of include/adms.h. There is no CPU fallback: if the
+library cannot be loaded, lib() raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libadms.so")
+
+ADMS_OK, ADMS_ERR_ARG, ADMS_ERR_BUDGET, ADMS_ERR_CUDA, ADMS_ERR_TIMEOUT, ADMS_ERR_NONFINITE, ADMS_ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6)
+LOSS = {"l1": 0, "logl1": 1, "l2": 2}
+
+
+class AdmsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"adms status {status}: {msg}")
+        self.status = status
+
+
+class adms_view(C.Structure):
+    _fields_ = [("mvp", C.c_float * 16), ("eye", C.c_float * 3), ("pad0", C.c_float),
+                ("light_pos", C.c_float * 3), ("light_I", C.c_float), ("light_dir", C.c_float * 3),
+                ("light_E", C.c_float)]
+
+
+class adms_mesh_desc(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_uv", C.c_int32), ("n_tris", C.c_int32), ("pos", C.c_void_p),
+                ("uv", C.c_void_p), ("tri_pos", C.c_void_p), ("tri_uv", C.c_void_p)]
+
+
+class adms_material_desc(C.Structure):
+    _fields_ = [("kd", C.c_void_p), ("orm", C.c_void_p), ("nrm", C.c_void_p), ("disp", C.c_void_p),
+                ("kd_h", C.c_int32), ("kd_w", C.c_int32), ("orm_h", C.c_int32), ("orm_w", C.c_int32),
+                ("nrm_h", C.c_int32), ("nrm_w", C.c_int32), ("disp_h", C.c_int32), ("disp_w", C.c_int32),
+                ("mips", C.c_int32)]
+
+
+class adms_opt_params(C.Structure):
+    _fields_ = [("optimize_pos", C.c_int32), ("optimize_kd", C.c_int32), ("optimize_orm", C.c_int32),
+                ("optimize_nrm", C.c_int32), ("optimize_disp", C.c_int32), ("loss", C.c_int32),
+                ("tess_levels", C.c_int32), ("batch_views", C.c_int32), ("relative_laplacian", C.c_int32),
+                ("aa", C.c_int32), ("lr0", C.c_float), ("lambda0", C.c_float)]
+
+
+class adms_param_view(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("kd", C.c_void_p), ("orm", C.c_void_p), ("nrm", C.c_void_p),
+                ("disp", C.c_void_p), ("g_pos", C.c_void_p), ("g_kd", C.c_void_p), ("g_orm", C.c_void_p),
+                ("g_nrm", C.c_void_p), ("g_disp", C.c_void_p), ("n_verts", C.c_int32),
+                ("n_tris_render", C.c_int32), ("kd_h", C.c_int32), ("kd_w", C.c_int32), ("orm_h", C.c_int32),
+                ("orm_w", C.c_int32), ("nrm_h", C.c_int32), ("nrm_w", C.c_int32), ("disp_h", C.c_int32),
+                ("disp_w", C.c_int32), ("kd_levels", C.c_int32), ("orm_levels", C.c_int32),
+                ("nrm_levels", C.c_int32), ("t", C.c_int32)]
+
+
+class adms_stats(C.Structure):
+    _fields_ = [("image_loss", C.c_float), ("laplacian", C.c_float), ("lambda_", C.c_float), ("lr", C.c_float),
+                ("t", C.c_int32), ("status", C.c_int32), ("tile_overflows", C.c_int64)]
+
+
+assert C.sizeof(adms_view) == 112
+
+# name -> (argtypes, restype)
+P = C.c_void_p
+SIGNATURES = {
+    "adms_ctx_create": ([C.POINTER(P), C.c_size_t, P], C.c_int),
+    "adms_ctx_destroy": ([P], C.c_int),
+    "adms_ctx_set_stream": ([P, P], C.c_int),
+    "adms_sync": ([P], C.c_int),
+    "adms_last_error": ([P], C.c_char_p),
+    "adms_bytes_in_use": ([P], C.c_size_t),
+    "adms_job_create": ([P, C.POINTER(adms_mesh_desc), C.POINTER(adms_material_desc), C.POINTER(adms_opt_params),
+                         C.c_uint64, C.POINTER(C.c_int32)], C.c_int),
+    "adms_job_destroy": ([P, C.c_int32], C.c_int),
+    "adms_job_params": ([P, C.c_int32, C.POINTER(adms_param_view)], C.c_int),
+    "adms_job_stats": ([P, C.c_int32, C.POINTER(adms_stats)], C.c_int),
+    "adms_render_reference": ([P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P], C.c_int),
+    "adms_forward_loss": ([P, P, C.c_int32, P, P, P, P, P, P], C.c_int),
+    "adms_backward": ([P, P, C.c_int32, C.c_int32], C.c_int),
+    "adms_optimizer_step": ([P, P, C.c_int32], C.c_int),
+    "adms_job_keys": ([P, C.c_int32, P, C.c_size_t], C.c_int),
+    "adms_job_export": ([P, C.c_int32, P, C.POINTER(C.c_size_t)], C.c_int),
+    "adms_job_import": ([P, C.POINTER(adms_mesh_desc), C.POINTER(adms_material_desc), C.POINTER(adms_opt_params),
+                         P, C.c_size_t, C.POINTER(C.c_int32)], C.c_int),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libadms.so (built by paper_2104_03989_gb300.build). Raises if missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(ctx, status):
+    if status != ADMS_OK:
+        msg = lib().adms_last_error(ctx).decode() if ctx else ""
+        raise AdmsError(status, msg)
+
+
+def ptr(x):
+    """Pointer of a numpy array (host) or torch tensor (host or device)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    return int(x)
+
+
+# ----------------------------------------------------------------------------- thin wrappers
+
+def adms_ctx_create(hbm_budget_bytes=0, stream=None):
+    out = P()
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(None, lib().adms_ctx_create(C.byref(out), hbm_budget_bytes, st))
+    return out
+
+
+def adms_ctx_destroy(ctx):
+    _check(None, lib().adms_ctx_destroy(ctx))
+
+
+def adms_ctx_set_stream(ctx, stream):
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(ctx, lib().adms_ctx_set_stream(ctx, st))
+
+
+def adms_sync(ctx):
+    _check(ctx, lib().adms_sync(ctx))
+
+
+def adms_bytes_in_use(ctx):
+    return int(lib().adms_bytes_in_use(ctx))
+
+
+def mesh_desc(pos, uv, tri_pos, tri_uv):
+    d = adms_mesh_desc(int(pos.shape[0]), int(uv.shape[0]), int(tri_pos.shape[0]), ptr(pos), ptr(uv), ptr(tri_pos),
+                       ptr(tri_uv))
+    d._keep = (pos, uv, tri_pos, tri_uv)
+    return d
+
+
+def material_desc(kd, orm, nrm, disp=None, mips=True):
+    d = adms_material_desc(ptr(kd), ptr(orm), ptr(nrm), ptr(disp), kd.shape[0], kd.shape[1], orm.shape[0],
+                           orm.shape[1], nrm.shape[0], nrm.shape[1], 0 if disp is None else disp.shape[0],
+                           0 if disp is None else disp.shape[1], 1 if mips else 0)
+    d._keep = (kd, orm, nrm, disp)
+    return d
+
+
+def opt_params(optimize=None, loss="logl1", tess_levels=0, batch_views=0, relative_laplacian=False, aa=True,
+               lr0=0.01, lambda0=0.0):
+    o = optimize or {}
+    return adms_opt_params(int(o.get("pos", 0)), int(o.get("kd", 0)), int(o.get("orm", 0)), int(o.get("nrm", 0)),
+                           int(o.get("disp", 0)), LOSS[loss], tess_levels, batch_views, int(relative_laplacian),
+                           int(aa), lr0, lambda0)
+
+
+def adms_job_create(ctx, mesh, mat, opt=None, seed=0):
+    out = C.c_int32()
+    _check(ctx, lib().adms_job_create(ctx, C.byref(mesh), C.byref(mat), C.byref(opt) if opt is not None else None,
+                                      seed, C.byref(out)))
+    return out.value
+
+
+def adms_job_destroy(ctx, job):
+    _check(ctx, lib().adms_job_destroy(ctx, job))
+
+
+def adms_job_params(ctx, job):
+    out = adms_param_view()
+    _check(ctx, lib().adms_job_params(ctx, job, C.byref(out)))
+    return out
+
+
+def adms_job_stats(ctx, job):
+    out = adms_stats()
+    _check(ctx, lib().adms_job_stats(ctx, job, C.byref(out)))
+    return out
+
+
+def adms_render_reference(ctx, job, views, H, W, out_rgb):
+    _check(ctx, lib().adms_render_reference(ctx, job, ptr(views), len(views), H, W, ptr(out_rgb)))
+
+
+def adms_forward_loss(ctx, jobs, views, views_per_job, hw, ref_rgb, out_loss, out_img=None):
+    n = len(jobs)
+    jobs_a = (C.c_int32 * n)(*jobs)
+    vpj = (C.c_int32 * n)(*views_per_job)
+    hw_a = (C.c_int32 * (2 * n))(*[int(x) for p in hw for x in p])
+    refs = (C.c_void_p * n)(*[ptr(r) for r in ref_rgb])
+    imgs = (C.c_void_p * n)(*[ptr(i) for i in out_img]) if out_img is not None else None
+    _check(ctx, lib().adms_forward_loss(ctx, jobs_a, n, ptr(views), vpj, hw_a, refs, ptr(out_loss), imgs))
+
+
+def adms_backward(ctx, jobs, recompute_raster=0):
+    n = len(jobs)
+    _check(ctx, lib().adms_backward(ctx, (C.c_int32 * n)(*jobs), n, int(recompute_raster)))
+
+
+def adms_optimizer_step(ctx, jobs):
+    n = len(jobs)
+    _check(ctx, lib().adms_optimizer_step(ctx, (C.c_int32 * n)(*jobs), n))
+
+
+def adms_job_keys(ctx, job, out_keys):
+    _check(ctx, lib().adms_job_keys(ctx, job, ptr(out_keys), out_keys.numel()))
+
+
+def adms_job_export(ctx, job):
+    n = C.c_size_t(0)
+    _check(ctx, lib().adms_job_export(ctx, job, None, C.byref(n)))
+    buf = np.zeros(n.value, dtype=np.uint8)
+    _check(ctx, lib().adms_job_export(ctx, job, ptr(buf), C.byref(n)))
+    return buf
+
+
+def adms_job_import(ctx, mesh, mat, opt, buf):
+    out = C.c_int32()
+    _check(ctx, lib().adms_job_import(ctx, C.byref(mesh), C.byref(mat), C.byref(opt) if opt is not None else None,
+                                      ptr(buf), buf.nbytes, C.byref(out)))
+    return out.value

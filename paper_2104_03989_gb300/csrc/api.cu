@@ -1,0 +1,661 @@
+// C ABI: contexts, jobs with resident state, and the step calls.
+//
+// Host-side preprocessing (topology is fixed, Sec. 3): edge adjacency for the
+// silhouette test, vertex -> face and one-ring CSR tables, mip-chain layout.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace adms;
+
+namespace {
+
+struct TexState {
+    float4* data = nullptr;  // mip chain
+    float4* grad = nullptr;  // mip chain (when optimized)
+    float4* m = nullptr;     // level 0
+    float4* v = nullptr;
+    int w = 0, h = 0, levels = 0;
+    int off[ADMS_MAX_LEVELS] = {0};
+    size_t total = 0;
+    bool opt = false;
+
+    TexDev dev() const {
+        TexDev t;
+        t.tex = data;
+        t.grad = opt ? grad : nullptr;
+        t.w0 = w;
+        t.h0 = h;
+        t.levels = levels;
+        for (int k = 0; k < ADMS_MAX_LEVELS; ++k) t.off[k] = off[k];
+        return t;
+    }
+};
+
+struct Job {
+    bool alive = false;
+    bool frozen = true;
+    adms_opt_params opt{};
+    uint64_t seed = 0;
+    int V = 0, T = 0, F = 0;
+    // latents and their optimizer state
+    float* pos = nullptr;
+    float* g_pos = nullptr;
+    float* m_pos = nullptr;
+    float* v_pos = nullptr;
+    TexState kd, orm, nrm;
+    // topology
+    float2* uv = nullptr;
+    int* tri = nullptr;
+    int* tri_uv = nullptr;
+    int* adj = nullptr;
+    int* vf_off = nullptr;
+    int* vf_face = nullptr;
+    int* ring_off = nullptr;
+    int* ring = nullptr;
+    float* delta_ref = nullptr;
+    // per-step derived state
+    float4 *vpos = nullptr, *vnrm = nullptr, *vtan = nullptr, *tmp_n = nullptr, *tmp_t = nullptr;
+    double *g_nrm = nullptr, *g_tan = nullptr, *g_pos_acc = nullptr;
+    float* delta = nullptr;
+    JobState* st = nullptr;
+    bool frame_valid = false;
+    // per-call scratch
+    size_t px_cap = 0, view_cap = 0, tile_cap = 0, rec_cap = 0;
+    unsigned long long* keys = nullptr;
+    float4* pre = nullptr;
+    float4* gprime = nullptr;
+    adms_view* views = nullptr;
+    RasterScratch rs{};
+    // latest forward
+    bool have_fwd = false;
+    int B = 0, H = 0, W = 0;
+    const float* ref = nullptr;
+    float loss_scale = 0.f;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct adms_ctx {
+    cudaStream_t stream = 0;
+    size_t budget = 0;
+    size_t in_use = 0;
+    std::string err;
+    std::vector<Job> jobs;
+};
+
+namespace {
+
+adms_status fail(adms_ctx* c, adms_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, ADMS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+adms_status job_alloc(adms_ctx* ctx, Job& j, T** out, size_t count) {
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    bytes = (bytes + 255) & ~size_t(255);
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        return fail(ctx, ADMS_ERR_BUDGET, "HBM budget exceeded (" + std::to_string(ctx->in_use + bytes) + " > " +
+                                              std::to_string(ctx->budget) + " bytes)");
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(ctx, ADMS_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    e = cudaMemsetAsync(p, 0, bytes, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, ADMS_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+    j.allocs.push_back(p);
+    j.bytes += bytes;
+    ctx->in_use += bytes;
+    *out = static_cast<T*>(p);
+    return ADMS_OK;
+}
+
+#define AL(ptr, n)                                             \
+    do {                                                       \
+        adms_status s_ = job_alloc(ctx, j, &(ptr), (size_t)(n)); \
+        if (s_ != ADMS_OK) return s_;                          \
+    } while (0)
+
+void job_free(adms_ctx* ctx, Job& j) {
+    for (void* p : j.allocs) cudaFree(p);
+    ctx->in_use -= std::min(ctx->in_use, j.bytes);
+    j = Job();
+}
+
+Job* get_job(adms_ctx* ctx, adms_job h) {
+    if (!ctx || h < 0 || h >= (adms_job)ctx->jobs.size() || !ctx->jobs[h].alive) return nullptr;
+    return &ctx->jobs[h];
+}
+
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// copy from host or device memory into a host vector
+template <typename T>
+adms_status to_host(adms_ctx* ctx, const T* src, size_t n, std::vector<T>& dst) {
+    dst.resize(n);
+    if (n) CK(cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDefault));
+    return ADMS_OK;
+}
+
+adms_status tex_create(adms_ctx* ctx, Job& j, TexState& t, const float* src, int h, int w, bool mips, bool opt) {
+    if (!src || !pow2(h) || !pow2(w)) return fail(ctx, ADMS_ERR_ARG, "texture sizes must be powers of two");
+    t.w = w;
+    t.h = h;
+    t.opt = opt;
+    int lw = 0, lh = 0;
+    while ((1 << lw) < w) ++lw;
+    while ((1 << lh) < h) ++lh;
+    t.levels = mips ? 1 + std::max(lw, lh) : 1;
+    if (t.levels > ADMS_MAX_LEVELS) return fail(ctx, ADMS_ERR_ARG, "texture too large");
+    size_t off = 0;
+    for (int k = 0; k < t.levels; ++k) {
+        t.off[k] = (int)off;
+        off += (size_t)std::max(w >> k, 1) * std::max(h >> k, 1);
+    }
+    t.total = off;
+    AL(t.data, t.total);
+    CK(cudaMemcpyAsync(t.data, src, (size_t)w * h * sizeof(float4), cudaMemcpyDefault, ctx->stream));
+    if (opt) {
+        AL(t.grad, t.total);
+        AL(t.m, (size_t)w * h);
+        AL(t.v, (size_t)w * h);
+    }
+    CK(mip_build(t.dev(), ctx->stream));
+    return ADMS_OK;
+}
+
+// grow per-call scratch to B views of H x W
+adms_status ensure_scratch(adms_ctx* ctx, Job& j, int B, int H, int W) {
+    size_t px = (size_t)B * H * W;
+    int tiles = ((W + ADMS_TILE - 1) / ADMS_TILE) * ((H + ADMS_TILE - 1) / ADMS_TILE);
+    size_t ntiles = (size_t)B * tiles;
+    if (px > j.px_cap) {
+        AL(j.keys, px);
+        AL(j.pre, px);
+        AL(j.gprime, px);
+        j.px_cap = px;
+    }
+    if ((size_t)B > j.view_cap) {
+        AL(j.views, B);
+        AL(j.rs.clip, (size_t)B * j.V);
+        AL(j.rs.scr, (size_t)B * j.V);
+        AL(j.rs.vs, (size_t)B * j.V);
+        AL(j.rs.rec, (size_t)B * j.F);
+        AL(j.rs.asign, (size_t)B * j.F);
+        j.view_cap = B;
+    }
+    if (ntiles > j.tile_cap) {
+        AL(j.rs.tile_count, ntiles);
+        AL(j.rs.tile_off, ntiles);
+        AL(j.rs.tile_cursor, ntiles);
+        j.tile_cap = ntiles;
+    }
+    // tile-list capacity: 8 entries per triangle and view, at least 4 per tile
+    size_t want = std::max<size_t>((size_t)8 * B * j.F, 4 * ntiles);
+    if ((long long)want > j.rs.list_capacity) {
+        AL(j.rs.list, want);
+        j.rs.list_capacity = (long long)want;
+    }
+    if (!j.rs.total_pairs) {
+        AL(j.rs.total_pairs, 1);
+        AL(j.rs.overflow_ctr, 1);
+    }
+    return ADMS_OK;
+}
+
+FrameArgs frame_args(Job& j) {
+    FrameArgs f;
+    f.V = j.V;
+    f.F = j.F;
+    f.pos = j.pos;
+    f.uv = j.uv;
+    f.tri = j.tri;
+    f.tri_uv = j.tri_uv;
+    f.vf_off = j.vf_off;
+    f.vf_face = j.vf_face;
+    f.vpos = j.vpos;
+    f.vnrm = j.vnrm;
+    f.vtan = j.vtan;
+    f.g_nrm = j.g_nrm;
+    f.g_tan = j.g_tan;
+    f.tmp_n = j.tmp_n;
+    f.tmp_t = j.tmp_t;
+    f.g_pos_acc = j.g_pos_acc;
+    f.g_pos = j.g_pos;
+    return f;
+}
+
+ShadeArgs shade_args(Job& j) {
+    ShadeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.B = j.B;
+    a.H = j.H;
+    a.W = j.W;
+    a.V = j.V;
+    a.F = j.F;
+    a.views = j.views;
+    a.clip = j.rs.clip;
+    a.scr = j.rs.scr;
+    a.vpos = j.vpos;
+    a.vnrm = j.vnrm;
+    a.vtan = j.vtan;
+    a.uv = j.uv;
+    a.tri = j.tri;
+    a.tri_uv = j.tri_uv;
+    a.adj = j.adj;
+    a.asign = j.rs.asign;
+    a.keys = j.keys;
+    a.kd = j.kd.dev();
+    a.orm = j.orm.dev();
+    a.nrm = j.nrm.dev();
+    a.pre = j.pre;
+    a.gprime = j.gprime;
+    a.loss_kind = j.opt.loss;
+    a.loss_scale = j.loss_scale;
+    a.aa = j.opt.aa;
+    a.g_pos = j.g_pos_acc;
+    a.g_nrm = j.g_nrm;
+    a.g_tan = j.g_tan;
+    return a;
+}
+
+// frame, raster and pre-AA shading of B views already copied to j.views
+adms_status render_core(adms_ctx* ctx, Job& j) {
+    if (!j.frame_valid) {
+        CK(frame_forward(frame_args(j), ctx->stream));
+        j.frame_valid = true;
+    }
+    RasterIn in;
+    in.pos = j.pos;
+    in.tri = j.tri;
+    in.views = j.views;
+    in.B = j.B;
+    in.V = j.V;
+    in.F = j.F;
+    in.W = j.W;
+    in.H = j.H;
+    in.keys = j.keys;
+    CK(raster_views(in, j.rs, ctx->stream));
+    CK(shade_forward(shade_args(j), ctx->stream));
+    return ADMS_OK;
+}
+
+void build_topology(const std::vector<int>& tri, int V, int F, std::vector<int>& adj, std::vector<int>& vf_off,
+                    std::vector<int>& vf_face, std::vector<int>& ring_off, std::vector<int>& ring) {
+    adj.assign((size_t)F * 3, -1);
+    std::unordered_map<uint64_t, std::vector<int>> edges;
+    edges.reserve((size_t)F * 2);
+    for (int f = 0; f < F; ++f)
+        for (int k = 0; k < 3; ++k) {
+            uint32_t a = tri[3 * f + k], b = tri[3 * f + (k + 1) % 3];
+            uint64_t key = ((uint64_t)std::min(a, b) << 32) | std::max(a, b);
+            edges[key].push_back(3 * f + k);
+        }
+    for (auto& kv : edges)
+        if (kv.second.size() == 2) {
+            adj[kv.second[0]] = kv.second[1] / 3;
+            adj[kv.second[1]] = kv.second[0] / 3;
+        }
+    vf_off.assign(V + 1, 0);
+    for (int f = 0; f < F; ++f)
+        for (int k = 0; k < 3; ++k) vf_off[tri[3 * f + k] + 1]++;
+    for (int v = 0; v < V; ++v) vf_off[v + 1] += vf_off[v];
+    vf_face.assign(vf_off[V], 0);
+    std::vector<int> cur(vf_off.begin(), vf_off.end() - 1);
+    for (int f = 0; f < F; ++f)
+        for (int k = 0; k < 3; ++k) vf_face[cur[tri[3 * f + k]]++] = f;
+    std::vector<std::vector<int>> nb(V);
+    for (int f = 0; f < F; ++f)
+        for (int k = 0; k < 3; ++k) {
+            int a = tri[3 * f + k], b = tri[3 * f + (k + 1) % 3];
+            nb[a].push_back(b);
+            nb[b].push_back(a);
+        }
+    ring_off.assign(V + 1, 0);
+    ring.clear();
+    for (int v = 0; v < V; ++v) {
+        auto& n = nb[v];
+        std::sort(n.begin(), n.end());
+        n.erase(std::unique(n.begin(), n.end()), n.end());
+        ring.insert(ring.end(), n.begin(), n.end());
+        ring_off[v + 1] = (int)ring.size();
+    }
+}
+
+template <typename T>
+adms_status upload(adms_ctx* ctx, Job& j, T** dst, const std::vector<T>& src) {
+    AL(*dst, src.size());
+    if (!src.empty()) CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return ADMS_OK;
+}
+
+#define UP(dst, src)                               \
+    do {                                           \
+        adms_status s_ = upload(ctx, j, &(dst), src); \
+        if (s_ != ADMS_OK) return s_;              \
+    } while (0)
+
+adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
+                            const adms_opt_params* opt, uint64_t seed, Job& j) {
+    if (!mesh || !mat || !mesh->pos || !mesh->uv || !mesh->tri_pos || !mesh->tri_uv || mesh->n_verts <= 0 ||
+        mesh->n_tris <= 0 || mesh->n_uv <= 0)
+        return fail(ctx, ADMS_ERR_ARG, "invalid mesh description");
+    j.alive = true;
+    j.seed = seed;
+    j.frozen = opt == nullptr;
+    if (opt) j.opt = *opt;
+    else {
+        memset(&j.opt, 0, sizeof(j.opt));
+        j.opt.aa = 1;
+    }
+    if (j.opt.tess_levels != 0) return fail(ctx, ADMS_ERR_ARG, "tessellated jobs are not supported by this build");
+    j.V = mesh->n_verts;
+    j.T = mesh->n_uv;
+    j.F = mesh->n_tris;
+    std::vector<int> tri, tri_uv;
+    adms_status s;
+    if ((s = to_host(ctx, mesh->tri_pos, (size_t)j.F * 3, tri))) return s;
+    if ((s = to_host(ctx, mesh->tri_uv, (size_t)j.F * 3, tri_uv))) return s;
+    for (int x : tri)
+        if (x < 0 || x >= j.V) return fail(ctx, ADMS_ERR_ARG, "position index out of range");
+    for (int x : tri_uv)
+        if (x < 0 || x >= j.T) return fail(ctx, ADMS_ERR_ARG, "uv index out of range");
+    std::vector<int> adj, vf_off, vf_face, ring_off, ring;
+    build_topology(tri, j.V, j.F, adj, vf_off, vf_face, ring_off, ring);
+    UP(j.tri, tri);
+    UP(j.tri_uv, tri_uv);
+    UP(j.adj, adj);
+    UP(j.vf_off, vf_off);
+    UP(j.vf_face, vf_face);
+    UP(j.ring_off, ring_off);
+    UP(j.ring, ring);
+    AL(j.pos, (size_t)j.V * 3);
+    CK(cudaMemcpyAsync(j.pos, mesh->pos, (size_t)j.V * 3 * sizeof(float), cudaMemcpyDefault, ctx->stream));
+    AL(j.uv, j.T);
+    CK(cudaMemcpyAsync(j.uv, mesh->uv, (size_t)j.T * 2 * sizeof(float), cudaMemcpyDefault, ctx->stream));
+    AL(j.g_pos, (size_t)j.V * 3);
+    if (j.opt.optimize_pos) {
+        AL(j.m_pos, (size_t)j.V * 3);
+        AL(j.v_pos, (size_t)j.V * 3);
+    }
+    AL(j.vpos, j.V);
+    AL(j.vnrm, j.V);
+    AL(j.vtan, j.V);
+    AL(j.tmp_n, j.V);
+    AL(j.tmp_t, j.V);
+    AL(j.g_nrm, (size_t)j.V * 3);
+    AL(j.g_tan, (size_t)j.V * 3);
+    AL(j.g_pos_acc, (size_t)j.V * 3);
+    AL(j.delta, (size_t)j.V * 3);
+    AL(j.st, 1);
+    bool mips = mat->mips != 0;
+    if ((s = tex_create(ctx, j, j.kd, mat->kd, mat->kd_h, mat->kd_w, mips, j.opt.optimize_kd))) return s;
+    if ((s = tex_create(ctx, j, j.orm, mat->orm, mat->orm_h, mat->orm_w, mips, j.opt.optimize_orm))) return s;
+    if ((s = tex_create(ctx, j, j.nrm, mat->nrm, mat->nrm_h, mat->nrm_w, mips, j.opt.optimize_nrm))) return s;
+    if (j.opt.relative_laplacian) {
+        AL(j.delta_ref, (size_t)j.V * 3);
+        LapArgs la{j.V, j.pos, j.ring_off, j.ring, nullptr, j.delta_ref, j.g_pos, j.st};
+        CK(laplacian_forward(la, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ADMS_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+adms_status adms_ctx_create(adms_ctx** out, size_t hbm_budget_bytes, void* cuda_stream) {
+    if (!out) return ADMS_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ADMS_ERR_CUDA;
+    adms_ctx* c = new adms_ctx();
+    c->stream = (cudaStream_t)cuda_stream;
+    c->budget = hbm_budget_bytes;
+    *out = c;
+    return ADMS_OK;
+}
+
+adms_status adms_ctx_destroy(adms_ctx* ctx) {
+    if (!ctx) return ADMS_ERR_ARG;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& j : ctx->jobs)
+        if (j.alive) job_free(ctx, j);
+    delete ctx;
+    return ADMS_OK;
+}
+
+adms_status adms_ctx_set_stream(adms_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return ADMS_ERR_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return ADMS_OK;
+}
+
+adms_status adms_sync(adms_ctx* ctx) {
+    if (!ctx) return ADMS_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ADMS_OK;
+}
+
+const char* adms_last_error(adms_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t adms_bytes_in_use(adms_ctx* ctx) { return ctx ? ctx->in_use : 0; }
+
+adms_status adms_job_create(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
+                            const adms_opt_params* opt, uint64_t seed, adms_job* out) {
+    if (!ctx || !out) return fail(ctx, ADMS_ERR_ARG, "null argument");
+    ctx->jobs.emplace_back();
+    Job& j = ctx->jobs.back();
+    adms_status s = job_create_impl(ctx, mesh, mat, opt, seed, j);
+    if (s != ADMS_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        job_free(ctx, ctx->jobs.back());
+        return s;
+    }
+    *out = (adms_job)(ctx->jobs.size() - 1);
+    return ADMS_OK;
+}
+
+adms_status adms_job_destroy(adms_ctx* ctx, adms_job job) {
+    Job* j = get_job(ctx, job);
+    if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    CK(cudaStreamSynchronize(ctx->stream));
+    job_free(ctx, *j);
+    return ADMS_OK;
+}
+
+adms_status adms_job_params(adms_ctx* ctx, adms_job job, adms_param_view* out) {
+    Job* j = get_job(ctx, job);
+    if (!j || !out) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    memset(out, 0, sizeof(*out));
+    out->pos = j->pos;
+    out->kd = (float*)j->kd.data;
+    out->orm = (float*)j->orm.data;
+    out->nrm = (float*)j->nrm.data;
+    out->g_pos = j->g_pos;
+    out->g_kd = (float*)j->kd.grad;
+    out->g_orm = (float*)j->orm.grad;
+    out->g_nrm = (float*)j->nrm.grad;
+    out->n_verts = j->V;
+    out->n_tris_render = j->F;
+    out->kd_h = j->kd.h;
+    out->kd_w = j->kd.w;
+    out->orm_h = j->orm.h;
+    out->orm_w = j->orm.w;
+    out->nrm_h = j->nrm.h;
+    out->nrm_w = j->nrm.w;
+    out->kd_levels = j->kd.levels;
+    out->orm_levels = j->orm.levels;
+    out->nrm_levels = j->nrm.levels;
+    JobState hs;
+    CK(cudaMemcpyAsync(&hs, j->st, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    out->t = hs.t;
+    return ADMS_OK;
+}
+
+adms_status adms_job_stats(adms_ctx* ctx, adms_job job, adms_stats* out) {
+    Job* j = get_job(ctx, job);
+    if (!j || !out) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    JobState hs;
+    unsigned long long ovf = 0;
+    CK(cudaMemcpyAsync(&hs, j->st, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
+    if (j->rs.overflow_ctr)
+        CK(cudaMemcpyAsync(&ovf, j->rs.overflow_ctr, sizeof(ovf), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    out->image_loss = hs.last_img_loss;
+    out->laplacian = hs.last_lap;
+    out->lambda = hs.lam;
+    out->lr = hs.lr;
+    out->t = hs.t;
+    out->status = hs.status;
+    out->tile_overflows = (int64_t)ovf;
+    return ADMS_OK;
+}
+
+adms_status adms_render_reference(adms_ctx* ctx, adms_job job, const adms_view* views, int32_t n_views, int32_t H,
+                                  int32_t W, float* out_rgb) {
+    Job* jp = get_job(ctx, job);
+    if (!jp || !views || !out_rgb || n_views <= 0 || H <= 0 || W <= 0 || H > 16384 || W > 16384)
+        return fail(ctx, ADMS_ERR_ARG, "invalid render_reference arguments");
+    Job& j = *jp;
+    adms_status s = ensure_scratch(ctx, j, n_views, H, W);
+    if (s) return s;
+    j.B = n_views;
+    j.H = H;
+    j.W = W;
+    CK(cudaMemcpyAsync(j.views, views, sizeof(adms_view) * n_views, cudaMemcpyDefault, ctx->stream));
+    if ((s = render_core(ctx, j))) return s;
+    ShadeArgs a = shade_args(j);
+    a.ref = nullptr;
+    a.loss_acc = nullptr;
+    a.out_img = out_rgb;
+    a.aa = 1;
+    CK(aa_loss_forward(a, ctx->stream));
+    j.have_fwd = false;
+    return ADMS_OK;
+}
+
+adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, const adms_view* views,
+                              const int32_t* views_per_job, const int32_t* hw, const float* const* ref_rgb,
+                              float* out_loss, float* const* out_img) {
+    if (!ctx || !jobs || n_jobs <= 0 || !views || !views_per_job || !hw || !ref_rgb)
+        return fail(ctx, ADMS_ERR_ARG, "invalid forward_loss arguments");
+    size_t vofs = 0;
+    for (int k = 0; k < n_jobs; ++k) {
+        Job* jp = get_job(ctx, jobs[k]);
+        int B = views_per_job[k], H = hw[2 * k], W = hw[2 * k + 1];
+        if (!jp || B <= 0 || H <= 0 || W <= 0 || H > 16384 || W > 16384 || !ref_rgb[k])
+            return fail(ctx, ADMS_ERR_ARG, "invalid job, view count, size or reference pointer");
+        Job& j = *jp;
+        adms_status s = ensure_scratch(ctx, j, B, H, W);
+        if (s) return s;
+        j.B = B;
+        j.H = H;
+        j.W = W;
+        j.ref = ref_rgb[k];
+        int norm_views = j.opt.batch_views > 0 ? j.opt.batch_views : B;
+        j.loss_scale = (float)(1.0 / (3.0 * (double)norm_views * H * W));
+        CK(cudaMemcpyAsync(j.views, views + vofs, sizeof(adms_view) * B, cudaMemcpyDefault, ctx->stream));
+        vofs += B;
+        if ((s = render_core(ctx, j))) return s;
+        ShadeArgs a = shade_args(j);
+        a.ref = j.ref;
+        a.loss_acc = &j.st->call_loss;
+        a.out_img = out_img ? out_img[k] : nullptr;
+        CK(cudaMemsetAsync(&j.st->call_loss, 0, sizeof(double), ctx->stream));
+        CK(aa_loss_forward(a, ctx->stream));
+        CK(finish_call_loss(j.st, out_loss ? out_loss + k : nullptr, ctx->stream));
+        j.have_fwd = true;
+    }
+    return ADMS_OK;
+}
+
+adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, int32_t recompute_raster) {
+    if (!ctx || !jobs || n_jobs <= 0) return fail(ctx, ADMS_ERR_ARG, "invalid backward arguments");
+    for (int k = 0; k < n_jobs; ++k) {
+        Job* jp = get_job(ctx, jobs[k]);
+        if (!jp) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+        Job& j = *jp;
+        if (!j.have_fwd) return fail(ctx, ADMS_ERR_STATE, "backward without a preceding forward_loss");
+        if (recompute_raster) {
+            adms_status s = render_core(ctx, j);
+            if (s) return s;
+        }
+        CK(cudaMemsetAsync(j.g_nrm, 0, sizeof(double) * 3 * j.V, ctx->stream));
+        CK(cudaMemsetAsync(j.g_tan, 0, sizeof(double) * 3 * j.V, ctx->stream));
+        ShadeArgs a = shade_args(j);
+        a.ref = j.ref;
+        CK(shade_backward(a, ctx->stream));
+        CK(frame_backward(frame_args(j), ctx->stream));
+        j.have_fwd = false;
+    }
+    return ADMS_OK;
+}
+
+adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs) {
+    if (!ctx || !jobs || n_jobs <= 0) return fail(ctx, ADMS_ERR_ARG, "invalid optimizer_step arguments");
+    for (int k = 0; k < n_jobs; ++k) {
+        Job* jp = get_job(ctx, jobs[k]);
+        if (!jp) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+        Job& j = *jp;
+        if (j.frozen) return fail(ctx, ADMS_ERR_STATE, "optimizer_step on a frozen job");
+        LapArgs la{j.V, j.pos, j.ring_off, j.ring, j.delta_ref, j.delta, j.g_pos, j.st};
+        if (j.opt.optimize_pos) CK(laplacian_forward(la, ctx->stream));
+        SchedArgs sa{j.st, j.opt.lr0, j.opt.lambda0, j.opt.optimize_pos, j.V};
+        CK(schedule_step(sa, ctx->stream));
+        if (j.opt.optimize_pos) {
+            CK(laplacian_backward(la, ctx->stream));
+            CK(adam_flat(j.pos, j.g_pos, j.m_pos, j.v_pos, (long long)j.V * 3, j.st, ctx->stream));
+        } else {
+            CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.V, ctx->stream));
+        }
+        TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
+        for (int m = 0; m < 3; ++m) {
+            if (!maps[m]->opt) continue;
+            CK(adam_texture(maps[m]->dev(), maps[m]->m, maps[m]->v, m, j.st, ctx->stream));
+            CK(mip_build(maps[m]->dev(), ctx->stream));
+        }
+        CK(advance_step(j.st, ctx->stream));
+        j.frame_valid = false;
+    }
+    return ADMS_OK;
+}
+
+adms_status adms_job_keys(adms_ctx* ctx, adms_job job, uint64_t* out_keys, size_t capacity) {
+    Job* j = get_job(ctx, job);
+    if (!j || !out_keys) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    size_t n = (size_t)j->B * j->H * j->W;
+    if (capacity < n) return fail(ctx, ADMS_ERR_ARG, "key buffer too small");
+    CK(cudaMemcpyAsync(out_keys, j->keys, n * sizeof(uint64_t), cudaMemcpyDefault, ctx->stream));
+    return ADMS_OK;
+}
+
+adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t* bytes) {
+    Job* j = get_job(ctx, job);
+    if (!j || !bytes) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    return fail(ctx, ADMS_ERR_STATE, "export not implemented in this build");
+}
+
+adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
+                            const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out) {
+    return fail(ctx, ADMS_ERR_STATE, "import not implemented in this build");
+}
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+// Kernel-side data structures and host launchers of the render-and-compare step.
+#pragma once
+
+#include "common.cuh"
+
+namespace adms {
+
+// transformed vertex of one view: snapped sub-pixel position, depth, usable flag
+struct VtxS {
+    int X, Y;
+    float z;
+    int ok;
+};
+
+// triangle setup record of one view: oriented edge functions s E_k = ea Sx + eb Sy + ec
+// (s = sign of the snapped area), fill-rule thresholds, depth plane, pixel bbox
+struct TriRec {
+    long long ec[3];
+    int ea[3], eb[3];
+    int thr[3];
+    float fA, z0, dz1, dz2;
+    int sg, id, valid;
+    short bx0, bx1, by0, by1;
+};
+
+struct RasterIn {
+    const float* pos;          // [V][3] render positions
+    const int* tri;            // [F][3]
+    const adms_view* views;    // device, [B]
+    int B, V, F, W, H;
+    unsigned long long* keys;  // [B][H][W]
+};
+
+// scratch of the raster (global memory beyond inputs and outputs)
+struct RasterScratch {
+    float4* clip;       // [B][V]
+    float4* scr;        // [B][V] screen position as (x_hi, x_lo, y_hi, y_lo) float pairs
+    VtxS* vs;           // [B][V]
+    TriRec* rec;        // [B][F]
+    int8_t* asign;      // [B][F]
+    int* tile_count;    // [B * tiles]
+    int* tile_off;      // [B * tiles]
+    int* tile_cursor;   // [B * tiles]
+    int* list;          // [list_capacity]
+    long long list_capacity;
+    long long* total_pairs;               // device scalar
+    unsigned long long* overflow_ctr;     // device scalar
+};
+
+cudaError_t raster_views(const RasterIn& in, RasterScratch& s, cudaStream_t st);
+
+// everything the per-pixel shading, AA, loss and backward kernels read
+struct ShadeArgs {
+    int B, H, W, V, F;
+    const adms_view* views;          // [B]
+    const float4* clip;              // [B][V]
+    const float4* scr;               // [B][V] (x_hi, x_lo, y_hi, y_lo)
+    const float4* vpos;              // [V] xyz
+    const float4* vnrm;              // [V] unit smooth normals
+    const float4* vtan;              // [V] unit tangents
+    const float2* uv;                // [T]
+    const int* tri;                  // [F][3]
+    const int* tri_uv;               // [F][3]
+    const int* adj;                  // [F][3] face across edge (tri[f][k], tri[f][k+1]) or -1
+    const int8_t* asign;             // [B][F]
+    const unsigned long long* keys;  // [B][H][W]
+    TexDev kd, orm, nrm;
+    float4* pre;                     // [B][H][W] pre-AA colour
+    const float* ref;                // [B][H][W][3]
+    float4* gprime;                  // [B][H][W] dL/d(AA colour)
+    float* out_img;                  // [B][H][W][3] or null
+    int loss_kind;
+    float loss_scale;                // 1 / (3 P)
+    int aa;
+    double* loss_acc;                // device scalar (sum of per-pixel losses times loss_scale)
+    double* g_pos;                   // [V][3] accumulated in float64
+    double* g_nrm;                   // [V][3] d/d(unit normal)
+    double* g_tan;                   // [V][3] d/d(unit tangent)
+};
+
+cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st);
+cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st);
+cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st);
+
+// mesh frame (smooth normals, tangents) and its adjoint
+struct FrameArgs {
+    int V, F;
+    const float* pos;     // [V][3]
+    const float2* uv;     // [T]
+    const int* tri;       // [F][3]
+    const int* tri_uv;    // [F][3]
+    const int* vf_off;    // [V+1] vertex -> incident faces CSR
+    const int* vf_face;   // [sum]
+    float4* vpos;         // out [V]
+    float4* vnrm;         // out [V]
+    float4* vtan;         // out [V]
+    const double* g_nrm;  // in  [V][3]
+    const double* g_tan;  // in  [V][3]
+    float4* tmp_n;        // scratch [V]
+    float4* tmp_t;        // scratch [V]
+    double* g_pos_acc;    // in  [V][3] pixel-stage position gradient; read and zeroed
+    float* g_pos;         // accumulated [V][3]
+};
+cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st);
+cudaError_t frame_backward(const FrameArgs& a, cudaStream_t st);
+
+// device-side per-job scalars
+struct JobState {
+    double call_loss;    // L_image of the current forward call
+    double img_loss;     // accumulated L_image since the last optimizer step
+    double lap_sum;      // sum_i |delta_i - delta'_i|^2
+    float lam, lam0, lr, bc1, bc2;
+    float last_img_loss, last_lap;
+    int t;
+    int status;
+    int pad;
+};
+
+struct LapArgs {
+    int V;
+    const float* pos;       // [V][3]
+    const int* ring_off;    // [V+1]
+    const int* ring;        // one-ring CSR
+    const float* delta_ref; // [V][3] or null (absolute)
+    float* delta;           // scratch [V][3]
+    float* g_pos;           // [V][3]
+    JobState* st;
+};
+cudaError_t laplacian_forward(const LapArgs& a, cudaStream_t st);
+cudaError_t laplacian_backward(const LapArgs& a, cudaStream_t st);
+
+struct SchedArgs {
+    JobState* st;
+    float lr0, lambda0_user;  // <= 0: heuristic
+    int has_pos;
+    int n_verts;
+};
+cudaError_t schedule_step(const SchedArgs& a, cudaStream_t st);
+
+// Adam on a flat float array (positions, displacement): no clamps
+cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const JobState* js, cudaStream_t st);
+// Adam on a float4 texture (level 0) with the mip-chain adjoint folded in; clamp_kind 0 kd, 1 orm, 2 nrm
+cudaError_t adam_texture(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js, cudaStream_t st);
+// rebuild levels 1.. of a mip chain from level 0 (2x2 box average)
+cudaError_t mip_build(const TexDev& t, cudaStream_t st);
+cudaError_t advance_step(JobState* js, cudaStream_t st);
+// out[j] = call_loss; img_loss += call_loss
+cudaError_t finish_call_loss(JobState* js, float* out, cudaStream_t st);
+
+}  // namespace adms

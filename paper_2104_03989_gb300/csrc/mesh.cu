@@ -1,0 +1,167 @@
+// Mesh operations (Sec. 5.1): smooth vertex normals and tangents from positions
+// and UVs, recomputed every step, with their adjoint; the uniform Laplacian
+// regularizer of Eq. 4.
+//
+// Both run one thread per vertex and gather over a vertex -> face (or one-ring)
+// CSR table, so results do not depend on atomic ordering.
+#include "kernels.cuh"
+
+namespace adms {
+
+struct FaceFrame {
+    float3 e1, e2, fn, tv;
+    float d1y, d2y;
+    int sgn;
+    int idx[3];
+};
+
+__device__ __forceinline__ FaceFrame face_frame(const FrameArgs& a, int f) {
+    FaceFrame r;
+    int i0 = a.tri[3 * f], i1 = a.tri[3 * f + 1], i2 = a.tri[3 * f + 2];
+    r.idx[0] = i0;
+    r.idx[1] = i1;
+    r.idx[2] = i2;
+    float3 p0 = f3(a.pos[3 * i0], a.pos[3 * i0 + 1], a.pos[3 * i0 + 2]);
+    float3 p1 = f3(a.pos[3 * i1], a.pos[3 * i1 + 1], a.pos[3 * i1 + 2]);
+    float3 p2 = f3(a.pos[3 * i2], a.pos[3 * i2 + 1], a.pos[3 * i2 + 2]);
+    float2 u0 = a.uv[a.tri_uv[3 * f]], u1 = a.uv[a.tri_uv[3 * f + 1]], u2 = a.uv[a.tri_uv[3 * f + 2]];
+    r.e1 = p1 - p0;
+    r.e2 = p2 - p0;
+    r.fn = cross3(r.e1, r.e2);
+    float d1x = u1.x - u0.x, d2x = u2.x - u0.x;
+    r.d1y = u1.y - u0.y;
+    r.d2y = u2.y - u0.y;
+    float det = d1x * r.d2y - d2x * r.d1y;
+    r.sgn = det > 0.f ? 1 : (det < 0.f ? -1 : 0);
+    r.tv = r.d2y * r.e1 - r.d1y * r.e2;
+    return r;
+}
+
+// unnormalised vertex normal (sum of face normals) and tangent (sum of signed unit face tangents)
+__device__ __forceinline__ void vertex_sums(const FrameArgs& a, int v, float3& n, float3& t) {
+    n = zero3();
+    t = zero3();
+    for (int j = a.vf_off[v]; j < a.vf_off[v + 1]; ++j) {
+        FaceFrame ff = face_frame(a, a.vf_face[j]);
+        n += ff.fn;
+        if (ff.sgn != 0) t += (float)ff.sgn * nrm3(ff.tv).y;
+    }
+}
+
+__global__ void k_frame_fwd(FrameArgs a) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.V) return;
+    float3 n, t;
+    vertex_sums(a, v, n, t);
+    float3 nn = nrm3(n).y, tn = nrm3(t).y;
+    a.vpos[v] = make_float4(a.pos[3 * v], a.pos[3 * v + 1], a.pos[3 * v + 2], 0.f);
+    a.vnrm[v] = make_float4(nn.x, nn.y, nn.z, 0.f);
+    a.vtan[v] = make_float4(tn.x, tn.y, tn.z, 0.f);
+}
+
+// phase 1: gradients w.r.t. the unnormalised sums
+__global__ void k_frame_bwd1(FrameArgs a) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.V) return;
+    float3 n, t;
+    vertex_sums(a, v, n, t);
+    float3 gn = nrm3_bwd(nrm3(n), f3((float)a.g_nrm[3 * v], (float)a.g_nrm[3 * v + 1], (float)a.g_nrm[3 * v + 2]));
+    float3 gt = nrm3_bwd(nrm3(t), f3((float)a.g_tan[3 * v], (float)a.g_tan[3 * v + 1], (float)a.g_tan[3 * v + 2]));
+    a.tmp_n[v] = make_float4(gn.x, gn.y, gn.z, 0.f);
+    a.tmp_t[v] = make_float4(gt.x, gt.y, gt.z, 0.f);
+}
+
+// phase 2: each vertex gathers its share of every incident face's adjoint
+__global__ void k_frame_bwd2(FrameArgs a) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.V) return;
+    float3 g = zero3();
+    for (int j = a.vf_off[v]; j < a.vf_off[v + 1]; ++j) {
+        FaceFrame ff = face_frame(a, a.vf_face[j]);
+        float3 Gfn = f3(a.tmp_n[ff.idx[0]]) + f3(a.tmp_n[ff.idx[1]]) + f3(a.tmp_n[ff.idx[2]]);
+        float3 ge1 = cross3(ff.e2, Gfn), ge2 = cross3(Gfn, ff.e1);
+        if (ff.sgn != 0) {
+            float3 Gft = f3(a.tmp_t[ff.idx[0]]) + f3(a.tmp_t[ff.idx[1]]) + f3(a.tmp_t[ff.idx[2]]);
+            float3 gtv = (float)ff.sgn * nrm3_bwd(nrm3(ff.tv), Gft);
+            ge1 += ff.d2y * gtv;
+            ge2 -= ff.d1y * gtv;
+        }
+        if (ff.idx[0] == v) g -= ge1 + ge2;
+        if (ff.idx[1] == v) g += ge1;
+        if (ff.idx[2] == v) g += ge2;
+    }
+    double* acc = a.g_pos_acc + 3 * v;
+    a.g_pos[3 * v] += (float)(acc[0] + (double)g.x);
+    a.g_pos[3 * v + 1] += (float)(acc[1] + (double)g.y);
+    a.g_pos[3 * v + 2] += (float)(acc[2] + (double)g.z);
+    acc[0] = 0.0;
+    acc[1] = 0.0;
+    acc[2] = 0.0;
+}
+
+cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st) {
+    k_frame_fwd<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t frame_backward(const FrameArgs& a, cudaStream_t st) {
+    k_frame_bwd1<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+    k_frame_bwd2<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Laplacian (Eq. 4)
+__global__ void k_lap_fwd(LapArgs a) {
+    __shared__ double red[4];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (i < a.V) {
+        int lo = a.ring_off[i], hi = a.ring_off[i + 1];
+        float3 m = zero3();
+        for (int j = lo; j < hi; ++j) {
+            int k = a.ring[j];
+            m += f3(a.pos[3 * k], a.pos[3 * k + 1], a.pos[3 * k + 2]);
+        }
+        float inv = hi > lo ? 1.f / (float)(hi - lo) : 0.f;
+        float3 d = f3(a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2]) - inv * m;
+        if (a.delta_ref) d -= f3(a.delta_ref[3 * i], a.delta_ref[3 * i + 1], a.delta_ref[3 * i + 2]);
+        a.delta[3 * i] = d.x;
+        a.delta[3 * i + 1] = d.y;
+        a.delta[3 * i + 2] = d.z;
+        s = (double)dot3(d, d);
+    }
+    s = warp_sum_d(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&a.st->lap_sum, red[0] + red[1] + red[2] + red[3]);
+}
+
+__global__ void k_lap_bwd(LapArgs a) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.V) return;
+    float lam = a.st->lam;
+    float scale = 2.f * lam / (float)a.V;
+    float3 g = f3(a.delta[3 * k], a.delta[3 * k + 1], a.delta[3 * k + 2]);
+    for (int j = a.ring_off[k]; j < a.ring_off[k + 1]; ++j) {
+        int i = a.ring[j];
+        float inv = 1.f / (float)(a.ring_off[i + 1] - a.ring_off[i]);
+        g -= inv * f3(a.delta[3 * i], a.delta[3 * i + 1], a.delta[3 * i + 2]);
+    }
+    a.g_pos[3 * k] += scale * g.x;
+    a.g_pos[3 * k + 1] += scale * g.y;
+    a.g_pos[3 * k + 2] += scale * g.z;
+}
+
+cudaError_t laplacian_forward(const LapArgs& a, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(&a.st->lap_sum, 0, sizeof(double), st);
+    if (e) return e;
+    k_lap_fwd<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t laplacian_backward(const LapArgs& a, cudaStream_t st) {
+    k_lap_bwd<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace adms

@@ -1,0 +1,160 @@
+// Optimizer step (Sec. 5.3): lambda and learning-rate schedules, Adam with
+// default parameters fused with the adjoint of the mip chain and the range
+// clamps, and the mip rebuild of the updated textures.
+#include "kernels.cuh"
+
+namespace adms {
+
+// lambda_t (Eq. 5 text, recursive reading), lambda_0 heuristic, lr_t, bias corrections
+__global__ void k_schedule(SchedArgs a) {
+    JobState* s = a.st;
+    int t = s->t;
+    double l_img = s->img_loss;
+    double l_lap = a.has_pos ? s->lap_sum / (double)a.n_verts : 0.0;
+    if (a.has_pos) {
+        if (t == 0) {
+            double lam0 = a.lambda0_user;
+            if (!(lam0 > 0.0)) {
+                if (l_lap > 0.0) {
+                    lam0 = 0.25 * l_img / l_lap;
+                } else {
+                    lam0 = 0.0;
+                    s->status = ADMS_ERR_ARG;
+                }
+            }
+            s->lam0 = (float)lam0;
+            s->lam = (float)lam0;
+        } else {
+            double lmin = 0.02 * (double)s->lam0;
+            s->lam = (float)(((double)s->lam - lmin) * pow(10.0, -1e-6 * (double)t) + lmin);
+        }
+    }
+    s->lr = (float)((double)a.lr0 * pow(10.0, -0.0002 * (double)t));
+    s->bc1 = (float)(1.0 - pow(0.9, (double)(t + 1)));
+    s->bc2 = (float)(1.0 - pow(0.999, (double)(t + 1)));
+    s->last_img_loss = (float)l_img;
+    s->last_lap = (float)l_lap;
+    s->img_loss = 0.0;
+}
+
+cudaError_t schedule_step(const SchedArgs& a, cudaStream_t st) {
+    k_schedule<<<1, 1, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+__global__ void k_advance(JobState* s) { s->t += 1; }
+
+__global__ void k_finish_call(JobState* s, float* out) {
+    if (out) *out = (float)s->call_loss;
+    s->img_loss += s->call_loss;
+}
+cudaError_t finish_call_loss(JobState* js, float* out, cudaStream_t st) {
+    k_finish_call<<<1, 1, 0, st>>>(js, out);
+    return cudaGetLastError();
+}
+cudaError_t advance_step(JobState* js, cudaStream_t st) {
+    k_advance<<<1, 1, 0, st>>>(js);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ float adam1(float p, float g, float& m, float& v, float lr, float bc1, float bc2) {
+    m = 0.9f * m + 0.1f * g;
+    v = 0.999f * v + 0.001f * g * g;
+    float mh = m / bc1, vh = v / bc2;
+    return p - lr * mh / (sqrtf(vh) + 1e-8f);
+}
+
+__global__ void k_adam_flat(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                            long long n, const JobState* __restrict__ js) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float lr = js->lr, bc1 = js->bc1, bc2 = js->bc2;
+    float mm = m[i], vv = v[i];
+    p[i] = adam1(p[i], g[i], mm, vv, lr, bc1, bc2);
+    m[i] = mm;
+    v[i] = vv;
+    g[i] = 0.f;
+}
+
+cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const JobState* js, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_adam_flat<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, g, m, v, n, js);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
+
+__global__ void k_adam_tex(TexDev t, float4* __restrict__ m, float4* __restrict__ v, int clamp_kind,
+                           const JobState* __restrict__ js) {
+    int n = t.w0 * t.h0;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int x = i % t.w0, y = i / t.w0;
+    float4 g = t.grad[i];
+    // adjoint of the box-filter chain: level k texel = mean of its children
+    float wgt = 1.f;
+    for (int k = 1; k < t.levels; ++k) {
+        int wp = max(t.w0 >> (k - 1), 1), hp = max(t.h0 >> (k - 1), 1);
+        wgt *= 1.f / (float)((wp > 1 ? 2 : 1) * (hp > 1 ? 2 : 1));
+        int wk = max(t.w0 >> k, 1);
+        float4 gk = t.grad[t.off[k] + (y >> k) * wk + (x >> k)];
+        g = f4madd(g, wgt, gk);
+    }
+    float lr = js->lr, bc1 = js->bc1, bc2 = js->bc2;
+    float4 p = t.tex[i], mm = m[i], vv = v[i];
+    p.x = adam1(p.x, g.x, mm.x, vv.x, lr, bc1, bc2);
+    p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
+    p.z = adam1(p.z, g.z, mm.z, vv.z, lr, bc1, bc2);
+    p.w = adam1(p.w, g.w, mm.w, vv.w, lr, bc1, bc2);
+    if (clamp_kind == 0) {
+        p = make_float4(clampf(p.x, 0.f, 1.f), clampf(p.y, 0.f, 1.f), clampf(p.z, 0.f, 1.f), clampf(p.w, 0.f, 1.f));
+    } else if (clamp_kind == 1) {
+        p.x = clampf(p.x, 0.f, 1.f);
+        p.y = clampf(p.y, ADMS_ROUGH_MIN, 1.f);
+        p.z = clampf(p.z, 0.f, 1.f);
+    } else if (clamp_kind == 2) {
+        p.x = clampf(p.x, -1.f, 1.f);
+        p.y = clampf(p.y, -1.f, 1.f);
+        p.z = clampf(p.z, 0.f, 1.f);
+    }
+    const_cast<float4*>(t.tex)[i] = p;
+    m[i] = mm;
+    v[i] = vv;
+    t.grad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+cudaError_t adam_texture(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js, cudaStream_t st) {
+    int n = t.w0 * t.h0;
+    k_adam_tex<<<(n + 255) / 256, 256, 0, st>>>(t, m, v, clamp_kind, js);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    if (t.levels > 1) {
+        size_t coarse = 0;
+        for (int k = 1; k < t.levels; ++k) coarse += (size_t)max(t.w0 >> k, 1) * max(t.h0 >> k, 1);
+        e = cudaMemsetAsync(t.grad + t.off[1], 0, coarse * sizeof(float4), st);
+    }
+    return e;
+}
+
+__global__ void k_mip_level(float4* __restrict__ tex, int src_off, int ws, int hs, int dst_off, int wd, int hd) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= wd * hd) return;
+    int x = i % wd, y = i / wd;
+    int sx = ws > 1 ? 2 : 1, sy = hs > 1 ? 2 : 1;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int dy = 0; dy < sy; ++dy)
+        for (int dx = 0; dx < sx; ++dx) acc = f4madd(acc, 1.f, tex[src_off + (y * sy + dy) * ws + (x * sx + dx)]);
+    tex[dst_off + i] = f4scale(acc, 1.f / (float)(sx * sy));
+}
+
+cudaError_t mip_build(const TexDev& t, cudaStream_t st) {
+    for (int k = 1; k < t.levels; ++k) {
+        int ws = max(t.w0 >> (k - 1), 1), hs = max(t.h0 >> (k - 1), 1);
+        int wd = max(t.w0 >> k, 1), hd = max(t.h0 >> k, 1);
+        k_mip_level<<<(wd * hd + 255) / 256, 256, 0, st>>>(const_cast<float4*>(t.tex), t.off[k - 1], ws, hs, t.off[k],
+                                                          wd, hd);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace adms

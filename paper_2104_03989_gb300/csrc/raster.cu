@@ -1,0 +1,250 @@
+// Vertex transform, triangle setup, binning and tiled fixed-point rasterization
+// with a packed depth|triangle-id z-buffer (Sec. 5.2: rasterization primitive).
+//
+// The visibility arithmetic is fixed bit for bit so that the keys are exact:
+//   clip_r = ((M[r][0] x + M[r][1] y) + M[r][2] z) + M[r][3]   (float32, each op RN, no FMA)
+//   sx = (clip.x / clip.w)(W/2) + W/2, sy = H/2 - (clip.y / clip.w)(H/2), X = rint(256 sx)
+//   E_ab(S) = (X_b - X_a)(S_y - Y_a) - (Y_b - Y_a)(S_x - X_a) in int64 at S = (256 i + 128, 256 j + 128)
+//   covered: every edge of the positively wound triangle has E > 0, or E = 0 on a top/left edge
+//   d = (z0 + b1 (z1 - z0)) + b2 (z2 - z0), b1 = (float)E_20 / (float)A, b2 = (float)E_01 / (float)A
+//   key = (float_bits(d) << 32) | triangle id, minimum per pixel.
+#include "kernels.cuh"
+
+namespace adms {
+
+__device__ __forceinline__ long long floor_div_ll(long long a, long long b) {  // b > 0
+    long long q = a / b;
+    if ((a % b != 0) && (a < 0)) q -= 1;
+    return q;
+}
+__device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return -floor_div_ll(-a, b); }
+
+// ---------------------------------------------------------------- transform
+__global__ void k_transform(const float* __restrict__ pos, int V, const adms_view* __restrict__ views, int B, int W,
+                            int H, float4* __restrict__ clip, VtxS* __restrict__ vs, float4* __restrict__ scr) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * V) return;
+    int b = i / V, v = i - b * V;
+    const float* M = views[b].mvp;
+    float x = pos[3 * v], y = pos[3 * v + 1], z = pos[3 * v + 2];
+    {
+        // shading-side screen position in float64, kept as a (hi, lo) float pair
+        double cd[4];
+        for (int r = 0; r < 4; ++r)
+            cd[r] = (double)M[4 * r] * x + (double)M[4 * r + 1] * y + (double)M[4 * r + 2] * z + (double)M[4 * r + 3];
+        double hWd = 0.5 * W, hHd = 0.5 * H;
+        double sx = cd[0] / cd[3] * hWd + hWd, sy = hHd - cd[1] / cd[3] * hHd;
+        float sxh = (float)sx, syh = (float)sy;
+        scr[i] = make_float4(sxh, (float)(sx - (double)sxh), syh, (float)(sy - (double)syh));
+    }
+    float c[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        float s = __fadd_rn(__fmul_rn(M[4 * r], x), __fmul_rn(M[4 * r + 1], y));
+        s = __fadd_rn(s, __fmul_rn(M[4 * r + 2], z));
+        c[r] = __fadd_rn(s, M[4 * r + 3]);
+    }
+    clip[i] = make_float4(c[0], c[1], c[2], c[3]);
+    VtxS o;
+    o.X = 0;
+    o.Y = 0;
+    o.z = 0.f;
+    o.ok = 0;
+    if (c[3] > 1e-6f) {
+        float hW = 0.5f * (float)W, hH = 0.5f * (float)H;
+        float sx = __fadd_rn(__fmul_rn(__fdiv_rn(c[0], c[3]), hW), hW);
+        float sy = __fsub_rn(hH, __fmul_rn(__fdiv_rn(c[1], c[3]), hH));
+        float fx = __fmul_rn(sx, 256.f), fy = __fmul_rn(sy, 256.f);
+        if (fabsf(fx) <= 134217728.f && fabsf(fy) <= 134217728.f) {
+            o.X = __float2int_rn(fx);
+            o.Y = __float2int_rn(fy);
+            o.z = __fadd_rn(__fmul_rn(__fdiv_rn(c[2], c[3]), 0.5f), 0.5f);
+            o.ok = 1;
+        }
+    }
+    vs[i] = o;
+}
+
+// ---------------------------------------------------------------- setup + tile counts
+__global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restrict__ vs, int V, int B, int W, int H,
+                        int tiles_x, int tiles_y, TriRec* __restrict__ rec, int8_t* __restrict__ asign,
+                        int* __restrict__ tile_count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * F) return;
+    int b = i / F, f = i - b * F;
+    int i0 = tri[3 * f], i1 = tri[3 * f + 1], i2 = tri[3 * f + 2];
+    const VtxS* vb = vs + (size_t)b * V;
+    VtxS a0 = vb[i0], a1 = vb[i1], a2 = vb[i2];
+    TriRec r;
+    r.valid = 0;
+    asign[i] = 0;
+    if (a0.ok && a1.ok && a2.ok) {
+        long long X0 = a0.X, Y0 = a0.Y, X1 = a1.X, Y1 = a1.Y, X2 = a2.X, Y2 = a2.Y;
+        long long A = (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0);
+        if (A != 0) {
+            int sg = A > 0 ? 1 : -1;
+            asign[i] = (int8_t)sg;
+            long long minX = min(X0, min(X1, X2)), maxX = max(X0, max(X1, X2));
+            long long minY = min(Y0, min(Y1, Y2)), maxY = max(Y0, max(Y1, Y2));
+            long long ilo = max(ceil_div_ll(minX - 128, 256), 0ll), ihi = min(floor_div_ll(maxX - 128, 256), (long long)W - 1);
+            long long jlo = max(ceil_div_ll(minY - 128, 256), 0ll), jhi = min(floor_div_ll(maxY - 128, 256), (long long)H - 1);
+            if (ilo <= ihi && jlo <= jhi) {
+                // original-order edges: e0 = 1->2, e1 = 2->0, e2 = 0->1
+                long long px[3] = {X0, X1, X2}, py[3] = {Y0, Y1, Y2};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    int a = (k + 1) % 3, c = (k + 2) % 3;
+                    long long dx = px[c] - px[a], dy = py[c] - py[a];
+                    // oriented value s E = a Sx + b Sy + cst with s = sign(A)
+                    r.ea[k] = (int)(-sg * dy);
+                    r.eb[k] = (int)(sg * dx);
+                    r.ec[k] = sg * (dy * px[a] - dx * py[a]);
+                    long long odx = sg * dx, ody = sg * dy;
+                    r.thr[k] = ((ody < 0) || (ody == 0 && odx > 0)) ? 0 : 1;
+                }
+                r.fA = __ll2float_rn(A);
+                r.sg = sg;
+                r.z0 = a0.z;
+                r.dz1 = __fsub_rn(a1.z, a0.z);
+                r.dz2 = __fsub_rn(a2.z, a0.z);
+                r.id = f;
+                r.valid = 1;
+                r.bx0 = (short)ilo;
+                r.bx1 = (short)ihi;
+                r.by0 = (short)jlo;
+                r.by1 = (short)jhi;
+                int tx0 = (int)ilo / ADMS_TILE, tx1 = (int)ihi / ADMS_TILE;
+                int ty0 = (int)jlo / ADMS_TILE, ty1 = (int)jhi / ADMS_TILE;
+                int* tc = tile_count + (size_t)b * tiles_x * tiles_y;
+                for (int ty = ty0; ty <= ty1; ++ty)
+                    for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tc + ty * tiles_x + tx, 1);
+            }
+        }
+    }
+    rec[i] = r;
+}
+
+// ---------------------------------------------------------------- exclusive scan (one block)
+__global__ void k_scan(const int* __restrict__ in, int n, int* __restrict__ out, long long* __restrict__ total) {
+    __shared__ long long part[1024];
+    int tid = threadIdx.x, nt = blockDim.x;
+    int chunk = (n + nt - 1) / nt;
+    int lo = tid * chunk, hi = min(lo + chunk, n);
+    long long s = 0;
+    for (int i = lo; i < hi; ++i) s += in[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int o = 1; o < nt; o <<= 1) {
+        long long v = tid >= o ? part[tid - o] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    long long run = part[tid] - s;
+    for (int i = lo; i < hi; ++i) {
+        out[i] = (int)min(run, (long long)0x7fffffff);
+        run += in[i];
+    }
+    if (tid == nt - 1) *total = part[tid];
+}
+
+// ---------------------------------------------------------------- tile lists
+__global__ void k_bin_fill(const TriRec* __restrict__ rec, int F, int B, int tiles_x, int tiles_y,
+                           const int* __restrict__ tile_off, int* __restrict__ tile_cursor, int* __restrict__ list,
+                           long long capacity) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * F) return;
+    const TriRec& r = rec[i];
+    if (!r.valid) return;
+    int b = i / F;
+    size_t tbase = (size_t)b * tiles_x * tiles_y;
+    int tx0 = r.bx0 / ADMS_TILE, tx1 = r.bx1 / ADMS_TILE, ty0 = r.by0 / ADMS_TILE, ty1 = r.by1 / ADMS_TILE;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            size_t t = tbase + ty * tiles_x + tx;
+            long long p = (long long)tile_off[t] + atomicAdd(tile_cursor + t, 1);
+            if (p < capacity) list[p] = r.id;
+        }
+}
+
+// coverage + depth key of one triangle at one sample
+__device__ __forceinline__ void test_tri(const TriRec& r, int Sx, int Sy, unsigned long long& best) {
+    long long e0 = (long long)r.ea[0] * Sx + (long long)r.eb[0] * Sy + r.ec[0];
+    long long e1 = (long long)r.ea[1] * Sx + (long long)r.eb[1] * Sy + r.ec[1];
+    long long e2 = (long long)r.ea[2] * Sx + (long long)r.eb[2] * Sy + r.ec[2];
+    if (e0 < r.thr[0] || e1 < r.thr[1] || e2 < r.thr[2]) return;
+    // back to the triangle's own vertex order: E_20 = s e1, E_01 = s e2
+    long long E20 = r.sg > 0 ? e1 : -e1;
+    long long E01 = r.sg > 0 ? e2 : -e2;
+    float b1 = __fdiv_rn(__ll2float_rn(E20), r.fA);
+    float b2 = __fdiv_rn(__ll2float_rn(E01), r.fA);
+    float d = __fadd_rn(__fadd_rn(r.z0, __fmul_rn(b1, r.dz1)), __fmul_rn(b2, r.dz2));
+    if (!(d >= 0.f && d <= 1.f)) return;
+    if (d == 0.f) d = 0.f;
+    unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)r.id;
+    if (key < best) best = key;
+}
+
+// ---------------------------------------------------------------- tiled raster
+// One block per (view, 16x16 tile), one pixel per thread; the tile's triangle
+// records are staged through shared memory in chunks of 256.
+__global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, int F, int W, int H, int tiles_x,
+                                                int tiles_y, const int* __restrict__ tile_off,
+                                                const int* __restrict__ tile_count, const int* __restrict__ list,
+                                                long long capacity, unsigned long long* __restrict__ keys,
+                                                unsigned long long* __restrict__ overflow_ctr) {
+    __shared__ TriRec sm[256];
+    int tile = blockIdx.x;
+    int b = blockIdx.y;
+    int tx = tile % tiles_x, ty = tile / tiles_x;
+    int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
+    int px = tx * ADMS_TILE + lx, py = ty * ADMS_TILE + ly;
+    int Sx = 256 * px + 128, Sy = 256 * py + 128;
+    unsigned long long best = ADMS_EMPTY_KEY;
+    size_t t = (size_t)b * tiles_x * tiles_y + tile;
+    long long off = tile_off[t];
+    int cnt = tile_count[t];
+    const TriRec* rb = rec + (size_t)b * F;
+    bool overflow = off + cnt > capacity;
+    int n = overflow ? F : cnt;
+    if (overflow && threadIdx.x == 0) atomicAdd(overflow_ctr, 1ull);
+    for (int c0 = 0; c0 < n; c0 += 256) {
+        int m = min(256, n - c0);
+        __syncthreads();
+        if ((int)threadIdx.x < m) {
+            int id = overflow ? c0 + threadIdx.x : list[off + c0 + threadIdx.x];
+            sm[threadIdx.x] = rb[id];
+        }
+        __syncthreads();
+        for (int k = 0; k < m; ++k) {
+            const TriRec& r = sm[k];
+            if (!r.valid) continue;
+            if (px < r.bx0 || px > r.bx1 || py < r.by0 || py > r.by1) continue;
+            test_tri(r, Sx, Sy, best);
+        }
+    }
+    if (px < W && py < H) keys[((size_t)b * H + py) * W + px] = best;
+}
+
+// ---------------------------------------------------------------- host launcher
+cudaError_t raster_views(const RasterIn& in, RasterScratch& s, cudaStream_t st) {
+    int B = in.B, V = in.V, F = in.F, W = in.W, H = in.H;
+    int tiles_x = (W + ADMS_TILE - 1) / ADMS_TILE, tiles_y = (H + ADMS_TILE - 1) / ADMS_TILE;
+    int ntiles = B * tiles_x * tiles_y;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(s.tile_count, 0, sizeof(int) * ntiles, st))) return e;
+    if ((e = cudaMemsetAsync(s.tile_cursor, 0, sizeof(int) * ntiles, st))) return e;
+    int bs = 256;
+    k_transform<<<(B * V + bs - 1) / bs, bs, 0, st>>>(in.pos, V, in.views, B, W, H, s.clip, s.vs, s.scr);
+    k_setup<<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec, s.asign,
+                                                s.tile_count);
+    k_scan<<<1, 1024, 0, st>>>(s.tile_count, ntiles, s.tile_off, s.total_pairs);
+    k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.rec, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
+                                                   s.list, s.list_capacity);
+    dim3 grid(tiles_x * tiles_y, B);
+    k_raster<<<grid, 256, 0, st>>>(s.rec, F, W, H, tiles_x, tiles_y, s.tile_off, s.tile_count, s.list,
+                                   s.list_capacity, in.keys, s.overflow_ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace adms

@@ -1,0 +1,623 @@
+// Per-pixel deferred shading, silhouette antialiasing, image loss and the fused
+// backward (Sec. 5.2 renderer, Sec. 5.3 objective).
+//
+// No G-buffer is stored: every per-pixel kernel recomputes the perspective-
+// correct barycentrics and the interpolated attributes from the visibility
+// key (triangle id) and the per-view vertex data.
+//
+// Precision: screen positions arrive as float-float pairs computed in float64
+// per vertex, so offsets from the pixel centre keep float32 relative
+// precision; attributes are interpolated as corner-0 value + weighted corner
+// differences, which keeps texel coordinates of large textures accurate and
+// lets the barycentric adjoint use (a_j - a) without cancellation. Vertex
+// gradients are accumulated in float64.
+#include "kernels.cuh"
+
+namespace adms {
+
+// ------------------------------------------------------------------ pixel geometry
+struct PixGeo {
+    int vi[3], ui[3];
+    float4 c[3];      // clip coordinates (w, and the adjoint of the projection)
+    float2 d[3];      // screen position minus pixel centre
+    float e[3], area, lam[3], r[3], R, beta[3];
+    float3 p, n, t;   // interpolated position, normal, tangent
+    float3 dp, dn, dt;  // interpolated minus corner 0
+    float2 duv;       // interpolated uv minus corner 0
+    TexCoord tc;
+    float2 duv_dx, duv_dy;
+};
+
+__device__ __forceinline__ float2 rel_screen(float4 S, float ox, float oy) {
+    return make_float2((S.x - ox) + S.y, (S.z - oy) + S.w);
+}
+
+__device__ __forceinline__ void pix_geo(const ShadeArgs& A, int b, int px, int py, int f, PixGeo& g) {
+    float qx = (float)px + 0.5f, qy = (float)py + 0.5f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        g.vi[k] = A.tri[3 * f + k];
+        g.ui[k] = A.tri_uv[3 * f + k];
+        size_t o = (size_t)b * A.V + g.vi[k];
+        g.c[k] = A.clip[o];
+        g.d[k] = rel_screen(A.scr[o], qx, qy);
+    }
+    g.e[0] = cross2(g.d[1], g.d[2]);
+    g.e[1] = cross2(g.d[2], g.d[0]);
+    g.e[2] = cross2(g.d[0], g.d[1]);
+    g.area = cross2(make_float2(g.d[1].x - g.d[0].x, g.d[1].y - g.d[0].y),
+                    make_float2(g.d[2].x - g.d[0].x, g.d[2].y - g.d[0].y));
+    float ia = 1.f / g.area;
+    g.R = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        g.lam[k] = g.e[k] * ia;
+        g.r[k] = g.lam[k] / g.c[k].w;
+        g.R += g.r[k];
+    }
+    float iR = 1.f / g.R;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g.beta[k] = g.r[k] * iR;
+    float3 p0 = f3(A.vpos[g.vi[0]]), n0 = f3(A.vnrm[g.vi[0]]), t0 = f3(A.vtan[g.vi[0]]);
+    float2 u0 = A.uv[g.ui[0]];
+    float2 u1 = A.uv[g.ui[1]], u2 = A.uv[g.ui[2]];
+    float2 du1 = make_float2(u1.x - u0.x, u1.y - u0.y), du2 = make_float2(u2.x - u0.x, u2.y - u0.y);
+    g.dp = g.beta[1] * (f3(A.vpos[g.vi[1]]) - p0) + g.beta[2] * (f3(A.vpos[g.vi[2]]) - p0);
+    g.dn = g.beta[1] * (f3(A.vnrm[g.vi[1]]) - n0) + g.beta[2] * (f3(A.vnrm[g.vi[2]]) - n0);
+    g.dt = g.beta[1] * (f3(A.vtan[g.vi[1]]) - t0) + g.beta[2] * (f3(A.vtan[g.vi[2]]) - t0);
+    g.p = p0 + g.dp;
+    g.n = n0 + g.dn;
+    g.t = t0 + g.dt;
+    g.duv = make_float2(g.beta[1] * du1.x + g.beta[2] * du2.x, g.beta[1] * du1.y + g.beta[2] * du2.y);
+    g.tc.u0 = u0.x;
+    g.tc.v0 = u0.y;
+    g.tc.du = g.duv.x;
+    g.tc.dv = g.duv.y;
+    // screen derivatives of the perspective-correct barycentrics (texture LOD only)
+    float dlx[3] = {(g.d[1].y - g.d[2].y) * ia, (g.d[2].y - g.d[0].y) * ia, (g.d[0].y - g.d[1].y) * ia};
+    float dly[3] = {(g.d[2].x - g.d[1].x) * ia, (g.d[0].x - g.d[2].x) * ia, (g.d[1].x - g.d[0].x) * ia};
+    float drx[3], dry[3], dRx = 0.f, dRy = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        drx[k] = dlx[k] / g.c[k].w;
+        dry[k] = dly[k] / g.c[k].w;
+        dRx += drx[k];
+        dRy += dry[k];
+    }
+    float db1x = (drx[1] * g.R - g.r[1] * dRx) * iR * iR, db2x = (drx[2] * g.R - g.r[2] * dRx) * iR * iR;
+    float db1y = (dry[1] * g.R - g.r[1] * dRy) * iR * iR, db2y = (dry[2] * g.R - g.r[2] * dRy) * iR * iR;
+    g.duv_dx = make_float2(db1x * du1.x + db2x * du2.x, db1x * du1.y + db2x * du2.y);
+    g.duv_dy = make_float2(db1y * du1.x + db2y * du2.x, db1y * du1.y + db2y * du2.y);
+}
+
+// ------------------------------------------------------------------ shading
+struct ShadeIn {
+    float3 p, n_i, t_i;
+    float4 kd, orm, nm;
+};
+
+struct ShadeGrad {
+    float3 p, n_i, t_i;
+    float4 kd, orm, nm;
+};
+
+// color = sum_lights E (n.l) kd (1 - m) / pi + (1 - gamma) D F(ks) G E / (4 n.v)
+template <bool BWD>
+__device__ __forceinline__ float3 shade_eval(const adms_view& vw, const ShadeIn& in, float3 gc, ShadeGrad* G) {
+    // shading frame
+    Nrm3 Nn = nrm3(in.n_i);
+    float3 N = Nn.y;
+    float s_tn = dot3(in.t_i, N);
+    float3 tt = in.t_i - s_tn * N;
+    Nrm3 Tn = nrm3(tt);
+    float3 T = Tn.y;
+    float3 Bt = cross3(N, T);
+    float3 mm = in.nm.x * T + in.nm.y * Bt + in.nm.z * N;
+    Nrm3 NSn = nrm3(mm);
+    float3 ns = NSn.y;
+    Nrm3 Vn = nrm3(f3(vw.eye[0], vw.eye[1], vw.eye[2]) - in.p);
+    float3 V = Vn.y;
+    float nv_raw = dot3(ns, V);
+    float nv = fmaxf(nv_raw, ADMS_NV_MIN);
+    float gam = in.orm.x, r = in.orm.y, m = in.orm.z;
+    float rr = fmaxf(r, ADMS_ROUGH_MIN);
+    float alpha = rr * rr, a2 = alpha * alpha;
+    float3 kd = f3(in.kd.x, in.kd.y, in.kd.z);
+    float3 ks = f3(0.04f, 0.04f, 0.04f) * (1.f - m) + m * kd;
+    float3 diff = kd * ((1.f - m) * (1.f / ADMS_PI));
+    float sqv = sqrtf(a2 + (1.f - a2) * nv * nv);
+    float G1v = 2.f * nv / (nv + sqv);
+
+    float3 color = zero3();
+    // backward accumulators
+    float3 g_ns = zero3(), g_V = zero3(), g_p = zero3(), g_ks = zero3(), g_diff = zero3();
+    float g_a2 = 0.f, g_nv = 0.f, g_gam = 0.f;
+
+#pragma unroll
+    for (int li = 0; li < 2; ++li) {
+        bool point = li == 0;
+        float strength = point ? vw.light_I : vw.light_E;
+        if (strength == 0.f) continue;
+        float3 l, d = zero3();
+        float E, dd = 0.f;
+        Nrm3 Ln;
+        if (point) {
+            d = f3(vw.light_pos[0], vw.light_pos[1], vw.light_pos[2]) - in.p;
+            Ln = nrm3(d);
+            l = Ln.y;
+            dd = dot3(d, d);
+            E = vw.light_I / dd;
+        } else {
+            l = f3(vw.light_dir[0], vw.light_dir[1], vw.light_dir[2]);
+            E = vw.light_E;
+        }
+        float nl = dot3(ns, l);
+        if (!(nl > 0.f)) continue;
+        Nrm3 Hn = nrm3(l + V);
+        float3 h = Hn.y;
+        float nh_raw = dot3(ns, h), vh_raw = dot3(V, h);
+        float nh = fmaxf(nh_raw, 0.f), vh = fmaxf(vh_raw, 0.f);
+        // nh^2 (a2 - 1) + 1 = (1 - nh^2) + a2 nh^2, with 1 - nh^2 = |ns x h|^2 for unit
+        // vectors: the cross-product form keeps float32 precision at sharp highlights
+        float3 nxh = cross3(ns, h);
+        float den = nh_raw > 0.f ? dot3(nxh, nxh) + a2 * nh * nh : 1.f;
+        float D = a2 / (ADMS_PI * den * den);
+        float om = 1.f - vh;
+        float om2 = om * om;
+        float om5 = om2 * om2 * om;
+        float3 F = ks + (f3(1.f, 1.f, 1.f) - ks) * om5;
+        float sql = sqrtf(a2 + (1.f - a2) * nl * nl);
+        float G1l = 2.f * nl / (nl + sql);
+        float q4 = E / (4.f * nv);
+        float S0 = D * G1l * G1v * q4;
+        float S = (1.f - gam) * S0;
+        color += (E * nl) * diff + S * F;
+        if (BWD) {
+            g_diff += (E * nl) * gc;
+            float gdotdiff = dot3(gc, diff);
+            float g_nl = E * gdotdiff;
+            float g_E = nl * gdotdiff;
+            float3 g_F = S * gc;
+            float g_S = dot3(gc, F);
+            g_gam += -g_S * S0;
+            float g_S0 = g_S * (1.f - gam);
+            float g_D = g_S0 * G1l * G1v * q4;
+            float g_G1l = g_S0 * D * G1v * q4;
+            float g_G1v = g_S0 * D * G1l * q4;
+            g_E += g_S0 * D * G1l * G1v / (4.f * nv);
+            g_nv += -g_S0 * S0 / nv;
+            g_ks += g_F * (1.f - om5);
+            float g_om5 = dot3(g_F, f3(1.f, 1.f, 1.f) - ks);
+            float g_vh = -5.f * om2 * om2 * g_om5;
+            float dl = sql * (nl + sql) * (nl + sql);
+            g_nl += g_G1l * 2.f * a2 / dl;
+            g_a2 += g_G1l * (-nl * (1.f - nl * nl) / dl);
+            float dv = sqv * (nv + sqv) * (nv + sqv);
+            g_nv += g_G1v * 2.f * a2 / dv;
+            g_a2 += g_G1v * (-nv * (1.f - nv * nv) / dv);
+            float pd3 = ADMS_PI * den * den * den;
+            g_a2 += g_D * (1.f / (ADMS_PI * den * den) - 2.f * a2 * nh * nh / pd3);
+            float g_nh = g_D * (-4.f * a2 * nh * (a2 - 1.f) / pd3);
+            float g_nhr = nh_raw >= 0.f ? g_nh : 0.f;
+            float g_vhr = vh_raw >= 0.f ? g_vh : 0.f;
+            float3 g_h = g_nhr * ns + g_vhr * V;
+            g_ns += g_nhr * h;
+            g_V += g_vhr * h;
+            float3 g_hu = nrm3_bwd(Hn, g_h);
+            float3 g_l = g_hu;
+            g_V += g_hu;
+            g_ns += g_nl * l;
+            g_l += g_nl * ns;
+            if (point) {
+                float3 g_d = nrm3_bwd(Ln, g_l) + (-2.f * E / dd * g_E) * d;
+                g_p -= g_d;
+            }
+        }
+    }
+    if (BWD) {
+        float g_alpha = 2.f * alpha * g_a2;
+        float g_rr = 2.f * rr * g_alpha;
+        float g_r = r >= ADMS_ROUGH_MIN ? g_rr : 0.f;
+        float3 g_kd = m * g_ks + ((1.f - m) * (1.f / ADMS_PI)) * g_diff;
+        float g_m = dot3(g_ks, kd - f3(0.04f, 0.04f, 0.04f)) - dot3(g_diff, kd) * (1.f / ADMS_PI);
+        float g_nvr = nv_raw >= ADMS_NV_MIN ? g_nv : 0.f;
+        g_ns += g_nvr * V;
+        g_V += g_nvr * ns;
+        g_p -= nrm3_bwd(Vn, g_V);
+        float3 g_mm = nrm3_bwd(NSn, g_ns);
+        float3 g_T = in.nm.x * g_mm, g_Bt = in.nm.y * g_mm, g_N = in.nm.z * g_mm;
+        g_N += cross3(T, g_Bt);
+        g_T += cross3(g_Bt, N);
+        float3 g_tt = nrm3_bwd(Tn, g_T);
+        float3 g_ti = g_tt;
+        float g_s = -dot3(N, g_tt);
+        g_N += -s_tn * g_tt;
+        g_ti += g_s * N;
+        g_N += g_s * in.t_i;
+        G->p = g_p;
+        G->n_i = nrm3_bwd(Nn, g_N);
+        G->t_i = g_ti;
+        G->kd = make_float4(g_kd.x, g_kd.y, g_kd.z, 0.f);
+        G->orm = make_float4(g_gam, g_r, g_m, 0.f);
+        G->nm = make_float4(dot3(g_mm, T), dot3(g_mm, Bt), dot3(g_mm, N), 0.f);
+    }
+    return color;
+}
+
+__device__ __forceinline__ int key_tri(unsigned long long k) { return k == ADMS_EMPTY_KEY ? -1 : (int)(k & 0xffffffffu); }
+
+__device__ __forceinline__ ShadeIn shade_inputs(const ShadeArgs& A, const PixGeo& g, float lod[3]) {
+    lod[0] = tex_lod(A.kd, g.duv_dx, g.duv_dy);
+    lod[1] = tex_lod(A.orm, g.duv_dx, g.duv_dy);
+    lod[2] = tex_lod(A.nrm, g.duv_dx, g.duv_dy);
+    ShadeIn in;
+    in.p = g.p;
+    in.n_i = g.n;
+    in.t_i = g.t;
+    in.kd = tex_sample(A.kd, g.tc, lod[0]);
+    in.orm = tex_sample(A.orm, g.tc, lod[1]);
+    in.nm = tex_sample(A.nrm, g.tc, lod[2]);
+    return in;
+}
+
+// ------------------------------------------------------------------ shading forward
+__global__ void __launch_bounds__(256) k_shade_fwd(ShadeArgs A) {
+    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    int b = blockIdx.y;
+    int px = (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15);
+    int py = (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4);
+    if (px >= A.W || py >= A.H) return;
+    size_t pix = ((size_t)b * A.H + py) * A.W + px;
+    int f = key_tri(A.keys[pix]);
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (f >= 0) {
+        PixGeo g;
+        pix_geo(A, b, px, py, f, g);
+        float lod[3];
+        ShadeIn in = shade_inputs(A, g, lod);
+        float3 c = shade_eval<false>(A.views[b], in, zero3(), nullptr);
+        out = make_float4(c.x, c.y, c.z, 1.f);
+    }
+    A.pre[pix] = out;
+}
+
+// ------------------------------------------------------------------ antialiasing
+struct PairTau {
+    int edge;       // -1: no blend
+    float tau, sp;
+    float2 a, b;    // edge endpoints relative to the owner's pixel centre
+    int va, vb;     // edge endpoints (position indices)
+};
+
+// The owner's silhouette edge crossing the open segment between the centres of
+// the owner (oi, oj) and the other pixel at +sigma along `axis`, nearest to the
+// owner; tau is the crossing's distance from the owner's centre in pixels.
+__device__ __forceinline__ PairTau pair_tau(const ShadeArgs& A, int b, int axis, int oi, int oj, int fo, float sigma) {
+    PairTau pt;
+    pt.edge = -1;
+    pt.tau = 0.5f;
+    float best = 1e30f;
+    float ox = (float)oi + 0.5f, oy = (float)oj + 0.5f;
+    const int8_t* sg = A.asign + (size_t)b * A.F;
+    int so = sg[fo];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        int nb = A.adj[3 * fo + e];
+        bool sil = nb < 0 || sg[nb] != so;
+        if (!sil) continue;
+        int va = A.tri[3 * fo + e], vb = A.tri[3 * fo + (e + 1) % 3];
+        float2 sa = rel_screen(A.scr[(size_t)b * A.V + va], ox, oy);
+        float2 sb = rel_screen(A.scr[(size_t)b * A.V + vb], ox, oy);
+        float au = axis == 0 ? sa.y : sa.x, bu = axis == 0 ? sb.y : sb.x;
+        float ax = axis == 0 ? sa.x : sa.y, bx = axis == 0 ? sb.x : sb.y;
+        float den = bu - au;
+        if (den == 0.f) continue;
+        float sp = -au / den;
+        if (!(sp >= 0.f && sp <= 1.f)) continue;
+        float tau = sigma * (ax + sp * (bx - ax));
+        if (tau > 0.f && tau < 1.f && tau < best) {
+            best = tau;
+            pt.edge = e;
+            pt.tau = tau;
+            pt.sp = sp;
+            pt.a = sa;
+            pt.b = sb;
+            pt.va = va;
+            pt.vb = vb;
+        }
+    }
+    return pt;
+}
+
+struct PairInfo {
+    bool p_owner;
+    float sigma;
+    PairTau t;
+};
+
+// pair of pixel p = (px, py) with its neighbour q; false when both show the same
+// triangle (or both are empty) or when no silhouette edge crosses between them
+__device__ __forceinline__ bool pair_eval(const ShadeArgs& A, int b, int px, int py, unsigned long long kp, int qx,
+                                          int qy, unsigned long long kq, int axis, PairInfo& pi) {
+    int tp = key_tri(kp), tq = key_tri(kq);
+    if (tp == tq) return false;
+    pi.p_owner = kp < kq;
+    int oi = pi.p_owner ? px : qx, oj = pi.p_owner ? py : qy;
+    int si = pi.p_owner ? qx : px, sj = pi.p_owner ? qy : py;
+    pi.sigma = axis == 0 ? (float)(si - oi) : (float)(sj - oj);
+    pi.t = pair_tau(A, b, axis, oi, oj, pi.p_owner ? tp : tq, pi.sigma);
+    return pi.t.edge >= 0;
+}
+
+__device__ __forceinline__ float3 f3of(float4 a) { return f3(a.x, a.y, a.z); }
+
+// Gamma(log(x + 1)) with the sRGB Gamma of Sec. 5.3, and its derivative
+__device__ __forceinline__ float tonemap(float x, float* dfdx) {
+    float y = log1pf(x);
+    float dy = 1.f / (1.f + x);
+    if (y <= 0.0031308f) {
+        *dfdx = 12.92f * dy;
+        return 12.92f * y;
+    }
+    float pw = powf(y, 1.f / 2.4f);
+    *dfdx = (1.055f / 2.4f) * pw / y * dy;
+    return 1.055f * pw - 0.055f;
+}
+
+__device__ __forceinline__ float loss_term(int kind, float x, float y, float* g) {
+    if (kind == ADMS_LOSS_L1) {
+        float d = x - y;
+        *g = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+        return fabsf(d);
+    }
+    if (kind == ADMS_LOSS_L2) {
+        float d = x - y;
+        *g = 2.f * d;
+        return d * d;
+    }
+    float dfx, dfy;
+    float fx = tonemap(x, &dfx), fy = tonemap(y, &dfy);
+    float d = fx - fy;
+    *g = d > 0.f ? dfx : (d < 0.f ? -dfx : 0.f);
+    return fabsf(d);
+}
+
+__device__ __forceinline__ void neighbour(int nbi, int px, int py, int& qx, int& qy) {
+    qx = px + (nbi == 0 ? -1 : nbi == 1 ? 1 : 0);
+    qy = py + (nbi == 2 ? -1 : nbi == 3 ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(256) k_aa_loss(ShadeArgs A) {
+    __shared__ double red[8];
+    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    int b = blockIdx.y;
+    int px = (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15);
+    int py = (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4);
+    bool inside = px < A.W && py < A.H;
+    double lsum = 0.0;
+    if (inside) {
+        size_t pix = ((size_t)b * A.H + py) * A.W + px;
+        unsigned long long kp = A.keys[pix];
+        float3 cp = f3of(A.pre[pix]);
+        float3 out = cp;
+        if (A.aa) {
+#pragma unroll
+            for (int nbi = 0; nbi < 4; ++nbi) {
+                int qx, qy;
+                neighbour(nbi, px, py, qx, qy);
+                if (qx < 0 || qx >= A.W || qy < 0 || qy >= A.H) continue;
+                size_t qpix = ((size_t)b * A.H + qy) * A.W + qx;
+                PairInfo pi;
+                if (!pair_eval(A, b, px, py, kp, qx, qy, A.keys[qpix], nbi < 2 ? 0 : 1, pi)) continue;
+                float om = pi.t.tau - 0.5f;
+                // the other pixel blends toward the owner when tau > 1/2, the owner toward it when tau < 1/2
+                bool p_target = om > 0.f ? !pi.p_owner : (om < 0.f ? pi.p_owner : false);
+                if (p_target) out += fabsf(om) * (f3of(A.pre[qpix]) - cp);
+            }
+        }
+        if (A.ref) {
+            const float* y = A.ref + pix * 3;
+            float g0, g1, g2;
+            lsum = (double)loss_term(A.loss_kind, out.x, y[0], &g0) + (double)loss_term(A.loss_kind, out.y, y[1], &g1) +
+                   (double)loss_term(A.loss_kind, out.z, y[2], &g2);
+            A.gprime[pix] = make_float4(g0 * A.loss_scale, g1 * A.loss_scale, g2 * A.loss_scale, 0.f);
+        }
+        if (A.out_img) {
+            A.out_img[pix * 3] = out.x;
+            A.out_img[pix * 3 + 1] = out.y;
+            A.out_img[pix * 3 + 2] = out.z;
+        }
+    }
+    lsum = warp_sum_d(lsum);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0 && A.loss_acc) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        atomicAdd(A.loss_acc, s * (double)A.loss_scale);
+    }
+}
+
+// ------------------------------------------------------------------ backward
+// Scatter 9 per-corner vertex gradients (position, unit normal, unit tangent)
+// for the triangle of each lane; lanes of a warp that share a triangle are
+// summed first, then one lane per value issues a float64 atomic.
+__device__ __forceinline__ void scatter_vertex_grads(const ShadeArgs& A, int f, const int vi[3], float v[27]) {
+    unsigned todo = __ballot_sync(0xffffffffu, f >= 0);
+    int lane = threadIdx.x & 31;
+    while (todo) {
+        int lead = __ffs(todo) - 1;
+        int ft = __shfl_sync(0xffffffffu, f, lead);
+        bool mine = f == ft;
+        unsigned grp = __ballot_sync(0xffffffffu, mine);
+        int v0 = __shfl_sync(0xffffffffu, vi[0], lead), v1 = __shfl_sync(0xffffffffu, vi[1], lead),
+            v2 = __shfl_sync(0xffffffffu, vi[2], lead);
+        float mineval = 0.f;
+#pragma unroll
+        for (int j = 0; j < 27; ++j) {
+            float x = warp_sum(mine ? v[j] : 0.f);
+            if (lane == j) mineval = x;
+        }
+        if (lane < 27 && mineval != 0.f) {
+            int corner = lane / 9, comp = lane % 9;
+            int vtx = corner == 0 ? v0 : (corner == 1 ? v1 : v2);
+            double* dst = comp < 3 ? A.g_pos : (comp < 6 ? A.g_nrm : A.g_tan);
+            atomicAdd(dst + 3 * vtx + comp % 3, (double)mineval);
+        }
+        todo &= ~grp;
+    }
+}
+
+__device__ __forceinline__ void atomic_add3(double* p, float3 v) {
+    atomicAdd(p, (double)v.x);
+    atomicAdd(p + 1, (double)v.y);
+    atomicAdd(p + 2, (double)v.z);
+}
+
+__global__ void __launch_bounds__(256) k_shade_bwd(ShadeArgs A) {
+    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    int b = blockIdx.y;
+    int px = (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15);
+    int py = (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4);
+    bool inside = px < A.W && py < A.H;
+    const adms_view& vw = A.views[b];
+    float hW = 0.5f * (float)A.W, hH = 0.5f * (float)A.H;
+    int f = -1;
+    int vi[3] = {0, 0, 0};
+    float vg[27];
+#pragma unroll
+    for (int j = 0; j < 27; ++j) vg[j] = 0.f;
+    if (inside) {
+        size_t pix = ((size_t)b * A.H + py) * A.W + px;
+        unsigned long long kp = A.keys[pix];
+        f = key_tri(kp);
+        float3 gp = f3of(A.gprime[pix]);
+        float3 gc = gp;
+        if (A.aa) {
+            float3 cp = f3of(A.pre[pix]);
+#pragma unroll
+            for (int nbi = 0; nbi < 4; ++nbi) {
+                int qx, qy;
+                neighbour(nbi, px, py, qx, qy);
+                if (qx < 0 || qx >= A.W || qy < 0 || qy >= A.H) continue;
+                size_t qpix = ((size_t)b * A.H + qy) * A.W + qx;
+                int axis = nbi < 2 ? 0 : 1;
+                PairInfo pi;
+                if (!pair_eval(A, b, px, py, kp, qx, qy, A.keys[qpix], axis, pi)) continue;
+                float om = pi.t.tau - 0.5f;
+                if (om == 0.f) continue;
+                bool p_target = om > 0.f ? !pi.p_owner : pi.p_owner;
+                float3 gq = f3of(A.gprime[qpix]);
+                float w = fabsf(om);
+                if (p_target) gc -= w * gp;
+                else gc += w * gq;
+                // d tau: once per pair, by its left / top pixel
+                if (nbi == 1 || nbi == 3) {
+                    float3 cq = f3of(A.pre[qpix]);
+                    float3 gT = p_target ? gp : gq;
+                    float3 cT = p_target ? cp : cq, cS = p_target ? cq : cp;
+                    float g_tau = (om > 0.f ? 1.f : -1.f) * dot3(gT, cS - cT);
+                    float au = axis == 0 ? pi.t.a.y : pi.t.a.x, bu = axis == 0 ? pi.t.b.y : pi.t.b.x;
+                    float ax = axis == 0 ? pi.t.a.x : pi.t.a.y, bx = axis == 0 ? pi.t.b.x : pi.t.b.y;
+                    float du = bu - au, dx = bx - ax, sp = pi.t.sp;
+                    float k = pi.sigma * g_tau;
+                    float ga_x = k * (1.f - sp), ga_u = k * dx * (sp - 1.f) / du;
+                    float gb_x = k * sp, gb_u = -k * dx * sp / du;
+                    float2 gsa = axis == 0 ? make_float2(ga_x, ga_u) : make_float2(ga_u, ga_x);
+                    float2 gsb = axis == 0 ? make_float2(gb_x, gb_u) : make_float2(gb_u, gb_x);
+                    float4 ca = A.clip[(size_t)b * A.V + pi.t.va], cb = A.clip[(size_t)b * A.V + pi.t.vb];
+                    atomic_add3(A.g_pos + 3 * pi.t.va, clip_to_pos_grad(vw.mvp, screen_bwd(ca, hW, hH, gsa)));
+                    atomic_add3(A.g_pos + 3 * pi.t.vb, clip_to_pos_grad(vw.mvp, screen_bwd(cb, hW, hH, gsb)));
+                }
+            }
+        }
+        if (f >= 0 && (gc.x != 0.f || gc.y != 0.f || gc.z != 0.f)) {
+            PixGeo g;
+            pix_geo(A, b, px, py, f, g);
+            float lod[3];
+            ShadeIn in = shade_inputs(A, g, lod);
+            ShadeGrad G;
+            shade_eval<true>(vw, in, gc, &G);
+            float2 guv = tex_sample_bwd(A.kd, g.tc, lod[0], G.kd);
+            float2 g2 = tex_sample_bwd(A.orm, g.tc, lod[1], G.orm);
+            float2 g3 = tex_sample_bwd(A.nrm, g.tc, lod[2], G.nm);
+            guv.x += g2.x + g3.x;
+            guv.y += g2.y + g3.y;
+            // interpolation: attr = sum_k beta_k attr_k, beta_k = r_k / R  =>  d attr / d r_j = (attr_j - attr) / R
+            float gr[3];
+            {
+                float2 u0 = A.uv[g.ui[0]];
+                float3 p0 = f3(A.vpos[g.vi[0]]), n0 = f3(A.vnrm[g.vi[0]]), t0 = f3(A.vtan[g.vi[0]]);
+                float iR = 1.f / g.R;
+                gr[0] = -(dot3(G.p, g.dp) + dot3(G.n_i, g.dn) + dot3(G.t_i, g.dt) + guv.x * g.duv.x + guv.y * g.duv.y) * iR;
+#pragma unroll
+                for (int k = 1; k < 3; ++k) {
+                    float2 uk = A.uv[g.ui[k]];
+                    float3 ep = f3(A.vpos[g.vi[k]]) - p0 - g.dp;
+                    float3 en = f3(A.vnrm[g.vi[k]]) - n0 - g.dn;
+                    float3 et = f3(A.vtan[g.vi[k]]) - t0 - g.dt;
+                    float eu = (uk.x - u0.x) - g.duv.x, ev = (uk.y - u0.y) - g.duv.y;
+                    gr[k] = (dot3(G.p, ep) + dot3(G.n_i, en) + dot3(G.t_i, et) + guv.x * eu + guv.y * ev) * iR;
+                }
+            }
+            float glam[3], gw[3], sgl = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                vi[k] = g.vi[k];
+                glam[k] = gr[k] / g.c[k].w;
+                gw[k] = -gr[k] * g.r[k] / g.c[k].w;
+                sgl += glam[k] * g.lam[k];
+            }
+            float ia = 1.f / g.area;
+            float ge[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) ge[k] = (glam[k] - sgl) * ia;
+            const float2* d = g.d;
+            float2 gs[3];
+            // e0 = cross(d1, d2), e1 = cross(d2, d0), e2 = cross(d0, d1)
+            gs[0] = make_float2(-ge[1] * d[2].y + ge[2] * d[1].y, ge[1] * d[2].x - ge[2] * d[1].x);
+            gs[1] = make_float2(ge[0] * d[2].y - ge[2] * d[0].y, -ge[0] * d[2].x + ge[2] * d[0].x);
+            gs[2] = make_float2(-ge[0] * d[1].y + ge[1] * d[0].y, ge[0] * d[1].x - ge[1] * d[0].x);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                float4 gcl = screen_bwd(g.c[k], hW, hH, gs[k]);
+                gcl.w += gw[k];
+                float3 gpk = g.beta[k] * G.p + clip_to_pos_grad(vw.mvp, gcl);
+                float3 gnk = g.beta[k] * G.n_i, gtk = g.beta[k] * G.t_i;
+                vg[9 * k + 0] = gpk.x;
+                vg[9 * k + 1] = gpk.y;
+                vg[9 * k + 2] = gpk.z;
+                vg[9 * k + 3] = gnk.x;
+                vg[9 * k + 4] = gnk.y;
+                vg[9 * k + 5] = gnk.z;
+                vg[9 * k + 6] = gtk.x;
+                vg[9 * k + 7] = gtk.y;
+                vg[9 * k + 8] = gtk.z;
+            }
+        } else {
+            f = -1;
+        }
+    }
+    scatter_vertex_grads(A, f, vi, vg);
+}
+
+// ------------------------------------------------------------------ launchers
+static dim3 pix_grid(const ShadeArgs& a) {
+    int tx = (a.W + ADMS_TILE - 1) / ADMS_TILE, ty = (a.H + ADMS_TILE - 1) / ADMS_TILE;
+    return dim3(tx * ty, a.B);
+}
+
+cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
+    k_shade_fwd<<<pix_grid(a), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st) {
+    k_aa_loss<<<pix_grid(a), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st) {
+    k_shade_bwd<<<pix_grid(a), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace adms

@@ -1,0 +1,134 @@
+"""Python front of the C ABI: jobs built from arrays, torch views of job state.
+
+Argument marshalling only; every step runs in libadms.so. Device buffers the
+caller passes (reference images, outputs) are torch CUDA tensors.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+class _DevArray:
+    """Exposes a raw device pointer through __cuda_array_interface__ so torch can wrap it."""
+
+    def __init__(self, ptr, shape, typestr="<f4"):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def device_view(ptr, shape, dtype=torch.float32):
+    """A torch tensor aliasing library-owned device memory (valid while the job lives)."""
+    if not ptr:
+        return None
+    typestr = {torch.float32: "<f4", torch.int64: "<i8"}[dtype]
+    return torch.as_tensor(_DevArray(ptr, shape, typestr), device="cuda")
+
+
+def _c32(a, dtype):
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+class Context:
+    """One adms context on the current CUDA device and a CUDA stream."""
+
+    def __init__(self, hbm_budget_bytes=0, stream=None):
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = B.adms_ctx_create(hbm_budget_bytes, self.stream)
+        self._keep = {}
+
+    def close(self):
+        if self.ctx:
+            B.adms_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ jobs
+    def create_job(self, scene, optimize=None, loss="logl1", lr0=0.01, lambda0=0.0, batch_views=0, aa=True,
+                   relative_laplacian=False, frozen=False, seed=0):
+        """scene: object with .mesh (pos, uv, tri_pos, tri_uv), .kd, .orm, .nrm, .mips (numpy)."""
+        m = scene.mesh
+        arrays = dict(pos=_c32(m.pos, np.float32), uv=_c32(m.uv, np.float32), tri=_c32(m.tri_pos, np.int32),
+                      tri_uv=_c32(m.tri_uv, np.int32), kd=_c32(scene.kd, np.float32),
+                      orm=_c32(scene.orm, np.float32), nrm=_c32(scene.nrm, np.float32))
+        mesh = B.mesh_desc(arrays["pos"], arrays["uv"], arrays["tri"], arrays["tri_uv"])
+        mat = B.material_desc(arrays["kd"], arrays["orm"], arrays["nrm"], None, getattr(scene, "mips", True))
+        opt = None
+        if not frozen:
+            opt = B.opt_params(optimize if optimize is not None else getattr(scene, "optimize", {}), loss=loss,
+                               batch_views=batch_views, relative_laplacian=relative_laplacian, aa=aa, lr0=lr0,
+                               lambda0=lambda0)
+        return B.adms_job_create(self.ctx, mesh, mat, opt, seed)
+
+    def destroy_job(self, job):
+        B.adms_job_destroy(self.ctx, job)
+
+    def params(self, job):
+        """torch views of a job's latents and gradients (level 0 of textures)."""
+        pv = B.adms_job_params(self.ctx, job)
+        V = pv.n_verts
+        out = {"t": pv.t}
+        out["pos"] = device_view(pv.pos, (V, 3))
+        out["g_pos"] = device_view(pv.g_pos, (V, 3))
+        for name in ("kd", "orm", "nrm"):
+            h, w, L = getattr(pv, name + "_h"), getattr(pv, name + "_w"), getattr(pv, name + "_levels")
+            total = sum(max(h >> k, 1) * max(w >> k, 1) for k in range(L))
+            out[name] = device_view(getattr(pv, name), (h, w, 4))
+            out["g_" + name] = device_view(getattr(pv, "g_" + name), (h, w, 4))
+            out["g_" + name + "_chain"] = device_view(getattr(pv, "g_" + name), (total, 4))
+            out[name + "_levels"] = L
+        return out
+
+    def stats(self, job):
+        s = B.adms_job_stats(self.ctx, job)
+        return dict(image_loss=s.image_loss, laplacian=s.laplacian, lam=s.lambda_, lr=s.lr, t=s.t,
+                    status=s.status, tile_overflows=s.tile_overflows)
+
+    # ------------------------------------------------------------------ the step
+    @staticmethod
+    def _views(views):
+        if isinstance(views, torch.Tensor):
+            return views
+        return np.ascontiguousarray(views)
+
+    def render_reference(self, job, views, H, W, out=None):
+        views = self._views(views)
+        n = len(views)
+        if out is None:
+            out = torch.empty((n, H, W, 3), dtype=torch.float32, device="cuda")
+        B.adms_render_reference(self.ctx, job, views, H, W, out)
+        return out
+
+    def forward_loss(self, jobs, views_list, refs, out_img=None, out_loss=None):
+        """jobs: list of handles; views_list: list of view arrays; refs: list of (B, H, W, 3) CUDA tensors."""
+        views = np.ascontiguousarray(np.concatenate([np.asarray(v) for v in views_list])) \
+            if not isinstance(views_list[0], torch.Tensor) else torch.cat(list(views_list))
+        vpj = [len(v) for v in views_list]
+        hw = [(int(r.shape[1]), int(r.shape[2])) for r in refs]
+        if out_loss is None:
+            out_loss = torch.zeros(len(jobs), dtype=torch.float32, device="cuda")
+        B.adms_forward_loss(self.ctx, list(jobs), views, vpj, hw, refs, out_loss, out_img)
+        self._keep["fwd"] = (views, refs)
+        return out_loss
+
+    def backward(self, jobs, recompute_raster=False):
+        B.adms_backward(self.ctx, list(jobs), int(recompute_raster))
+
+    def step(self, jobs):
+        B.adms_optimizer_step(self.ctx, list(jobs))
+
+    def keys(self, job, shape):
+        out = torch.empty(shape, dtype=torch.int64, device="cuda")
+        B.adms_job_keys(self.ctx, job, out)
+        return out
+
+    def sync(self):
+        B.adms_sync(self.ctx)

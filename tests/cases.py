@@ -1,0 +1,115 @@
+"""Shared parity-test cases: seeded scenes, views and reference images.
+
+Reference images fed to both sides come from the oracle (float64, rounded to
+float32 once), never from the CUDA path."""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import synth
+from oracle import step as S
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).reshape(-1)
+    b = np.asarray(b, dtype=np.float64).reshape(-1)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def small_case():
+    """One 256^2 view, 320-tri candidate with 256^2 maps vs the 20,480-tri reference, plain L1."""
+    c = synth.config_small()
+    views = synth.fixed_view(256, 256)
+    return c, views, 256, 256
+
+
+def plain_case(res=128, n_views=8, tex=256, ref_tex=256, ref_freq=32, seed=5):
+    """The batched-view workload shrunk for the oracle: 5,120-tri candidate, 8 random views."""
+    c = synth.config_plain(tex_res=tex, ref_tex_res=ref_tex, ref_freq=ref_freq, n_views=n_views, res=res)
+    views = synth.sample_views(seed, 0, n_views, res, res)
+    return c, views, res, res
+
+
+def oracle_reference(scene, views, H, W):
+    img, keys = S.render_reference(scene, views, H, W)
+    return img.numpy().astype(np.float32), keys
+
+
+def fold_mips(g, h, w, levels):
+    """Level-0 gradient of a texture from the gradients of its whole mip chain.
+
+    g: (total_texels, 4) laid out level after level; each level-k texel is the
+    mean of its 2^k x 2^k level-0 texels (square power-of-two textures)."""
+    out = g[: h * w].reshape(h, w, 4).double().clone()
+    off = h * w
+    for k in range(1, levels):
+        hk, wk = max(h >> k, 1), max(w >> k, 1)
+        lv = g[off: off + hk * wk].reshape(hk, wk, 4).double()
+        out += lv.repeat_interleave(h // hk, 0).repeat_interleave(w // wk, 1) / float((h // hk) * (w // wk))
+        off += hk * wk
+    return out
+
+
+def oracle_grads(scene, views, refs, H, W, loss):
+    """Oracle image-loss gradients (lambda = 0), images, keys, loss, and the
+    vertices whose gradient is not unique at float32 resolution."""
+    job = S.OracleJob(scene, loss=loss)
+    params = {k: v.clone().requires_grad_(job.optimize[k]) for k, v in job.params.items()}
+    diags = []
+    obj = S.objective(job, params, views, torch.as_tensor(refs.astype(np.float64)), H, W, lam=0.0, diags=diags)
+    live = [k for k in params if job.optimize[k]]
+    grads = dict(zip(live, [g.detach().numpy() for g in torch.autograd.grad(obj["total"], [params[k] for k in live])]))
+    img = obj["out"]["img"].detach().numpy()
+    amb = ambiguous_vertices(diags, obj["out"]["keys"], img, refs, job.tri_np, loss)
+    return dict(grads=grads, img=img, pre=obj["out"]["pre"].detach().numpy(), keys=obj["out"]["keys"],
+                loss=float(obj["image"].detach()), ambiguous=amb)
+
+
+# Margins to the discrete decisions inside the differentiable path. The CUDA
+# path evaluates texel coordinates to ~1e-6 texels and screen positions to
+# ~1e-6 pixels, so a lookup or crossing farther than these margins from its
+# boundary takes the same side on both sides of the comparison.
+TEXEL_MARGIN = 5e-5   # texels: bilinear cell boundary (uv-derivative is one-sided there)
+NL_MARGIN = 1e-5      # n.l = 0: a light switches on or off
+AA_MARGIN = 1e-4      # pixels: silhouette crossing tests and tau = 1/2
+LOSS_MARGIN = 1e-5    # |f(x) - f(y)|: sign of the L1 residual
+
+
+def ambiguous_vertices(diags, keys, img, refs, tri, loss):
+    """Vertices touched by pixels within a margin of a kink of the forward.
+
+    At such a pixel the forward is continuous but its derivative is one-sided,
+    and the float32 kernel may legitimately take the other side: the gradient
+    is not unique there, so parity tests compare the other vertices exactly
+    and these only for validity."""
+    from oracle import render as R
+
+    tri = np.asarray(tri)
+    verts = set()
+    for b, dg in enumerate(diags):
+        if not dg:
+            continue
+        kb = keys[b]
+        tid = np.where(kb == np.uint64(R.EMPTY), -1, (kb & np.uint64(0xFFFFFFFF)).astype(np.int64)).reshape(-1)
+        bad = set(dg["tri"][(dg["texel_margin"] < TEXEL_MARGIN) | (dg["nl_margin"] < NL_MARGIN)].tolist())
+        for o, s, m in dg.get("aa_pairs", []):
+            sel = m < AA_MARGIN
+            bad |= set(tid[o[sel]].tolist()) | set(tid[s[sel]].tolist())
+        x = torch.as_tensor(img[b].astype(np.float64))
+        y = torch.as_tensor(np.asarray(refs[b], dtype=np.float64))
+        if loss == "logl1":
+            x, y = R.tonemap(x), R.tonemap(y)
+        close = ((x - y).abs() < LOSS_MARGIN).any(dim=2).numpy() & ((x - y).abs().sum(dim=2) > 0).numpy()
+        H, W = close.shape
+        for j, i in zip(*np.nonzero(close)):
+            for dj, di in ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)):
+                jj, ii = j + dj, i + di
+                if 0 <= jj < H and 0 <= ii < W:
+                    bad.add(int(tid[jj * W + ii]))
+        bad.discard(-1)
+        for f in bad:
+            verts |= set(tri[f].tolist())
+    return verts
