@@ -203,6 +203,21 @@ adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t*
 adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
                             const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out);
 
+/* ---- tracing ------------------------------------------------------------- */
+
+/* Bracket every stage launched through this context with CUDA events on its
+ * stream (enable = 1) or stop doing so (0). No paper counterpart: tooling. */
+adms_status adms_ctx_profile(adms_ctx* ctx, int32_t enable);
+/* Synchronise, then return and reset the GPU milliseconds and stage launch
+ * counts accumulated per stage since the previous call. ms_out and
+ * launches_out (nullable) hold n_stages >= adms_stage_count() entries. */
+adms_status adms_ctx_stage_times(adms_ctx* ctx, double* ms_out, int64_t* launches_out, int32_t n_stages);
+int32_t adms_stage_count(void);
+/* Name of stage i ("raster", "shade_bwd", ...), "" if out of range. */
+const char* adms_stage_name(int32_t i);
+/* Kernels this library has launched in this process (host-side count). */
+int64_t adms_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

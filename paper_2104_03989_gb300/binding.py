@@ -92,6 +92,11 @@ SIGNATURES = {
     "adms_job_export": ([P, C.c_int32, P, C.POINTER(C.c_size_t)], C.c_int),
     "adms_job_import": ([P, C.POINTER(adms_mesh_desc), C.POINTER(adms_material_desc), C.POINTER(adms_opt_params),
                          P, C.c_size_t, C.POINTER(C.c_int32)], C.c_int),
+    "adms_ctx_profile": ([P, C.c_int32], C.c_int),
+    "adms_ctx_stage_times": ([P, P, P, C.c_int32], C.c_int),
+    "adms_stage_count": ([], C.c_int32),
+    "adms_stage_name": ([C.c_int32], C.c_char_p),
+    "adms_launch_count": ([], C.c_int64),
 }
 
 _lib = None
@@ -244,3 +249,20 @@ def adms_job_import(ctx, mesh, mat, opt, buf):
     _check(ctx, lib().adms_job_import(ctx, C.byref(mesh), C.byref(mat), C.byref(opt) if opt is not None else None,
                                       ptr(buf), buf.nbytes, C.byref(out)))
     return out.value
+
+
+def adms_ctx_profile(ctx, enable=True):
+    _check(ctx, lib().adms_ctx_profile(ctx, int(enable)))
+
+
+def adms_ctx_stage_times(ctx):
+    """{stage name: (gpu ms, launches)} accumulated since the previous call."""
+    n = int(lib().adms_stage_count())
+    ms = np.zeros(n, dtype=np.float64)
+    cnt = np.zeros(n, dtype=np.int64)
+    _check(ctx, lib().adms_ctx_stage_times(ctx, ptr(ms), ptr(cnt), n))
+    return {lib().adms_stage_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(n)}
+
+
+def adms_launch_count():
+    return int(lib().adms_launch_count())

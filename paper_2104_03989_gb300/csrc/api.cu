@@ -83,12 +83,50 @@ struct Job {
 
 }  // namespace
 
+enum Stage {
+    ST_FRAME = 0,
+    ST_RASTER_SETUP,
+    ST_RASTER,
+    ST_SHADE,
+    ST_AA_LOSS,
+    ST_SHADE_BWD,
+    ST_FRAME_BWD,
+    ST_LAPLACIAN,
+    ST_ADAM,
+    ST_MIP,
+    ST_SMALL,
+    ST_COUNT
+};
+static const char* kStageNames[ST_COUNT] = {"frame",     "raster_setup", "raster", "shade",     "aa_loss", "shade_bwd",
+                                            "frame_bwd", "laplacian",    "adam",   "mip_build", "scalars"};
+
+struct StageRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+
 struct adms_ctx {
     cudaStream_t stream = 0;
     size_t budget = 0;
     size_t in_use = 0;
     std::string err;
     std::vector<Job> jobs;
+    // optional per-stage timing with CUDA events on the context's stream
+    bool profile = false;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    std::vector<StageRec> recs;
+    double stage_ms[ST_COUNT] = {0};
+    long long stage_n[ST_COUNT] = {0};
+
+    cudaEvent_t event() {
+        if (pool_used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[pool_used++];
+    }
 };
 
 namespace {
@@ -104,6 +142,21 @@ adms_status fail(adms_ctx* c, adms_status s, const std::string& msg) {
         if (e_ != cudaSuccess)                                                                \
             return fail(ctx, ADMS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
+
+// run one launcher, bracketed by events when the context profiles
+template <typename F>
+cudaError_t timed(adms_ctx* ctx, int stage, F&& f) {
+    if (!ctx->profile) return f();
+    cudaEvent_t a = ctx->event();
+    cudaEventRecord(a, ctx->stream);
+    cudaError_t e = f();
+    cudaEvent_t b = ctx->event();
+    cudaEventRecord(b, ctx->stream);
+    ctx->recs.push_back({stage, a, b});
+    return e;
+}
+
+#define TIMED(stage, call) timed(ctx, stage, [&]() { return (call); })
 
 template <typename T>
 adms_status job_alloc(adms_ctx* ctx, Job& j, T** out, size_t count) {
@@ -276,7 +329,7 @@ ShadeArgs shade_args(Job& j) {
 // frame, raster and pre-AA shading of B views already copied to j.views
 adms_status render_core(adms_ctx* ctx, Job& j) {
     if (!j.frame_valid) {
-        CK(frame_forward(frame_args(j), ctx->stream));
+        CK(TIMED(ST_FRAME, frame_forward(frame_args(j), ctx->stream)));
         j.frame_valid = true;
     }
     RasterIn in;
@@ -289,8 +342,9 @@ adms_status render_core(adms_ctx* ctx, Job& j) {
     in.W = j.W;
     in.H = j.H;
     in.keys = j.keys;
-    CK(raster_views(in, j.rs, ctx->stream));
-    CK(shade_forward(shade_args(j), ctx->stream));
+    CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
+    CK(TIMED(ST_RASTER, raster_tiles(in, j.rs, ctx->stream)));
+    CK(TIMED(ST_SHADE, shade_forward(shade_args(j), ctx->stream)));
     return ADMS_OK;
 }
 
@@ -547,7 +601,7 @@ adms_status adms_render_reference(adms_ctx* ctx, adms_job job, const adms_view* 
     a.loss_acc = nullptr;
     a.out_img = out_rgb;
     a.aa = 1;
-    CK(aa_loss_forward(a, ctx->stream));
+    CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
     j.have_fwd = false;
     return ADMS_OK;
 }
@@ -580,8 +634,8 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
         a.loss_acc = &j.st->call_loss;
         a.out_img = out_img ? out_img[k] : nullptr;
         CK(cudaMemsetAsync(&j.st->call_loss, 0, sizeof(double), ctx->stream));
-        CK(aa_loss_forward(a, ctx->stream));
-        CK(finish_call_loss(j.st, out_loss ? out_loss + k : nullptr, ctx->stream));
+        CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
+        CK(TIMED(ST_SMALL, finish_call_loss(j.st, out_loss ? out_loss + k : nullptr, ctx->stream)));
         j.have_fwd = true;
     }
     return ADMS_OK;
@@ -602,8 +656,8 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
         CK(cudaMemsetAsync(j.g_tan, 0, sizeof(double) * 3 * j.V, ctx->stream));
         ShadeArgs a = shade_args(j);
         a.ref = j.ref;
-        CK(shade_backward(a, ctx->stream));
-        CK(frame_backward(frame_args(j), ctx->stream));
+        CK(TIMED(ST_SHADE_BWD, shade_backward(a, ctx->stream)));
+        CK(TIMED(ST_FRAME_BWD, frame_backward(frame_args(j), ctx->stream)));
         j.have_fwd = false;
     }
     return ADMS_OK;
@@ -617,22 +671,22 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         Job& j = *jp;
         if (j.frozen) return fail(ctx, ADMS_ERR_STATE, "optimizer_step on a frozen job");
         LapArgs la{j.V, j.pos, j.ring_off, j.ring, j.delta_ref, j.delta, j.g_pos, j.st};
-        if (j.opt.optimize_pos) CK(laplacian_forward(la, ctx->stream));
+        if (j.opt.optimize_pos) CK(TIMED(ST_LAPLACIAN, laplacian_forward(la, ctx->stream)));
         SchedArgs sa{j.st, j.opt.lr0, j.opt.lambda0, j.opt.optimize_pos, j.V};
-        CK(schedule_step(sa, ctx->stream));
+        CK(TIMED(ST_SMALL, schedule_step(sa, ctx->stream)));
         if (j.opt.optimize_pos) {
-            CK(laplacian_backward(la, ctx->stream));
-            CK(adam_flat(j.pos, j.g_pos, j.m_pos, j.v_pos, (long long)j.V * 3, j.st, ctx->stream));
+            CK(TIMED(ST_LAPLACIAN, laplacian_backward(la, ctx->stream)));
+            CK(TIMED(ST_ADAM, adam_flat(j.pos, j.g_pos, j.m_pos, j.v_pos, (long long)j.V * 3, j.st, ctx->stream)));
         } else {
             CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.V, ctx->stream));
         }
         TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
         for (int m = 0; m < 3; ++m) {
             if (!maps[m]->opt) continue;
-            CK(adam_texture(maps[m]->dev(), maps[m]->m, maps[m]->v, m, j.st, ctx->stream));
-            CK(mip_build(maps[m]->dev(), ctx->stream));
+            CK(TIMED(ST_ADAM, adam_texture(maps[m]->dev(), maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
+            CK(TIMED(ST_MIP, mip_build(maps[m]->dev(), ctx->stream)));
         }
-        CK(advance_step(j.st, ctx->stream));
+        CK(TIMED(ST_SMALL, advance_step(j.st, ctx->stream)));
         j.frame_valid = false;
     }
     return ADMS_OK;
@@ -657,5 +711,37 @@ adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
                             const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out) {
     return fail(ctx, ADMS_ERR_STATE, "import not implemented in this build");
 }
+
+adms_status adms_ctx_profile(adms_ctx* ctx, int32_t enable) {
+    if (!ctx) return ADMS_ERR_ARG;
+    ctx->profile = enable != 0;
+    return ADMS_OK;
+}
+
+adms_status adms_ctx_stage_times(adms_ctx* ctx, double* ms_out, int64_t* launches_out, int32_t n_stages) {
+    if (!ctx || !ms_out || n_stages < ST_COUNT) return fail(ctx, ADMS_ERR_ARG, "stage buffer too small");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (const StageRec& r : ctx->recs) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, r.a, r.b));
+        ctx->stage_ms[r.stage] += ms;
+        ctx->stage_n[r.stage] += 1;
+    }
+    ctx->recs.clear();
+    ctx->pool_used = 0;
+    for (int s = 0; s < ST_COUNT; ++s) {
+        ms_out[s] = ctx->stage_ms[s];
+        if (launches_out) launches_out[s] = ctx->stage_n[s];
+        ctx->stage_ms[s] = 0.0;
+        ctx->stage_n[s] = 0;
+    }
+    return ADMS_OK;
+}
+
+int32_t adms_stage_count(void) { return ST_COUNT; }
+
+const char* adms_stage_name(int32_t i) { return (i >= 0 && i < ST_COUNT) ? kStageNames[i] : ""; }
+
+int64_t adms_launch_count(void) { return (int64_t)g_launches.load(); }
 
 }  // extern "C"

@@ -1,9 +1,15 @@
 // Kernel-side data structures and host launchers of the render-and-compare step.
 #pragma once
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace adms {
+
+// kernels launched by this library in this process (counted on the host at each launch)
+inline std::atomic<long long> g_launches{0};
+inline void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // transformed vertex of one view: snapped sub-pixel position, depth, usable flag
 struct VtxS {
@@ -48,6 +54,10 @@ struct RasterScratch {
 };
 
 cudaError_t raster_views(const RasterIn& in, RasterScratch& s, cudaStream_t st);
+// transform, setup, tile counts, scan and tile lists
+cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st);
+// the per-tile z-buffer pass
+cudaError_t raster_tiles(const RasterIn& in, RasterScratch& s, cudaStream_t st);
 
 // everything the per-pixel shading, AA, loss and backward kernels read
 struct ShadeArgs {

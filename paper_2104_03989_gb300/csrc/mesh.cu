@@ -101,12 +101,14 @@ __global__ void k_frame_bwd2(FrameArgs a) {
 
 cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st) {
     k_frame_fwd<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t frame_backward(const FrameArgs& a, cudaStream_t st) {
     k_frame_bwd1<<<(a.V + 127) / 128, 128, 0, st>>>(a);
     k_frame_bwd2<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -156,11 +158,13 @@ cudaError_t laplacian_forward(const LapArgs& a, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(&a.st->lap_sum, 0, sizeof(double), st);
     if (e) return e;
     k_lap_fwd<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t laplacian_backward(const LapArgs& a, cudaStream_t st) {
     k_lap_bwd<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ __global__ void k_schedule(SchedArgs a) {
 
 cudaError_t schedule_step(const SchedArgs& a, cudaStream_t st) {
     k_schedule<<<1, 1, 0, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -50,10 +51,12 @@ __global__ void k_finish_call(JobState* s, float* out) {
 }
 cudaError_t finish_call_loss(JobState* js, float* out, cudaStream_t st) {
     k_finish_call<<<1, 1, 0, st>>>(js, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t advance_step(JobState* js, cudaStream_t st) {
     k_advance<<<1, 1, 0, st>>>(js);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -79,6 +82,7 @@ __global__ void k_adam_flat(float* __restrict__ p, float* __restrict__ g, float*
 cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const JobState* js, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_adam_flat<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, g, m, v, n, js);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -126,6 +130,7 @@ __global__ void k_adam_tex(TexDev t, float4* __restrict__ m, float4* __restrict_
 cudaError_t adam_texture(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js, cudaStream_t st) {
     int n = t.w0 * t.h0;
     k_adam_tex<<<(n + 255) / 256, 256, 0, st>>>(t, m, v, clamp_kind, js);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e) return e;
     if (t.levels > 1) {
@@ -153,6 +158,7 @@ cudaError_t mip_build(const TexDev& t, cudaStream_t st) {
         int wd = max(t.w0 >> k, 1), hd = max(t.h0 >> k, 1);
         k_mip_level<<<(wd * hd + 255) / 256, 256, 0, st>>>(const_cast<float4*>(t.tex), t.off[k - 1], ws, hs, t.off[k],
                                                           wd, hd);
+        count_launches(1);
     }
     return cudaGetLastError();
 }

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, 
 }
 
 // ---------------------------------------------------------------- host launcher
-cudaError_t raster_views(const RasterIn& in, RasterScratch& s, cudaStream_t st) {
+cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st) {
     int B = in.B, V = in.V, F = in.F, W = in.W, H = in.H;
     int tiles_x = (W + ADMS_TILE - 1) / ADMS_TILE, tiles_y = (H + ADMS_TILE - 1) / ADMS_TILE;
     int ntiles = B * tiles_x * tiles_y;
@@ -241,10 +241,23 @@ cudaError_t raster_views(const RasterIn& in, RasterScratch& s, cudaStream_t st) 
     k_scan<<<1, 1024, 0, st>>>(s.tile_count, ntiles, s.tile_off, s.total_pairs);
     k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.rec, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
                                                    s.list, s.list_capacity);
-    dim3 grid(tiles_x * tiles_y, B);
-    k_raster<<<grid, 256, 0, st>>>(s.rec, F, W, H, tiles_x, tiles_y, s.tile_off, s.tile_count, s.list,
-                                   s.list_capacity, in.keys, s.overflow_ctr);
+    count_launches(4);
     return cudaGetLastError();
+}
+
+cudaError_t raster_tiles(const RasterIn& in, RasterScratch& s, cudaStream_t st) {
+    int tiles_x = (in.W + ADMS_TILE - 1) / ADMS_TILE, tiles_y = (in.H + ADMS_TILE - 1) / ADMS_TILE;
+    dim3 grid(tiles_x * tiles_y, in.B);
+    k_raster<<<grid, 256, 0, st>>>(s.rec, in.F, in.W, in.H, tiles_x, tiles_y, s.tile_off, s.tile_count, s.list,
+                                   s.list_capacity, in.keys, s.overflow_ctr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t raster_views(const RasterIn& in, RasterScratch& s, cudaStream_t st) {
+    cudaError_t e = raster_prepare(in, s, st);
+    if (e) return e;
+    return raster_tiles(in, s, st);
 }
 
 }  // namespace adms

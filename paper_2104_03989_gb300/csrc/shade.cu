@@ -609,14 +609,17 @@ static dim3 pix_grid(const ShadeArgs& a) {
 
 cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
     k_shade_fwd<<<pix_grid(a), 256, 0, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st) {
     k_aa_loss<<<pix_grid(a), 256, 0, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st) {
     k_shade_bwd<<<pix_grid(a), 256, 0, st>>>(a);
+    count_launches(1);
     return cudaGetLastError();
 }
 
