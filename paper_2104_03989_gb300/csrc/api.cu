@@ -248,6 +248,7 @@ adms_status ensure_scratch(adms_ctx* ctx, Job& j, int B, int H, int W) {
         AL(j.rs.scr, (size_t)B * j.V);
         AL(j.rs.vs, (size_t)B * j.V);
         AL(j.rs.rec, (size_t)B * j.F);
+        AL(j.rs.bin, (size_t)B * j.F);
         AL(j.rs.asign, (size_t)B * j.F);
         j.view_cap = B;
     }

@@ -29,6 +29,15 @@ struct TriRec {
     short bx0, bx1, by0, by1;
 };
 
+// pixel bounding box of a binned triangle of one view; empty (bx0 > bx1) for
+// triangles rasterized by the small-triangle pass or not drawn at all
+struct TriBin {
+    short bx0, bx1, by0, by1;
+};
+
+// triangles with at most this many samples in their pixel bbox skip binning
+#define ADMS_SMALL_PX 16
+
 struct RasterIn {
     const float* pos;          // [V][3] render positions
     const int* tri;            // [F][3]
@@ -42,7 +51,8 @@ struct RasterScratch {
     float4* clip;       // [B][V]
     float4* scr;        // [B][V] screen position as (x_hi, x_lo, y_hi, y_lo) float pairs
     VtxS* vs;           // [B][V]
-    TriRec* rec;        // [B][F]
+    TriRec* rec;        // [B][F] (written for binned triangles only)
+    TriBin* bin;        // [B][F]
     int8_t* asign;      // [B][F]
     int* tile_count;    // [B * tiles]
     int* tile_off;      // [B * tiles]

@@ -65,65 +65,6 @@ __global__ void k_transform(const float* __restrict__ pos, int V, const adms_vie
     vs[i] = o;
 }
 
-// ---------------------------------------------------------------- setup + tile counts
-__global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restrict__ vs, int V, int B, int W, int H,
-                        int tiles_x, int tiles_y, TriRec* __restrict__ rec, int8_t* __restrict__ asign,
-                        int* __restrict__ tile_count) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B * F) return;
-    int b = i / F, f = i - b * F;
-    int i0 = tri[3 * f], i1 = tri[3 * f + 1], i2 = tri[3 * f + 2];
-    const VtxS* vb = vs + (size_t)b * V;
-    VtxS a0 = vb[i0], a1 = vb[i1], a2 = vb[i2];
-    TriRec r;
-    r.valid = 0;
-    asign[i] = 0;
-    if (a0.ok && a1.ok && a2.ok) {
-        long long X0 = a0.X, Y0 = a0.Y, X1 = a1.X, Y1 = a1.Y, X2 = a2.X, Y2 = a2.Y;
-        long long A = (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0);
-        if (A != 0) {
-            int sg = A > 0 ? 1 : -1;
-            asign[i] = (int8_t)sg;
-            long long minX = min(X0, min(X1, X2)), maxX = max(X0, max(X1, X2));
-            long long minY = min(Y0, min(Y1, Y2)), maxY = max(Y0, max(Y1, Y2));
-            long long ilo = max(ceil_div_ll(minX - 128, 256), 0ll), ihi = min(floor_div_ll(maxX - 128, 256), (long long)W - 1);
-            long long jlo = max(ceil_div_ll(minY - 128, 256), 0ll), jhi = min(floor_div_ll(maxY - 128, 256), (long long)H - 1);
-            if (ilo <= ihi && jlo <= jhi) {
-                // original-order edges: e0 = 1->2, e1 = 2->0, e2 = 0->1
-                long long px[3] = {X0, X1, X2}, py[3] = {Y0, Y1, Y2};
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    int a = (k + 1) % 3, c = (k + 2) % 3;
-                    long long dx = px[c] - px[a], dy = py[c] - py[a];
-                    // oriented value s E = a Sx + b Sy + cst with s = sign(A)
-                    r.ea[k] = (int)(-sg * dy);
-                    r.eb[k] = (int)(sg * dx);
-                    r.ec[k] = sg * (dy * px[a] - dx * py[a]);
-                    long long odx = sg * dx, ody = sg * dy;
-                    r.thr[k] = ((ody < 0) || (ody == 0 && odx > 0)) ? 0 : 1;
-                }
-                r.fA = __ll2float_rn(A);
-                r.sg = sg;
-                r.z0 = a0.z;
-                r.dz1 = __fsub_rn(a1.z, a0.z);
-                r.dz2 = __fsub_rn(a2.z, a0.z);
-                r.id = f;
-                r.valid = 1;
-                r.bx0 = (short)ilo;
-                r.bx1 = (short)ihi;
-                r.by0 = (short)jlo;
-                r.by1 = (short)jhi;
-                int tx0 = (int)ilo / ADMS_TILE, tx1 = (int)ihi / ADMS_TILE;
-                int ty0 = (int)jlo / ADMS_TILE, ty1 = (int)jhi / ADMS_TILE;
-                int* tc = tile_count + (size_t)b * tiles_x * tiles_y;
-                for (int ty = ty0; ty <= ty1; ++ty)
-                    for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tc + ty * tiles_x + tx, 1);
-            }
-        }
-    }
-    rec[i] = r;
-}
-
 // ---------------------------------------------------------------- exclusive scan (one block)
 __global__ void k_scan(const int* __restrict__ in, int n, int* __restrict__ out, long long* __restrict__ total) {
     __shared__ long long part[1024];
@@ -148,26 +89,8 @@ __global__ void k_scan(const int* __restrict__ in, int n, int* __restrict__ out,
     if (tid == nt - 1) *total = part[tid];
 }
 
-// ---------------------------------------------------------------- tile lists
-__global__ void k_bin_fill(const TriRec* __restrict__ rec, int F, int B, int tiles_x, int tiles_y,
-                           const int* __restrict__ tile_off, int* __restrict__ tile_cursor, int* __restrict__ list,
-                           long long capacity) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B * F) return;
-    const TriRec& r = rec[i];
-    if (!r.valid) return;
-    int b = i / F;
-    size_t tbase = (size_t)b * tiles_x * tiles_y;
-    int tx0 = r.bx0 / ADMS_TILE, tx1 = r.bx1 / ADMS_TILE, ty0 = r.by0 / ADMS_TILE, ty1 = r.by1 / ADMS_TILE;
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            size_t t = tbase + ty * tiles_x + tx;
-            long long p = (long long)tile_off[t] + atomicAdd(tile_cursor + t, 1);
-            if (p < capacity) list[p] = r.id;
-        }
-}
-
-// coverage + depth key of one triangle at one sample
+// ---------------------------------------------------------------- coverage test
+// coverage + depth key of one triangle at one sample (keeps the minimum in best)
 __device__ __forceinline__ void test_tri(const TriRec& r, int Sx, int Sy, unsigned long long& best) {
     long long e0 = (long long)r.ea[0] * Sx + (long long)r.eb[0] * Sy + r.ec[0];
     long long e1 = (long long)r.ea[1] * Sx + (long long)r.eb[1] * Sy + r.ec[1];
@@ -185,13 +108,119 @@ __device__ __forceinline__ void test_tri(const TriRec& r, int Sx, int Sy, unsign
     if (key < best) best = key;
 }
 
+// ---------------------------------------------------------------- setup, small triangles, tile counts
+// One thread per (view, triangle). Triangles whose pixel bounding box holds at
+// most ADMS_SMALL_PX samples are rasterized here directly, one 64-bit
+// atomicMin per covered sample (the minimum does not depend on the order);
+// larger ones get a setup record and are counted into the tiles they overlap.
+__global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restrict__ vs, int V, int B, int W, int H,
+                        int tiles_x, int tiles_y, TriRec* __restrict__ rec, TriBin* __restrict__ bin,
+                        int8_t* __restrict__ asign, int* __restrict__ tile_count, unsigned long long* __restrict__ keys) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * F) return;
+    int b = i / F, f = i - b * F;
+    int i0 = tri[3 * f], i1 = tri[3 * f + 1], i2 = tri[3 * f + 2];
+    const VtxS* vb = vs + (size_t)b * V;
+    VtxS a0 = vb[i0], a1 = vb[i1], a2 = vb[i2];
+    TriBin tb;
+    tb.bx0 = 1;
+    tb.bx1 = 0;
+    tb.by0 = 1;
+    tb.by1 = 0;
+    int8_t sgn = 0;
+    if (a0.ok && a1.ok && a2.ok) {
+        long long X0 = a0.X, Y0 = a0.Y, X1 = a1.X, Y1 = a1.Y, X2 = a2.X, Y2 = a2.Y;
+        long long A = (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0);
+        if (A != 0) {
+            int sg = A > 0 ? 1 : -1;
+            sgn = (int8_t)sg;
+            long long minX = min(X0, min(X1, X2)), maxX = max(X0, max(X1, X2));
+            long long minY = min(Y0, min(Y1, Y2)), maxY = max(Y0, max(Y1, Y2));
+            long long ilo = max(ceil_div_ll(minX - 128, 256), 0ll), ihi = min(floor_div_ll(maxX - 128, 256), (long long)W - 1);
+            long long jlo = max(ceil_div_ll(minY - 128, 256), 0ll), jhi = min(floor_div_ll(maxY - 128, 256), (long long)H - 1);
+            if (ilo <= ihi && jlo <= jhi) {
+                TriRec r;
+                // original-order edges: e0 = 1->2, e1 = 2->0, e2 = 0->1
+                long long px[3] = {X0, X1, X2}, py[3] = {Y0, Y1, Y2};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    int a = (k + 1) % 3, c = (k + 2) % 3;
+                    long long dx = px[c] - px[a], dy = py[c] - py[a];
+                    // oriented value s E = a Sx + b Sy + cst with s = sign(A)
+                    r.ea[k] = (int)(-sg * dy);
+                    r.eb[k] = (int)(sg * dx);
+                    r.ec[k] = sg * (dy * px[a] - dx * py[a]);
+                    long long odx = sg * dx, ody = sg * dy;
+                    r.thr[k] = ((ody < 0) || (ody == 0 && odx > 0)) ? 0 : 1;
+                }
+                r.fA = __ll2float_rn(A);
+                r.sg = sg;
+                r.z0 = a0.z;
+                r.dz1 = __fsub_rn(a1.z, a0.z);
+                r.dz2 = __fsub_rn(a2.z, a0.z);
+                r.id = f;
+                r.valid = 1;
+                r.bx0 = (short)ilo;
+                r.bx1 = (short)ihi;
+                r.by0 = (short)jlo;
+                r.by1 = (short)jhi;
+                long long npx = (ihi - ilo + 1) * (jhi - jlo + 1);
+                if (npx <= ADMS_SMALL_PX) {
+                    unsigned long long* kb = keys + (size_t)b * H * W;
+                    for (int y = (int)jlo; y <= (int)jhi; ++y)
+                        for (int x = (int)ilo; x <= (int)ihi; ++x) {
+                            unsigned long long best = ADMS_EMPTY_KEY;
+                            test_tri(r, 256 * x + 128, 256 * y + 128, best);
+                            if (best != ADMS_EMPTY_KEY) atomicMin(kb + (size_t)y * W + x, best);
+                        }
+                } else {
+                    rec[i] = r;
+                    tb.bx0 = r.bx0;
+                    tb.bx1 = r.bx1;
+                    tb.by0 = r.by0;
+                    tb.by1 = r.by1;
+                    int tx0 = (int)ilo / ADMS_TILE, tx1 = (int)ihi / ADMS_TILE;
+                    int ty0 = (int)jlo / ADMS_TILE, ty1 = (int)jhi / ADMS_TILE;
+                    int* tc = tile_count + (size_t)b * tiles_x * tiles_y;
+                    for (int ty = ty0; ty <= ty1; ++ty)
+                        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tc + ty * tiles_x + tx, 1);
+                }
+            }
+        }
+    }
+    asign[i] = sgn;
+    bin[i] = tb;
+}
+
+// ---------------------------------------------------------------- tile lists
+__global__ void k_bin_fill(const TriBin* __restrict__ bin, int F, int B, int tiles_x, int tiles_y,
+                           const int* __restrict__ tile_off, int* __restrict__ tile_cursor, int* __restrict__ list,
+                           long long capacity) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * F) return;
+    TriBin tb = bin[i];
+    if (tb.bx0 > tb.bx1) return;
+    int b = i / F, f = i - b * F;
+    size_t tbase = (size_t)b * tiles_x * tiles_y;
+    int tx0 = tb.bx0 / ADMS_TILE, tx1 = tb.bx1 / ADMS_TILE, ty0 = tb.by0 / ADMS_TILE, ty1 = tb.by1 / ADMS_TILE;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            size_t t = tbase + ty * tiles_x + tx;
+            long long p = (long long)tile_off[t] + atomicAdd(tile_cursor + t, 1);
+            if (p < capacity) list[p] = f;
+        }
+}
+
 // ---------------------------------------------------------------- tiled raster
 // One block per (view, 16x16 tile), one pixel per thread; the tile's triangle
-// records are staged through shared memory in chunks of 256.
-__global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, int F, int W, int H, int tiles_x,
-                                                int tiles_y, const int* __restrict__ tile_off,
-                                                const int* __restrict__ tile_count, const int* __restrict__ list,
-                                                long long capacity, unsigned long long* __restrict__ keys,
+// records are staged through shared memory in chunks of 256. Each pixel starts
+// from the key left by the small-triangle pass. A tile whose list did not fit
+// the list buffer scans every binned triangle of its view instead.
+__global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, const TriBin* __restrict__ bin, int F,
+                                                int W, int H, int tiles_x, int tiles_y,
+                                                const int* __restrict__ tile_off, const int* __restrict__ tile_count,
+                                                const int* __restrict__ list, long long capacity,
+                                                unsigned long long* __restrict__ keys,
                                                 unsigned long long* __restrict__ overflow_ctr) {
     __shared__ TriRec sm[256];
     int tile = blockIdx.x;
@@ -200,11 +229,14 @@ __global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, 
     int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
     int px = tx * ADMS_TILE + lx, py = ty * ADMS_TILE + ly;
     int Sx = 256 * px + 128, Sy = 256 * py + 128;
-    unsigned long long best = ADMS_EMPTY_KEY;
+    bool inside = px < W && py < H;
+    size_t pix = ((size_t)b * H + py) * W + px;
+    unsigned long long best = inside ? keys[pix] : ADMS_EMPTY_KEY;
     size_t t = (size_t)b * tiles_x * tiles_y + tile;
     long long off = tile_off[t];
     int cnt = tile_count[t];
     const TriRec* rb = rec + (size_t)b * F;
+    const TriBin* bb = bin + (size_t)b * F;
     bool overflow = off + cnt > capacity;
     int n = overflow ? F : cnt;
     if (overflow && threadIdx.x == 0) atomicAdd(overflow_ctr, 1ull);
@@ -212,8 +244,14 @@ __global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, 
         int m = min(256, n - c0);
         __syncthreads();
         if ((int)threadIdx.x < m) {
-            int id = overflow ? c0 + threadIdx.x : list[off + c0 + threadIdx.x];
-            sm[threadIdx.x] = rb[id];
+            if (overflow) {
+                int id = c0 + threadIdx.x;
+                TriBin tb = bb[id];
+                if (tb.bx0 <= tb.bx1) sm[threadIdx.x] = rb[id];
+                else sm[threadIdx.x].valid = 0;
+            } else {
+                sm[threadIdx.x] = rb[list[off + c0 + threadIdx.x]];
+            }
         }
         __syncthreads();
         for (int k = 0; k < m; ++k) {
@@ -223,23 +261,24 @@ __global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, 
             test_tri(r, Sx, Sy, best);
         }
     }
-    if (px < W && py < H) keys[((size_t)b * H + py) * W + px] = best;
+    if (inside) keys[pix] = best;
 }
 
-// ---------------------------------------------------------------- host launcher
+// ---------------------------------------------------------------- host launchers
 cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st) {
     int B = in.B, V = in.V, F = in.F, W = in.W, H = in.H;
     int tiles_x = (W + ADMS_TILE - 1) / ADMS_TILE, tiles_y = (H + ADMS_TILE - 1) / ADMS_TILE;
     int ntiles = B * tiles_x * tiles_y;
     cudaError_t e;
+    if ((e = cudaMemsetAsync(in.keys, 0xFF, sizeof(unsigned long long) * B * H * W, st))) return e;
     if ((e = cudaMemsetAsync(s.tile_count, 0, sizeof(int) * ntiles, st))) return e;
     if ((e = cudaMemsetAsync(s.tile_cursor, 0, sizeof(int) * ntiles, st))) return e;
     int bs = 256;
     k_transform<<<(B * V + bs - 1) / bs, bs, 0, st>>>(in.pos, V, in.views, B, W, H, s.clip, s.vs, s.scr);
-    k_setup<<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec, s.asign,
-                                                s.tile_count);
+    k_setup<<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec, s.bin,
+                                                s.asign, s.tile_count, in.keys);
     k_scan<<<1, 1024, 0, st>>>(s.tile_count, ntiles, s.tile_off, s.total_pairs);
-    k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.rec, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
+    k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.bin, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
                                                    s.list, s.list_capacity);
     count_launches(4);
     return cudaGetLastError();
@@ -248,7 +287,7 @@ cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st
 cudaError_t raster_tiles(const RasterIn& in, RasterScratch& s, cudaStream_t st) {
     int tiles_x = (in.W + ADMS_TILE - 1) / ADMS_TILE, tiles_y = (in.H + ADMS_TILE - 1) / ADMS_TILE;
     dim3 grid(tiles_x * tiles_y, in.B);
-    k_raster<<<grid, 256, 0, st>>>(s.rec, in.F, in.W, in.H, tiles_x, tiles_y, s.tile_off, s.tile_count, s.list,
+    k_raster<<<grid, 256, 0, st>>>(s.rec, s.bin, in.F, in.W, in.H, tiles_x, tiles_y, s.tile_off, s.tile_count, s.list,
                                    s.list_capacity, in.keys, s.overflow_ctr);
     count_launches(1);
     return cudaGetLastError();
