@@ -684,8 +684,7 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
         for (int m = 0; m < 3; ++m) {
             if (!maps[m]->opt) continue;
-            CK(TIMED(ST_ADAM, adam_texture(maps[m]->dev(), maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
-            CK(TIMED(ST_MIP, mip_build(maps[m]->dev(), ctx->stream)));
+            CK(TIMED(ST_ADAM, adam_texture_and_mips(maps[m]->dev(), maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
         }
         CK(TIMED(ST_SMALL, advance_step(j.st, ctx->stream)));
         j.frame_valid = false;

@@ -163,6 +163,9 @@ cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const
 cudaError_t adam_texture(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js, cudaStream_t st);
 // rebuild levels 1.. of a mip chain from level 0 (2x2 box average)
 cudaError_t mip_build(const TexDev& t, cudaStream_t st);
+// Adam on a texture fused with the rebuild of its mip chain (tiles of 32x32 texels)
+cudaError_t adam_texture_and_mips(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js,
+                                  cudaStream_t st);
 cudaError_t advance_step(JobState* js, cudaStream_t st);
 // out[j] = call_loss; img_loss += call_loss
 cudaError_t finish_call_loss(JobState* js, float* out, cudaStream_t st);

@@ -127,6 +127,119 @@ __global__ void k_adam_tex(TexDev t, float4* __restrict__ m, float4* __restrict_
     t.grad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+__device__ __forceinline__ float4 adam_texel(const TexDev& t, float4* __restrict__ m, float4* __restrict__ v, int i,
+                                             int x, int y, int clamp_kind, float lr, float bc1, float bc2) {
+    float4 g = t.grad[i];
+    float wgt = 1.f;
+    for (int k = 1; k < t.levels; ++k) {
+        int wp = max(t.w0 >> (k - 1), 1), hp = max(t.h0 >> (k - 1), 1);
+        wgt *= 1.f / (float)((wp > 1 ? 2 : 1) * (hp > 1 ? 2 : 1));
+        int wk = max(t.w0 >> k, 1);
+        g = f4madd(g, wgt, t.grad[t.off[k] + (y >> k) * wk + (x >> k)]);
+    }
+    float4 p = t.tex[i], mm = m[i], vv = v[i];
+    p.x = adam1(p.x, g.x, mm.x, vv.x, lr, bc1, bc2);
+    p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
+    p.z = adam1(p.z, g.z, mm.z, vv.z, lr, bc1, bc2);
+    p.w = adam1(p.w, g.w, mm.w, vv.w, lr, bc1, bc2);
+    if (clamp_kind == 0) {
+        p = make_float4(clampf(p.x, 0.f, 1.f), clampf(p.y, 0.f, 1.f), clampf(p.z, 0.f, 1.f), clampf(p.w, 0.f, 1.f));
+    } else if (clamp_kind == 1) {
+        p.x = clampf(p.x, 0.f, 1.f);
+        p.y = clampf(p.y, ADMS_ROUGH_MIN, 1.f);
+        p.z = clampf(p.z, 0.f, 1.f);
+    } else if (clamp_kind == 2) {
+        p.x = clampf(p.x, -1.f, 1.f);
+        p.y = clampf(p.y, -1.f, 1.f);
+        p.z = clampf(p.z, 0.f, 1.f);
+    }
+    const_cast<float4*>(t.tex)[i] = p;
+    m[i] = mm;
+    v[i] = vv;
+    t.grad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return p;
+}
+
+// Adam on one 32x32 texel tile of level 0, then levels 1..5 of that tile built
+// in shared memory from the updated texels (2x2 box average, same order of
+// summation as k_mip_level), so level 0 is read once for both.
+__global__ void __launch_bounds__(256) k_adam_tex_tile(TexDev t, float4* __restrict__ m, float4* __restrict__ v,
+                                                       int clamp_kind, const JobState* __restrict__ js) {
+    __shared__ float4 tile[32][32];
+    int tiles_x = t.w0 >> 5;
+    int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
+    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    float lr = js->lr, bc1 = js->bc1, bc2 = js->bc2;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int x = (bx << 5) + tx, y = (by << 5) + ty + 8 * r;
+        tile[ty + 8 * r][tx] = adam_texel(t, m, v, y * t.w0 + x, x, y, clamp_kind, lr, bc1, bc2);
+    }
+    int top = min(5, t.levels - 1);
+    for (int k = 1; k <= top; ++k) {
+        int n = 32 >> k;
+        __syncthreads();
+        float4 acc;
+        int cx = 0, cy = 0;
+        bool act = (int)threadIdx.x < n * n;
+        if (act) {
+            cx = threadIdx.x % n;
+            cy = threadIdx.x / n;
+            acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) acc = f4madd(acc, 1.f, tile[2 * cy + dy][2 * cx + dx]);
+            acc = f4scale(acc, 0.25f);
+        }
+        __syncthreads();
+        if (act) {
+            tile[cy][cx] = acc;
+            int wk = t.w0 >> k;
+            const_cast<float4*>(t.tex)[t.off[k] + (by * n + cy) * wk + bx * n + cx] = acc;
+        }
+    }
+}
+
+// levels 6.. of a chain from level 5, in one block (global memory, level by level)
+__global__ void __launch_bounds__(1024) k_mip_coarse(TexDev t, int first) {
+    float4* tex = const_cast<float4*>(t.tex);
+    for (int k = first; k < t.levels; ++k) {
+        int ws = max(t.w0 >> (k - 1), 1), hs = max(t.h0 >> (k - 1), 1);
+        int wd = max(t.w0 >> k, 1), hd = max(t.h0 >> k, 1);
+        int sx = ws > 1 ? 2 : 1, sy = hs > 1 ? 2 : 1;
+        for (int i = threadIdx.x; i < wd * hd; i += blockDim.x) {
+            int x = i % wd, y = i / wd;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int dy = 0; dy < sy; ++dy)
+                for (int dx = 0; dx < sx; ++dx) acc = f4madd(acc, 1.f, tex[t.off[k - 1] + (y * sy + dy) * ws + (x * sx + dx)]);
+            tex[t.off[k] + i] = f4scale(acc, 1.f / (float)(sx * sy));
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t adam_texture_and_mips(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js,
+                                  cudaStream_t st) {
+    bool tiled = t.levels > 5 && (t.w0 % 32) == 0 && (t.h0 % 32) == 0;
+    if (!tiled) {
+        cudaError_t e = adam_texture(t, m, v, clamp_kind, js, st);
+        if (e) return e;
+        return mip_build(t, st);
+    }
+    k_adam_tex_tile<<<(t.w0 >> 5) * (t.h0 >> 5), 256, 0, st>>>(t, m, v, clamp_kind, js);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    if (t.levels > 6) {
+        k_mip_coarse<<<1, 1024, 0, st>>>(t, 6);
+        count_launches(1);
+    }
+    size_t coarse = 0;
+    for (int k = 1; k < t.levels; ++k) coarse += (size_t)max(t.w0 >> k, 1) * max(t.h0 >> k, 1);
+    e = cudaMemsetAsync(t.grad + t.off[1], 0, coarse * sizeof(float4), st);
+    if (e) return e;
+    return cudaGetLastError();
+}
+
 cudaError_t adam_texture(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js, cudaStream_t st) {
     int n = t.w0 * t.h0;
     k_adam_tex<<<(n + 255) / 256, 256, 0, st>>>(t, m, v, clamp_kind, js);

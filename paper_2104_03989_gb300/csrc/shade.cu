@@ -474,7 +474,9 @@ __device__ __forceinline__ void atomic_add3(double* p, float3 v) {
     atomicAdd(p + 2, (double)v.z);
 }
 
-__global__ void __launch_bounds__(256) k_shade_bwd(ShadeArgs A) {
+// two blocks per SM: 128 registers per thread (a few bytes of spills) doubles
+// the resident warps that hide the gather latency of this kernel
+__global__ void __launch_bounds__(256, 2) k_shade_bwd(ShadeArgs A) {
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
     int b = blockIdx.y;
     int px = (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15);
