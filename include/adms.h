@@ -203,6 +203,24 @@ adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t*
 adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
                             const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out);
 
+/* ---- CUDA graphs ----------------------------------------------------------- */
+
+typedef struct adms_graph adms_graph;
+
+/* Record, rather than run, the adms calls made on this context's stream until
+ * adms_graph_end (CUDA stream capture, thread-local mode), so a whole step
+ * (render_reference, forward_loss, backward, optimizer_step) replays as one
+ * graph launch. The stream must not be the legacy default stream. Recorded
+ * calls must not need new scratch (ADMS_ERR_STATE): make the same calls once
+ * before capturing. Pointers passed while capturing are baked into the graph:
+ * views and reference images must live at fixed device addresses whose
+ * contents the caller refreshes between launches. */
+adms_status adms_graph_begin(adms_ctx* ctx);
+adms_status adms_graph_end(adms_ctx* ctx, adms_graph** out);
+/* Enqueue one replay of a recorded graph on the context's stream. */
+adms_status adms_graph_launch(adms_ctx* ctx, adms_graph* graph);
+adms_status adms_graph_destroy(adms_graph* graph);
+
 /* ---- tracing ------------------------------------------------------------- */
 
 /* Bracket every stage launched through this context with CUDA events on its

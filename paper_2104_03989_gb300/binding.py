@@ -92,6 +92,10 @@ SIGNATURES = {
     "adms_job_export": ([P, C.c_int32, P, C.POINTER(C.c_size_t)], C.c_int),
     "adms_job_import": ([P, C.POINTER(adms_mesh_desc), C.POINTER(adms_material_desc), C.POINTER(adms_opt_params),
                          P, C.c_size_t, C.POINTER(C.c_int32)], C.c_int),
+    "adms_graph_begin": ([P], C.c_int),
+    "adms_graph_end": ([P, C.POINTER(P)], C.c_int),
+    "adms_graph_launch": ([P, P], C.c_int),
+    "adms_graph_destroy": ([P], C.c_int),
     "adms_ctx_profile": ([P, C.c_int32], C.c_int),
     "adms_ctx_stage_times": ([P, P, P, C.c_int32], C.c_int),
     "adms_stage_count": ([], C.c_int32),
@@ -249,6 +253,24 @@ def adms_job_import(ctx, mesh, mat, opt, buf):
     _check(ctx, lib().adms_job_import(ctx, C.byref(mesh), C.byref(mat), C.byref(opt) if opt is not None else None,
                                       ptr(buf), buf.nbytes, C.byref(out)))
     return out.value
+
+
+def adms_graph_begin(ctx):
+    _check(ctx, lib().adms_graph_begin(ctx))
+
+
+def adms_graph_end(ctx):
+    g = P()
+    _check(ctx, lib().adms_graph_end(ctx, C.byref(g)))
+    return g
+
+
+def adms_graph_launch(ctx, graph):
+    _check(ctx, lib().adms_graph_launch(ctx, graph))
+
+
+def adms_graph_destroy(graph):
+    _check(None, lib().adms_graph_destroy(graph))
 
 
 def adms_ctx_profile(ctx, enable=True):

@@ -105,12 +105,18 @@ struct StageRec {
     cudaEvent_t a, b;
 };
 
+struct adms_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 struct adms_ctx {
     cudaStream_t stream = 0;
     size_t budget = 0;
     size_t in_use = 0;
     std::string err;
     std::vector<Job> jobs;
+    bool capturing = false;
     // optional per-stage timing with CUDA events on the context's stream
     bool profile = false;
     std::vector<cudaEvent_t> pool;
@@ -162,6 +168,8 @@ template <typename T>
 adms_status job_alloc(adms_ctx* ctx, Job& j, T** out, size_t count) {
     size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
     bytes = (bytes + 255) & ~size_t(255);
+    if (ctx->capturing)
+        return fail(ctx, ADMS_ERR_STATE, "a call inside graph capture needs new scratch: run it once before capturing");
     if (ctx->budget && ctx->in_use + bytes > ctx->budget)
         return fail(ctx, ADMS_ERR_BUDGET, "HBM budget exceeded (" + std::to_string(ctx->in_use + bytes) + " > " +
                                               std::to_string(ctx->budget) + " bytes)");
@@ -250,6 +258,7 @@ adms_status ensure_scratch(adms_ctx* ctx, Job& j, int B, int H, int W) {
         AL(j.rs.rec, (size_t)B * j.F);
         AL(j.rs.bin, (size_t)B * j.F);
         AL(j.rs.asign, (size_t)B * j.F);
+        AL(j.rs.silmask, (size_t)B * j.F);
         j.view_cap = B;
     }
     if (ntiles > j.tile_cap) {
@@ -312,6 +321,7 @@ ShadeArgs shade_args(Job& j) {
     a.tri_uv = j.tri_uv;
     a.adj = j.adj;
     a.asign = j.rs.asign;
+    a.silmask = j.rs.silmask;
     a.keys = j.keys;
     a.kd = j.kd.dev();
     a.orm = j.orm.dev();
@@ -336,6 +346,7 @@ adms_status render_core(adms_ctx* ctx, Job& j) {
     RasterIn in;
     in.pos = j.pos;
     in.tri = j.tri;
+    in.adj = j.adj;
     in.views = j.views;
     in.B = j.B;
     in.V = j.V;
@@ -710,6 +721,44 @@ adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t*
 adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
                             const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out) {
     return fail(ctx, ADMS_ERR_STATE, "import not implemented in this build");
+}
+
+adms_status adms_graph_begin(adms_ctx* ctx) {
+    if (!ctx || ctx->capturing) return fail(ctx, ADMS_ERR_STATE, "already capturing");
+    if (!ctx->stream) return fail(ctx, ADMS_ERR_STATE, "graph capture needs a non-default stream");
+    if (ctx->profile) return fail(ctx, ADMS_ERR_STATE, "disable stage profiling before capturing");
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    return ADMS_OK;
+}
+
+adms_status adms_graph_end(adms_ctx* ctx, adms_graph** out) {
+    if (!ctx || !out || !ctx->capturing) return fail(ctx, ADMS_ERR_STATE, "not capturing");
+    ctx->capturing = false;
+    adms_graph* g = new adms_graph();
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g->graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return fail(ctx, ADMS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    *out = g;
+    return ADMS_OK;
+}
+
+adms_status adms_graph_launch(adms_ctx* ctx, adms_graph* g) {
+    if (!ctx || !g) return fail(ctx, ADMS_ERR_ARG, "null graph");
+    CK(cudaGraphLaunch(g->exec, ctx->stream));
+    return ADMS_OK;
+}
+
+adms_status adms_graph_destroy(adms_graph* g) {
+    if (!g) return ADMS_ERR_ARG;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return ADMS_OK;
 }
 
 adms_status adms_ctx_profile(adms_ctx* ctx, int32_t enable) {

@@ -41,6 +41,7 @@ struct TriBin {
 struct RasterIn {
     const float* pos;          // [V][3] render positions
     const int* tri;            // [F][3]
+    const int* adj;            // [F][3] face across edge k, or -1
     const adms_view* views;    // device, [B]
     int B, V, F, W, H;
     unsigned long long* keys;  // [B][H][W]
@@ -54,6 +55,7 @@ struct RasterScratch {
     TriRec* rec;        // [B][F] (written for binned triangles only)
     TriBin* bin;        // [B][F]
     int8_t* asign;      // [B][F]
+    uint8_t* silmask;   // [B][F] bit e: edge e is a silhouette edge in that view
     int* tile_count;    // [B * tiles]
     int* tile_off;      // [B * tiles]
     int* tile_cursor;   // [B * tiles]
@@ -83,6 +85,7 @@ struct ShadeArgs {
     const int* tri_uv;               // [F][3]
     const int* adj;                  // [F][3] face across edge (tri[f][k], tri[f][k+1]) or -1
     const int8_t* asign;             // [B][F]
+    const uint8_t* silmask;          // [B][F]
     const unsigned long long* keys;  // [B][H][W]
     TexDev kd, orm, nrm;
     float4* pre;                     // [B][H][W] pre-AA colour

@@ -127,16 +127,20 @@ __global__ void k_adam_tex(TexDev t, float4* __restrict__ m, float4* __restrict_
     t.grad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__device__ __forceinline__ float4 adam_texel(const TexDev& t, float4* __restrict__ m, float4* __restrict__ v, int i,
-                                             int x, int y, int clamp_kind, float lr, float bc1, float bc2) {
-    float4 g = t.grad[i];
-    float wgt = 1.f;
-    for (int k = 1; k < t.levels; ++k) {
-        int wp = max(t.w0 >> (k - 1), 1), hp = max(t.h0 >> (k - 1), 1);
-        wgt *= 1.f / (float)((wp > 1 ? 2 : 1) * (hp > 1 ? 2 : 1));
-        int wk = max(t.w0 >> k, 1);
-        g = f4madd(g, wgt, t.grad[t.off[k] + (y >> k) * wk + (x >> k)]);
+// weight of a level-k texel's gradient in each of its level-0 texels (product of
+// the 2x2 / 2x1 box-filter factors down the chain)
+__device__ __forceinline__ float level_weight(const TexDev& t, int k) {
+    float w = 1.f;
+    for (int j = 1; j <= k; ++j) {
+        int wp = max(t.w0 >> (j - 1), 1), hp = max(t.h0 >> (j - 1), 1);
+        w *= 1.f / (float)((wp > 1 ? 2 : 1) * (hp > 1 ? 2 : 1));
     }
+    return w;
+}
+
+// Adam + clamps on one level-0 texel whose gradient g already includes the mip adjoint
+__device__ __forceinline__ float4 adam_texel(const TexDev& t, float4* __restrict__ m, float4* __restrict__ v, int i,
+                                             float4 g, int clamp_kind, float lr, float bc1, float bc2) {
     float4 p = t.tex[i], mm = m[i], vv = v[i];
     p.x = adam1(p.x, g.x, mm.x, vv.x, lr, bc1, bc2);
     p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
@@ -166,14 +170,40 @@ __device__ __forceinline__ float4 adam_texel(const TexDev& t, float4* __restrict
 __global__ void __launch_bounds__(256) k_adam_tex_tile(TexDev t, float4* __restrict__ m, float4* __restrict__ v,
                                                        int clamp_kind, const JobState* __restrict__ js) {
     __shared__ float4 tile[32][32];
+    // mip adjoint pushed down the tile's pyramid: push level k (k = 1..5) holds
+    // sum_{j >= k} weight_j * grad_j at the level-k texels of this tile
+    __shared__ float4 push[256 + 64 + 16 + 4 + 1];
+    const int poff[6] = {0, 0, 256, 320, 336, 340};
     int tiles_x = t.w0 >> 5;
     int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
     int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     float lr = js->lr, bc1 = js->bc1, bc2 = js->bc2;
+    if (threadIdx.x == 0) {
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 6; k < t.levels; ++k) {
+            int wk = max(t.w0 >> k, 1);
+            c = f4madd(c, level_weight(t, k), t.grad[t.off[k] + ((by << 5) >> k) * wk + ((bx << 5) >> k)]);
+        }
+        push[poff[5]] = f4madd(c, level_weight(t, 5), t.grad[t.off[5] + by * (t.w0 >> 5) + bx]);
+    }
+    for (int k = 4; k >= 1; --k) {
+        __syncthreads();
+        int n = 32 >> k, wk = t.w0 >> k;
+        float wl = level_weight(t, k);
+        for (int idx = threadIdx.x; idx < n * n; idx += 256) {
+            int cx = idx % n, cy = idx / n;
+            float4 g = t.grad[t.off[k] + (((by << 5) >> k) + cy) * wk + ((bx << 5) >> k) + cx];
+            push[poff[k] + idx] = f4madd(push[poff[k + 1] + (cy >> 1) * (n >> 1) + (cx >> 1)], wl, g);
+        }
+    }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        int x = (bx << 5) + tx, y = (by << 5) + ty + 8 * r;
-        tile[ty + 8 * r][tx] = adam_texel(t, m, v, y * t.w0 + x, x, y, clamp_kind, lr, bc1, bc2);
+        int lx = tx, ly = ty + 8 * r;
+        int x = (bx << 5) + lx, y = (by << 5) + ly;
+        int i = y * t.w0 + x;
+        float4 g = f4madd(t.grad[i], 1.f, push[(ly >> 1) * 16 + (lx >> 1)]);
+        tile[ly][lx] = adam_texel(t, m, v, i, g, clamp_kind, lr, bc1, bc2);
     }
     int top = min(5, t.levels - 1);
     for (int k = 1; k <= top; ++k) {

@@ -192,6 +192,27 @@ __global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restri
     bin[i] = tb;
 }
 
+// ---------------------------------------------------------------- silhouette edges
+// bit e of silmask[b][f] is set when edge e of triangle f is a silhouette edge in
+// view b: no neighbour across it, or a neighbour whose snapped area has another sign
+__global__ void k_silmask(const int* __restrict__ adj, const int8_t* __restrict__ asign, int F, int B,
+                          uint8_t* __restrict__ silmask) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * F) return;
+    int b = i / F, f = i - b * F;
+    const int8_t* sg = asign + (size_t)b * F;
+    int s = sg[f];
+    uint8_t m = 0;
+    if (s != 0) {
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            int nb = adj[3 * f + e];
+            if (nb < 0 || sg[nb] != s) m |= (uint8_t)(1u << e);
+        }
+    }
+    silmask[i] = m;
+}
+
 // ---------------------------------------------------------------- tile lists
 __global__ void k_bin_fill(const TriBin* __restrict__ bin, int F, int B, int tiles_x, int tiles_y,
                            const int* __restrict__ tile_off, int* __restrict__ tile_cursor, int* __restrict__ list,
@@ -280,7 +301,8 @@ cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st
     k_scan<<<1, 1024, 0, st>>>(s.tile_count, ntiles, s.tile_off, s.total_pairs);
     k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.bin, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
                                                    s.list, s.list_capacity);
-    count_launches(4);
+    k_silmask<<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.adj, s.asign, F, B, s.silmask);
+    count_launches(5);
     return cudaGetLastError();
 }
 

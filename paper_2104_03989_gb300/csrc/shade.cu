@@ -298,13 +298,11 @@ __device__ __forceinline__ PairTau pair_tau(const ShadeArgs& A, int b, int axis,
     pt.tau = 0.5f;
     float best = 1e30f;
     float ox = (float)oi + 0.5f, oy = (float)oj + 0.5f;
-    const int8_t* sg = A.asign + (size_t)b * A.F;
-    int so = sg[fo];
+    unsigned mask = A.silmask[(size_t)b * A.F + fo];
+    if (!mask) return pt;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        int nb = A.adj[3 * fo + e];
-        bool sil = nb < 0 || sg[nb] != so;
-        if (!sil) continue;
+        if (!((mask >> e) & 1u)) continue;
         int va = A.tri[3 * fo + e], vb = A.tri[3 * fo + (e + 1) % 3];
         float2 sa = rel_screen(A.scr[(size_t)b * A.V + va], ox, oy);
         float2 sb = rel_screen(A.scr[(size_t)b * A.V + vb], ox, oy);
