@@ -203,6 +203,36 @@ adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t*
 adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
                             const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out);
 
+/* ---- visibility without allocation -------------------------------------------- */
+
+/* Visibility keys of n_views views, for callers that cannot call cudaMalloc
+ * (code inside another framework's memory pool or a fixed arena, or a frame
+ * loop where an allocation and the synchronisation it brings are not
+ * allowed). The paper has no counterpart: it is a deployment variant of the
+ * raster that adms_render_reference and adms_forward_loss run.
+ *
+ * Inputs (device): pos [n_verts][3] float32, tri [n_tris][3] int32 with every
+ * index in [0, n_verts), views [n_views] adms_view. Output (device, caller-
+ * owned): keys [n_views][H][W] with the same bits as the context path's keys.
+ * Work is enqueued on cuda_stream (NULL: legacy default stream).
+ *
+ * Allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ * Its scratch is one file-scope device array of 32 MiB that every GPU loading
+ * this library holds until the process exits. It must hold
+ *   n_views * n_verts * 48 + n_views * n_tris * 106 + n_tris * 12
+ *   + tiles * 28 bytes (tiles = n_views * ceil(W/16) * ceil(H/16)), plus
+ * 256-byte rounding per part; larger problems return ADMS_ERR_ARG. Tile lists
+ * use whatever space is left; a tile whose list does not fit scans every
+ * triangle, with the same keys. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture. Every call shares the one
+ * array, so calls that overlap on the GPU (different streams, or threads
+ * using different streams) race: serialise them. Returns ADMS_ERR_CUDA if a
+ * CUDA call fails. */
+adms_status adms_visibility_noalloc(const float* pos, int32_t n_verts, const int32_t* tri, int32_t n_tris,
+                                    const adms_view* views, int32_t n_views, int32_t H, int32_t W,
+                                    uint64_t* keys, void* cuda_stream);
+
 /* ---- CUDA graphs ----------------------------------------------------------- */
 
 typedef struct adms_graph adms_graph;

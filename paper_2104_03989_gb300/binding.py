@@ -92,6 +92,7 @@ SIGNATURES = {
     "adms_job_export": ([P, C.c_int32, P, C.POINTER(C.c_size_t)], C.c_int),
     "adms_job_import": ([P, C.POINTER(adms_mesh_desc), C.POINTER(adms_material_desc), C.POINTER(adms_opt_params),
                          P, C.c_size_t, C.POINTER(C.c_int32)], C.c_int),
+    "adms_visibility_noalloc": ([P, C.c_int32, P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
     "adms_graph_begin": ([P], C.c_int),
     "adms_graph_end": ([P, C.POINTER(P)], C.c_int),
     "adms_graph_launch": ([P, P], C.c_int),
@@ -253,6 +254,15 @@ def adms_job_import(ctx, mesh, mat, opt, buf):
     _check(ctx, lib().adms_job_import(ctx, C.byref(mesh), C.byref(mat), C.byref(opt) if opt is not None else None,
                                       ptr(buf), buf.nbytes, C.byref(out)))
     return out.value
+
+
+def adms_visibility_noalloc(pos, tri, views, n_views, H, W, keys, stream=None):
+    """Keys [n_views][H][W] into `keys` without any allocation (see include/adms.h)."""
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    status = lib().adms_visibility_noalloc(ptr(pos), int(pos.shape[0]), ptr(tri), int(tri.shape[0]), ptr(views),
+                                           int(n_views), int(H), int(W), ptr(keys), st)
+    if status != ADMS_OK:
+        raise AdmsError(status, "adms_visibility_noalloc")
 
 
 def adms_graph_begin(ctx):
