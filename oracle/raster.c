@@ -88,6 +88,94 @@ void oracle_transform(const float* mvp, const float* pos, int V, int W, int H,
     }
 }
 
+/* Displaced tessellated positions in float32 (Sec. 5.1, Eq. 3), the positions
+ * that visibility sees for tessellated meshes. Every operation is one IEEE
+ * float32 operation, rounded to nearest, in the order written:
+ *   face normal fn = e1 x e2 (e1 = p1 - p0, e2 = p2 - p0), component
+ *     x = e1.y*e2.z - e1.z*e2.y (and cyclic);
+ *   base vertex normal: sum of fn over its incident faces in increasing face
+ *     order, starting from 0; l2 = (x*x + y*y) + z*z; n = sum / sqrt(max(l2, 1e-20));
+ *   tessellated vertex with integer weights (i0, i1, i2) / n_seg on base face
+ *     (a, b, c): w_k = (float)i_k / (float)n_seg,
+ *     v = (w0*pa + w1*pb) + w2*pc, s = (w0*na + w1*nb) + w2*nc, normalised as above;
+ *   displacement d = bilinear level-0 lookup at (u, v): x = u*W - 0.5,
+ *     x0 = floor(x), fx = x - x0 (u wraps, v clamps),
+ *     d = ((1-fx)(1-fy) t00 + fx(1-fy) t10) + ((1-fx) fy t01 + fx fy t11);
+ *   out = v + d*n.
+ * vf_off/vf_face: vertex -> incident faces, faces ascending. */
+void oracle_tess_positions(const float* base_pos, const int32_t* base_tri, const int32_t* vf_off,
+                           const int32_t* vf_face, int n_base,
+                           int n_tess, const int32_t* owner_idx /* [n_tess][3] base vertex ids */,
+                           const int32_t* weights /* [n_tess][3] */, int n_seg,
+                           const float* vert_uv /* [n_tess][2] */, const float* disp, int dh, int dw,
+                           float* base_nrm /* out [n_base][3] */, float* out_pos /* out [n_tess][3] */)
+{
+    for (int v = 0; v < n_base; ++v) {
+        float s[3] = {0.0f, 0.0f, 0.0f};
+        for (int j = vf_off[v]; j < vf_off[v + 1]; ++j) {
+            const int32_t* t = base_tri + 3 * vf_face[j];
+            const float* p0 = base_pos + 3 * t[0];
+            const float* p1 = base_pos + 3 * t[1];
+            const float* p2 = base_pos + 3 * t[2];
+            float e1[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+            float e2[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]};
+            float a, b;
+            a = e1[1] * e2[2]; b = e1[2] * e2[1]; s[0] = s[0] + (a - b);
+            a = e1[2] * e2[0]; b = e1[0] * e2[2]; s[1] = s[1] + (a - b);
+            a = e1[0] * e2[1]; b = e1[1] * e2[0]; s[2] = s[2] + (a - b);
+        }
+        float l2 = s[0] * s[0];
+        l2 = l2 + s[1] * s[1];
+        l2 = l2 + s[2] * s[2];
+        float len = sqrtf(l2 > 1e-20f ? l2 : 1e-20f);
+        base_nrm[3 * v] = s[0] / len;
+        base_nrm[3 * v + 1] = s[1] / len;
+        base_nrm[3 * v + 2] = s[2] / len;
+    }
+    const float fn = (float)n_seg;
+    for (int t = 0; t < n_tess; ++t) {
+        const int32_t* o = owner_idx + 3 * t;
+        float w0 = (float)weights[3 * t] / fn, w1 = (float)weights[3 * t + 1] / fn, w2 = (float)weights[3 * t + 2] / fn;
+        float vv[3], ns[3];
+        for (int c = 0; c < 3; ++c) {
+            float x = w0 * base_pos[3 * o[0] + c];
+            float y = w1 * base_pos[3 * o[1] + c];
+            float z = w2 * base_pos[3 * o[2] + c];
+            vv[c] = (x + y) + z;
+            x = w0 * base_nrm[3 * o[0] + c];
+            y = w1 * base_nrm[3 * o[1] + c];
+            z = w2 * base_nrm[3 * o[2] + c];
+            ns[c] = (x + y) + z;
+        }
+        float l2 = ns[0] * ns[0];
+        l2 = l2 + ns[1] * ns[1];
+        l2 = l2 + ns[2] * ns[2];
+        float len = sqrtf(l2 > 1e-20f ? l2 : 1e-20f);
+        float u = vert_uv[2 * t], vc = vert_uv[2 * t + 1];
+        float x = u * (float)dw - 0.5f, y = vc * (float)dh - 0.5f;
+        float x0 = floorf(x), y0 = floorf(y);
+        float fx = x - x0, fy = y - y0;
+        int ix = (int)x0, iy = (int)y0;
+        int ixa = ix % dw;
+        if (ixa < 0) ixa += dw;
+        int ixb = ixa + 1 == dw ? 0 : ixa + 1;
+        int iya = iy < 0 ? 0 : (iy > dh - 1 ? dh - 1 : iy);
+        int iyb = iy + 1 < 0 ? 0 : (iy + 1 > dh - 1 ? dh - 1 : iy + 1);
+        float gx = 1.0f - fx, gy = 1.0f - fy;
+        float t00 = disp[iya * dw + ixa], t10 = disp[iya * dw + ixb];
+        float t01 = disp[iyb * dw + ixa], t11 = disp[iyb * dw + ixb];
+        float q0 = (gx * gy) * t00;
+        float q1 = (fx * gy) * t10;
+        float q2 = (gx * fy) * t01;
+        float q3 = (fx * fy) * t11;
+        float d = (q0 + q1) + (q2 + q3);
+        for (int c = 0; c < 3; ++c) {
+            float nc = ns[c] / len;
+            out_pos[3 * t + c] = vv[c] + d * nc;
+        }
+    }
+}
+
 static int64_t edge_fn(int64_t xa, int64_t ya, int64_t xb, int64_t yb, int64_t sx, int64_t sy)
 {
     return (xb - xa) * (sy - ya) - (yb - ya) * (sx - xa);

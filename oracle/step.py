@@ -89,7 +89,11 @@ def render(job, params, views, height, width, aa=True, vis=None, lods=None, diag
     geo = geometry(job, params)
     tex = texture_levels(job, params)
     if vis is None:
-        pos32 = geo["pos"].detach().numpy().astype(np.float32)
+        if job.tess is None:
+            pos32 = geo["pos"].detach().numpy().astype(np.float32)
+        else:   # float32 contract of the displaced positions (raster.c)
+            pos32 = job.tess.positions_f32(params["pos"].detach().numpy(), job.tri_np,
+                                           params["disp"].detach().numpy())
         vis = visibility.raster_views(views, pos32, geo["tri"].numpy(), width, height)
     keys, asign = vis
     pres, imgs = [], []

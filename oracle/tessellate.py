@@ -51,7 +51,9 @@ class Tessellation:
         owner_face = first // L
         owner_loc = first % L
         self.n_verts = first.size
+        self.n_seg = n
         self.face = owner_face
+        self.wi = w[owner_loc].astype(np.int32)                          # (Vt, 3) integer weights
         self.w = w[owner_loc].astype(np.float64) / n                     # (Vt, 3)
         self.base_idx = tri[owner_face]                                   # (Vt, 3)
         self.vert_uv = (self.w[:, :, None] * uv[tri_uv[owner_face]]).sum(axis=1)  # (Vt, 2) displacement lookup
@@ -69,6 +71,30 @@ class Tessellation:
         corner_uv = (w[None, :, :, None].astype(np.float64) / n * uv[tri_uv][:, None, :, :]).sum(axis=2)
         self.corner_uv = corner_uv.reshape(-1, 2)                         # (F L, 2)
         self.tri_uv = (np.arange(F)[:, None, None] * L + lt[None]).reshape(-1, 3)
+
+    def positions_f32(self, base_pos, base_tri, disp):
+        """The float32 displaced positions visibility uses (contract in raster.c)."""
+        from . import visibility
+
+        base_pos = np.ascontiguousarray(base_pos, dtype=np.float32)
+        base_tri = np.ascontiguousarray(base_tri, dtype=np.int32)
+        nb = base_pos.shape[0]
+        counts = np.bincount(base_tri.reshape(-1), minlength=nb)
+        vf_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+        faces = np.repeat(np.arange(base_tri.shape[0], dtype=np.int32), 3)
+        order = np.argsort(base_tri.reshape(-1), kind="stable")      # faces ascending within each vertex
+        vf_face = np.ascontiguousarray(faces[order], dtype=np.int32)
+        disp = np.ascontiguousarray(disp, dtype=np.float32)
+        out = np.zeros((self.n_verts, 3), np.float32)
+        nrm = np.zeros((nb, 3), np.float32)
+        lib = visibility._load()
+        P = visibility._ptr
+        lib.oracle_tess_positions(P(base_pos), P(base_tri), P(vf_off), P(vf_face), nb, self.n_verts,
+                                  P(np.ascontiguousarray(self.base_idx, dtype=np.int32)),
+                                  P(np.ascontiguousarray(self.wi)), self.n_seg,
+                                  P(np.ascontiguousarray(self.vert_uv, dtype=np.float32)), P(disp),
+                                  disp.shape[0], disp.shape[1], P(nrm), P(out))
+        return out
 
     def displaced_positions(self, base_pos, base_nrm, disp):
         w = torch.as_tensor(self.w)

@@ -26,6 +26,9 @@ def _load():
         lib.oracle_transform.restype = None
         lib.oracle_raster.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
         lib.oracle_raster.restype = None
+        lib.oracle_tess_positions.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P,
+                                              ctypes.c_int, ctypes.c_int, P, P]
+        lib.oracle_tess_positions.restype = None
         _lib = lib
     return _lib
 

@@ -42,13 +42,26 @@ struct Job {
     bool frozen = true;
     adms_opt_params opt{};
     uint64_t seed = 0;
-    int V = 0, T = 0, F = 0;
-    // latents and their optimizer state
+    int V = 0, T = 0, F = 0;  // render mesh (the tessellation for tessellated jobs)
+    int LV = 0;               // latent (base) vertices
+    // latents and their optimizer state (base positions for tessellated jobs)
     float* pos = nullptr;
     float* g_pos = nullptr;
     float* m_pos = nullptr;
     float* v_pos = nullptr;
     TexState kd, orm, nrm;
+    // render-mesh positions and their gradient (alias pos / g_pos without tessellation)
+    float* rpos = nullptr;
+    float* g_rpos = nullptr;
+    // tessellation + displacement (Sec. 5.1)
+    bool tess = false;
+    int Fb = 0, n_seg = 0, dh = 0, dw = 0;
+    int *btri = nullptr, *btri_uv = nullptr, *bvf_off = nullptr, *bvf_face = nullptr, *owner = nullptr, *wts = nullptr;
+    float2 *vert_uv = nullptr, *buv = nullptr;
+    float* bnrm = nullptr;
+    double *g_bnrm = nullptr, *g_btan0 = nullptr, *g_bpos_acc = nullptr;
+    float4 *b_vpos = nullptr, *b_vnrm = nullptr, *b_vtan = nullptr, *b_tmp_n = nullptr, *b_tmp_t = nullptr;
+    float *disp = nullptr, *g_disp = nullptr, *m_disp = nullptr, *v_disp = nullptr;
     // topology
     float2* uv = nullptr;
     int* tri = nullptr;
@@ -284,7 +297,7 @@ FrameArgs frame_args(Job& j) {
     FrameArgs f;
     f.V = j.V;
     f.F = j.F;
-    f.pos = j.pos;
+    f.pos = j.rpos;
     f.uv = j.uv;
     f.tri = j.tri;
     f.tri_uv = j.tri_uv;
@@ -298,8 +311,56 @@ FrameArgs frame_args(Job& j) {
     f.tmp_n = j.tmp_n;
     f.tmp_t = j.tmp_t;
     f.g_pos_acc = j.g_pos_acc;
+    f.g_pos = j.g_rpos;
+    return f;
+}
+
+// frame of the base mesh of a tessellated job (its normals feed the displacement)
+FrameArgs base_frame_args(Job& j) {
+    FrameArgs f;
+    f.V = j.LV;
+    f.F = j.Fb;
+    f.pos = j.pos;
+    f.uv = j.buv;
+    f.tri = j.btri;
+    f.tri_uv = j.btri_uv;
+    f.vf_off = j.bvf_off;
+    f.vf_face = j.bvf_face;
+    f.vpos = j.b_vpos;
+    f.vnrm = j.b_vnrm;
+    f.vtan = j.b_vtan;
+    f.g_nrm = j.g_bnrm;
+    f.g_tan = j.g_btan0;
+    f.tmp_n = j.b_tmp_n;
+    f.tmp_t = j.b_tmp_t;
+    f.g_pos_acc = j.g_bpos_acc;
     f.g_pos = j.g_pos;
     return f;
+}
+
+TessArgs tess_args(Job& j) {
+    TessArgs a;
+    a.Vb = j.LV;
+    a.Fb = j.Fb;
+    a.Vt = j.V;
+    a.n_seg = j.n_seg;
+    a.base_pos = j.pos;
+    a.base_tri = j.btri;
+    a.bvf_off = j.bvf_off;
+    a.bvf_face = j.bvf_face;
+    a.base_nrm = j.bnrm;
+    a.owner = j.owner;
+    a.wts = j.wts;
+    a.vert_uv = j.vert_uv;
+    a.disp = j.disp;
+    a.dh = j.dh;
+    a.dw = j.dw;
+    a.pos_out = j.rpos;
+    a.g_pos_t = j.g_rpos;
+    a.g_base_pos = j.g_bpos_acc;
+    a.g_base_nrm = j.g_bnrm;
+    a.g_disp = j.g_disp;
+    return a;
 }
 
 ShadeArgs shade_args(Job& j) {
@@ -340,11 +401,12 @@ ShadeArgs shade_args(Job& j) {
 // frame, raster and pre-AA shading of B views already copied to j.views
 adms_status render_core(adms_ctx* ctx, Job& j) {
     if (!j.frame_valid) {
+        if (j.tess) CK(TIMED(ST_FRAME, tess_forward(tess_args(j), ctx->stream)));
         CK(TIMED(ST_FRAME, frame_forward(frame_args(j), ctx->stream)));
         j.frame_valid = true;
     }
     RasterIn in;
-    in.pos = j.pos;
+    in.pos = j.rpos;
     in.tri = j.tri;
     in.adj = j.adj;
     in.views = j.views;
@@ -415,6 +477,92 @@ adms_status upload(adms_ctx* ctx, Job& j, T** dst, const std::vector<T>& src) {
         if (s_ != ADMS_OK) return s_;              \
     } while (0)
 
+// Host side of the tessellation (Sec. 5.1): the lattice of n = 2^levels segments
+// per base edge. Tessellated triangles are ordered base face by base face, and
+// within a face by lattice row a and column b (the "up" triangle of cell (a, b),
+// then its "down" triangle). A vertex shared by several base faces is owned by
+// the lowest-numbered one, which fixes its weights and displacement UV.
+struct TessHost {
+    int n = 0, L = 0, NT = 0, Vt = 0;
+    std::vector<int> rtri, rtri_uv, owner, wts;
+    std::vector<float> corner_uv, vert_uv;
+};
+
+void build_tessellation(const std::vector<int>& tri, const std::vector<int>& tri_uv, const std::vector<float>& uv,
+                        int F, int levels, TessHost& t) {
+    int n = 1 << levels;
+    t.n = n;
+    std::vector<int> loc((n + 1) * (n + 1), -1), li, lj;
+    for (int i = 0; i <= n; ++i)
+        for (int jj = 0; jj <= n - i; ++jj) {
+            loc[i * (n + 1) + jj] = (int)li.size();
+            li.push_back(i);
+            lj.push_back(jj);
+        }
+    t.L = (int)li.size();
+    std::vector<int> lt;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n - a; ++b) {
+            lt.insert(lt.end(), {loc[a * (n + 1) + b], loc[(a + 1) * (n + 1) + b], loc[a * (n + 1) + b + 1]});
+            if (a + b + 1 < n)
+                lt.insert(lt.end(), {loc[(a + 1) * (n + 1) + b], loc[(a + 1) * (n + 1) + b + 1], loc[a * (n + 1) + b + 1]});
+        }
+    t.NT = (int)lt.size() / 3;
+    struct Key {
+        long long a, b, c;
+        bool operator==(const Key& o) const { return a == o.a && b == o.b && c == o.c; }
+    };
+    struct KH {
+        size_t operator()(const Key& k) const { return std::hash<long long>()(k.a * 1000003LL ^ k.b * 998244353LL ^ k.c); }
+    };
+    std::unordered_map<Key, int, KH> index;
+    std::vector<int> gidx((size_t)F * t.L);
+    for (int f = 0; f < F; ++f) {
+        for (int l = 0; l < t.L; ++l) {
+            int w[3] = {n - li[l] - lj[l], li[l], lj[l]};
+            long long id[3] = {tri[3 * f], tri[3 * f + 1], tri[3 * f + 2]};
+            // canonical key: (vertex id, weight) pairs with weight > 0, sorted by id
+            long long pr[3];
+            int m = 0;
+            for (int k = 0; k < 3; ++k)
+                if (w[k] > 0) pr[m++] = id[k] * 4096 + w[k];
+            std::sort(pr, pr + m);
+            Key key{m > 0 ? pr[0] : -1, m > 1 ? pr[1] : -1, m > 2 ? pr[2] : -1};
+            auto it = index.find(key);
+            if (it == index.end()) {
+                int v = (int)index.size();
+                index.emplace(key, v);
+                t.owner.insert(t.owner.end(), {tri[3 * f], tri[3 * f + 1], tri[3 * f + 2]});
+                t.wts.insert(t.wts.end(), {w[0], w[1], w[2]});
+                double u = 0.0, vv = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    double wk = (double)w[k] / (double)n;
+                    u += wk * (double)uv[2 * tri_uv[3 * f + k]];
+                    vv += wk * (double)uv[2 * tri_uv[3 * f + k] + 1];
+                }
+                t.vert_uv.push_back((float)u);
+                t.vert_uv.push_back((float)vv);
+                gidx[(size_t)f * t.L + l] = v;
+            } else {
+                gidx[(size_t)f * t.L + l] = it->second;
+            }
+            double u = 0.0, vv = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                double wk = (double)w[k] / (double)n;
+                u += wk * (double)uv[2 * tri_uv[3 * f + k]];
+                vv += wk * (double)uv[2 * tri_uv[3 * f + k] + 1];
+            }
+            t.corner_uv.push_back((float)u);
+            t.corner_uv.push_back((float)vv);
+        }
+        for (int k = 0; k < t.NT * 3; ++k) {
+            t.rtri.push_back(gidx[(size_t)f * t.L + lt[k]]);
+            t.rtri_uv.push_back(f * t.L + lt[k]);
+        }
+    }
+    t.Vt = (int)index.size();
+}
+
 adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
                             const adms_opt_params* opt, uint64_t seed, Job& j) {
     if (!mesh || !mat || !mesh->pos || !mesh->uv || !mesh->tri_pos || !mesh->tri_uv || mesh->n_verts <= 0 ||
@@ -428,36 +576,97 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
         memset(&j.opt, 0, sizeof(j.opt));
         j.opt.aa = 1;
     }
-    if (j.opt.tess_levels != 0) return fail(ctx, ADMS_ERR_ARG, "tessellated jobs are not supported by this build");
-    j.V = mesh->n_verts;
-    j.T = mesh->n_uv;
-    j.F = mesh->n_tris;
+    if (j.opt.tess_levels < 0 || j.opt.tess_levels > 6) return fail(ctx, ADMS_ERR_ARG, "tess_levels must be in [0, 6]");
+    j.tess = j.opt.tess_levels > 0;
+    if (j.tess && (!mat->disp || !pow2(mat->disp_h) || !pow2(mat->disp_w)))
+        return fail(ctx, ADMS_ERR_ARG, "a tessellated job needs a power-of-two displacement map");
+    int Vb = mesh->n_verts, Tb = mesh->n_uv, Fb = mesh->n_tris;
+    j.LV = Vb;
     std::vector<int> tri, tri_uv;
     adms_status s;
-    if ((s = to_host(ctx, mesh->tri_pos, (size_t)j.F * 3, tri))) return s;
-    if ((s = to_host(ctx, mesh->tri_uv, (size_t)j.F * 3, tri_uv))) return s;
+    if ((s = to_host(ctx, mesh->tri_pos, (size_t)Fb * 3, tri))) return s;
+    if ((s = to_host(ctx, mesh->tri_uv, (size_t)Fb * 3, tri_uv))) return s;
     for (int x : tri)
-        if (x < 0 || x >= j.V) return fail(ctx, ADMS_ERR_ARG, "position index out of range");
+        if (x < 0 || x >= Vb) return fail(ctx, ADMS_ERR_ARG, "position index out of range");
     for (int x : tri_uv)
-        if (x < 0 || x >= j.T) return fail(ctx, ADMS_ERR_ARG, "uv index out of range");
-    std::vector<int> adj, vf_off, vf_face, ring_off, ring;
-    build_topology(tri, j.V, j.F, adj, vf_off, vf_face, ring_off, ring);
-    UP(j.tri, tri);
-    UP(j.tri_uv, tri_uv);
+        if (x < 0 || x >= Tb) return fail(ctx, ADMS_ERR_ARG, "uv index out of range");
+    // latent (base) positions, their Laplacian topology and optimizer state
+    std::vector<int> badj, bvf_off, bvf_face, ring_off, ring;
+    build_topology(tri, Vb, Fb, badj, bvf_off, bvf_face, ring_off, ring);
+    UP(j.ring_off, ring_off);
+    UP(j.ring, ring);
+    AL(j.pos, (size_t)Vb * 3);
+    CK(cudaMemcpyAsync(j.pos, mesh->pos, (size_t)Vb * 3 * sizeof(float), cudaMemcpyDefault, ctx->stream));
+    AL(j.g_pos, (size_t)Vb * 3);
+    if (j.opt.optimize_pos) {
+        AL(j.m_pos, (size_t)Vb * 3);
+        AL(j.v_pos, (size_t)Vb * 3);
+    }
+    AL(j.delta, (size_t)Vb * 3);
+    // render mesh: the base mesh itself, or its tessellation
+    std::vector<int> rtri = tri, rtri_uv = tri_uv;
+    if (!j.tess) {
+        j.V = Vb;
+        j.T = Tb;
+        j.F = Fb;
+        AL(j.uv, j.T);
+        CK(cudaMemcpyAsync(j.uv, mesh->uv, (size_t)j.T * 2 * sizeof(float), cudaMemcpyDefault, ctx->stream));
+        j.rpos = j.pos;
+        j.g_rpos = j.g_pos;
+    } else {
+        std::vector<float> uvh;
+        if ((s = to_host(ctx, mesh->uv, (size_t)Tb * 2, uvh))) return s;
+        TessHost th;
+        build_tessellation(tri, tri_uv, uvh, Fb, j.opt.tess_levels, th);
+        j.V = th.Vt;
+        j.F = Fb * th.NT;
+        j.T = Fb * th.L;
+        j.n_seg = th.n;
+        rtri = th.rtri;
+        rtri_uv = th.rtri_uv;
+        AL(j.uv, j.T);
+        CK(cudaMemcpyAsync(j.uv, th.corner_uv.data(), th.corner_uv.size() * sizeof(float), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        UP(j.btri, tri);
+        UP(j.btri_uv, tri_uv);
+        UP(j.bvf_off, bvf_off);
+        UP(j.bvf_face, bvf_face);
+        UP(j.owner, th.owner);
+        UP(j.wts, th.wts);
+        AL(j.vert_uv, j.V);
+        CK(cudaMemcpyAsync(j.vert_uv, th.vert_uv.data(), th.vert_uv.size() * sizeof(float), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        AL(j.buv, Tb);
+        CK(cudaMemcpyAsync(j.buv, mesh->uv, (size_t)Tb * 2 * sizeof(float), cudaMemcpyDefault, ctx->stream));
+        AL(j.bnrm, (size_t)Vb * 3);
+        AL(j.rpos, (size_t)j.V * 3);
+        AL(j.g_rpos, (size_t)j.V * 3);
+        AL(j.g_bnrm, (size_t)Vb * 3);
+        AL(j.g_btan0, (size_t)Vb * 3);
+        AL(j.g_bpos_acc, (size_t)Vb * 3);
+        AL(j.b_vpos, Vb);
+        AL(j.b_vnrm, Vb);
+        AL(j.b_vtan, Vb);
+        AL(j.b_tmp_n, Vb);
+        AL(j.b_tmp_t, Vb);
+        j.Fb = Fb;
+        j.dh = mat->disp_h;
+        j.dw = mat->disp_w;
+        AL(j.disp, (size_t)j.dh * j.dw);
+        CK(cudaMemcpyAsync(j.disp, mat->disp, (size_t)j.dh * j.dw * sizeof(float), cudaMemcpyDefault, ctx->stream));
+        if (j.opt.optimize_disp) {
+            AL(j.g_disp, (size_t)j.dh * j.dw);
+            AL(j.m_disp, (size_t)j.dh * j.dw);
+            AL(j.v_disp, (size_t)j.dh * j.dw);
+        }
+    }
+    std::vector<int> adj, vf_off, vf_face, rring_off, rring;
+    build_topology(rtri, j.V, j.F, adj, vf_off, vf_face, rring_off, rring);
+    UP(j.tri, rtri);
+    UP(j.tri_uv, rtri_uv);
     UP(j.adj, adj);
     UP(j.vf_off, vf_off);
     UP(j.vf_face, vf_face);
-    UP(j.ring_off, ring_off);
-    UP(j.ring, ring);
-    AL(j.pos, (size_t)j.V * 3);
-    CK(cudaMemcpyAsync(j.pos, mesh->pos, (size_t)j.V * 3 * sizeof(float), cudaMemcpyDefault, ctx->stream));
-    AL(j.uv, j.T);
-    CK(cudaMemcpyAsync(j.uv, mesh->uv, (size_t)j.T * 2 * sizeof(float), cudaMemcpyDefault, ctx->stream));
-    AL(j.g_pos, (size_t)j.V * 3);
-    if (j.opt.optimize_pos) {
-        AL(j.m_pos, (size_t)j.V * 3);
-        AL(j.v_pos, (size_t)j.V * 3);
-    }
     AL(j.vpos, j.V);
     AL(j.vnrm, j.V);
     AL(j.vtan, j.V);
@@ -466,15 +675,14 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
     AL(j.g_nrm, (size_t)j.V * 3);
     AL(j.g_tan, (size_t)j.V * 3);
     AL(j.g_pos_acc, (size_t)j.V * 3);
-    AL(j.delta, (size_t)j.V * 3);
     AL(j.st, 1);
     bool mips = mat->mips != 0;
     if ((s = tex_create(ctx, j, j.kd, mat->kd, mat->kd_h, mat->kd_w, mips, j.opt.optimize_kd))) return s;
     if ((s = tex_create(ctx, j, j.orm, mat->orm, mat->orm_h, mat->orm_w, mips, j.opt.optimize_orm))) return s;
     if ((s = tex_create(ctx, j, j.nrm, mat->nrm, mat->nrm_h, mat->nrm_w, mips, j.opt.optimize_nrm))) return s;
     if (j.opt.relative_laplacian) {
-        AL(j.delta_ref, (size_t)j.V * 3);
-        LapArgs la{j.V, j.pos, j.ring_off, j.ring, nullptr, j.delta_ref, j.g_pos, j.st};
+        AL(j.delta_ref, (size_t)Vb * 3);
+        LapArgs la{Vb, j.pos, j.ring_off, j.ring, nullptr, j.delta_ref, j.g_pos, j.st};
         CK(laplacian_forward(la, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
@@ -558,7 +766,11 @@ adms_status adms_job_params(adms_ctx* ctx, adms_job job, adms_param_view* out) {
     out->g_kd = (float*)j->kd.grad;
     out->g_orm = (float*)j->orm.grad;
     out->g_nrm = (float*)j->nrm.grad;
-    out->n_verts = j->V;
+    out->disp = j->disp;
+    out->g_disp = j->g_disp;
+    out->disp_h = j->dh;
+    out->disp_w = j->dw;
+    out->n_verts = j->LV;
     out->n_tris_render = j->F;
     out->kd_h = j->kd.h;
     out->kd_w = j->kd.w;
@@ -668,8 +880,16 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
         CK(cudaMemsetAsync(j.g_tan, 0, sizeof(double) * 3 * j.V, ctx->stream));
         ShadeArgs a = shade_args(j);
         a.ref = j.ref;
+        if (j.tess) CK(cudaMemsetAsync(j.g_rpos, 0, sizeof(float) * 3 * j.V, ctx->stream));
         CK(TIMED(ST_SHADE_BWD, shade_backward(a, ctx->stream)));
         CK(TIMED(ST_FRAME_BWD, frame_backward(frame_args(j), ctx->stream)));
+        if (j.tess) {
+            // render positions -> base positions, base normals and displacement texels,
+            // then the base normals' adjoint back to base positions
+            CK(cudaMemsetAsync(j.g_bnrm, 0, sizeof(double) * 3 * j.LV, ctx->stream));
+            CK(TIMED(ST_FRAME_BWD, tess_backward(tess_args(j), ctx->stream)));
+            CK(TIMED(ST_FRAME_BWD, frame_backward(base_frame_args(j), ctx->stream)));
+        }
         j.have_fwd = false;
     }
     return ADMS_OK;
@@ -682,15 +902,20 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         if (!jp) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
         Job& j = *jp;
         if (j.frozen) return fail(ctx, ADMS_ERR_STATE, "optimizer_step on a frozen job");
-        LapArgs la{j.V, j.pos, j.ring_off, j.ring, j.delta_ref, j.delta, j.g_pos, j.st};
+        LapArgs la{j.LV, j.pos, j.ring_off, j.ring, j.delta_ref, j.delta, j.g_pos, j.st};
         if (j.opt.optimize_pos) CK(TIMED(ST_LAPLACIAN, laplacian_forward(la, ctx->stream)));
-        SchedArgs sa{j.st, j.opt.lr0, j.opt.lambda0, j.opt.optimize_pos, j.V};
+        SchedArgs sa{j.st, j.opt.lr0, j.opt.lambda0, j.opt.optimize_pos, j.LV};
         CK(TIMED(ST_SMALL, schedule_step(sa, ctx->stream)));
         if (j.opt.optimize_pos) {
             CK(TIMED(ST_LAPLACIAN, laplacian_backward(la, ctx->stream)));
-            CK(TIMED(ST_ADAM, adam_flat(j.pos, j.g_pos, j.m_pos, j.v_pos, (long long)j.V * 3, j.st, ctx->stream)));
+            CK(TIMED(ST_ADAM, adam_flat(j.pos, j.g_pos, j.m_pos, j.v_pos, (long long)j.LV * 3, j.st, ctx->stream)));
         } else {
-            CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.V, ctx->stream));
+            CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.LV, ctx->stream));
+        }
+        if (j.tess) {
+            if (j.opt.optimize_disp)
+                CK(TIMED(ST_ADAM, adam_flat(j.disp, j.g_disp, j.m_disp, j.v_disp, (long long)j.dh * j.dw, j.st,
+                                            ctx->stream)));
         }
         TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
         for (int m = 0; m < 3; ++m) {

@@ -127,6 +127,28 @@ struct FrameArgs {
 cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st);
 cudaError_t frame_backward(const FrameArgs& a, cudaStream_t st);
 
+// tessellation + displacement (latent base mesh -> render mesh) and its adjoint
+struct TessArgs {
+    int Vb, Fb, Vt, n_seg;
+    const float* base_pos;   // [Vb][3] latent
+    const int* base_tri;     // [Fb][3]
+    const int* bvf_off;      // [Vb+1] base vertex -> incident faces (ascending)
+    const int* bvf_face;
+    float* base_nrm;         // [Vb][3] base normals (float32 contract)
+    const int* owner;        // [Vt][3] base vertices of the owning base face
+    const int* wts;          // [Vt][3] integer lattice weights (sum n_seg)
+    const float2* vert_uv;   // [Vt] displacement lookup coordinates
+    const float* disp;       // [dh][dw] latent displacement map
+    int dh, dw;
+    float* pos_out;          // [Vt][3] render positions
+    const float* g_pos_t;    // [Vt][3] gradient w.r.t. render positions
+    double* g_base_pos;      // [Vb][3] accumulated
+    double* g_base_nrm;      // [Vb][3] accumulated
+    float* g_disp;           // [dh][dw] accumulated, or null
+};
+cudaError_t tess_forward(const TessArgs& a, cudaStream_t st);
+cudaError_t tess_backward(const TessArgs& a, cudaStream_t st);
+
 // device-side per-job scalars
 struct JobState {
     double call_loss;    // L_image of the current forward call

@@ -59,13 +59,19 @@ class Context:
         arrays = dict(pos=_c32(m.pos, np.float32), uv=_c32(m.uv, np.float32), tri=_c32(m.tri_pos, np.int32),
                       tri_uv=_c32(m.tri_uv, np.int32), kd=_c32(scene.kd, np.float32),
                       orm=_c32(scene.orm, np.float32), nrm=_c32(scene.nrm, np.float32))
+        disp = getattr(scene, "disp", None)
+        arrays["disp"] = None if disp is None else _c32(disp, np.float32)
+        levels = int(getattr(scene, "tess_levels", 0))
         mesh = B.mesh_desc(arrays["pos"], arrays["uv"], arrays["tri"], arrays["tri_uv"])
-        mat = B.material_desc(arrays["kd"], arrays["orm"], arrays["nrm"], None, getattr(scene, "mips", True))
+        mat = B.material_desc(arrays["kd"], arrays["orm"], arrays["nrm"], arrays["disp"], getattr(scene, "mips", True))
         opt = None
-        if not frozen:
+        if not frozen or levels:
             opt = B.opt_params(optimize if optimize is not None else getattr(scene, "optimize", {}), loss=loss,
-                               batch_views=batch_views, relative_laplacian=relative_laplacian, aa=aa, lr0=lr0,
-                               lambda0=lambda0)
+                               tess_levels=levels, batch_views=batch_views, relative_laplacian=relative_laplacian,
+                               aa=aa, lr0=lr0, lambda0=lambda0)
+            if frozen:
+                for k in ("optimize_pos", "optimize_kd", "optimize_orm", "optimize_nrm", "optimize_disp"):
+                    setattr(opt, k, 0)
         return B.adms_job_create(self.ctx, mesh, mat, opt, seed)
 
     def destroy_job(self, job):
@@ -85,6 +91,9 @@ class Context:
             out["g_" + name] = device_view(getattr(pv, "g_" + name), (h, w, 4))
             out["g_" + name + "_chain"] = device_view(getattr(pv, "g_" + name), (total, 4))
             out[name + "_levels"] = L
+        if pv.disp:
+            out["disp"] = device_view(pv.disp, (pv.disp_h, pv.disp_w))
+            out["g_disp"] = device_view(pv.g_disp, (pv.disp_h, pv.disp_w))
         return out
 
     def stats(self, job):

@@ -33,6 +33,18 @@ def plain_case(res=128, n_views=8, tex=256, ref_tex=256, ref_freq=32, seed=5):
     return c, views, res, res
 
 
+def tess_case(res=128, n_views=2, base_freq=4, levels=2, seed=8):
+    """The displacement workload shrunk for the oracle: a frequency-4 base
+    icosphere (320 tris) split twice (5,120 tris), a 32^2 displacement map, a
+    64^2 normal map, against a frequency-24 fBm reference."""
+    c = synth.config_tess(ref_freq=24, base_freq=base_freq, levels=levels, disp_res=32, nrm_res=64, n_views=n_views,
+                          res=res)
+    rng = np.random.default_rng(seed)
+    c["cand"].disp = rng.uniform(-0.03, 0.03, c["cand"].disp.shape).astype(np.float32)
+    views = synth.sample_views(seed, 0, n_views, res, res, r_min=2.4, r_max=3.0)
+    return c, views, res, res
+
+
 def oracle_reference(scene, views, H, W):
     img, keys = S.render_reference(scene, views, H, W)
     return img.numpy().astype(np.float32), keys
@@ -63,7 +75,15 @@ def oracle_grads(scene, views, refs, H, W, loss):
     live = [k for k in params if job.optimize[k]]
     grads = dict(zip(live, [g.detach().numpy() for g in torch.autograd.grad(obj["total"], [params[k] for k in live])]))
     img = obj["out"]["img"].detach().numpy()
-    amb = ambiguous_vertices(diags, obj["out"]["keys"], img, refs, job.tri_np, loss)
+    if job.tess is None:
+        amb = ambiguous_vertices(diags, obj["out"]["keys"], img, refs, job.tri_np, loss)
+    else:
+        # render vertices -> the base vertices they are interpolated from
+        amb_r = ambiguous_vertices(diags, obj["out"]["keys"], img, refs, job.tess.tri, loss)
+        base = set()
+        for v in amb_r:
+            base |= set(job.tess.base_idx[v].tolist())
+        amb = base
     return dict(grads=grads, img=img, pre=obj["out"]["pre"].detach().numpy(), keys=obj["out"]["keys"],
                 loss=float(obj["image"].detach()), ambiguous=amb)
 

@@ -13,7 +13,7 @@ import synth
 from oracle import step as S
 from oracle import visibility as OV
 
-from cases import fold_mips, oracle_grads, oracle_reference, plain_case, rel_l2, small_case
+from cases import fold_mips, oracle_grads, oracle_reference, plain_case, rel_l2, small_case, tess_case
 
 pytestmark = pytest.mark.gpu
 
@@ -111,6 +111,38 @@ def test_gradients(which, request):
         else:
             err = rel_l2(got, want)
         assert err < GRAD_TOL, f"{name}: rel L2 {err:.3e}"
+
+
+@pytest.fixture(scope="module")
+def tess(ctx):
+    case = tess_case()
+    c, views, H, W = case
+    gpu = _run_case(ctx, case, "logl1")
+    orc = oracle_grads(c["cand"], views, gpu["ref_np"], H, W, "logl1")
+    p = ctx.params(gpu["job"])
+    gpu["grads"]["disp"] = p["g_disp"].double().cpu().numpy()
+    return case, gpu, orc
+
+
+def test_tessellated_keys_images_and_gradients(tess):
+    """Tessellated + displaced render mesh (Sec. 5.1, Eq. 3): keys bit-exact
+    (float32 contract of the displaced positions), images within 1e-5,
+    gradients w.r.t. base positions, displacement and normal map within 1e-3."""
+    case, gpu, orc = tess
+    np.testing.assert_array_equal(gpu["keys"], orc["keys"])
+    assert (gpu["keys"] != OV.EMPTY_KEY).any()
+    assert rel_l2(gpu["img"], orc["img"]) < IMG_TOL
+    for name in ("disp", "nrm"):
+        err = rel_l2(gpu["grads"][name], orc["grads"][name])
+        print(f"tess {name}: rel L2 {err:.3e}")
+        assert err < GRAD_TOL, name
+    want, got = orc["grads"]["pos"], gpu["grads"]["pos"]
+    amb = np.zeros(len(want), bool)
+    amb[sorted(orc["ambiguous"])] = True
+    err = rel_l2(got[~amb], want[~amb])
+    print(f"tess pos: {amb.sum()} of {len(amb)} base vertices one-sided; rel L2 of the rest {err:.3e}")
+    assert err < GRAD_TOL
+    assert rel_l2(got, want) < 1e-2
 
 
 def test_reference_render_parity(ctx):

@@ -425,6 +425,22 @@ def test_tessellation_counts_and_flat_positions():
     assert len(s) == len(e) and all((y, x) in s for x, y in s)
 
 
+def test_tessellation_float32_contract_matches_float64():
+    """The float32 positions visibility uses equal the float64 displaced positions
+    to float32 rounding, for a random displacement map."""
+    p, tri = synth.icosphere(3)
+    uv, tri_uv = synth.equirect_uv_corners(p, tri)
+    ts = TS.Tessellation(tri.astype(np.int64), tri_uv.astype(np.int64), uv.astype(np.float64), 2)
+    rng = np.random.default_rng(4)
+    disp = rng.uniform(-0.05, 0.05, (16, 16)).astype(np.float32)
+    pos32 = p.astype(np.float32)
+    f32 = ts.positions_f32(pos32, tri, disp)
+    bp = torch.as_tensor(pos32.astype(np.float64))
+    nrm = R.vertex_normals(bp, torch.as_tensor(tri.astype(np.int64)))
+    f64 = ts.displaced_positions(bp, nrm, torch.as_tensor(disp.astype(np.float64))).numpy()
+    assert np.abs(f32 - f64).max() < 2e-6
+
+
 # ----------------------------------------------------------------------------- gradients vs central differences
 
 def _tiny_job(loss="logl1", tess=0):
