@@ -126,6 +126,7 @@ typedef struct {
     int32_t t;            /* optimizer steps taken */
     int32_t status;       /* 0, or an adms_status latched on the device */
     int64_t tile_overflows; /* raster tiles that fell back to a full triangle scan */
+    double call_loss;     /* L_image of the latest forward_loss call, float64 accumulation */
 } adms_stats;
 
 /* ---- context ------------------------------------------------------------- */
@@ -188,6 +189,21 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
  * adjoint of the mip chain and followed by clamping and a mip rebuild; zeroes
  * the gradients and advances t. */
 adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs);
+
+/* Level-0 gradient of each optimized texture with the adjoint of the box-filter
+ * mip chain folded in (what the optimizer step applies), written to device
+ * buffers [h][w][4] (NULL entries skipped); nothing is updated or zeroed.
+ * ADMS_ERR_STATE for a texture that is not optimized. */
+adms_status adms_job_fold_gradients(adms_ctx* ctx, adms_job job, float* g_kd, float* g_orm, float* g_nrm);
+/* Zero every gradient buffer of a job (positions, displacement, textures). */
+adms_status adms_job_zero_gradients(adms_ctx* ctx, adms_job job);
+/* Rebuild the mip chains from level 0 and recompute the vertex frame at the
+ * next forward: call after writing latents through adms_job_params pointers. */
+adms_status adms_job_invalidate(adms_ctx* ctx, adms_job job);
+/* L_delta of the job's current positions (Eq. 4; delta' = 0 unless the job
+ * was created with relative_laplacian) into out_loss (device scalar), and
+ * dL_delta/dpos into g_pos (device [V][3], overwritten; NULL skips it). */
+adms_status adms_laplacian(adms_ctx* ctx, adms_job job, float* out_loss, float* g_pos);
 
 /* Raw visibility of the latest forward_loss / render_reference of a job:
  * copies [B][H][W] keys into out_keys (device). */

@@ -65,7 +65,7 @@ class adms_param_view(C.Structure):
 
 class adms_stats(C.Structure):
     _fields_ = [("image_loss", C.c_float), ("laplacian", C.c_float), ("lambda_", C.c_float), ("lr", C.c_float),
-                ("t", C.c_int32), ("status", C.c_int32), ("tile_overflows", C.c_int64)]
+                ("t", C.c_int32), ("status", C.c_int32), ("tile_overflows", C.c_int64), ("call_loss", C.c_double)]
 
 
 assert C.sizeof(adms_view) == 112
@@ -89,6 +89,10 @@ SIGNATURES = {
     "adms_backward": ([P, P, C.c_int32, C.c_int32], C.c_int),
     "adms_optimizer_step": ([P, P, C.c_int32], C.c_int),
     "adms_job_keys": ([P, C.c_int32, P, C.c_size_t], C.c_int),
+    "adms_job_fold_gradients": ([P, C.c_int32, P, P, P], C.c_int),
+    "adms_job_zero_gradients": ([P, C.c_int32], C.c_int),
+    "adms_job_invalidate": ([P, C.c_int32], C.c_int),
+    "adms_laplacian": ([P, C.c_int32, P, P], C.c_int),
     "adms_job_export": ([P, C.c_int32, P, C.POINTER(C.c_size_t)], C.c_int),
     "adms_job_import": ([P, C.POINTER(adms_mesh_desc), C.POINTER(adms_material_desc), C.POINTER(adms_opt_params),
                          P, C.c_size_t, C.POINTER(C.c_int32)], C.c_int),
@@ -239,6 +243,22 @@ def adms_optimizer_step(ctx, jobs):
 
 def adms_job_keys(ctx, job, out_keys):
     _check(ctx, lib().adms_job_keys(ctx, job, ptr(out_keys), out_keys.numel()))
+
+
+def adms_job_fold_gradients(ctx, job, g_kd=None, g_orm=None, g_nrm=None):
+    _check(ctx, lib().adms_job_fold_gradients(ctx, job, ptr(g_kd), ptr(g_orm), ptr(g_nrm)))
+
+
+def adms_job_zero_gradients(ctx, job):
+    _check(ctx, lib().adms_job_zero_gradients(ctx, job))
+
+
+def adms_job_invalidate(ctx, job):
+    _check(ctx, lib().adms_job_invalidate(ctx, job))
+
+
+def adms_laplacian(ctx, job, out_loss, g_pos=None):
+    _check(ctx, lib().adms_laplacian(ctx, job, ptr(out_loss), ptr(g_pos)))
 
 
 def adms_job_export(ctx, job):

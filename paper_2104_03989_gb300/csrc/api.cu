@@ -804,6 +804,7 @@ adms_status adms_job_stats(adms_ctx* ctx, adms_job job, adms_stats* out) {
     out->t = hs.t;
     out->status = hs.status;
     out->tile_overflows = (int64_t)ovf;
+    out->call_loss = hs.call_loss;
     return ADMS_OK;
 }
 
@@ -873,8 +874,14 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
         Job& j = *jp;
         if (!j.have_fwd) return fail(ctx, ADMS_ERR_STATE, "backward without a preceding forward_loss");
         if (recompute_raster) {
+            // rebuild keys, pre-AA colours and dL/d(AA colour) from the latents and the
+            // caller's reference images instead of reading what the forward kept
             adms_status s = render_core(ctx, j);
             if (s) return s;
+            ShadeArgs r = shade_args(j);
+            r.ref = j.ref;
+            r.loss_acc = nullptr;
+            CK(TIMED(ST_AA_LOSS, aa_loss_forward(r, ctx->stream)));
         }
         CK(cudaMemsetAsync(j.g_nrm, 0, sizeof(double) * 3 * j.V, ctx->stream));
         CK(cudaMemsetAsync(j.g_tan, 0, sizeof(double) * 3 * j.V, ctx->stream));
@@ -925,6 +932,51 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         CK(TIMED(ST_SMALL, advance_step(j.st, ctx->stream)));
         j.frame_valid = false;
     }
+    return ADMS_OK;
+}
+
+adms_status adms_job_fold_gradients(adms_ctx* ctx, adms_job job, float* g_kd, float* g_orm, float* g_nrm) {
+    Job* j = get_job(ctx, job);
+    if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    TexState* maps[3] = {&j->kd, &j->orm, &j->nrm};
+    float* outs[3] = {g_kd, g_orm, g_nrm};
+    for (int m = 0; m < 3; ++m) {
+        if (!outs[m]) continue;
+        if (!maps[m]->opt) return fail(ctx, ADMS_ERR_STATE, "texture is not optimized: no gradient");
+        CK(fold_mip_gradient(maps[m]->dev(), reinterpret_cast<float4*>(outs[m]), ctx->stream));
+    }
+    return ADMS_OK;
+}
+
+adms_status adms_job_zero_gradients(adms_ctx* ctx, adms_job job) {
+    Job* jp = get_job(ctx, job);
+    if (!jp) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    Job& j = *jp;
+    CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.LV, ctx->stream));
+    if (j.g_disp) CK(cudaMemsetAsync(j.g_disp, 0, sizeof(float) * j.dh * j.dw, ctx->stream));
+    TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
+    for (int m = 0; m < 3; ++m)
+        if (maps[m]->grad) CK(cudaMemsetAsync(maps[m]->grad, 0, sizeof(float4) * maps[m]->total, ctx->stream));
+    return ADMS_OK;
+}
+
+adms_status adms_job_invalidate(adms_ctx* ctx, adms_job job) {
+    Job* j = get_job(ctx, job);
+    if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    TexState* maps[3] = {&j->kd, &j->orm, &j->nrm};
+    for (int m = 0; m < 3; ++m) CK(TIMED(ST_MIP, mip_build(maps[m]->dev(), ctx->stream)));
+    j->frame_valid = false;
+    return ADMS_OK;
+}
+
+adms_status adms_laplacian(adms_ctx* ctx, adms_job job, float* out_loss, float* g_pos) {
+    Job* jp = get_job(ctx, job);
+    if (!jp || !out_loss) return fail(ctx, ADMS_ERR_ARG, "invalid laplacian arguments");
+    Job& j = *jp;
+    LapArgs la{j.LV, j.pos, j.ring_off, j.ring, j.delta_ref, j.delta, g_pos, j.st};
+    CK(TIMED(ST_LAPLACIAN, laplacian_forward(la, ctx->stream)));
+    CK(TIMED(ST_LAPLACIAN, laplacian_value(la, out_loss, ctx->stream)));
+    if (g_pos) CK(TIMED(ST_LAPLACIAN, laplacian_gradient(la, 1.0f, ctx->stream)));
     return ADMS_OK;
 }
 

@@ -173,6 +173,12 @@ struct LapArgs {
 };
 cudaError_t laplacian_forward(const LapArgs& a, cudaStream_t st);
 cudaError_t laplacian_backward(const LapArgs& a, cudaStream_t st);
+// *out = L_delta after laplacian_forward
+cudaError_t laplacian_value(const LapArgs& a, float* out, cudaStream_t st);
+// a.g_pos = scale * dL_delta/dpos (overwrites) after laplacian_forward
+cudaError_t laplacian_gradient(const LapArgs& a, float scale, cudaStream_t st);
+// level-0 texture gradient with the mip-chain adjoint folded in
+cudaError_t fold_mip_gradient(const TexDev& t, float4* out, cudaStream_t st);
 
 struct SchedArgs {
     JobState* st;

@@ -162,6 +162,36 @@ cudaError_t laplacian_forward(const LapArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+__global__ void k_lap_value(LapArgs a, float* out) { *out = (float)(a.st->lap_sum / (double)a.V); }
+
+// g = scale * dL_delta/dpos, written (not accumulated) into a.g_pos
+__global__ void k_lap_grad_out(LapArgs a, float scale) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.V) return;
+    float s = 2.f * scale / (float)a.V;
+    float3 g = f3(a.delta[3 * k], a.delta[3 * k + 1], a.delta[3 * k + 2]);
+    for (int j = a.ring_off[k]; j < a.ring_off[k + 1]; ++j) {
+        int i = a.ring[j];
+        float inv = 1.f / (float)(a.ring_off[i + 1] - a.ring_off[i]);
+        g -= inv * f3(a.delta[3 * i], a.delta[3 * i + 1], a.delta[3 * i + 2]);
+    }
+    a.g_pos[3 * k] = s * g.x;
+    a.g_pos[3 * k + 1] = s * g.y;
+    a.g_pos[3 * k + 2] = s * g.z;
+}
+
+cudaError_t laplacian_value(const LapArgs& a, float* out, cudaStream_t st) {
+    k_lap_value<<<1, 1, 0, st>>>(a, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t laplacian_gradient(const LapArgs& a, float scale, cudaStream_t st) {
+    k_lap_grad_out<<<(a.V + 127) / 128, 128, 0, st>>>(a, scale);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t laplacian_backward(const LapArgs& a, cudaStream_t st) {
     k_lap_bwd<<<(a.V + 127) / 128, 128, 0, st>>>(a);
     count_launches(1);

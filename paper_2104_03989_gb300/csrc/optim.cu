@@ -270,6 +270,27 @@ cudaError_t adam_texture_and_mips(const TexDev& t, float4* m, float4* v, int cla
     return cudaGetLastError();
 }
 
+// level-0 gradient including the adjoint of the mip chain, written to out (no update)
+__global__ void k_fold_mips(TexDev t, float4* __restrict__ out) {
+    int n = t.w0 * t.h0;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int x = i % t.w0, y = i / t.w0;
+    float4 g = t.grad[i];
+    for (int k = 1; k < t.levels; ++k) {
+        int wk = max(t.w0 >> k, 1);
+        g = f4madd(g, level_weight(t, k), t.grad[t.off[k] + (y >> k) * wk + (x >> k)]);
+    }
+    out[i] = g;
+}
+
+cudaError_t fold_mip_gradient(const TexDev& t, float4* out, cudaStream_t st) {
+    int n = t.w0 * t.h0;
+    k_fold_mips<<<(n + 255) / 256, 256, 0, st>>>(t, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t adam_texture(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js, cudaStream_t st) {
     int n = t.w0 * t.h0;
     k_adam_tex<<<(n + 255) / 256, 256, 0, st>>>(t, m, v, clamp_kind, js);

@@ -99,7 +99,7 @@ class Context:
     def stats(self, job):
         s = B.adms_job_stats(self.ctx, job)
         return dict(image_loss=s.image_loss, laplacian=s.laplacian, lam=s.lambda_, lr=s.lr, t=s.t,
-                    status=s.status, tile_overflows=s.tile_overflows)
+                    status=s.status, tile_overflows=s.tile_overflows, call_loss=s.call_loss)
 
     # ------------------------------------------------------------------ the step
     @staticmethod
