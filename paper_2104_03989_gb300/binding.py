@@ -97,6 +97,8 @@ SIGNATURES = {
     "adms_job_import": ([P, C.POINTER(adms_mesh_desc), C.POINTER(adms_material_desc), C.POINTER(adms_opt_params),
                          P, C.c_size_t, C.POINTER(C.c_int32)], C.c_int),
     "adms_visibility_noalloc": ([P, C.c_int32, P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
+    "adms_autotune": ([P, P, C.c_int32, P, P, P, P], C.c_int),
+    "adms_ctx_tuning": ([P, P], C.c_int),
     "adms_graph_begin": ([P], C.c_int),
     "adms_graph_end": ([P, C.POINTER(P)], C.c_int),
     "adms_graph_launch": ([P, P], C.c_int),
@@ -274,6 +276,22 @@ def adms_job_import(ctx, mesh, mat, opt, buf):
     _check(ctx, lib().adms_job_import(ctx, C.byref(mesh), C.byref(mat), C.byref(opt) if opt is not None else None,
                                       ptr(buf), buf.nbytes, C.byref(out)))
     return out.value
+
+
+def adms_autotune(ctx, jobs, views, views_per_job, hw, ref_rgb):
+    n = len(jobs)
+    jobs_a = (C.c_int32 * n)(*jobs)
+    vpj = (C.c_int32 * n)(*views_per_job)
+    hw_a = (C.c_int32 * (2 * n))(*[int(x) for p in hw for x in p])
+    refs = (C.c_void_p * n)(*[ptr(r) for r in ref_rgb])
+    _check(ctx, lib().adms_autotune(ctx, jobs_a, n, ptr(views), vpj, hw_a, refs))
+
+
+def adms_ctx_tuning(ctx):
+    out = (C.c_int32 * 5)()
+    _check(ctx, lib().adms_ctx_tuning(ctx, out))
+    return {"tile_w": out[0], "blocks_per_sm": {"shade": out[1], "aa_loss": out[2], "backward": out[3],
+                                                "raster": out[4]}}
 
 
 def adms_visibility_noalloc(pos, tri, views, n_views, H, W, keys, stream=None):

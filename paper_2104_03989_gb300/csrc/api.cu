@@ -123,6 +123,21 @@ struct adms_graph {
     cudaGraphExec_t exec = nullptr;
 };
 
+// device-side arguments and work items of the batched (many-job) launches
+struct BatchState {
+    std::vector<long long> key;  // (job, B, H, W) per job + tile width: the item lists depend on it
+    std::vector<ShadeArgs> h_args;
+    std::vector<RasterJob> h_rargs;
+    ShadeArgs* d_args = nullptr;
+    RasterJob* d_rargs = nullptr;
+    WorkItem* d_px = nullptr;
+    WorkItem* d_rt = nullptr;
+    int* d_counter = nullptr;
+    size_t cap_args = 0, cap_px = 0, cap_rt = 0;
+    int n_px = 0, n_rt = 0;
+    std::vector<void*> allocs;
+};
+
 struct adms_ctx {
     cudaStream_t stream = 0;
     size_t budget = 0;
@@ -130,6 +145,15 @@ struct adms_ctx {
     std::string err;
     std::vector<Job> jobs;
     bool capturing = false;
+    // one argument / work-item state per job set (and tile width): a graph recorded
+    // for one batch keeps valid device arguments while other batches run
+    std::vector<BatchState> batches;
+    std::vector<void*> batch_allocs;
+    int sm_count = 148;
+    // tile width (pixels; tiles are tw x 256/tw) and persistent blocks per SM of the
+    // batched launches: [shade, aa+loss, backward, raster]; set by adms_autotune
+    int tune_tw = 16;
+    int tune_bpsm[4] = {4, 4, 2, 4};
     // optional per-stage timing with CUDA events on the context's stream
     bool profile = false;
     std::vector<cudaEvent_t> pool;
@@ -689,6 +713,138 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
     return ADMS_OK;
 }
 
+// frame (and tessellation) plus the per-job raster preparation of a batched call
+adms_status frame_and_prepare(adms_ctx* ctx, Job& j) {
+    if (!j.frame_valid) {
+        if (j.tess) CK(TIMED(ST_FRAME, tess_forward(tess_args(j), ctx->stream)));
+        CK(TIMED(ST_FRAME, frame_forward(frame_args(j), ctx->stream)));
+        j.frame_valid = true;
+    }
+    RasterIn in;
+    in.pos = j.rpos;
+    in.tri = j.tri;
+    in.adj = j.adj;
+    in.views = j.views;
+    in.B = j.B;
+    in.V = j.V;
+    in.F = j.F;
+    in.W = j.W;
+    in.H = j.H;
+    in.keys = j.keys;
+    CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
+    return ADMS_OK;
+}
+
+template <typename T>
+adms_status ctx_alloc(adms_ctx* ctx, T** out, size_t count) {
+    size_t bytes = ((std::max<size_t>(count, 1) * sizeof(T)) + 255) & ~size_t(255);
+    if (ctx->capturing) return fail(ctx, ADMS_ERR_STATE, "batched launch needs new scratch during capture");
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget) return fail(ctx, ADMS_ERR_BUDGET, "HBM budget exceeded");
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(ctx, ADMS_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    ctx->batch_allocs.push_back(p);
+    ctx->in_use += bytes;
+    *out = static_cast<T*>(p);
+    return ADMS_OK;
+}
+
+// Arguments and work items of a batched call. Uploaded only when the job set,
+// their image sizes, the tile width or the jobs' buffers change, so a warmed-up
+// batched step records into a CUDA graph without host-to-device copies.
+adms_status batch_upload(adms_ctx* ctx, const std::vector<Job*>& js, float* const* out_img, BatchState** out_bs,
+                         bool backward = false) {
+    int n = (int)js.size();
+    std::vector<long long> key;
+    for (Job* j : js) {
+        key.push_back((long long)(j - ctx->jobs.data()));
+        key.push_back(j->B);
+        key.push_back(j->H);
+        key.push_back(j->W);
+    }
+    key.push_back(ctx->tune_tw);
+    BatchState* found = nullptr;
+    for (BatchState& b : ctx->batches)
+        if (b.key == key) found = &b;
+    if (!found) {
+        if (ctx->capturing) return fail(ctx, ADMS_ERR_STATE, "new batch during capture: make the same call once before");
+        ctx->batches.emplace_back();
+        found = &ctx->batches.back();
+    }
+    BatchState& bs = *found;
+    *out_bs = found;
+    bool same = key == bs.key;
+    if (backward && same) return ADMS_OK;  // the forward's arguments serve the backward
+    std::vector<ShadeArgs> args(n);
+    std::vector<RasterJob> rargs(n);
+    for (int k = 0; k < n; ++k) {
+        Job& j = *js[k];
+        args[k] = shade_args(j);
+        args[k].ref = j.ref;
+        args[k].loss_acc = &j.st->call_loss;
+        args[k].out_img = out_img ? out_img[k] : nullptr;
+        RasterJob& r = rargs[k];
+        memset(&r, 0, sizeof(r));
+        r.rec = j.rs.rec;
+        r.bin = j.rs.bin;
+        r.F = j.F;
+        r.W = j.W;
+        r.H = j.H;
+        r.tiles_x = (j.W + ADMS_TILE - 1) / ADMS_TILE;
+        r.tiles_y = (j.H + ADMS_TILE - 1) / ADMS_TILE;
+        r.tile_off = j.rs.tile_off;
+        r.tile_count = j.rs.tile_count;
+        r.list = j.rs.list;
+        r.capacity = j.rs.list_capacity;
+        r.keys = j.keys;
+        r.overflow_ctr = j.rs.overflow_ctr;
+    }
+    bool args_same = same && bs.h_args.size() == args.size() &&
+                     memcmp(bs.h_args.data(), args.data(), sizeof(ShadeArgs) * n) == 0 &&
+                     memcmp(bs.h_rargs.data(), rargs.data(), sizeof(RasterJob) * n) == 0;
+    if (args_same) return ADMS_OK;
+    if (ctx->capturing)
+        return fail(ctx, ADMS_ERR_STATE, "batched arguments changed during capture: make the same call once before");
+    adms_status s;
+    if ((size_t)n > bs.cap_args) {
+        if ((s = ctx_alloc(ctx, &bs.d_args, n))) return s;
+        if ((s = ctx_alloc(ctx, &bs.d_rargs, n))) return s;
+        if (!bs.d_counter && (s = ctx_alloc(ctx, &bs.d_counter, 1))) return s;
+        bs.cap_args = n;
+    }
+    bs.h_args = args;
+    bs.h_rargs = rargs;
+    CK(cudaMemcpyAsync(bs.d_args, bs.h_args.data(), sizeof(ShadeArgs) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(bs.d_rargs, bs.h_rargs.data(), sizeof(RasterJob) * n, cudaMemcpyHostToDevice, ctx->stream));
+    if (!same) {
+        int tw = ctx->tune_tw, th = 256 / tw;
+        std::vector<WorkItem> px, rt;
+        for (int k = 0; k < n; ++k) {
+            const Job& j = *js[k];
+            for (int b = 0; b < j.B; ++b) {
+                for (int y0 = 0; y0 < j.H; y0 += th)
+                    for (int x0 = 0; x0 < j.W; x0 += tw) px.push_back({k, b, x0, y0});
+                for (int y0 = 0; y0 < j.H; y0 += ADMS_TILE)
+                    for (int x0 = 0; x0 < j.W; x0 += ADMS_TILE) rt.push_back({k, b, x0, y0});
+            }
+        }
+        if (px.size() > bs.cap_px) {
+            if ((s = ctx_alloc(ctx, &bs.d_px, px.size()))) return s;
+            bs.cap_px = px.size();
+        }
+        if (rt.size() > bs.cap_rt) {
+            if ((s = ctx_alloc(ctx, &bs.d_rt, rt.size()))) return s;
+            bs.cap_rt = rt.size();
+        }
+        CK(cudaMemcpy(bs.d_px, px.data(), px.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(bs.d_rt, rt.data(), rt.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+        bs.n_px = (int)px.size();
+        bs.n_rt = (int)rt.size();
+        bs.key = key;
+    }
+    return ADMS_OK;
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -702,6 +858,8 @@ adms_status adms_ctx_create(adms_ctx** out, size_t hbm_budget_bytes, void* cuda_
     adms_ctx* c = new adms_ctx();
     c->stream = (cudaStream_t)cuda_stream;
     c->budget = hbm_budget_bytes;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) c->sm_count = sms;
     *out = c;
     return ADMS_OK;
 }
@@ -711,7 +869,90 @@ adms_status adms_ctx_destroy(adms_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& j : ctx->jobs)
         if (j.alive) job_free(ctx, j);
+    for (void* p : ctx->batch_allocs) cudaFree(p);
+    for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     delete ctx;
+    return ADMS_OK;
+}
+
+adms_status adms_autotune(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, const adms_view* views,
+                          const int32_t* views_per_job, const int32_t* hw, const float* const* ref_rgb) {
+    if (!ctx || n_jobs < 2) return fail(ctx, ADMS_ERR_ARG, "autotune needs a batch of at least two jobs");
+    if (ctx->capturing || ctx->profile) return fail(ctx, ADMS_ERR_STATE, "autotune while capturing or profiling");
+    const int tws[3] = {8, 16, 32};
+    const int bps[3] = {1, 2, 4};
+    float best_total = 1e30f;
+    int best_tw = ctx->tune_tw, best_b[4] = {ctx->tune_bpsm[0], ctx->tune_bpsm[1], ctx->tune_bpsm[2], ctx->tune_bpsm[3]};
+    cudaEvent_t ev[5];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    std::vector<Job*> js;
+    for (int k = 0; k < n_jobs; ++k) {
+        Job* j = get_job(ctx, jobs[k]);
+        if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+        js.push_back(j);
+    }
+    // a forward sizes every job's scratch; then time each (tile width, blocks per SM) pair
+    adms_status s = adms_forward_loss(ctx, jobs, n_jobs, views, views_per_job, hw, ref_rgb, nullptr, nullptr);
+    if (s) return s;
+    for (int tw : tws) {
+        ctx->tune_tw = tw;
+        BatchState* bsp = nullptr;
+        if ((s = batch_upload(ctx, js, nullptr, &bsp))) return s;
+        BatchState& bs = *bsp;
+        float t_kind[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+        int b_kind[4] = {4, 4, 2, 4};
+        for (int bp : bps) {
+            for (int rep = 0; rep < 2; ++rep) {
+                int blocks = ctx->sm_count * bp;
+                CK(cudaEventRecord(ev[0], ctx->stream));
+                CK(raster_tiles_batched(bs.d_rargs, bs.d_rt, bs.n_rt, bs.d_counter, blocks, ctx->stream));
+                CK(cudaEventRecord(ev[1], ctx->stream));
+                CK(pixels_batched(0, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, tw, blocks, ctx->stream));
+                CK(cudaEventRecord(ev[2], ctx->stream));
+                CK(pixels_batched(1, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, tw, blocks, ctx->stream));
+                CK(cudaEventRecord(ev[3], ctx->stream));
+                if (bp <= 2) CK(pixels_batched(2, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, tw, blocks, ctx->stream));
+                CK(cudaEventRecord(ev[4], ctx->stream));
+                CK(cudaEventSynchronize(ev[4]));
+                if (rep == 0) continue;
+                float t[4];
+                CK(cudaEventElapsedTime(&t[3], ev[0], ev[1]));
+                CK(cudaEventElapsedTime(&t[0], ev[1], ev[2]));
+                CK(cudaEventElapsedTime(&t[1], ev[2], ev[3]));
+                CK(cudaEventElapsedTime(&t[2], ev[3], ev[4]));
+                for (int kk = 0; kk < 4; ++kk) {
+                    if (kk == 2 && bp > 2) continue;
+                    if (t[kk] < t_kind[kk]) {
+                        t_kind[kk] = t[kk];
+                        b_kind[kk] = bp;
+                    }
+                }
+            }
+        }
+        float total = t_kind[0] + t_kind[1] + t_kind[2] + t_kind[3];
+        if (total < best_total) {
+            best_total = total;
+            best_tw = tw;
+            for (int kk = 0; kk < 4; ++kk) best_b[kk] = b_kind[kk];
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    ctx->tune_tw = best_tw;
+    for (int kk = 0; kk < 4; ++kk) ctx->tune_bpsm[kk] = best_b[kk];
+    // leave the jobs as they were: no gradients, no pending forward, no loss recorded
+    for (Job* j : js) {
+        if ((s = adms_job_zero_gradients(ctx, (adms_job)(j - ctx->jobs.data())))) return s;
+        CK(cudaMemsetAsync(j->st, 0, 2 * sizeof(double), ctx->stream));  // call_loss, img_loss
+        j->have_fwd = false;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ADMS_OK;
+}
+
+adms_status adms_ctx_tuning(adms_ctx* ctx, int32_t* out5) {
+    if (!ctx || !out5) return ADMS_ERR_ARG;
+    out5[0] = ctx->tune_tw;
+    for (int k = 0; k < 4; ++k) out5[1 + k] = ctx->tune_bpsm[k];
     return ADMS_OK;
 }
 
@@ -837,11 +1078,15 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
     if (!ctx || !jobs || n_jobs <= 0 || !views || !views_per_job || !hw || !ref_rgb)
         return fail(ctx, ADMS_ERR_ARG, "invalid forward_loss arguments");
     size_t vofs = 0;
+    std::vector<Job*> js;
     for (int k = 0; k < n_jobs; ++k) {
         Job* jp = get_job(ctx, jobs[k]);
         int B = views_per_job[k], H = hw[2 * k], W = hw[2 * k + 1];
         if (!jp || B <= 0 || H <= 0 || W <= 0 || H > 16384 || W > 16384 || !ref_rgb[k])
             return fail(ctx, ADMS_ERR_ARG, "invalid job, view count, size or reference pointer");
+        for (Job* o : js)
+            if (o == jp) return fail(ctx, ADMS_ERR_ARG, "a job appears twice in one call");
+        js.push_back(jp);
         Job& j = *jp;
         adms_status s = ensure_scratch(ctx, j, B, H, W);
         if (s) return s;
@@ -853,24 +1098,47 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
         j.loss_scale = (float)(1.0 / (3.0 * (double)norm_views * H * W));
         CK(cudaMemcpyAsync(j.views, views + vofs, sizeof(adms_view) * B, cudaMemcpyDefault, ctx->stream));
         vofs += B;
-        if ((s = render_core(ctx, j))) return s;
-        ShadeArgs a = shade_args(j);
-        a.ref = j.ref;
-        a.loss_acc = &j.st->call_loss;
-        a.out_img = out_img ? out_img[k] : nullptr;
         CK(cudaMemsetAsync(&j.st->call_loss, 0, sizeof(double), ctx->stream));
-        CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
-        CK(TIMED(ST_SMALL, finish_call_loss(j.st, out_loss ? out_loss + k : nullptr, ctx->stream)));
-        j.have_fwd = true;
+        if (n_jobs == 1) {
+            if ((s = render_core(ctx, j))) return s;
+            ShadeArgs a = shade_args(j);
+            a.ref = j.ref;
+            a.loss_acc = &j.st->call_loss;
+            a.out_img = out_img ? out_img[k] : nullptr;
+            CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
+        } else {
+            if ((s = frame_and_prepare(ctx, j))) return s;
+        }
+    }
+    if (n_jobs > 1) {
+        // one persistent launch per stage over the tiles of every job and view
+        BatchState* bsp = nullptr;
+        adms_status s = batch_upload(ctx, js, out_img, &bsp);
+        if (s) return s;
+        BatchState& bs = *bsp;
+        CK(TIMED(ST_RASTER, raster_tiles_batched(bs.d_rargs, bs.d_rt, bs.n_rt, bs.d_counter,
+                                                 ctx->sm_count * ctx->tune_bpsm[3], ctx->stream)));
+        CK(TIMED(ST_SHADE, pixels_batched(0, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, ctx->tune_tw,
+                                          ctx->sm_count * ctx->tune_bpsm[0], ctx->stream)));
+        CK(TIMED(ST_AA_LOSS, pixels_batched(1, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, ctx->tune_tw,
+                                            ctx->sm_count * ctx->tune_bpsm[1], ctx->stream)));
+    }
+    for (int k = 0; k < n_jobs; ++k) {
+        CK(TIMED(ST_SMALL, finish_call_loss(js[k]->st, out_loss ? out_loss + k : nullptr, ctx->stream)));
+        js[k]->have_fwd = true;
     }
     return ADMS_OK;
 }
 
 adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, int32_t recompute_raster) {
     if (!ctx || !jobs || n_jobs <= 0) return fail(ctx, ADMS_ERR_ARG, "invalid backward arguments");
+    std::vector<Job*> js;
     for (int k = 0; k < n_jobs; ++k) {
         Job* jp = get_job(ctx, jobs[k]);
         if (!jp) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+        for (Job* o : js)
+            if (o == jp) return fail(ctx, ADMS_ERR_ARG, "a job appears twice in one call");
+        js.push_back(jp);
         Job& j = *jp;
         if (!j.have_fwd) return fail(ctx, ADMS_ERR_STATE, "backward without a preceding forward_loss");
         if (recompute_raster) {
@@ -885,10 +1153,23 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
         }
         CK(cudaMemsetAsync(j.g_nrm, 0, sizeof(double) * 3 * j.V, ctx->stream));
         CK(cudaMemsetAsync(j.g_tan, 0, sizeof(double) * 3 * j.V, ctx->stream));
-        ShadeArgs a = shade_args(j);
-        a.ref = j.ref;
         if (j.tess) CK(cudaMemsetAsync(j.g_rpos, 0, sizeof(float) * 3 * j.V, ctx->stream));
-        CK(TIMED(ST_SHADE_BWD, shade_backward(a, ctx->stream)));
+        if (n_jobs == 1) {
+            ShadeArgs a = shade_args(j);
+            a.ref = j.ref;
+            CK(TIMED(ST_SHADE_BWD, shade_backward(a, ctx->stream)));
+        }
+    }
+    if (n_jobs > 1) {
+        BatchState* bsp = nullptr;
+        adms_status s = batch_upload(ctx, js, nullptr, &bsp, true);
+        if (s) return s;
+        BatchState& bs = *bsp;
+        CK(TIMED(ST_SHADE_BWD, pixels_batched(2, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, ctx->tune_tw,
+                                              ctx->sm_count * ctx->tune_bpsm[2], ctx->stream)));
+    }
+    for (int k = 0; k < n_jobs; ++k) {
+        Job& j = *js[k];
         CK(TIMED(ST_FRAME_BWD, frame_backward(frame_args(j), ctx->stream)));
         if (j.tess) {
             // render positions -> base positions, base normals and displacement texels,
@@ -953,6 +1234,11 @@ adms_status adms_job_zero_gradients(adms_ctx* ctx, adms_job job) {
     if (!jp) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
     Job& j = *jp;
     CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.LV, ctx->stream));
+    CK(cudaMemsetAsync(j.g_pos_acc, 0, sizeof(double) * 3 * j.V, ctx->stream));
+    if (j.tess) {
+        CK(cudaMemsetAsync(j.g_rpos, 0, sizeof(float) * 3 * j.V, ctx->stream));
+        CK(cudaMemsetAsync(j.g_bpos_acc, 0, sizeof(double) * 3 * j.LV, ctx->stream));
+    }
     if (j.g_disp) CK(cudaMemsetAsync(j.g_disp, 0, sizeof(float) * j.dh * j.dw, ctx->stream));
     TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
     for (int m = 0; m < 3; ++m)

@@ -105,6 +105,31 @@ cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st);
 cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st);
 cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st);
 
+// one unit of work of a batched launch: a tile of one view of one job
+struct WorkItem {
+    int job, view, x0, y0;
+};
+// persistent launch over work items of many jobs; kind 0 shade, 1 AA + loss, 2 backward;
+// tiles are tw x (256 / tw) pixels; counter: device int (reset here)
+cudaError_t pixels_batched(int kind, const ShadeArgs* jobs, const WorkItem* items, int n_items, int* counter, int tw,
+                           int blocks, cudaStream_t st);
+
+// per-job arguments of the tile raster
+struct RasterJob {
+    const TriRec* rec;
+    const TriBin* bin;
+    int F, W, H, tiles_x, tiles_y;
+    const int* tile_off;
+    const int* tile_count;
+    const int* list;
+    long long capacity;
+    unsigned long long* keys;
+    unsigned long long* overflow_ctr;
+};
+// persistent launch of the 16x16-tile raster over (job, view, tile) items
+cudaError_t raster_tiles_batched(const RasterJob* jobs, const WorkItem* items, int n_items, int* counter, int blocks,
+                                 cudaStream_t st);
+
 // mesh frame (smooth normals, tangents) and its adjoint
 struct FrameArgs {
     int V, F;

@@ -237,15 +237,13 @@ __global__ void k_bin_fill(const TriBin* __restrict__ bin, int F, int B, int til
 // records are staged through shared memory in chunks of 256. Each pixel starts
 // from the key left by the small-triangle pass. A tile whose list did not fit
 // the list buffer scans every binned triangle of its view instead.
-__global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, const TriBin* __restrict__ bin, int F,
-                                                int W, int H, int tiles_x, int tiles_y,
-                                                const int* __restrict__ tile_off, const int* __restrict__ tile_count,
-                                                const int* __restrict__ list, long long capacity,
-                                                unsigned long long* __restrict__ keys,
-                                                unsigned long long* __restrict__ overflow_ctr) {
-    __shared__ TriRec sm[256];
-    int tile = blockIdx.x;
-    int b = blockIdx.y;
+__device__ __forceinline__ void raster_tile_body(const TriRec* __restrict__ rec, const TriBin* __restrict__ bin, int F,
+                                                 int W, int H, int tiles_x, int tiles_y,
+                                                 const int* __restrict__ tile_off, const int* __restrict__ tile_count,
+                                                 const int* __restrict__ list, long long capacity,
+                                                 unsigned long long* __restrict__ keys,
+                                                 unsigned long long* __restrict__ overflow_ctr, int b, int tile,
+                                                 TriRec* sm) {
     int tx = tile % tiles_x, ty = tile / tiles_x;
     int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
     int px = tx * ADMS_TILE + lx, py = ty * ADMS_TILE + ly;
@@ -283,6 +281,46 @@ __global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, 
         }
     }
     if (inside) keys[pix] = best;
+}
+
+__global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, const TriBin* __restrict__ bin, int F,
+                                                int W, int H, int tiles_x, int tiles_y,
+                                                const int* __restrict__ tile_off, const int* __restrict__ tile_count,
+                                                const int* __restrict__ list, long long capacity,
+                                                unsigned long long* __restrict__ keys,
+                                                unsigned long long* __restrict__ overflow_ctr) {
+    __shared__ TriRec sm[256];
+    raster_tile_body(rec, bin, F, W, H, tiles_x, tiles_y, tile_off, tile_count, list, capacity, keys, overflow_ctr,
+                     blockIdx.y, blockIdx.x, sm);
+}
+
+// persistent: blocks take (job, view, tile) items from a counter until none are left
+__global__ void __launch_bounds__(256) k_raster_batch(const RasterJob* __restrict__ jobs,
+                                                      const WorkItem* __restrict__ items, int n,
+                                                      int* __restrict__ counter) {
+    __shared__ TriRec sm[256];
+    __shared__ int s_it;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_it = atomicAdd(counter, 1);
+        __syncthreads();
+        int it = s_it;
+        if (it >= n) break;
+        WorkItem w = items[it];
+        const RasterJob& R = jobs[w.job];
+        int tile = (w.y0 / ADMS_TILE) * R.tiles_x + w.x0 / ADMS_TILE;
+        raster_tile_body(R.rec, R.bin, R.F, R.W, R.H, R.tiles_x, R.tiles_y, R.tile_off, R.tile_count, R.list,
+                         R.capacity, R.keys, R.overflow_ctr, w.view, tile, sm);
+    }
+}
+
+cudaError_t raster_tiles_batched(const RasterJob* jobs, const WorkItem* items, int n_items, int* counter, int blocks,
+                                 cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e) return e;
+    k_raster_batch<<<blocks, 256, 0, st>>>(jobs, items, n_items, counter);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- host launchers

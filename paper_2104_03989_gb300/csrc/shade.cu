@@ -261,11 +261,7 @@ __device__ __forceinline__ ShadeIn shade_inputs(const ShadeArgs& A, const PixGeo
 }
 
 // ------------------------------------------------------------------ shading forward
-__global__ void __launch_bounds__(256) k_shade_fwd(ShadeArgs A) {
-    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    int b = blockIdx.y;
-    int px = (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15);
-    int py = (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4);
+__device__ __forceinline__ void shade_fwd_px(const ShadeArgs& A, int b, int px, int py) {
     if (px >= A.W || py >= A.H) return;
     size_t pix = ((size_t)b * A.H + py) * A.W + px;
     int f = key_tri(A.keys[pix]);
@@ -385,12 +381,9 @@ __device__ __forceinline__ void neighbour(int nbi, int px, int py, int& qx, int&
     qy = py + (nbi == 2 ? -1 : nbi == 3 ? 1 : 0);
 }
 
-__global__ void __launch_bounds__(256) k_aa_loss(ShadeArgs A) {
-    __shared__ double red[8];
-    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    int b = blockIdx.y;
-    int px = (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15);
-    int py = (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4);
+// one block of pixels: AA, loss terms and dL/d(AA colour); the block's loss sum
+// goes to A.loss_acc (block-collective: every thread of the block calls it)
+__device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px, int py, double* red) {
     bool inside = px < A.W && py < A.H;
     double lsum = 0.0;
     if (inside) {
@@ -427,6 +420,7 @@ __global__ void __launch_bounds__(256) k_aa_loss(ShadeArgs A) {
         }
     }
     lsum = warp_sum_d(lsum);
+    __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
     __syncthreads();
     if (threadIdx.x == 0 && A.loss_acc) {
@@ -472,13 +466,8 @@ __device__ __forceinline__ void atomic_add3(double* p, float3 v) {
     atomicAdd(p + 2, (double)v.z);
 }
 
-// two blocks per SM: 128 registers per thread (a few bytes of spills) doubles
-// the resident warps that hide the gather latency of this kernel
-__global__ void __launch_bounds__(256, 2) k_shade_bwd(ShadeArgs A) {
-    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    int b = blockIdx.y;
-    int px = (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15);
-    int py = (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4);
+// one pixel of the fused backward; warp-collective (vertex scatter)
+__device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, int py) {
     bool inside = px < A.W && py < A.H;
     const adms_view& vw = A.views[b];
     float hW = 0.5f * (float)A.W, hH = 0.5f * (float)A.H;
@@ -601,6 +590,67 @@ __global__ void __launch_bounds__(256, 2) k_shade_bwd(ShadeArgs A) {
     scatter_vertex_grads(A, f, vi, vg);
 }
 
+// ------------------------------------------------------------------ single-job kernels (16x16 tiles)
+__global__ void __launch_bounds__(256) k_shade_fwd(ShadeArgs A) {
+    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    shade_fwd_px(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
+                 (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
+}
+
+__global__ void __launch_bounds__(256) k_aa_loss(ShadeArgs A) {
+    __shared__ double red[8];
+    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    aa_loss_block(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
+                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4), red);
+}
+
+// two blocks per SM: 128 registers per thread (a few bytes of spills) doubles
+// the resident warps that hide the gather latency of this kernel
+__global__ void __launch_bounds__(256, 2) k_shade_bwd(ShadeArgs A) {
+    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    shade_bwd_px(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
+                 (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
+}
+
+// ------------------------------------------------------------------ persistent batched kernels
+// One launch covers (job, view, tile) work items of many jobs with different
+// meshes, textures, view counts and resolutions. Each block takes items from a
+// global counter until none are left; a tile is tw x (256 / tw) pixels and the
+// job's arguments are staged in shared memory whenever the job changes.
+__device__ __forceinline__ void stage_args(ShadeArgs& dst, const ShadeArgs* src) {
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(ShadeArgs) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256, KIND == 2 ? 2 : 1)
+    k_pixels_batch(const ShadeArgs* __restrict__ jobs, const WorkItem* __restrict__ items, int n,
+                   int* __restrict__ counter, int tw) {
+    __shared__ ShadeArgs sA;
+    __shared__ int s_it, s_job;
+    __shared__ double red[8];
+    if (threadIdx.x == 0) s_job = -1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_it = atomicAdd(counter, 1);
+        __syncthreads();
+        int it = s_it;
+        if (it >= n) break;
+        WorkItem w = items[it];
+        if (w.job != s_job) {
+            stage_args(sA, jobs + w.job);
+            __syncthreads();
+            if (threadIdx.x == 0) s_job = w.job;
+            __syncthreads();
+        }
+        int px = w.x0 + (int)threadIdx.x % tw, py = w.y0 + (int)threadIdx.x / tw;
+        if (KIND == 0) shade_fwd_px(sA, w.view, px, py);
+        else if (KIND == 1) aa_loss_block(sA, w.view, px, py, red);
+        else shade_bwd_px(sA, w.view, px, py);
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 static dim3 pix_grid(const ShadeArgs& a) {
     int tx = (a.W + ADMS_TILE - 1) / ADMS_TILE, ty = (a.H + ADMS_TILE - 1) / ADMS_TILE;
@@ -619,6 +669,17 @@ cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st) {
 }
 cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st) {
     k_shade_bwd<<<pix_grid(a), 256, 0, st>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t pixels_batched(int kind, const ShadeArgs* jobs, const WorkItem* items, int n_items, int* counter, int tw,
+                           int blocks, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e) return e;
+    if (kind == 0) k_pixels_batch<0><<<blocks, 256, 0, st>>>(jobs, items, n_items, counter, tw);
+    else if (kind == 1) k_pixels_batch<1><<<blocks, 256, 0, st>>>(jobs, items, n_items, counter, tw);
+    else k_pixels_batch<2><<<blocks, 256, 0, st>>>(jobs, items, n_items, counter, tw);
     count_launches(1);
     return cudaGetLastError();
 }
