@@ -151,7 +151,22 @@ size_t adms_bytes_in_use(adms_ctx* ctx);
  * seed is kept with the job (checkpointed). Synchronises the stream. */
 adms_status adms_job_create(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
                             const adms_opt_params* opt, uint64_t seed, adms_job* out);
+/* Free a job's resident state and the batched argument lists of every job set
+ * it was part of; graphs that recorded calls on this job must not be launched
+ * afterwards. Synchronises the stream. */
 adms_status adms_job_destroy(adms_ctx* ctx, adms_job job);
+/* Free the cached argument and work-item lists of all batched (n_jobs > 1)
+ * calls; the next batched call rebuilds its own. Graphs that recorded a batched
+ * call must not be launched afterwards. For schedulers whose job set changes
+ * (a set's lists live until one of its jobs is destroyed otherwise).
+ * Synchronises the stream. */
+adms_status adms_ctx_release_batches(adms_ctx* ctx);
+/* Allocate the job's per-call render scratch for n_views views of H x W now
+ * (keys, per-pixel buffers, per-view transforms, bins), so that later calls of
+ * that size or smaller allocate nothing for this job. Lets a scheduler admit
+ * work against the HBM budget up front: ADMS_ERR_BUDGET if it does not fit
+ * (the job stays valid), ADMS_ERR_ARG for non-positive or > 16384 sizes. */
+adms_status adms_job_reserve(adms_ctx* ctx, adms_job job, int32_t n_views, int32_t H, int32_t W);
 adms_status adms_job_params(adms_ctx* ctx, adms_job job, adms_param_view* out);
 adms_status adms_job_stats(adms_ctx* ctx, adms_job job, adms_stats* out);
 

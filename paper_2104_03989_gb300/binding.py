@@ -82,6 +82,8 @@ SIGNATURES = {
     "adms_job_create": ([P, C.POINTER(adms_mesh_desc), C.POINTER(adms_material_desc), C.POINTER(adms_opt_params),
                          C.c_uint64, C.POINTER(C.c_int32)], C.c_int),
     "adms_job_destroy": ([P, C.c_int32], C.c_int),
+    "adms_job_reserve": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32], C.c_int),
+    "adms_ctx_release_batches": ([P], C.c_int),
     "adms_job_params": ([P, C.c_int32, C.POINTER(adms_param_view)], C.c_int),
     "adms_job_stats": ([P, C.c_int32, C.POINTER(adms_stats)], C.c_int),
     "adms_render_reference": ([P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P], C.c_int),
@@ -205,6 +207,14 @@ def adms_job_create(ctx, mesh, mat, opt=None, seed=0):
 
 def adms_job_destroy(ctx, job):
     _check(ctx, lib().adms_job_destroy(ctx, job))
+
+
+def adms_ctx_release_batches(ctx):
+    _check(ctx, lib().adms_ctx_release_batches(ctx))
+
+
+def adms_job_reserve(ctx, job, n_views, H, W):
+    _check(ctx, lib().adms_job_reserve(ctx, job, int(n_views), int(H), int(W)))
 
 
 def adms_job_params(ctx, job):

@@ -136,6 +136,12 @@ struct BatchState {
     size_t cap_args = 0, cap_px = 0, cap_rt = 0;
     int n_px = 0, n_rt = 0;
     std::vector<void*> allocs;
+    size_t bytes = 0;
+    bool has_job(long long job) const {  // key layout: 4 entries per job, then the tile width
+        for (size_t k = 0; k + 4 < key.size(); k += 4)
+            if (key[k] == job) return true;
+        return false;
+    }
 };
 
 struct adms_ctx {
@@ -148,7 +154,6 @@ struct adms_ctx {
     // one argument / work-item state per job set (and tile width): a graph recorded
     // for one batch keeps valid device arguments while other batches run
     std::vector<BatchState> batches;
-    std::vector<void*> batch_allocs;
     int sm_count = 148;
     // tile width (pixels; tiles are tw x 256/tw) and persistent blocks per SM of the
     // batched launches: [shade, aa+loss, backward, raster]; set by adms_autotune
@@ -736,17 +741,37 @@ adms_status frame_and_prepare(adms_ctx* ctx, Job& j) {
 }
 
 template <typename T>
-adms_status ctx_alloc(adms_ctx* ctx, T** out, size_t count) {
+adms_status batch_alloc(adms_ctx* ctx, BatchState& bs, T** out, size_t count) {
     size_t bytes = ((std::max<size_t>(count, 1) * sizeof(T)) + 255) & ~size_t(255);
     if (ctx->capturing) return fail(ctx, ADMS_ERR_STATE, "batched launch needs new scratch during capture");
     if (ctx->budget && ctx->in_use + bytes > ctx->budget) return fail(ctx, ADMS_ERR_BUDGET, "HBM budget exceeded");
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) return fail(ctx, ADMS_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    ctx->batch_allocs.push_back(p);
+    bs.allocs.push_back(p);
+    bs.bytes += bytes;
     ctx->in_use += bytes;
     *out = static_cast<T*>(p);
     return ADMS_OK;
+}
+
+void batch_free(adms_ctx* ctx, BatchState& bs) {
+    for (void* p : bs.allocs) cudaFree(p);
+    ctx->in_use -= std::min(ctx->in_use, bs.bytes);
+    bs = BatchState();
+}
+
+// drop the batched argument lists of every job set that holds this job (the
+// caller has synchronized the stream)
+void batch_release(adms_ctx* ctx, long long job) {
+    std::vector<BatchState> keep;
+    for (BatchState& b : ctx->batches) {
+        if (b.has_job(job))
+            batch_free(ctx, b);
+        else
+            keep.push_back(std::move(b));
+    }
+    ctx->batches = std::move(keep);
 }
 
 // Arguments and work items of a batched call. Uploaded only when the job set,
@@ -807,9 +832,9 @@ adms_status batch_upload(adms_ctx* ctx, const std::vector<Job*>& js, float* cons
         return fail(ctx, ADMS_ERR_STATE, "batched arguments changed during capture: make the same call once before");
     adms_status s;
     if ((size_t)n > bs.cap_args) {
-        if ((s = ctx_alloc(ctx, &bs.d_args, n))) return s;
-        if ((s = ctx_alloc(ctx, &bs.d_rargs, n))) return s;
-        if (!bs.d_counter && (s = ctx_alloc(ctx, &bs.d_counter, 1))) return s;
+        if ((s = batch_alloc(ctx, bs, &bs.d_args, n))) return s;
+        if ((s = batch_alloc(ctx, bs, &bs.d_rargs, n))) return s;
+        if (!bs.d_counter && (s = batch_alloc(ctx, bs, &bs.d_counter, 1))) return s;
         bs.cap_args = n;
     }
     bs.h_args = args;
@@ -829,11 +854,11 @@ adms_status batch_upload(adms_ctx* ctx, const std::vector<Job*>& js, float* cons
             }
         }
         if (px.size() > bs.cap_px) {
-            if ((s = ctx_alloc(ctx, &bs.d_px, px.size()))) return s;
+            if ((s = batch_alloc(ctx, bs, &bs.d_px, px.size()))) return s;
             bs.cap_px = px.size();
         }
         if (rt.size() > bs.cap_rt) {
-            if ((s = ctx_alloc(ctx, &bs.d_rt, rt.size()))) return s;
+            if ((s = batch_alloc(ctx, bs, &bs.d_rt, rt.size()))) return s;
             bs.cap_rt = rt.size();
         }
         CK(cudaMemcpy(bs.d_px, px.data(), px.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
@@ -869,7 +894,7 @@ adms_status adms_ctx_destroy(adms_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& j : ctx->jobs)
         if (j.alive) job_free(ctx, j);
-    for (void* p : ctx->batch_allocs) cudaFree(p);
+    for (BatchState& b : ctx->batches) batch_free(ctx, b);
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     delete ctx;
     return ADMS_OK;
@@ -992,7 +1017,24 @@ adms_status adms_job_destroy(adms_ctx* ctx, adms_job job) {
     if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
     CK(cudaStreamSynchronize(ctx->stream));
     job_free(ctx, *j);
+    batch_release(ctx, job);
     return ADMS_OK;
+}
+
+adms_status adms_ctx_release_batches(adms_ctx* ctx) {
+    if (!ctx) return ADMS_ERR_ARG;
+    if (ctx->capturing) return fail(ctx, ADMS_ERR_STATE, "cannot release batched state during capture");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (BatchState& b : ctx->batches) batch_free(ctx, b);
+    ctx->batches.clear();
+    return ADMS_OK;
+}
+
+adms_status adms_job_reserve(adms_ctx* ctx, adms_job job, int32_t n_views, int32_t H, int32_t W) {
+    Job* j = get_job(ctx, job);
+    if (!j || n_views <= 0 || H <= 0 || W <= 0 || H > 16384 || W > 16384)
+        return fail(ctx, ADMS_ERR_ARG, "invalid job handle or size");
+    return ensure_scratch(ctx, *j, n_views, H, W);
 }
 
 adms_status adms_job_params(adms_ctx* ctx, adms_job job, adms_param_view* out) {

@@ -77,6 +77,12 @@ class Context:
     def destroy_job(self, job):
         B.adms_job_destroy(self.ctx, job)
 
+    def reserve(self, job, n_views, H, W):
+        B.adms_job_reserve(self.ctx, job, n_views, H, W)
+
+    def bytes_in_use(self):
+        return B.adms_bytes_in_use(self.ctx)
+
     def params(self, job):
         """torch views of a job's latents and gradients (level 0 of textures)."""
         pv = B.adms_job_params(self.ctx, job)

@@ -19,6 +19,21 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
+def sphere_scene(freq, tex, seed, tess=0):
+    """A frequency-`freq` icosphere with tex^2 noise maps, every latent
+    optimized; with tess > 0 also a 32^2 random displacement map and that many
+    levels of edge-midpoint splitting."""
+    from synth.workloads import Scene
+    p, tri = synth.icosphere(freq)
+    uv, tri_uv = synth.equirect_uv_corners(p, tri)
+    mesh = synth.Mesh(p.astype(np.float32), uv, tri, tri_uv)
+    kd, nrm = synth.noise_textures(tex, seed=seed)
+    orm = synth.scenes.uniform_orm(tex, seed)
+    disp = np.random.default_rng(seed).uniform(-0.02, 0.02, (32, 32)).astype(np.float32) if tess else None
+    return Scene(mesh=mesh, kd=kd, orm=orm, nrm=nrm, disp=disp, tess_levels=tess,
+                 optimize={"pos": True, "kd": True, "orm": True, "nrm": True, "disp": bool(tess)})
+
+
 def small_case():
     """One 256^2 view, 320-tri candidate with 256^2 maps vs the 20,480-tri reference, plain L1."""
     c = synth.config_small()

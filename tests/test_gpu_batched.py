@@ -8,22 +8,9 @@ import pytest
 import torch
 
 import synth
-from synth.workloads import Scene
-
-from cases import rel_l2
+from cases import rel_l2, sphere_scene as _scene
 
 pytestmark = pytest.mark.gpu
-
-
-def _scene(freq, tex, seed, tess=0):
-    p, tri = synth.icosphere(freq)
-    uv, tri_uv = synth.equirect_uv_corners(p, tri)
-    mesh = synth.Mesh(p.astype(np.float32), uv, tri, tri_uv)
-    kd, nrm = synth.noise_textures(tex, seed=seed)
-    orm = synth.scenes.uniform_orm(tex, seed)
-    disp = np.random.default_rng(seed).uniform(-0.02, 0.02, (32, 32)).astype(np.float32) if tess else None
-    return Scene(mesh=mesh, kd=kd, orm=orm, nrm=nrm, disp=disp, tess_levels=tess,
-                 optimize={"pos": True, "kd": True, "orm": True, "nrm": True, "disp": bool(tess)})
 
 
 SPECS = [  # (freq, texture, views, H, W, tessellation levels)
