@@ -500,8 +500,11 @@ def srgb(x):
 
 
 def tonemap(x):
-    """x' = Gamma(log(x + 1)), natural log (reading of Sec. 5.3)."""
-    return srgb(torch.log(x + 1))
+    """x' = Gamma(log(x + 1)), natural log (reading of Sec. 5.3), of the
+    radiance clamped at 0: the antialiasing blends can leave a pixel below
+    zero and even below -1, where the log has no value (reading: a negative
+    colour counts as black). torch.clamp keeps NaN."""
+    return srgb(torch.log(torch.clamp(x, min=0.0) + 1))
 
 
 def image_loss(img, ref, kind):

@@ -345,10 +345,16 @@ __device__ __forceinline__ bool pair_eval(const ShadeArgs& A, int b, int px, int
 
 __device__ __forceinline__ float3 f3of(float4 a) { return f3(a.x, a.y, a.z); }
 
-// Gamma(log(x + 1)) with the sRGB Gamma of Sec. 5.3, and its derivative
+// Gamma(log(max(x, 0) + 1)) with the sRGB Gamma of Sec. 5.3, and its
+// derivative. Radiance is non-negative; the antialiasing blends can undershoot
+// below zero beside a bright pixel (a pixel blended toward several darker
+// neighbours), and log(x + 1) has no value below -1, so negative colours count
+// as black (derivative 0). NaN stays NaN.
 __device__ __forceinline__ float tonemap(float x, float* dfdx) {
+    bool neg = x < 0.f;
+    if (neg) x = 0.f;
     float y = log1pf(x);
-    float dy = 1.f / (1.f + x);
+    float dy = neg ? 0.f : 1.f / (1.f + x);
     if (y <= 0.0031308f) {
         *dfdx = 12.92f * dy;
         return 12.92f * y;

@@ -207,3 +207,25 @@ def test_ragged_size_and_empty_view(ctx):
     p = ctx.params(job)
     assert rel_l2(p["g_pos"].double().cpu().numpy(), orc["grads"]["pos"]) < GRAD_TOL
     ctx.destroy_job(job)
+
+
+def test_negative_reference_radiance(ctx):
+    """The tone map counts negative radiance as black on both sides (a pixel
+    below -1 has no log(x + 1)): a reference with patches at -2.5 and -0.5
+    gives a finite loss and the oracle's loss and gradients."""
+    c, views, H, W = plain_case(res=64, n_views=2, tex=64, ref_tex=64, ref_freq=16, seed=9)
+    ref_np, _ = oracle_reference(c["ref"], views, H, W)
+    ref_np = ref_np.copy()
+    ref_np[0, 20:36, 20:36, :] = -2.5
+    ref_np[1, 10:30, 30:50, 1] = -0.5
+    refs = torch.as_tensor(ref_np).cuda()
+    job = ctx.create_job(c["cand"], loss="logl1", lr0=0.01)
+    loss = float(ctx.forward_loss([job], [views], [refs])[0])
+    ctx.backward([job])
+    torch.cuda.synchronize()
+    orc = oracle_grads(c["cand"], views, ref_np, H, W, "logl1")
+    assert np.isfinite(loss) and abs(loss - orc["loss"]) / orc["loss"] < IMG_TOL
+    p = ctx.params(job)
+    got = fold_mips(p["g_kd_chain"].cpu(), *p["kd"].shape[:2], p["kd_levels"]).numpy()
+    assert rel_l2(got, orc["grads"]["kd"]) < GRAD_TOL
+    ctx.destroy_job(job)

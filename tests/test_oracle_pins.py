@@ -319,6 +319,21 @@ def test_tonemap_values():
     assert float(y[1]) == pytest.approx(1.0)   # Gamma(1) = 1.055 - 0.055
 
 
+def test_tonemap_counts_negative_radiance_as_black():
+    # below zero (and below -1, where log(x + 1) has no value) the tone map is
+    # flat at Gamma(log 1) = 0 with zero slope; NaN is kept so a broken job shows
+    x = torch.tensor([-3.0, -1.0, -0.25, 0.0, 0.5], dtype=F64, requires_grad=True)
+    y = R.tonemap(x)
+    assert torch.all(y[:4] == 0.0) and float(y[4]) > 0.0
+    (g,) = torch.autograd.grad(y.sum(), x)
+    assert torch.all(g[:3] == 0.0) and float(g[4]) > 0.0
+    assert math.isnan(float(R.tonemap(torch.as_tensor([float("nan")], dtype=F64))[0]))
+    a = torch.as_tensor([[[[-2.0, 0.3, 0.1]]]], dtype=F64)
+    b = torch.as_tensor([[[[0.0, 0.3, 0.1]]]], dtype=F64)
+    ref = torch.full_like(a, 0.2)
+    assert float(R.image_loss(a, ref, "logl1")) == float(R.image_loss(b, ref, "logl1"))
+
+
 @pytest.mark.parametrize("kind", ["l1", "logl1", "l2"])
 def test_loss_zero_at_equality_with_zero_gradient(kind):
     rng = np.random.default_rng(0)
