@@ -239,17 +239,23 @@ adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
 /* adms_forward_loss and adms_backward with n_jobs > 1 run the per-pixel stages
  * (tile raster, shading, AA + loss, fused backward) as one persistent launch
  * each over (job, view, tile) work items of every job, whatever their meshes,
- * textures, view counts and resolutions. adms_autotune times those launches
- * on the given batch for tile widths 8, 16, 32 pixels (tiles of 256 pixels)
- * and 1, 2, 4 resident blocks per SM, and keeps the fastest choice in the
- * context. It leaves the jobs as it found them (gradients zeroed, no pending
- * forward, no recorded loss) and synchronises the stream. Arguments as for
- * adms_forward_loss. */
+ * textures, view counts and resolutions. Block k of a launch takes items k,
+ * k + grid, ...; the grid is SMs x blocks per SM, at most the resident count
+ * (persistent), or one block per item (blocks per SM = 0). adms_autotune
+ * times those launches on the given batch for tile widths 8, 16, 32 pixels
+ * (tiles of 256 pixels) with one block per item and with half the resident
+ * blocks per SM up to all of them, and keeps the fastest choice. It leaves the
+ * jobs as it found them (gradients zeroed, no pending forward, no recorded
+ * loss) and synchronises the stream. Arguments as for adms_forward_loss. */
 adms_status adms_autotune(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, const adms_view* views,
                           const int32_t* views_per_job, const int32_t* hw, const float* const* ref_rgb);
 /* The context's batched-launch choices: out5 = {tile width, blocks per SM for
  * shading, AA + loss, backward, raster}. */
 adms_status adms_ctx_tuning(adms_ctx* ctx, int32_t* out5);
+/* Set those choices (same layout); blocks per SM <= 0 select one block per
+ * item, others are clamped to the resident count. ADMS_ERR_ARG for a tile width other than 8, 16 or 32. Calls already
+ * recorded into a graph keep the choices they were recorded with. */
+adms_status adms_ctx_set_tuning(adms_ctx* ctx, const int32_t* in5);
 
 /* ---- visibility without allocation -------------------------------------------- */
 

@@ -101,6 +101,7 @@ SIGNATURES = {
     "adms_visibility_noalloc": ([P, C.c_int32, P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
     "adms_autotune": ([P, P, C.c_int32, P, P, P, P], C.c_int),
     "adms_ctx_tuning": ([P, P], C.c_int),
+    "adms_ctx_set_tuning": ([P, C.POINTER(C.c_int32)], C.c_int),
     "adms_graph_begin": ([P], C.c_int),
     "adms_graph_end": ([P, C.POINTER(P)], C.c_int),
     "adms_graph_launch": ([P, P], C.c_int),
@@ -295,6 +296,10 @@ def adms_autotune(ctx, jobs, views, views_per_job, hw, ref_rgb):
     hw_a = (C.c_int32 * (2 * n))(*[int(x) for p in hw for x in p])
     refs = (C.c_void_p * n)(*[ptr(r) for r in ref_rgb])
     _check(ctx, lib().adms_autotune(ctx, jobs_a, n, ptr(views), vpj, hw_a, refs))
+
+
+def adms_ctx_set_tuning(ctx, tile_w, shade, aa_loss, backward, raster):
+    _check(ctx, lib().adms_ctx_set_tuning(ctx, (C.c_int32 * 5)(tile_w, shade, aa_loss, backward, raster)))
 
 
 def adms_ctx_tuning(ctx):

@@ -126,15 +126,12 @@ struct adms_graph {
 // device-side arguments and work items of the batched (many-job) launches
 struct BatchState {
     std::vector<long long> key;  // (job, B, H, W) per job + tile width: the item lists depend on it
-    std::vector<ShadeArgs> h_args;
+    std::vector<ShadeArgs> h_args;   // passed to each launch as kernel parameters
     std::vector<RasterJob> h_rargs;
-    ShadeArgs* d_args = nullptr;
-    RasterJob* d_rargs = nullptr;
+    std::vector<int> px_off, rt_off;  // job k's items: [off[k], off[k + 1])
     WorkItem* d_px = nullptr;
     WorkItem* d_rt = nullptr;
-    int* d_counter = nullptr;
-    size_t cap_args = 0, cap_px = 0, cap_rt = 0;
-    int n_px = 0, n_rt = 0;
+    size_t cap_px = 0, cap_rt = 0;
     std::vector<void*> allocs;
     size_t bytes = 0;
     bool has_job(long long job) const {  // key layout: 4 entries per job, then the tile width
@@ -158,7 +155,10 @@ struct adms_ctx {
     // tile width (pixels; tiles are tw x 256/tw) and persistent blocks per SM of the
     // batched launches: [shade, aa+loss, backward, raster]; set by adms_autotune
     int tune_tw = 16;
-    int tune_bpsm[4] = {4, 4, 2, 4};
+    // (0: one block per item, the default: the ~4k-instruction pixel kernels lose
+    // instruction-cache locality when persistent blocks drift apart in the loop)
+    int tune_bpsm[4] = {0, 0, 0, 0};
+    int occ[4] = {4, 4, 2, 4};  // resident blocks per SM of each persistent kernel
     // optional per-stage timing with CUDA events on the context's stream
     bool profile = false;
     std::vector<cudaEvent_t> pool;
@@ -761,6 +761,12 @@ void batch_free(adms_ctx* ctx, BatchState& bs) {
     bs = BatchState();
 }
 
+// grid of a batched launch: SMs x blocks per SM (persistent), or one block per
+// item when the tuning says 0 (the launchers clamp the grid to the item count)
+int batch_grid(const adms_ctx* ctx, int kind) {
+    return ctx->tune_bpsm[kind] > 0 ? ctx->sm_count * ctx->tune_bpsm[kind] : INT32_MAX;
+}
+
 // drop the batched argument lists of every job set that holds this job (the
 // caller has synchronized the stream)
 void batch_release(adms_ctx* ctx, long long job) {
@@ -824,26 +830,16 @@ adms_status batch_upload(adms_ctx* ctx, const std::vector<Job*>& js, float* cons
         r.keys = j.keys;
         r.overflow_ctr = j.rs.overflow_ctr;
     }
-    bool args_same = same && bs.h_args.size() == args.size() &&
-                     memcmp(bs.h_args.data(), args.data(), sizeof(ShadeArgs) * n) == 0 &&
-                     memcmp(bs.h_rargs.data(), rargs.data(), sizeof(RasterJob) * n) == 0;
-    if (args_same) return ADMS_OK;
-    if (ctx->capturing)
-        return fail(ctx, ADMS_ERR_STATE, "batched arguments changed during capture: make the same call once before");
-    adms_status s;
-    if ((size_t)n > bs.cap_args) {
-        if ((s = batch_alloc(ctx, bs, &bs.d_args, n))) return s;
-        if ((s = batch_alloc(ctx, bs, &bs.d_rargs, n))) return s;
-        if (!bs.d_counter && (s = batch_alloc(ctx, bs, &bs.d_counter, 1))) return s;
-        bs.cap_args = n;
-    }
     bs.h_args = args;
     bs.h_rargs = rargs;
-    CK(cudaMemcpyAsync(bs.d_args, bs.h_args.data(), sizeof(ShadeArgs) * n, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(bs.d_rargs, bs.h_rargs.data(), sizeof(RasterJob) * n, cudaMemcpyHostToDevice, ctx->stream));
+    adms_status s;
     if (!same) {
+        if (ctx->capturing)
+            return fail(ctx, ADMS_ERR_STATE, "new batched work items during capture: make the same call once before");
         int tw = ctx->tune_tw, th = 256 / tw;
         std::vector<WorkItem> px, rt;
+        bs.px_off.assign(1, 0);
+        bs.rt_off.assign(1, 0);
         for (int k = 0; k < n; ++k) {
             const Job& j = *js[k];
             for (int b = 0; b < j.B; ++b) {
@@ -852,6 +848,8 @@ adms_status batch_upload(adms_ctx* ctx, const std::vector<Job*>& js, float* cons
                 for (int y0 = 0; y0 < j.H; y0 += ADMS_TILE)
                     for (int x0 = 0; x0 < j.W; x0 += ADMS_TILE) rt.push_back({k, b, x0, y0});
             }
+            bs.px_off.push_back((int)px.size());
+            bs.rt_off.push_back((int)rt.size());
         }
         if (px.size() > bs.cap_px) {
             if ((s = batch_alloc(ctx, bs, &bs.d_px, px.size()))) return s;
@@ -863,8 +861,6 @@ adms_status batch_upload(adms_ctx* ctx, const std::vector<Job*>& js, float* cons
         }
         CK(cudaMemcpy(bs.d_px, px.data(), px.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(bs.d_rt, rt.data(), rt.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
-        bs.n_px = (int)px.size();
-        bs.n_rt = (int)rt.size();
         bs.key = key;
     }
     return ADMS_OK;
@@ -885,6 +881,7 @@ adms_status adms_ctx_create(adms_ctx** out, size_t hbm_budget_bytes, void* cuda_
     c->budget = hbm_budget_bytes;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) c->sm_count = sms;
+    for (int k = 0; k < 4; ++k) c->occ[k] = adms::batched_occupancy(k);
     *out = c;
     return ADMS_OK;
 }
@@ -905,10 +902,9 @@ adms_status adms_autotune(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, c
     if (!ctx || n_jobs < 2) return fail(ctx, ADMS_ERR_ARG, "autotune needs a batch of at least two jobs");
     if (ctx->capturing || ctx->profile) return fail(ctx, ADMS_ERR_STATE, "autotune while capturing or profiling");
     const int tws[3] = {8, 16, 32};
-    const int bps[3] = {1, 2, 4};
     float best_total = 1e30f;
     int best_tw = ctx->tune_tw, best_b[4] = {ctx->tune_bpsm[0], ctx->tune_bpsm[1], ctx->tune_bpsm[2], ctx->tune_bpsm[3]};
-    cudaEvent_t ev[5];
+    cudaEvent_t ev[2];
     for (auto& e : ev) CK(cudaEventCreate(&e));
     std::vector<Job*> js;
     for (int k = 0; k < n_jobs; ++k) {
@@ -916,7 +912,10 @@ adms_status adms_autotune(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, c
         if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
         js.push_back(j);
     }
-    // a forward sizes every job's scratch; then time each (tile width, blocks per SM) pair
+    // a forward sizes every job's scratch; then time each kernel at each tile
+    // width with one block per item and with persistent grids of occ/2 .. occ
+    // resident blocks per SM (second of two runs; every kernel here is
+    // idempotent or accumulates into buffers reset below)
     adms_status s = adms_forward_loss(ctx, jobs, n_jobs, views, views_per_job, hw, ref_rgb, nullptr, nullptr);
     if (s) return s;
     for (int tw : tws) {
@@ -924,41 +923,40 @@ adms_status adms_autotune(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, c
         BatchState* bsp = nullptr;
         if ((s = batch_upload(ctx, js, nullptr, &bsp))) return s;
         BatchState& bs = *bsp;
-        float t_kind[4] = {1e30f, 1e30f, 1e30f, 1e30f};
-        int b_kind[4] = {4, 4, 2, 4};
-        for (int bp : bps) {
-            for (int rep = 0; rep < 2; ++rep) {
-                int blocks = ctx->sm_count * bp;
-                CK(cudaEventRecord(ev[0], ctx->stream));
-                CK(raster_tiles_batched(bs.d_rargs, bs.d_rt, bs.n_rt, bs.d_counter, blocks, ctx->stream));
-                CK(cudaEventRecord(ev[1], ctx->stream));
-                CK(pixels_batched(0, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, tw, blocks, ctx->stream));
-                CK(cudaEventRecord(ev[2], ctx->stream));
-                CK(pixels_batched(1, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, tw, blocks, ctx->stream));
-                CK(cudaEventRecord(ev[3], ctx->stream));
-                if (bp <= 2) CK(pixels_batched(2, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, tw, blocks, ctx->stream));
-                CK(cudaEventRecord(ev[4], ctx->stream));
-                CK(cudaEventSynchronize(ev[4]));
-                if (rep == 0) continue;
-                float t[4];
-                CK(cudaEventElapsedTime(&t[3], ev[0], ev[1]));
-                CK(cudaEventElapsedTime(&t[0], ev[1], ev[2]));
-                CK(cudaEventElapsedTime(&t[1], ev[2], ev[3]));
-                CK(cudaEventElapsedTime(&t[2], ev[3], ev[4]));
-                for (int kk = 0; kk < 4; ++kk) {
-                    if (kk == 2 && bp > 2) continue;
-                    if (t[kk] < t_kind[kk]) {
-                        t_kind[kk] = t[kk];
-                        b_kind[kk] = bp;
+        float total = 0.f;
+        int b_kind[4] = {best_b[0], best_b[1], best_b[2], best_b[3]};
+        for (int kind = 0; kind < 4; ++kind) {
+            if (kind == 3 && tw != tws[0]) continue;  // the raster's items do not depend on tw
+            float t_best = 1e30f;
+            std::vector<int> cands(1, 0);  // 0: one block per item
+            for (int bp = std::max(1, ctx->occ[kind] / 2); bp <= ctx->occ[kind]; ++bp) cands.push_back(bp);
+            for (int bp : cands) {
+                for (int rep = 0; rep < 2; ++rep) {
+                    int blocks = bp ? ctx->sm_count * bp : INT32_MAX;
+                    CK(cudaEventRecord(ev[0], ctx->stream));
+                    if (kind == 3)
+                        CK(raster_tiles_batched(bs.h_rargs.data(), bs.rt_off.data(), n_jobs, bs.d_rt, blocks,
+                                                ctx->stream));
+                    else
+                        CK(pixels_batched(kind, bs.h_args.data(), bs.px_off.data(), n_jobs, bs.d_px, tw, blocks,
+                                          ctx->stream));
+                    CK(cudaEventRecord(ev[1], ctx->stream));
+                    CK(cudaEventSynchronize(ev[1]));
+                    float t = 0.f;
+                    CK(cudaEventElapsedTime(&t, ev[0], ev[1]));
+                    if (rep == 1 && t < t_best) {
+                        t_best = t;
+                        b_kind[kind] = bp;
                     }
                 }
             }
+            if (kind == 3) best_b[3] = b_kind[3];
+            else total += t_best;
         }
-        float total = t_kind[0] + t_kind[1] + t_kind[2] + t_kind[3];
         if (total < best_total) {
             best_total = total;
             best_tw = tw;
-            for (int kk = 0; kk < 4; ++kk) best_b[kk] = b_kind[kk];
+            for (int kk = 0; kk < 3; ++kk) best_b[kk] = b_kind[kk];
         }
     }
     for (auto& e : ev) cudaEventDestroy(e);
@@ -971,6 +969,14 @@ adms_status adms_autotune(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, c
         j->have_fwd = false;
     }
     CK(cudaStreamSynchronize(ctx->stream));
+    return ADMS_OK;
+}
+
+adms_status adms_ctx_set_tuning(adms_ctx* ctx, const int32_t* in5) {
+    if (!ctx || !in5) return ADMS_ERR_ARG;
+    if (in5[0] != 8 && in5[0] != 16 && in5[0] != 32) return fail(ctx, ADMS_ERR_ARG, "tile width must be 8, 16 or 32");
+    ctx->tune_tw = in5[0];
+    for (int k = 0; k < 4; ++k) ctx->tune_bpsm[k] = in5[1 + k] <= 0 ? 0 : std::min(in5[1 + k], ctx->occ[k]);
     return ADMS_OK;
 }
 
@@ -1158,12 +1164,12 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
         adms_status s = batch_upload(ctx, js, out_img, &bsp);
         if (s) return s;
         BatchState& bs = *bsp;
-        CK(TIMED(ST_RASTER, raster_tiles_batched(bs.d_rargs, bs.d_rt, bs.n_rt, bs.d_counter,
-                                                 ctx->sm_count * ctx->tune_bpsm[3], ctx->stream)));
-        CK(TIMED(ST_SHADE, pixels_batched(0, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, ctx->tune_tw,
-                                          ctx->sm_count * ctx->tune_bpsm[0], ctx->stream)));
-        CK(TIMED(ST_AA_LOSS, pixels_batched(1, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, ctx->tune_tw,
-                                            ctx->sm_count * ctx->tune_bpsm[1], ctx->stream)));
+        CK(TIMED(ST_RASTER, raster_tiles_batched(bs.h_rargs.data(), bs.rt_off.data(), n_jobs, bs.d_rt,
+                                                 batch_grid(ctx, 3), ctx->stream)));
+        CK(TIMED(ST_SHADE, pixels_batched(0, bs.h_args.data(), bs.px_off.data(), n_jobs, bs.d_px, ctx->tune_tw,
+                                          batch_grid(ctx, 0), ctx->stream)));
+        CK(TIMED(ST_AA_LOSS, pixels_batched(1, bs.h_args.data(), bs.px_off.data(), n_jobs, bs.d_px, ctx->tune_tw,
+                                            batch_grid(ctx, 1), ctx->stream)));
     }
     for (int k = 0; k < n_jobs; ++k) {
         CK(TIMED(ST_SMALL, finish_call_loss(js[k]->st, out_loss ? out_loss + k : nullptr, ctx->stream)));
@@ -1207,8 +1213,8 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
         adms_status s = batch_upload(ctx, js, nullptr, &bsp, true);
         if (s) return s;
         BatchState& bs = *bsp;
-        CK(TIMED(ST_SHADE_BWD, pixels_batched(2, bs.d_args, bs.d_px, bs.n_px, bs.d_counter, ctx->tune_tw,
-                                              ctx->sm_count * ctx->tune_bpsm[2], ctx->stream)));
+        CK(TIMED(ST_SHADE_BWD, pixels_batched(2, bs.h_args.data(), bs.px_off.data(), n_jobs, bs.d_px, ctx->tune_tw,
+                                              batch_grid(ctx, 2), ctx->stream)));
     }
     for (int k = 0; k < n_jobs; ++k) {
         Job& j = *js[k];

@@ -1,7 +1,9 @@
 // Kernel-side data structures and host launchers of the render-and-compare step.
 #pragma once
 
+#include <algorithm>
 #include <atomic>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -109,10 +111,21 @@ cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st);
 struct WorkItem {
     int job, view, x0, y0;
 };
-// persistent launch over work items of many jobs; kind 0 shade, 1 AA + loss, 2 backward;
-// tiles are tw x (256 / tw) pixels; counter: device int (reset here)
-cudaError_t pixels_batched(int kind, const ShadeArgs* jobs, const WorkItem* items, int n_items, int* counter, int tw,
-                           int blocks, cudaStream_t st);
+// Jobs per batched launch: their arguments travel in the launch's parameter
+// space (64 x 496 B, under the 32 KB limit), read-only and captured with the
+// launch by a graph; larger job sets take one launch per 64 jobs.
+#define ADMS_BATCH_JOBS 64
+struct ShadeBatch {
+    ShadeArgs a[ADMS_BATCH_JOBS];
+};
+// persistent launch over work items of many jobs; kind 0 shade, 1 AA + loss, 2 backward.
+// args: host array of n_jobs arguments; items (device) are ordered by job, job k's
+// items being [item_off[k], item_off[k+1]) (item_off: host, n_jobs + 1 entries);
+// tiles are tw x (256 / tw) pixels; blocks should not exceed the resident count
+cudaError_t pixels_batched(int kind, const ShadeArgs* args, const int* item_off, int n_jobs, const WorkItem* items,
+                           int tw, int blocks, cudaStream_t st);
+// resident blocks per SM of the persistent launches: kind 0-2 as above, 3 the raster
+int batched_occupancy(int kind);
 
 // per-job arguments of the tile raster
 struct RasterJob {
@@ -126,9 +139,14 @@ struct RasterJob {
     unsigned long long* keys;
     unsigned long long* overflow_ctr;
 };
-// persistent launch of the 16x16-tile raster over (job, view, tile) items
-cudaError_t raster_tiles_batched(const RasterJob* jobs, const WorkItem* items, int n_items, int* counter, int blocks,
-                                 cudaStream_t st);
+struct RasterBatch {
+    RasterJob a[ADMS_BATCH_JOBS];
+};
+// persistent launch of the 16x16-tile raster over (job, view, tile) items; arguments
+// and item ranges as for pixels_batched
+cudaError_t raster_tiles_batched(const RasterJob* args, const int* item_off, int n_jobs, const WorkItem* items,
+                                 int blocks, cudaStream_t st);
+int raster_batch_occupancy();
 
 // mesh frame (smooth normals, tangents) and its adjoint
 struct FrameArgs {

@@ -258,6 +258,7 @@ __device__ __forceinline__ void raster_tile_body(const TriRec* __restrict__ rec,
     const TriBin* bb = bin + (size_t)b * F;
     bool overflow = off + cnt > capacity;
     int n = overflow ? F : cnt;
+    if (n == 0) return;  // no binned triangle: the small-triangle pass left the final keys
     if (overflow && threadIdx.x == 0) atomicAdd(overflow_ctr, 1ull);
     for (int c0 = 0; c0 < n; c0 += 256) {
         int m = min(256, n - c0);
@@ -294,33 +295,41 @@ __global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, 
                      blockIdx.y, blockIdx.x, sm);
 }
 
-// persistent: blocks take (job, view, tile) items from a counter until none are left
-__global__ void __launch_bounds__(256) k_raster_batch(const RasterJob* __restrict__ jobs,
-                                                      const WorkItem* __restrict__ items, int n,
-                                                      int* __restrict__ counter) {
+// persistent: block k takes items k, k + gridDim.x, ... (the items are equal
+// 16x16 tiles, so a static stride balances them without a shared counter); the
+// jobs' arguments are kernel parameters (up to 64 jobs per launch)
+__global__ void __launch_bounds__(256) k_raster_batch(const RasterBatch P, const WorkItem* __restrict__ items, int n,
+                                                      int job0) {
     __shared__ TriRec sm[256];
-    __shared__ int s_it;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_it = atomicAdd(counter, 1);
-        __syncthreads();
-        int it = s_it;
-        if (it >= n) break;
+    for (int it = blockIdx.x; it < n; it += gridDim.x) {
         WorkItem w = items[it];
-        const RasterJob& R = jobs[w.job];
+        const RasterJob& R = P.a[w.job - job0];
         int tile = (w.y0 / ADMS_TILE) * R.tiles_x + w.x0 / ADMS_TILE;
         raster_tile_body(R.rec, R.bin, R.F, R.W, R.H, R.tiles_x, R.tiles_y, R.tile_off, R.tile_count, R.list,
                          R.capacity, R.keys, R.overflow_ctr, w.view, tile, sm);
     }
 }
 
-cudaError_t raster_tiles_batched(const RasterJob* jobs, const WorkItem* items, int n_items, int* counter, int blocks,
-                                 cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
-    if (e) return e;
-    k_raster_batch<<<blocks, 256, 0, st>>>(jobs, items, n_items, counter);
-    count_launches(1);
-    return cudaGetLastError();
+int raster_batch_occupancy() {
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_raster_batch, 256, 0);
+    return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+cudaError_t raster_tiles_batched(const RasterJob* args, const int* item_off, int n_jobs, const WorkItem* items,
+                                 int blocks, cudaStream_t st) {
+    RasterBatch P;
+    for (int j0 = 0; j0 < n_jobs; j0 += ADMS_BATCH_JOBS) {
+        int j1 = std::min(n_jobs, j0 + ADMS_BATCH_JOBS);
+        int s0 = item_off[j0], n = item_off[j1] - s0;
+        if (n <= 0) continue;
+        memcpy(P.a, args + j0, sizeof(RasterJob) * (j1 - j0));
+        k_raster_batch<<<std::min(blocks, n), 256, 0, st>>>(P, items + s0, n, j0);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+    }
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- host launchers

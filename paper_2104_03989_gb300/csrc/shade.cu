@@ -619,41 +619,23 @@ __global__ void __launch_bounds__(256, 2) k_shade_bwd(ShadeArgs A) {
 }
 
 // ------------------------------------------------------------------ persistent batched kernels
-// One launch covers (job, view, tile) work items of many jobs with different
-// meshes, textures, view counts and resolutions. Each block takes items from a
-// global counter until none are left; a tile is tw x (256 / tw) pixels and the
-// job's arguments are staged in shared memory whenever the job changes.
-__device__ __forceinline__ void stage_args(ShadeArgs& dst, const ShadeArgs* src) {
-    const int* s = reinterpret_cast<const int*>(src);
-    int* d = reinterpret_cast<int*>(&dst);
-    for (int i = threadIdx.x; i < (int)(sizeof(ShadeArgs) / 4); i += blockDim.x) d[i] = s[i];
-}
-
+// One launch covers (job, view, tile) work items of up to 64 jobs with
+// different meshes, textures, view counts and resolutions. Block k takes items
+// k, k + gridDim.x, ... (equal tiles of tw x (256 / tw) pixels, so a static
+// stride balances them without a shared counter). The jobs' arguments are
+// kernel parameters: read-only, no copy per block, and no aliasing with the
+// stores and atomics of the pixel code.
 template <int KIND>
-__global__ void __launch_bounds__(256, KIND == 2 ? 2 : 1)
-    k_pixels_batch(const ShadeArgs* __restrict__ jobs, const WorkItem* __restrict__ items, int n,
-                   int* __restrict__ counter, int tw) {
-    __shared__ ShadeArgs sA;
-    __shared__ int s_it, s_job;
+__global__ void __launch_bounds__(256, KIND == 2 ? 2 : 4)
+    k_pixels_batch(const ShadeBatch P, const WorkItem* __restrict__ items, int n, int tw, int job0) {
     __shared__ double red[8];
-    if (threadIdx.x == 0) s_job = -1;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_it = atomicAdd(counter, 1);
-        __syncthreads();
-        int it = s_it;
-        if (it >= n) break;
+    for (int it = blockIdx.x; it < n; it += gridDim.x) {
         WorkItem w = items[it];
-        if (w.job != s_job) {
-            stage_args(sA, jobs + w.job);
-            __syncthreads();
-            if (threadIdx.x == 0) s_job = w.job;
-            __syncthreads();
-        }
+        const ShadeArgs& A = P.a[w.job - job0];
         int px = w.x0 + (int)threadIdx.x % tw, py = w.y0 + (int)threadIdx.x / tw;
-        if (KIND == 0) shade_fwd_px(sA, w.view, px, py);
-        else if (KIND == 1) aa_loss_block(sA, w.view, px, py, red);
-        else shade_bwd_px(sA, w.view, px, py);
+        if (KIND == 0) shade_fwd_px(A, w.view, px, py);
+        else if (KIND == 1) aa_loss_block(A, w.view, px, py, red);
+        else shade_bwd_px(A, w.view, px, py);
     }
 }
 
@@ -679,15 +661,32 @@ cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t pixels_batched(int kind, const ShadeArgs* jobs, const WorkItem* items, int n_items, int* counter, int tw,
-                           int blocks, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
-    if (e) return e;
-    if (kind == 0) k_pixels_batch<0><<<blocks, 256, 0, st>>>(jobs, items, n_items, counter, tw);
-    else if (kind == 1) k_pixels_batch<1><<<blocks, 256, 0, st>>>(jobs, items, n_items, counter, tw);
-    else k_pixels_batch<2><<<blocks, 256, 0, st>>>(jobs, items, n_items, counter, tw);
-    count_launches(1);
-    return cudaGetLastError();
+int batched_occupancy(int kind) {
+    if (kind == 3) return raster_batch_occupancy();
+    int n = 0;
+    cudaError_t e = kind == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pixels_batch<0>, 256, 0)
+                    : kind == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pixels_batch<1>, 256, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pixels_batch<2>, 256, 0);
+    return e == cudaSuccess && n > 0 ? n : 1;
+}
+
+cudaError_t pixels_batched(int kind, const ShadeArgs* args, const int* item_off, int n_jobs, const WorkItem* items,
+                           int tw, int blocks, cudaStream_t st) {
+    ShadeBatch P;
+    for (int j0 = 0; j0 < n_jobs; j0 += ADMS_BATCH_JOBS) {
+        int j1 = std::min(n_jobs, j0 + ADMS_BATCH_JOBS);
+        int s0 = item_off[j0], n = item_off[j1] - s0;
+        if (n <= 0) continue;
+        memcpy(P.a, args + j0, sizeof(ShadeArgs) * (j1 - j0));
+        int g = std::min(blocks, n);
+        if (kind == 0) k_pixels_batch<0><<<g, 256, 0, st>>>(P, items + s0, n, tw, j0);
+        else if (kind == 1) k_pixels_batch<1><<<g, 256, 0, st>>>(P, items + s0, n, tw, j0);
+        else k_pixels_batch<2><<<g, 256, 0, st>>>(P, items + s0, n, tw, j0);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace adms

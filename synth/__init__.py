@@ -32,4 +32,5 @@ from .workloads import (  # noqa: F401
     config_plain,
     config_tess,
     job_mix,
+    job_scenes,
 )

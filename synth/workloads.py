@@ -136,3 +136,29 @@ def job_mix(n_jobs=64, seed=0, tri_range=(500, 20000), tex_choices=(256, 512, 10
             )
         )
     return jobs
+
+
+_REF_MAPS = {}
+
+
+def job_scenes(recipe, ref_tex_cap=1024):
+    """(candidate, reference) scenes of one job_mix recipe.
+
+    Candidate: frequency-`cand_freq` icosphere with `tex_res`^2 noise maps and
+    full mip chains, every latent optimized. Reference: frequency-`ref_freq`
+    icosphere with 4-octave fBm radial displacement seeded by the job, and
+    procedural maps at min(tex_res, ref_tex_cap)^2 (seed 3) shared by all
+    jobs of that size: the maps only feed frozen reference renders, and the
+    host-side generator costs seconds per 2048^2 set.
+    """
+    r = recipe
+    rt = min(r["tex_res"], ref_tex_cap)
+    if rt not in _REF_MAPS:
+        _REF_MAPS[rt] = scenes.procedural_textures(rt, seed=3)
+    rkd, rorm, rnrm = _REF_MAPS[rt]
+    ref = Scene(mesh=_mesh(r["ref_freq"], lambda p: scenes.radial_fbm(p, seed=1000 + r["seed"])),
+                kd=rkd, orm=rorm, nrm=rnrm)
+    kd, nrm = scenes.noise_textures(r["tex_res"], seed=r["seed"])
+    cand = Scene(mesh=_mesh(r["cand_freq"]), kd=kd, orm=scenes.uniform_orm(r["tex_res"], seed=r["seed"]), nrm=nrm,
+                 optimize={"pos": True, "kd": True, "orm": True, "nrm": True})
+    return cand, ref
