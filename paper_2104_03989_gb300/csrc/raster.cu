@@ -19,6 +19,55 @@ __device__ __forceinline__ long long floor_div_ll(long long a, long long b) {  /
 }
 __device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return -floor_div_ll(-a, b); }
 
+// ---------------------------------------------------------------- double-float
+// hi + lo with |lo| <= ulp(hi) / 2: about 48 significant bits from float32
+// operations. Error-free sum (Knuth's TwoSum) and product (Dekker's, with an
+// FMA for the product's rounding error); each operation is explicitly rounded
+// so that no FMA contraction changes the error terms.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// m0 x + m1 y + m2 z + m3 (float inputs, double-float result)
+__device__ __forceinline__ DF df_row(const float* m, float x, float y, float z) {
+    DF p0 = df_two_prod(m[0], x), p1 = df_two_prod(m[1], y), p2 = df_two_prod(m[2], z);
+    DF s = df_two_sum(p0.hi, p1.hi);
+    float t = __fadd_rn(s.lo, __fadd_rn(p0.lo, p1.lo));
+    DF u = df_two_sum(s.hi, p2.hi);
+    t = __fadd_rn(t, __fadd_rn(u.lo, p2.lo));
+    DF v = df_two_sum(u.hi, m[3]);
+    t = __fadd_rn(t, v.lo);
+    return df_fast_two_sum(v.hi, t);
+}
+// a / b
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    DF p = df_two_prod(q1, b.hi);
+    // r = a - q1 b, the leading terms cancel exactly up to p.lo
+    float r = __fsub_rn(__fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo), __fmul_rn(q1, b.lo));
+    return df_fast_two_sum(q1, __fdiv_rn(r, b.hi));
+}
+// c0 + s q (float c0, s; double-float q)
+__device__ __forceinline__ DF df_affine(float c0, float s, DF q) {
+    DF p = df_two_prod(q.hi, s);
+    float e = __fmaf_rn(q.lo, s, p.lo);
+    DF u = df_two_sum(c0, p.hi);
+    return df_fast_two_sum(u.hi, __fadd_rn(u.lo, e));
+}
+
 // ---------------------------------------------------------------- transform
 __global__ void k_transform(const float* __restrict__ pos, int V, const adms_view* __restrict__ views, int B, int W,
                             int H, float4* __restrict__ clip, VtxS* __restrict__ vs, float4* __restrict__ scr) {
@@ -28,14 +77,14 @@ __global__ void k_transform(const float* __restrict__ pos, int V, const adms_vie
     const float* M = views[b].mvp;
     float x = pos[3 * v], y = pos[3 * v + 1], z = pos[3 * v + 2];
     {
-        // shading-side screen position in float64, kept as a (hi, lo) float pair
-        double cd[4];
-        for (int r = 0; r < 4; ++r)
-            cd[r] = (double)M[4 * r] * x + (double)M[4 * r + 1] * y + (double)M[4 * r + 2] * z + (double)M[4 * r + 3];
-        double hWd = 0.5 * W, hHd = 0.5 * H;
-        double sx = cd[0] / cd[3] * hWd + hWd, sy = hHd - cd[1] / cd[3] * hHd;
-        float sxh = (float)sx, syh = (float)sy;
-        scr[i] = make_float4(sxh, (float)(sx - (double)sxh), syh, (float)(sy - (double)syh));
+        // shading-side screen position to ~48 bits as a (hi, lo) float pair:
+        // sx = (W/2) (cx / cw) + W/2, sy = H/2 - (H/2) (cy / cw) in double-float
+        // arithmetic (float64 runs at a small fraction of the float32 rate here)
+        DF cx = df_row(M, x, y, z), cy = df_row(M + 4, x, y, z), cw = df_row(M + 12, x, y, z);
+        float hW = 0.5f * (float)W, hH = 0.5f * (float)H;
+        DF sx = df_affine(hW, hW, df_div(cx, cw));
+        DF sy = df_affine(hH, -hH, df_div(cy, cw));
+        scr[i] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
     }
     float c[4];
 #pragma unroll
