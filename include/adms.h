@@ -226,11 +226,19 @@ adms_status adms_job_keys(adms_ctx* ctx, adms_job job, uint64_t* out_keys, size_
 
 /* ---- checkpoint / resume --------------------------------------------------- */
 
-/* Serialise a job (latents, Adam moments, t, lambda, seed) into host memory.
- * With host_buf == NULL only *bytes is set. Synchronises the stream. */
+/* Serialise a job's resumable state into host memory: a versioned header
+ * (shapes, options, seed) followed by the positions and their Adam moments,
+ * each texture's whole mip chain and level-0 moments, the displacement map and
+ * its moments, the relative-Laplacian reference and the job state (t, lambda_0,
+ * lambda, lr, bias corrections, latched status). Gradients are not kept:
+ * export between optimizer steps. With host_buf == NULL only *bytes is set;
+ * otherwise *bytes is the buffer's capacity on entry (ADMS_ERR_ARG if too
+ * small) and the blob's size on return. Synchronises the stream. */
 adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t* bytes);
-/* Recreate a job from adms_job_export output; mesh and material give the
- * topology and texture sizes (their latent values are overwritten). */
+/* Recreate a job from adms_job_export output (checkpoint/resume): mesh, mat and
+ * opt must describe the job that was exported (same topology, texture sizes,
+ * options); their latent values are replaced by the blob's. ADMS_ERR_ARG if
+ * the blob is not a checkpoint of this version or does not match them. */
 adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
                             const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out);
 

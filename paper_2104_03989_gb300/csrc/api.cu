@@ -866,6 +866,86 @@ adms_status batch_upload(adms_ctx* ctx, const std::vector<Job*>& js, float* cons
     return ADMS_OK;
 }
 
+// ------------------------------------------------------------------ checkpoints
+// A job's resumable state as one host blob: a fixed header (shapes and options,
+// so a blob is only loaded into a job of the same layout) and the device
+// buffers below, in this order. Gradients and per-step scratch are not kept:
+// export between optimizer steps.
+const char kCkptMagic[8] = {'A', 'D', 'M', 'S', 'C', 'K', 'P', 'T'};
+const uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, n_sections;
+    uint64_t seed;
+    int32_t LV, V, F, tess_levels, dh, dw;
+    int32_t tex_w[3], tex_h[3], tex_levels[3], tex_opt[3];
+    int32_t optimize[5];  // pos, kd, orm, nrm, disp
+    int32_t loss, relative_laplacian, batch_views, aa;
+    float lr0, lambda0;
+    uint64_t section_bytes[16];
+};
+
+struct CkptSection {
+    void* ptr;
+    size_t bytes;
+};
+
+void ckpt_describe(Job& j, CkptHeader& h, std::vector<CkptSection>& secs) {
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kCkptMagic, 8);
+    h.version = kCkptVersion;
+    h.seed = j.seed;
+    h.LV = j.LV;
+    h.V = j.V;
+    h.F = j.F;
+    h.tess_levels = j.opt.tess_levels;
+    h.dh = j.dh;
+    h.dw = j.dw;
+    const TexState* tx[3] = {&j.kd, &j.orm, &j.nrm};
+    for (int k = 0; k < 3; ++k) {
+        h.tex_w[k] = tx[k]->w;
+        h.tex_h[k] = tx[k]->h;
+        h.tex_levels[k] = tx[k]->levels;
+        h.tex_opt[k] = tx[k]->opt;
+    }
+    h.optimize[0] = j.opt.optimize_pos;
+    h.optimize[1] = j.opt.optimize_kd;
+    h.optimize[2] = j.opt.optimize_orm;
+    h.optimize[3] = j.opt.optimize_nrm;
+    h.optimize[4] = j.opt.optimize_disp;
+    h.loss = j.opt.loss;
+    h.relative_laplacian = j.opt.relative_laplacian;
+    h.batch_views = j.opt.batch_views;
+    h.aa = j.opt.aa;
+    h.lr0 = j.opt.lr0;
+    h.lambda0 = j.opt.lambda0;
+    secs.clear();
+    auto add = [&](void* p, size_t n) {
+        if (p && n) secs.push_back({p, n});
+    };
+    size_t pv = (size_t)j.LV * 3 * sizeof(float);
+    add(j.pos, pv);
+    add(j.m_pos, pv);
+    add(j.v_pos, pv);
+    for (int k = 0; k < 3; ++k) {
+        TexState& t = *const_cast<TexState*>(tx[k]);
+        add(t.data, t.total * sizeof(float4));  // the whole chain: resumes without a rebuild
+        if (t.opt) {
+            add(t.m, (size_t)t.w * t.h * sizeof(float4));
+            add(t.v, (size_t)t.w * t.h * sizeof(float4));
+        }
+    }
+    size_t pd = (size_t)j.dh * j.dw * sizeof(float);
+    add(j.disp, pd);
+    add(j.m_disp, pd);
+    add(j.v_disp, pd);
+    add(j.delta_ref, pv);
+    add(j.st, sizeof(JobState));
+    h.n_sections = (uint32_t)secs.size();
+    for (size_t k = 0; k < secs.size() && k < 16; ++k) h.section_bytes[k] = secs[k].bytes;
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -1326,12 +1406,63 @@ adms_status adms_job_keys(adms_ctx* ctx, adms_job job, uint64_t* out_keys, size_
 adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t* bytes) {
     Job* j = get_job(ctx, job);
     if (!j || !bytes) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
-    return fail(ctx, ADMS_ERR_STATE, "export not implemented in this build");
+    CkptHeader h;
+    std::vector<CkptSection> secs;
+    ckpt_describe(*j, h, secs);
+    size_t total = sizeof(CkptHeader);
+    for (const CkptSection& c : secs) total += c.bytes;
+    if (!host_buf) {
+        *bytes = total;
+        return ADMS_OK;
+    }
+    if (*bytes < total) return fail(ctx, ADMS_ERR_ARG, "checkpoint buffer too small");
+    CK(cudaStreamSynchronize(ctx->stream));
+    unsigned char* out = static_cast<unsigned char*>(host_buf);
+    memcpy(out, &h, sizeof(h));
+    size_t off = sizeof(h);
+    for (const CkptSection& c : secs) {
+        CK(cudaMemcpy(out + off, c.ptr, c.bytes, cudaMemcpyDeviceToHost));
+        off += c.bytes;
+    }
+    *bytes = total;
+    return ADMS_OK;
 }
 
 adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
                             const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out) {
-    return fail(ctx, ADMS_ERR_STATE, "import not implemented in this build");
+    if (!ctx || !host_buf || !out) return fail(ctx, ADMS_ERR_ARG, "null argument");
+    if (bytes < sizeof(CkptHeader)) return fail(ctx, ADMS_ERR_ARG, "checkpoint shorter than its header");
+    CkptHeader want;
+    memcpy(&want, host_buf, sizeof(want));
+    if (memcmp(want.magic, kCkptMagic, 8) != 0 || want.version != kCkptVersion)
+        return fail(ctx, ADMS_ERR_ARG, "not an adms checkpoint of this version");
+    adms_job h = -1;
+    adms_status s = adms_job_create(ctx, mesh, mat, opt, want.seed, &h);
+    if (s) return s;
+    Job& j = ctx->jobs[h];
+    CkptHeader got;
+    std::vector<CkptSection> secs;
+    ckpt_describe(j, got, secs);
+    size_t total = sizeof(CkptHeader);
+    for (const CkptSection& c : secs) total += c.bytes;
+    if (memcmp(&got, &want, sizeof(CkptHeader)) != 0 || total != bytes) {
+        adms_job_destroy(ctx, h);
+        return fail(ctx, ADMS_ERR_ARG, "checkpoint does not match the mesh, textures or options given");
+    }
+    const unsigned char* in = static_cast<const unsigned char*>(host_buf);
+    size_t off = sizeof(CkptHeader);
+    for (const CkptSection& c : secs) {
+        cudaError_t e = cudaMemcpy(c.ptr, in + off, c.bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            adms_job_destroy(ctx, h);
+            return fail(ctx, ADMS_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+        }
+        off += c.bytes;
+    }
+    j.frame_valid = false;
+    j.have_fwd = false;
+    *out = h;
+    return ADMS_OK;
 }
 
 adms_status adms_graph_begin(adms_ctx* ctx) {

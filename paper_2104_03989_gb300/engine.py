@@ -55,6 +55,24 @@ class Context:
     def create_job(self, scene, optimize=None, loss="logl1", lr0=0.01, lambda0=0.0, batch_views=0, aa=True,
                    relative_laplacian=False, frozen=False, seed=0):
         """scene: object with .mesh (pos, uv, tri_pos, tri_uv), .kd, .orm, .nrm, .mips (numpy)."""
+        mesh, mat, opt, keep = self._descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian,
+                                           frozen)
+        return B.adms_job_create(self.ctx, mesh, mat, opt, seed)
+
+    def export_job(self, job):
+        """The job's resumable state as a uint8 numpy array (a checkpoint)."""
+        return B.adms_job_export(self.ctx, job)
+
+    def import_job(self, blob, scene, optimize=None, loss="logl1", lr0=0.01, lambda0=0.0, batch_views=0, aa=True,
+                   relative_laplacian=False, frozen=False):
+        """A new job resumed from export_job's output; scene and options as given
+        when the exported job was created."""
+        mesh, mat, opt, keep = self._descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian,
+                                           frozen)
+        return B.adms_job_import(self.ctx, mesh, mat, opt, np.ascontiguousarray(blob, dtype=np.uint8))
+
+    @staticmethod
+    def _descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian, frozen):
         m = scene.mesh
         arrays = dict(pos=_c32(m.pos, np.float32), uv=_c32(m.uv, np.float32), tri=_c32(m.tri_pos, np.int32),
                       tri_uv=_c32(m.tri_uv, np.int32), kd=_c32(scene.kd, np.float32),
@@ -72,7 +90,7 @@ class Context:
             if frozen:
                 for k in ("optimize_pos", "optimize_kd", "optimize_orm", "optimize_nrm", "optimize_disp"):
                     setattr(opt, k, 0)
-        return B.adms_job_create(self.ctx, mesh, mat, opt, seed)
+        return mesh, mat, opt, arrays
 
     def destroy_job(self, job):
         B.adms_job_destroy(self.ctx, job)
