@@ -439,7 +439,11 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
 // ------------------------------------------------------------------ backward
 // Scatter 9 per-corner vertex gradients (position, unit normal, unit tangent)
 // for the triangle of each lane; lanes of a warp that share a triangle are
-// summed first, then one lane per value issues a float64 atomic.
+// summed first, then one lane per value issues a float64 atomic. The 27 sums
+// are a butterfly transpose-reduction: at each of the 5 steps every lane keeps
+// half of its partial sums and trades the other half with its partner, so lane
+// j ends with the sum of value j after 31 shuffles (27 separate warp sums
+// would take 135).
 __device__ __forceinline__ void scatter_vertex_grads(const ShadeArgs& A, int f, const int vi[3], float v[27]) {
     unsigned todo = __ballot_sync(0xffffffffu, f >= 0);
     int lane = threadIdx.x & 31;
@@ -450,12 +454,20 @@ __device__ __forceinline__ void scatter_vertex_grads(const ShadeArgs& A, int f, 
         unsigned grp = __ballot_sync(0xffffffffu, mine);
         int v0 = __shfl_sync(0xffffffffu, vi[0], lead), v1 = __shfl_sync(0xffffffffu, vi[1], lead),
             v2 = __shfl_sync(0xffffffffu, vi[2], lead);
-        float mineval = 0.f;
+        float x[32];
 #pragma unroll
-        for (int j = 0; j < 27; ++j) {
-            float x = warp_sum(mine ? v[j] : 0.f);
-            if (lane == j) mineval = x;
+        for (int j = 0; j < 32; ++j) x[j] = (j < 27 && mine) ? v[j] : 0.f;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < o; ++i) {
+                float send = up ? x[i] : x[i + o];
+                float keep = up ? x[i + o] : x[i];
+                x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
         }
+        float mineval = x[0];  // the sum of value `lane`
         if (lane < 27 && mineval != 0.f) {
             int corner = lane / 9, comp = lane % 9;
             int vtx = corner == 0 ? v0 : (corner == 1 ? v1 : v2);
@@ -597,22 +609,25 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
 }
 
 // ------------------------------------------------------------------ single-job kernels (16x16 tiles)
-__global__ void __launch_bounds__(256) k_shade_fwd(ShadeArgs A) {
+// register caps measured on the plain-method step: 5 blocks/SM for shading,
+// 8 for AA + loss, 3 for the backward (a few hundred bytes of spills cost less
+// than the latency the extra resident warps hide)
+__global__ void __launch_bounds__(256, 5) k_shade_fwd(ShadeArgs A) {
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
     shade_fwd_px(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
 }
 
-__global__ void __launch_bounds__(256) k_aa_loss(ShadeArgs A) {
+__global__ void __launch_bounds__(256, 8) k_aa_loss(ShadeArgs A) {
     __shared__ double red[8];
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
     aa_loss_block(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
                   (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4), red);
 }
 
-// two blocks per SM: 128 registers per thread (a few bytes of spills) doubles
-// the resident warps that hide the gather latency of this kernel
-__global__ void __launch_bounds__(256, 2) k_shade_bwd(ShadeArgs A) {
+// three blocks per SM: 85 registers per thread; the spills cost less than the
+// gather latency the extra resident warps hide (0.289 -> 0.265 ms per step)
+__global__ void __launch_bounds__(256, 3) k_shade_bwd(ShadeArgs A) {
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
     shade_bwd_px(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
@@ -626,7 +641,7 @@ __global__ void __launch_bounds__(256, 2) k_shade_bwd(ShadeArgs A) {
 // kernel parameters: read-only, no copy per block, and no aliasing with the
 // stores and atomics of the pixel code.
 template <int KIND>
-__global__ void __launch_bounds__(256, KIND == 2 ? 2 : 4)
+__global__ void __launch_bounds__(256, KIND == 2 ? 3 : (KIND == 1 ? 8 : 5))
     k_pixels_batch(const ShadeBatch P, const WorkItem* __restrict__ items, int n, int tw, int job0) {
     __shared__ double red[8];
     for (int it = blockIdx.x; it < n; it += gridDim.x) {
