@@ -20,6 +20,7 @@ struct TexState {
     float4* grad = nullptr;  // mip chain (when optimized)
     float4* m = nullptr;     // level 0
     float4* v = nullptr;
+    int* done = nullptr;     // tiles finished in the current tiled Adam launch
     int w = 0, h = 0, levels = 0;
     int off[ADMS_MAX_LEVELS] = {0};
     size_t total = 0;
@@ -276,6 +277,7 @@ adms_status tex_create(adms_ctx* ctx, Job& j, TexState& t, const float* src, int
         AL(t.grad, t.total);
         AL(t.m, (size_t)w * h);
         AL(t.v, (size_t)w * h);
+        AL(t.done, 1);
     }
     CK(mip_build(t.dev(), ctx->stream));
     return ADMS_OK;
@@ -1313,11 +1315,18 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
 
 adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs) {
     if (!ctx || !jobs || n_jobs <= 0) return fail(ctx, ADMS_ERR_ARG, "invalid optimizer_step arguments");
+    std::vector<Job*> js;
     for (int k = 0; k < n_jobs; ++k) {
         Job* jp = get_job(ctx, jobs[k]);
         if (!jp) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+        if (jp->frozen) return fail(ctx, ADMS_ERR_STATE, "optimizer_step on a frozen job");
+        js.push_back(jp);
+    }
+    // schedules, Laplacian and the flat latents per job; then every job's tiled
+    // textures in one launch; then the step counters
+    std::vector<TexAdam> tiled;
+    for (Job* jp : js) {
         Job& j = *jp;
-        if (j.frozen) return fail(ctx, ADMS_ERR_STATE, "optimizer_step on a frozen job");
         LapArgs la{j.LV, j.pos, j.ring_off, j.ring, j.delta_ref, j.delta, j.g_pos, j.st};
         if (j.opt.optimize_pos) CK(TIMED(ST_LAPLACIAN, laplacian_forward(la, ctx->stream)));
         SchedArgs sa{j.st, j.opt.lr0, j.opt.lambda0, j.opt.optimize_pos, j.LV};
@@ -1336,10 +1345,15 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
         for (int m = 0; m < 3; ++m) {
             if (!maps[m]->opt) continue;
-            CK(TIMED(ST_ADAM, adam_texture_and_mips(maps[m]->dev(), maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
+            TexDev td = maps[m]->dev();
+            if (adam_tiled(td)) tiled.push_back(TexAdam{td, maps[m]->m, maps[m]->v, j.st, maps[m]->done, m, 0});
+            else CK(TIMED(ST_ADAM, adam_texture_and_mips(td, maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
         }
-        CK(TIMED(ST_SMALL, advance_step(j.st, ctx->stream)));
-        j.frame_valid = false;
+    }
+    if (!tiled.empty()) CK(TIMED(ST_ADAM, adam_textures_tiled(tiled, ctx->stream)));
+    for (Job* jp : js) {
+        CK(TIMED(ST_SMALL, advance_step(jp->st, ctx->stream)));
+        jp->frame_valid = false;
     }
     return ADMS_OK;
 }

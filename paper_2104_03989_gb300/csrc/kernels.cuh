@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 
@@ -237,9 +238,29 @@ cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const
 cudaError_t adam_texture(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js, cudaStream_t st);
 // rebuild levels 1.. of a mip chain from level 0 (2x2 box average)
 cudaError_t mip_build(const TexDev& t, cudaStream_t st);
-// Adam on a texture fused with the rebuild of its mip chain (tiles of 32x32 texels)
+// Adam on a texture, then the rebuild of its mip chain (textures that do not tile)
 cudaError_t adam_texture_and_mips(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js,
                                   cudaStream_t st);
+// one optimized texture of a tiled Adam launch
+struct TexAdam {
+    TexDev t;
+    float4* m;
+    float4* v;
+    const JobState* js;
+    int* done;       // device counter of finished tiles: zero between launches (the last tile resets it)
+    int clamp_kind;  // 0 kd, 1 orm, 2 nrm
+    int tile0;       // set by the launcher
+};
+#define ADMS_ADAM_TEX 160  // textures per launch: their arguments are kernel parameters (< 32 KB)
+struct TexAdamBatch {
+    TexAdam a[ADMS_ADAM_TEX];
+    int n;
+};
+// whether a texture takes the tiled path (both sides multiples of 32, at least 6 levels)
+bool adam_tiled(const TexDev& t);
+// Adam + mip rebuild of every listed texture (all adam_tiled, any jobs), one 32x32-texel
+// tile per block, one launch per ADMS_ADAM_TEX textures
+cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st);
 cudaError_t advance_step(JobState* js, cudaStream_t st);
 // out[j] = call_loss; img_loss += call_loss
 cudaError_t finish_call_loss(JobState* js, float* out, cudaStream_t st);
