@@ -115,27 +115,53 @@ __global__ void k_transform(const float* __restrict__ pos, int V, const adms_vie
 }
 
 // ---------------------------------------------------------------- exclusive scan (one block)
-__global__ void k_scan(const int* __restrict__ in, int n, int* __restrict__ out, long long* __restrict__ total) {
-    __shared__ long long part[1024];
-    int tid = threadIdx.x, nt = blockDim.x;
-    int chunk = (n + nt - 1) / nt;
-    int lo = tid * chunk, hi = min(lo + chunk, n);
-    long long s = 0;
-    for (int i = lo; i < hi; ++i) s += in[i];
-    part[tid] = s;
-    __syncthreads();
-    for (int o = 1; o < nt; o <<= 1) {
-        long long v = tid >= o ? part[tid - o] : 0;
+// exclusive scan of the per-tile counts in one block of 1024 threads: rounds of
+// 8192 entries, 8 consecutive entries per thread, warp scans by shuffles and
+// one scan of the 32 warp sums; out saturates at INT_MAX (the list-capacity
+// check catches an overflow), *total is exact
+__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int n, int* __restrict__ out,
+                                               long long* __restrict__ total) {
+    __shared__ long long wsum[32];
+    int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    long long carry = 0;
+    for (int base = 0; base < n; base += 8192) {
+        int v[8];
+        long long s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int i = base + tid * 8 + k;
+            v[k] = i < n ? in[i] : 0;
+            s += v[k];
+        }
+        long long x = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
         __syncthreads();
-        part[tid] += v;
+        if (wid == 0) {
+            long long w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        long long run = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - s;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int i = base + tid * 8 + k;
+            if (i < n) out[i] = (int)min(run, (long long)0x7fffffff);
+            run += v[k];
+        }
+        carry += wsum[31];
         __syncthreads();
     }
-    long long run = part[tid] - s;
-    for (int i = lo; i < hi; ++i) {
-        out[i] = (int)min(run, (long long)0x7fffffff);
-        run += in[i];
-    }
-    if (tid == nt - 1) *total = part[tid];
+    if (tid == 0) *total = carry;
 }
 
 // ---------------------------------------------------------------- coverage test
@@ -241,36 +267,33 @@ __global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restri
     bin[i] = tb;
 }
 
-// ---------------------------------------------------------------- silhouette edges
-// bit e of silmask[b][f] is set when edge e of triangle f is a silhouette edge in
-// view b: no neighbour across it, or a neighbour whose snapped area has another sign
-__global__ void k_silmask(const int* __restrict__ adj, const int8_t* __restrict__ asign, int F, int B,
-                          uint8_t* __restrict__ silmask) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B * F) return;
-    int b = i / F, f = i - b * F;
-    const int8_t* sg = asign + (size_t)b * F;
-    int s = sg[f];
-    uint8_t m = 0;
-    if (s != 0) {
-#pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            int nb = adj[3 * f + e];
-            if (nb < 0 || sg[nb] != s) m |= (uint8_t)(1u << e);
-        }
-    }
-    silmask[i] = m;
-}
-
 // ---------------------------------------------------------------- tile lists
+// Per (view, triangle), after the scan of the tile counts: the triangle's
+// silhouette-edge mask, then its entries in the tile lists. Bit e of
+// silmask[b][f] is set when edge e of triangle f is a silhouette edge in view b:
+// no neighbour across it, or a neighbour whose snapped area has another sign.
 __global__ void k_bin_fill(const TriBin* __restrict__ bin, int F, int B, int tiles_x, int tiles_y,
                            const int* __restrict__ tile_off, int* __restrict__ tile_cursor, int* __restrict__ list,
-                           long long capacity) {
+                           long long capacity, const int* __restrict__ adj, const int8_t* __restrict__ asign,
+                           uint8_t* __restrict__ silmask) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * F) return;
+    int b = i / F, f = i - b * F;
+    {
+        const int8_t* sg = asign + (size_t)b * F;
+        int sf = sg[f];
+        uint8_t msk = 0;
+        if (sf != 0) {
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                int nb = adj[3 * f + e];
+                if (nb < 0 || sg[nb] != sf) msk |= (uint8_t)(1u << e);
+            }
+        }
+        silmask[i] = msk;
+    }
     TriBin tb = bin[i];
     if (tb.bx0 > tb.bx1) return;
-    int b = i / F, f = i - b * F;
     size_t tbase = (size_t)b * tiles_x * tiles_y;
     int tx0 = tb.bx0 / ADMS_TILE, tx1 = tb.bx1 / ADMS_TILE, ty0 = tb.by0 / ADMS_TILE, ty1 = tb.by1 / ADMS_TILE;
     for (int ty = ty0; ty <= ty1; ++ty)
@@ -396,9 +419,8 @@ cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st
                                                 s.asign, s.tile_count, in.keys);
     k_scan<<<1, 1024, 0, st>>>(s.tile_count, ntiles, s.tile_off, s.total_pairs);
     k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.bin, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
-                                                   s.list, s.list_capacity);
-    k_silmask<<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.adj, s.asign, F, B, s.silmask);
-    count_launches(5);
+                                                   s.list, s.list_capacity, in.adj, s.asign, s.silmask);
+    count_launches(4);
     return cudaGetLastError();
 }
 
