@@ -397,6 +397,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
         unsigned long long kp = A.keys[pix];
         float3 cp = f3of(A.pre[pix]);
         float3 out = cp;
+        unsigned amask = 0;  // neighbours whose pair blends (tau != 1/2): the backward visits only these
         if (A.aa) {
 #pragma unroll
             for (int nbi = 0; nbi < 4; ++nbi) {
@@ -407,6 +408,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
                 PairInfo pi;
                 if (!pair_eval(A, b, px, py, kp, qx, qy, A.keys[qpix], nbi < 2 ? 0 : 1, pi)) continue;
                 float om = pi.t.tau - 0.5f;
+                if (om != 0.f) amask |= 1u << nbi;
                 // the other pixel blends toward the owner when tau > 1/2, the owner toward it when tau < 1/2
                 bool p_target = om > 0.f ? !pi.p_owner : (om < 0.f ? pi.p_owner : false);
                 if (p_target) out += fabsf(om) * (f3of(A.pre[qpix]) - cp);
@@ -417,7 +419,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
             float g0, g1, g2;
             lsum = (double)loss_term(A.loss_kind, out.x, y[0], &g0) + (double)loss_term(A.loss_kind, out.y, y[1], &g1) +
                    (double)loss_term(A.loss_kind, out.z, y[2], &g2);
-            A.gprime[pix] = make_float4(g0 * A.loss_scale, g1 * A.loss_scale, g2 * A.loss_scale, 0.f);
+            A.gprime[pix] = make_float4(g0 * A.loss_scale, g1 * A.loss_scale, g2 * A.loss_scale, __uint_as_float(amask));
         }
         if (A.out_img) {
             A.out_img[pix * 3] = out.x;
@@ -498,12 +500,15 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
         size_t pix = ((size_t)b * A.H + py) * A.W + px;
         unsigned long long kp = A.keys[pix];
         f = key_tri(kp);
-        float3 gp = f3of(A.gprime[pix]);
+        float4 gp4 = A.gprime[pix];
+        float3 gp = f3of(gp4);
         float3 gc = gp;
-        if (A.aa) {
+        unsigned amask = __float_as_uint(gp4.w);  // pairs that blended in the forward (bit per neighbour)
+        if (amask) {
             float3 cp = f3of(A.pre[pix]);
 #pragma unroll
             for (int nbi = 0; nbi < 4; ++nbi) {
+                if (!((amask >> nbi) & 1u)) continue;
                 int qx, qy;
                 neighbour(nbi, px, py, qx, qy);
                 if (qx < 0 || qx >= A.W || qy < 0 || qy >= A.H) continue;
