@@ -84,6 +84,7 @@ struct Job {
     unsigned long long* keys = nullptr;
     float4* pre = nullptr;
     float4* gprime = nullptr;
+    int* refine = nullptr;
     adms_view* views = nullptr;
     RasterScratch rs{};
     // latest forward
@@ -292,6 +293,7 @@ adms_status ensure_scratch(adms_ctx* ctx, Job& j, int B, int H, int W) {
         AL(j.keys, px);
         AL(j.pre, px);
         AL(j.gprime, px);
+        AL(j.refine, px + 1);
         j.px_cap = px;
     }
     if ((size_t)B > j.view_cap) {
@@ -420,6 +422,7 @@ ShadeArgs shade_args(Job& j) {
     a.nrm = j.nrm.dev();
     a.pre = j.pre;
     a.gprime = j.gprime;
+    a.refine = j.refine;
     a.loss_kind = j.opt.loss;
     a.loss_scale = j.loss_scale;
     a.aa = j.opt.aa;

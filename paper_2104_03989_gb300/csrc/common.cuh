@@ -63,6 +63,63 @@ __device__ __forceinline__ double warp_sum_d(double x) {
     return x;
 }
 
+// ------------------------------------------------------------------ double-float
+// hi + lo with |lo| <= ulp(hi) / 2: about 48 significant bits from float32
+// operations. Error-free sum (Knuth's TwoSum) and product (Dekker's, with an
+// FMA for the product's rounding error); each operation is explicitly rounded
+// so that no FMA contraction changes the error terms.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// a + b, a * b, a / b on double-float values (about 2^-44 relative)
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+    DF s = df_two_sum(a.hi, b);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    DF p = df_two_prod(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return df_fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ DF df_div_f(DF a, float b) {
+    float q1 = __fdiv_rn(a.hi, b);
+    DF p = df_two_prod(q1, b);
+    float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p.hi), p.lo), a.lo);
+    return df_fast_two_sum(q1, __fdiv_rn(r, b));
+}
+__device__ __forceinline__ DF df_div_df(DF a, DF b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    DF p = df_mul(DF{q1, 0.f}, b);  // q1 * b
+    DF r = df_sub(a, p);
+    return df_fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+// a * b + c * d in float with one product's rounding error recovered (Kahan)
+__device__ __forceinline__ float dot2_acc(float a, float b, float c, float d) {
+    float w = __fmul_rn(c, d);
+    float e = __fmaf_rn(c, d, -w);
+    float f = __fmaf_rn(a, b, w);
+    return __fadd_rn(f, e);
+}
+
 // ------------------------------------------------------------------ textures
 // One texture with its full mip chain in one buffer, float4 texels.
 struct TexDev {
@@ -87,20 +144,39 @@ __device__ __forceinline__ float tex_lod(const TexDev& t, float2 dx, float2 dy) 
 }
 
 // Texture coordinate kept as (u0 + du, v0 + dv): u0 is the UV of the triangle's
-// first corner and du the interpolated offset from it, so texel coordinates
-// u w - 1/2 keep the offset's relative precision instead of that of u itself.
+// first corner and du the interpolated offset from it as a double-float
+// (du + du_lo). The offset spans up to the triangle's texel extent (tens of
+// texels on 1024² maps), and with noise textures under sharp highlights a
+// texel-coordinate error of 1e-6 texel already moves a pixel by ~1e-5.
 struct TexCoord {
-    float u0, v0, du, dv;
+    float u0, v0, du, dv, du_lo, dv_lo;
 };
 
-// integer part and fraction of (a0 * n - 1/2) + d * n, n a power of two
-__device__ __forceinline__ void texel_coord(float a0, float d, int n, int& i, float& f) {
+// integer part and fraction of (a0 * n - 1/2) + (d + dlo) * n, n a power of two;
+// the fraction keeps float32 precision whatever the offset's size
+__device__ __forceinline__ void texel_coord(float a0, float d, float dlo, int n, int& i, float& f) {
     float X0 = a0 * (float)n - 0.5f;  // exact: power-of-two scale, then a half-ulp-safe shift
     float i0 = floorf(X0);
-    float r = (X0 - i0) + d * (float)n;
-    float ri = floorf(r);
+    if (dlo == 0.f) {  // float32 offset
+        float r = (X0 - i0) + d * (float)n;
+        float ri = floorf(r);
+        i = (int)i0 + (int)ri;
+        f = r - ri;
+        return;
+    }
+    DF s = df_two_sum(X0 - i0, d * (float)n);  // X0 - i0 and d n exact
+    float lo = __fadd_rn(s.lo, dlo * (float)n);
+    float ri = floorf(s.hi);
+    float fr = __fadd_rn(s.hi - ri, lo);      // s.hi - ri exact
+    if (fr < 0.f) {
+        fr = __fadd_rn(fr, 1.f);
+        ri -= 1.f;
+    } else if (fr >= 1.f) {
+        fr = __fsub_rn(fr, 1.f);
+        ri += 1.f;
+    }
     i = (int)i0 + (int)ri;
-    f = r - ri;
+    f = fr;
 }
 
 struct BilinTap {
@@ -113,8 +189,8 @@ __device__ __forceinline__ BilinTap bilin_tap(const TexDev& t, int k, const TexC
     BilinTap b;
     int w = lvl_w(t, k), h = lvl_h(t, k);
     int ix0, iy0;
-    texel_coord(tc.u0, tc.du, w, ix0, b.fx);
-    texel_coord(tc.v0, tc.dv, h, iy0, b.fy);
+    texel_coord(tc.u0, tc.du, tc.du_lo, w, ix0, b.fx);
+    texel_coord(tc.v0, tc.dv, tc.dv_lo, h, iy0, b.fy);
     int ixa = ix0 % w;
     if (ixa < 0) ixa += w;
     int ixb = ixa + 1 == w ? 0 : ixa + 1;

@@ -93,6 +93,8 @@ struct ShadeArgs {
     TexDev kd, orm, nrm;
     float4* pre;                     // [B][H][W] pre-AA colour
     const float* ref;                // [B][H][W][3]
+    int* refine;                     // [0]: count, then pixel indices shaded again with a refined
+                                     // texture coordinate (null: none)
     float4* gprime;                  // [B][H][W] dL/d(AA colour) in xyz; w: bit n set (as raw bits)
                                      // when the pair with neighbour n (-x, +x, -y, +y) blended
     float* out_img;                  // [B][H][W][3] or null

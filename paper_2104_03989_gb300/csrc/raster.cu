@@ -19,28 +19,6 @@ __device__ __forceinline__ long long floor_div_ll(long long a, long long b) {  /
 }
 __device__ __forceinline__ long long ceil_div_ll(long long a, long long b) { return -floor_div_ll(-a, b); }
 
-// ---------------------------------------------------------------- double-float
-// hi + lo with |lo| <= ulp(hi) / 2: about 48 significant bits from float32
-// operations. Error-free sum (Knuth's TwoSum) and product (Dekker's, with an
-// FMA for the product's rounding error); each operation is explicitly rounded
-// so that no FMA contraction changes the error terms.
-struct DF {
-    float hi, lo;
-};
-__device__ __forceinline__ DF df_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
-    float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ DF df_two_prod(float a, float b) {
-    float p = __fmul_rn(a, b);
-    return {p, __fmaf_rn(a, b, -p)};
-}
 // m0 x + m1 y + m2 z + m3 (float inputs, double-float result)
 __device__ __forceinline__ DF df_row(const float* m, float x, float y, float z) {
     DF p0 = df_two_prod(m[0], x), p1 = df_two_prod(m[1], y), p2 = df_two_prod(m[2], z);

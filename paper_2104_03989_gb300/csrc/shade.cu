@@ -32,6 +32,8 @@ __device__ __forceinline__ float2 rel_screen(float4 S, float ox, float oy) {
     return make_float2((S.x - ox) + S.y, (S.z - oy) + S.w);
 }
 
+// Perspective-correct barycentrics and interpolated attributes (corner 0 plus
+// weighted differences) of pixel (px, py) inside triangle f.
 __device__ __forceinline__ void pix_geo(const ShadeArgs& A, int b, int px, int py, int f, PixGeo& g) {
     float qx = (float)px + 0.5f, qy = (float)py + 0.5f;
 #pragma unroll
@@ -73,6 +75,8 @@ __device__ __forceinline__ void pix_geo(const ShadeArgs& A, int b, int px, int p
     g.tc.v0 = u0.y;
     g.tc.du = g.duv.x;
     g.tc.dv = g.duv.y;
+    g.tc.du_lo = 0.f;
+    g.tc.dv_lo = 0.f;
     // screen derivatives of the perspective-correct barycentrics (texture LOD only)
     float dlx[3] = {(g.d[1].y - g.d[2].y) * ia, (g.d[2].y - g.d[0].y) * ia, (g.d[0].y - g.d[1].y) * ia};
     float dly[3] = {(g.d[2].x - g.d[1].x) * ia, (g.d[0].x - g.d[2].x) * ia, (g.d[1].x - g.d[0].x) * ia};
@@ -260,6 +264,81 @@ __device__ __forceinline__ ShadeIn shade_inputs(const ShadeArgs& A, const PixGeo
     return in;
 }
 
+// The texture coordinate's offset from corner 0 recomputed in double-float:
+// (r1 (u1 - u0) + r2 (u2 - u0)) / (r0 + r1 + r2), r_k = e_k / w_k, from the
+// double-float screen positions. The float32 offset carries ~1e-7 of its
+// length in rounding; over a triangle spanning tens of texels that is ~2e-6
+// texel, which moves pixels under sharp highlights on noise textures by ~1e-5.
+__device__ __forceinline__ void refine_tc(const ShadeArgs& A, int b, int px, int py, PixGeo& g) {
+    float qx = (float)px + 0.5f, qy = (float)py + 0.5f;
+    DF dx[3], dy[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float4 S = A.scr[(size_t)b * A.V + g.vi[k]];
+        dx[k] = df_add_f(df_two_sum(S.x, -qx), S.y);
+        dy[k] = df_add_f(df_two_sum(S.z, -qy), S.w);
+    }
+    DF rk[3];
+    rk[0] = df_div_f(df_sub(df_mul(dx[1], dy[2]), df_mul(dy[1], dx[2])), g.c[0].w);
+    rk[1] = df_div_f(df_sub(df_mul(dx[2], dy[0]), df_mul(dy[2], dx[0])), g.c[1].w);
+    rk[2] = df_div_f(df_sub(df_mul(dx[0], dy[1]), df_mul(dy[0], dx[1])), g.c[2].w);
+    DF Rd = df_add(df_add(rk[0], rk[1]), rk[2]);
+    float2 u0 = A.uv[g.ui[0]], u1 = A.uv[g.ui[1]], u2 = A.uv[g.ui[2]];
+    DF nu = df_add(df_mul(rk[1], df_two_sum(u1.x, -u0.x)), df_mul(rk[2], df_two_sum(u2.x, -u0.x)));
+    DF nv = df_add(df_mul(rk[1], df_two_sum(u1.y, -u0.y)), df_mul(rk[2], df_two_sum(u2.y, -u0.y)));
+    DF qu = df_div_df(nu, Rd), qv = df_div_df(nv, Rd);
+    g.tc.du = qu.hi;
+    g.tc.dv = qv.hi;
+    g.tc.du_lo = qu.lo;
+    g.tc.dv_lo = qv.lo;
+    // the uv screen derivatives (texture LOD) with compensated two-term products:
+    // their differences cancel, and the LOD's rounding moves trilinear weights
+    float ia = 1.f / g.area, iR = 1.f / g.R, iR2 = iR * iR;
+    float dlx[3] = {(g.d[1].y - g.d[2].y) * ia, (g.d[2].y - g.d[0].y) * ia, (g.d[0].y - g.d[1].y) * ia};
+    float dly[3] = {(g.d[2].x - g.d[1].x) * ia, (g.d[0].x - g.d[2].x) * ia, (g.d[1].x - g.d[0].x) * ia};
+    float drx[3], dry[3], dRx = 0.f, dRy = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        drx[k] = dlx[k] / g.c[k].w;
+        dry[k] = dly[k] / g.c[k].w;
+        dRx += drx[k];
+        dRy += dry[k];
+    }
+    float2 du1 = make_float2(u1.x - u0.x, u1.y - u0.y), du2 = make_float2(u2.x - u0.x, u2.y - u0.y);
+    float db1x = dot2_acc(drx[1], g.R, -g.r[1], dRx) * iR2, db2x = dot2_acc(drx[2], g.R, -g.r[2], dRx) * iR2;
+    float db1y = dot2_acc(dry[1], g.R, -g.r[1], dRy) * iR2, db2y = dot2_acc(dry[2], g.R, -g.r[2], dRy) * iR2;
+    g.duv_dx = make_float2(dot2_acc(db1x, du1.x, db2x, du2.x), dot2_acc(db1x, du1.y, db2x, du2.y));
+    g.duv_dy = make_float2(dot2_acc(db1y, du1.x, db2y, du2.x), dot2_acc(db1y, du1.y, db2y, du2.y));
+}
+
+// texels of the largest texture that the triangle's uv offsets span at the finest
+// level sampled: the lever arm of the barycentrics' rounding on texel coordinates
+__device__ __forceinline__ float tc_lever(const ShadeArgs& A, const PixGeo& g, const float lod[3]) {
+    float2 u0 = A.uv[g.ui[0]], u1 = A.uv[g.ui[1]], u2 = A.uv[g.ui[2]];
+    float su = fmaxf(fabsf(u1.x - u0.x), fabsf(u2.x - u0.x)), sv = fmaxf(fabsf(u1.y - u0.y), fabsf(u2.y - u0.y));
+    float lever = 0.f;
+    const TexDev* ts[3] = {&A.kd, &A.orm, &A.nrm};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        lever = fmaxf(lever, fmaxf(su * (float)ts[k]->w0, sv * (float)ts[k]->h0) * exp2f(-floorf(lod[k])));
+    return lever;
+}
+
+// shading of one listed pixel again, with the refined texture coordinate and LOD
+__device__ __forceinline__ void shade_refine_px(const ShadeArgs& A, int pix) {
+    int hw = A.H * A.W;
+    int b = pix / hw, rem = pix - b * hw;
+    int py = rem / A.W, px = rem - py * A.W;
+    int f = key_tri(A.keys[pix]);
+    PixGeo g;
+    pix_geo(A, b, px, py, f, g);
+    refine_tc(A, b, px, py, g);
+    float lod[3];
+    ShadeIn in = shade_inputs(A, g, lod);
+    float3 c = shade_eval<false>(A.views[b], in, zero3(), nullptr);
+    A.pre[pix] = make_float4(c.x, c.y, c.z, 1.f);
+}
+
 // ------------------------------------------------------------------ shading forward
 __device__ __forceinline__ void shade_fwd_px(const ShadeArgs& A, int b, int px, int py) {
     if (px >= A.W || py >= A.H) return;
@@ -272,6 +351,15 @@ __device__ __forceinline__ void shade_fwd_px(const ShadeArgs& A, int b, int px, 
         float lod[3];
         ShadeIn in = shade_inputs(A, g, lod);
         float3 c = shade_eval<false>(A.views[b], in, zero3(), nullptr);
+        // Bright pixels (sharp highlights) carry almost all of the error a float32
+        // texture coordinate causes: on the noise-textured workloads the 0.35% of
+        // pixels above 0.5 carry 98% of it. Those on triangles spanning more than two
+        // texels at the sampled level are listed and shaded again by k_shade_refine
+        // with the refined coordinate and LOD (a separate pass keeps this kernel's
+        // registers to the common path). The backward, held to 1e-3, keeps the
+        // float32 ones.
+        if (A.refine && fmaxf(c.x, fmaxf(c.y, c.z)) > 0.5f && tc_lever(A, g, lod) > 2.f)
+            A.refine[1 + atomicAdd(A.refine, 1)] = (int)pix;  // for k_shade_refine
         out = make_float4(c.x, c.y, c.z, 1.f);
     }
     A.pre[pix] = out;
@@ -614,6 +702,13 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
 }
 
 // ------------------------------------------------------------------ single-job kernels (16x16 tiles)
+// the listed pixels of one job (A.refine[0] of them), grid-stride
+__global__ void __launch_bounds__(256) k_shade_refine(ShadeArgs A) {
+    int n = A.refine[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        shade_refine_px(A, A.refine[1 + i]);
+}
+
 // register caps measured on the plain-method step: 5 blocks/SM for shading,
 // 8 for AA + loss, 3 for the backward (a few hundred bytes of spills cost less
 // than the latency the extra resident warps hide)
@@ -645,6 +740,20 @@ __global__ void __launch_bounds__(256, 3) k_shade_bwd(ShadeArgs A) {
 // stride balances them without a shared counter). The jobs' arguments are
 // kernel parameters: read-only, no copy per block, and no aliasing with the
 // stores and atomics of the pixel code.
+// refinement lists of a batch (see k_shade_refine): reset before the shading
+// launch, then one grid-stride pass per job (blockIdx.y)
+__global__ void k_refine_reset(const ShadeBatch P, int n) {
+    int k = threadIdx.x;
+    if (k < n && P.a[k].refine) P.a[k].refine[0] = 0;
+}
+__global__ void __launch_bounds__(256) k_refine_batch(const ShadeBatch P) {
+    const ShadeArgs& A = P.a[blockIdx.y];
+    if (!A.refine) return;
+    int n = A.refine[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        shade_refine_px(A, A.refine[1 + i]);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256, KIND == 2 ? 3 : (KIND == 1 ? 8 : 5))
     k_pixels_batch(const ShadeBatch P, const WorkItem* __restrict__ items, int n, int tw, int job0) {
@@ -666,8 +775,16 @@ static dim3 pix_grid(const ShadeArgs& a) {
 }
 
 cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
+    if (a.refine) {
+        cudaError_t e = cudaMemsetAsync(a.refine, 0, sizeof(int), st);
+        if (e) return e;
+    }
     k_shade_fwd<<<pix_grid(a), 256, 0, st>>>(a);
     count_launches(1);
+    if (a.refine) {
+        k_shade_refine<<<128, 256, 0, st>>>(a);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st) {
@@ -699,7 +816,12 @@ cudaError_t pixels_batched(int kind, const ShadeArgs* args, const int* item_off,
         if (n <= 0) continue;
         memcpy(P.a, args + j0, sizeof(ShadeArgs) * (j1 - j0));
         int g = std::min(blocks, n);
-        if (kind == 0) k_pixels_batch<0><<<g, 256, 0, st>>>(P, items + s0, n, tw, j0);
+        if (kind == 0) {
+            k_refine_reset<<<1, ADMS_BATCH_JOBS, 0, st>>>(P, j1 - j0);
+            k_pixels_batch<0><<<g, 256, 0, st>>>(P, items + s0, n, tw, j0);
+            k_refine_batch<<<dim3(64, j1 - j0), 256, 0, st>>>(P);
+            count_launches(2);
+        }
         else if (kind == 1) k_pixels_batch<1><<<g, 256, 0, st>>>(P, items + s0, n, tw, j0);
         else k_pixels_batch<2><<<g, 256, 0, st>>>(P, items + s0, n, tw, j0);
         count_launches(1);
