@@ -49,6 +49,32 @@ def _rank_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+# ----------------------------------------------------------------------------- replicas
+# "Replicas only": each rank runs the whole step on its own GPU with its own
+# views; nothing is exchanged but the timing, and the job's throughput is the
+# sum over ranks of pixels over the slowest rank's time.
+def replica_seed(rank):
+    """Seed of a rank's camera/light stream (disjoint streams per rank)."""
+    return rank * 100003 + 7
+
+
+def max_over_ranks(x, world, device):
+    """The maximum of a per-rank scalar over all ranks (every rank gets it)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_mpix(world, px_step, steps, seconds):
+    """Whole-job Mpixels/s: every rank processed px_step pixels per step."""
+    return world * px_step * steps / seconds / 1e6
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -229,7 +255,7 @@ def run_native(args):
     cand = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01)
     plain = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, batch_views=VIEWS)
     n_steps = args.warmup + args.steps
-    host_views = [synth.sample_views(rank * 100003 + 7, i, VIEWS, RES, RES) for i in range(n_steps)]
+    host_views = [synth.sample_views(replica_seed(rank), i, VIEWS, RES, RES) for i in range(n_steps)]
     view_np = np.stack([v.view(np.uint8) for v in host_views])                  # (steps, 8*112)
     dev_views = torch.from_numpy(view_np).to(dev)
     pinned_views = torch.from_numpy(view_np).pin_memory()
@@ -284,12 +310,7 @@ def run_native(args):
             evs[s + 1].record(stream)
         barrier()
         per = [evs[s].elapsed_time(evs[s + 1]) for s in range(k)]
-        total = evs[0].elapsed_time(evs[-1])
-        if world > 1:
-            t = torch.tensor([total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t)
-        return total, per
+        return max_over_ranks(evs[0].elapsed_time(evs[-1]), world, dev), per
 
     # warm-up (also sizes all scratch), then record one step as a CUDA graph
     for i in range(args.warmup):
@@ -332,10 +353,7 @@ def run_native(args):
     e2e_s = time.perf_counter() - t0
     clocks = sampler.stop()
     clocks["window"] = "graph, fused, plain, profiled and end-to-end timed regions"
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t)
+    e2e_s = max_over_ranks(e2e_s, world, dev)
 
     # workload facts for the bytes model
     keys = ctx.keys(cand, (VIEWS, RES, RES))
@@ -349,10 +367,10 @@ def run_native(args):
               V=cfg["cand"].mesh.n_verts, F=cfg["cand"].mesh.n_tris, Fr=cfg["ref"].mesh.n_tris)
 
     px_step = VIEWS * RES * RES
-    value = world * px_step * args.steps / (total_ms / 1e3) / 1e6
-    nograph_value = world * px_step * args.steps / (fused_ms_nograph / 1e3) / 1e6
-    plain_value = world * px_step * args.steps / (plain_ms / 1e3) / 1e6
-    e2e_value = world * px_step * args.steps / e2e_s / 1e6
+    value = whole_job_mpix(world, px_step, args.steps, total_ms / 1e3)
+    nograph_value = whole_job_mpix(world, px_step, args.steps, fused_ms_nograph / 1e3)
+    plain_value = whole_job_mpix(world, px_step, args.steps, plain_ms / 1e3)
+    e2e_value = whole_job_mpix(world, px_step, args.steps, e2e_s)
     per_sorted = sorted(per)
 
     # roofline of the dominant kernel stage
