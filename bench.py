@@ -37,13 +37,12 @@ WORKLOAD = ("reference 200k-tri fBm icosphere with 2048^2 procedural maps; candi
 # DRAM bytes per launch of the dominant kernel from an ncu capture, valid only
 # for the source it was measured on (sha256 of the listed files).
 TRAFFIC = {
-    "shade_bwd": {"bytes_per_launch": 181112320 + 26294784,
+    "shade_bwd": {"bytes_per_launch": 163197696 + 59788544,
                   "files": ["paper_2104_03989_gb300/csrc/shade.cu", "paper_2104_03989_gb300/csrc/common.cuh",
                             "paper_2104_03989_gb300/csrc/kernels.cuh"],
-                  "sha": "537f78f6adcd0b08",
+                  "sha": "1dc4bc555dacdcb5",
                   "capture": "profiles/shade_bwd_plain_workload.md"},
 }
-
 
 def _rank_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
