@@ -562,7 +562,7 @@ def adam_update(p, g, m, v, t, lr, name):
     mh = m / (1 - ADAM_B1 ** (t + 1))
     vh = v / (1 - ADAM_B2 ** (t + 1))
     p = p - lr * mh / (torch.sqrt(vh) + ADAM_EPS)
-    cl = CLAMPS.get(name)
+    cl = CLAMPS.get(name.split("@")[0])  # a per-level texture "kd@3" clamps like kd
     if cl is not None:
         chans = []
         for c, (lo, hi) in enumerate(cl):

@@ -24,7 +24,7 @@ class OracleJob:
 
     scene: synth.Scene. Textures are (h, w, 4); `disp` (h, w) when present."""
 
-    def __init__(self, scene, loss="logl1", lr0=0.01, lam0=None, relative_laplacian=False):
+    def __init__(self, scene, loss="logl1", lr0=0.01, lam0=None, relative_laplacian=False, per_level=False):
         m = scene.mesh
         self.tri = torch.as_tensor(m.tri_pos.astype(np.int64))
         self.tri_uv = torch.as_tensor(m.tri_uv.astype(np.int64))
@@ -41,6 +41,19 @@ class OracleJob:
         self.tess_levels = int(scene.tess_levels)
         self.mips = bool(scene.mips)
         self.optimize = {k: bool(scene.optimize.get(k, False)) for k in self.params}
+        # Per-level latent textures (the prefiltering variant of Sec. 6): every mip
+        # level of an optimized texture is its own latent "name@k" (k >= 1), starting
+        # from the box-filter chain of the given level 0 (reading: the paper does not
+        # say how the levels start)
+        self.per_level = bool(per_level) and self.mips
+        if self.per_level:
+            for name in ("kd", "orm", "nrm"):
+                if not self.optimize[name]:
+                    continue
+                chain = R.mip_chain(self.params[name])
+                for k in range(1, len(chain)):
+                    self.params[f"{name}@{k}"] = chain[k].detach().clone()
+                    self.optimize[f"{name}@{k}"] = True
         self.loss = loss
         self.lr0 = float(lr0)
         self.lam0_user = lam0
@@ -78,7 +91,11 @@ def geometry(job, params):
 def texture_levels(job, params):
     out = {}
     for name in ("kd", "orm", "nrm"):
-        out[name] = R.mip_chain(params[name]) if job.mips else [params[name]]
+        if job.per_level and f"{name}@1" in params:
+            n = 1 + sum(1 for k in params if k.startswith(name + "@"))
+            out[name] = [params[name]] + [params[f"{name}@{k}"] for k in range(1, n)]
+        else:
+            out[name] = R.mip_chain(params[name]) if job.mips else [params[name]]
     return out
 
 

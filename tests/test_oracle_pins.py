@@ -514,3 +514,64 @@ def test_gradients_match_central_differences(loss, tess):
     # only |.| and the clamps are kinks; a pick straddling one within +-h may disagree
     assert np.median(errs) < 1e-5
     assert (errs < 1e-3).mean() >= 0.95
+
+
+# ---------------------------------------------------------------- per-level latent textures (Sec. 6)
+def _per_level_case():
+    c = synth.config_small()
+    c["cand"].optimize = {"pos": True, "kd": True, "orm": False, "nrm": True}
+    views = synth.fixed_view(64, 64)
+    ref = S.render_reference(c["ref"], views, 64, 64)[0].numpy()
+    return c, views, ref
+
+
+def _grads(job, views, ref):
+    params = {k: v.clone().requires_grad_(job.optimize[k]) for k, v in job.params.items()}
+    obj = S.objective(job, params, views, torch.as_tensor(ref.astype(np.float64)), 64, 64, lam=0.0)
+    live = [k for k in params if job.optimize[k]]
+    gs = torch.autograd.grad(obj["total"], [params[k] for k in live], allow_unused=True)
+    return obj, {k: (g if g is not None else torch.zeros_like(params[k])) for k, g in zip(live, gs)}
+
+
+def test_per_level_textures_start_as_the_box_filter_chain():
+    c, views, ref = _per_level_case()
+    std, lev = S.OracleJob(c["cand"], loss="l1"), S.OracleJob(c["cand"], loss="l1", per_level=True)
+    assert sum(k.startswith("kd@") for k in lev.params) == 8   # 256^2: levels 1..8
+    a = S.render(std, std.params, views, 64, 64)["img"]
+    b = S.render(lev, lev.params, views, 64, 64)["img"]
+    assert torch.equal(a, b)
+
+
+def test_per_level_gradients_fold_to_the_standard_gradient():
+    # the standard job's level-0 gradient is the adjoint of the box-filter chain applied
+    # to the per-level gradients: sum over k of 4^-k times level k's gradient, spread
+    # over each level-k texel's 2^k x 2^k block of level-0 texels
+    c, views, ref = _per_level_case()
+    std, lev = S.OracleJob(c["cand"], loss="l1"), S.OracleJob(c["cand"], loss="l1", per_level=True)
+    _, gs = _grads(std, views, ref)
+    _, gl = _grads(lev, views, ref)
+    for name in ("kd", "nrm"):
+        fold = gl[name].clone()
+        k = 1
+        while f"{name}@{k}" in gl:
+            g = gl[f"{name}@{k}"]
+            fold += g.repeat_interleave(2 ** k, 0).repeat_interleave(2 ** k, 1) / 4.0 ** k
+            k += 1
+        assert float(fold.abs().max()) > 0
+        assert torch.allclose(fold, gs[name], rtol=1e-10, atol=1e-14 * float(gs[name].abs().max()))
+        assert float(gl[f"{name}@2"].abs().max()) > 0   # a sampled coarse level gets its own gradient
+
+
+def test_per_level_step_updates_levels_independently():
+    c, views, ref = _per_level_case()
+    lev = S.OracleJob(c["cand"], loss="l1", per_level=True, lam0=1.0)
+    before = {k: v.clone() for k, v in lev.params.items()}
+    S.step(lev, views, ref, 64, 64)
+    # the 1x1 level is not sampled at this view's LOD: zero gradient, unchanged by Adam
+    assert torch.equal(lev.params["kd@8"], before["kd@8"])
+    # a sampled level moved on its own: it is no longer the box filter of the new level 0
+    assert not torch.equal(lev.params["kd@2"], before["kd@2"])
+    chain = R.mip_chain(lev.params["kd"])
+    assert not torch.allclose(chain[2], lev.params["kd@2"])
+    # clamps act per level as on level 0
+    assert float(lev.params["kd@2"].min()) >= 0.0 and float(lev.params["kd@2"].max()) <= 1.0
