@@ -251,8 +251,9 @@ def run_native(args):
     torch.cuda.set_stream(stream)
     ctx = Context(stream=stream)
     ref_job = ctx.create_job(cfg["ref"], frozen=True)
-    cand = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01)
-    plain = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, batch_views=VIEWS)
+    pl = bool(args.per_level_textures)
+    cand = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, per_level_textures=pl)
+    plain = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, batch_views=VIEWS, per_level_textures=pl)
     n_steps = args.warmup + args.steps
     host_views = [synth.sample_views(replica_seed(rank), i, VIEWS, RES, RES) for i in range(n_steps)]
     view_np = np.stack([v.view(np.uint8) for v in host_views])                  # (steps, 8*112)
@@ -359,10 +360,12 @@ def run_native(args):
     covered = int((keys != -1).sum())
     pv = ctx.params(cand)
     texels = sum(pv[n].shape[0] * pv[n].shape[1] for n in ("kd", "orm", "nrm"))
+    # latent texels Adam updates: level 0, or every level of each chain with per-level latents
+    latent_texels = sum(pv[n + "_chain"].shape[0] for n in ("kd", "orm", "nrm")) if pl else texels
     ctx.render_reference(ref_job, host_views[-1], RES, RES, out=ref_buf)
     rkeys = ctx.keys(ref_job, (VIEWS, RES, RES))
     covered_ref = int((rkeys != -1).sum())
-    wl = dict(P=VIEWS * RES * RES, C=covered, Cr=covered_ref, texels=texels, texel_floats=4 * texels,
+    wl = dict(P=VIEWS * RES * RES, C=covered, Cr=covered_ref, texels=texels, texel_floats=4 * latent_texels,
               V=cfg["cand"].mesh.n_verts, F=cfg["cand"].mesh.n_tris, Fr=cfg["ref"].mesh.n_tris)
 
     px_step = VIEWS * RES * RES
@@ -408,7 +411,8 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": VIEWS * world, "seq_len": None,
+            "config": {"workload": WORKLOAD + ("; every mip level of each texture its own latent (Sec. 6)" if pl else ""),
+                       "global_batch": VIEWS * world, "seq_len": None,
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "launch": "one CUDA graph per step (reference render, forward+loss, backward, Adam)",
                        "l2": "working set > 126 MB L2 (textures, moments, buffers); no flush"},
@@ -629,6 +633,8 @@ def main():
     ap.add_argument("--iterations", type=int, default=200, help="serving: iterations per job")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: HBM budget")
     ap.add_argument("--per-job-iterations", type=int, default=3, help="serving: iterations of the per-job loop")
+    ap.add_argument("--per-level-textures", action="store_true",
+                    help="plain workload with every mip level of each texture an independent latent (Sec. 6)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference_arm(args)

@@ -101,6 +101,12 @@ typedef struct {
     int32_t aa;              /* 1: silhouette antialiasing (default), 0: off */
     float lr0;               /* initial learning rate (Sec. 5.3), e.g. 0.01 */
     float lambda0;           /* initial Laplacian weight; <= 0 selects 0.25 L_image / L_delta at t = 0 */
+    int32_t per_level_textures; /* 1: every mip level of each optimized texture is its own latent
+                                  (Sec. 6, prefiltering for several rendering resolutions): the
+                                  levels start as the box-filter chain of the given level 0, each
+                                  level takes its own gradient and Adam moments, and nothing is
+                                  folded or rebuilt; needs mips. 0: one latent per texture (level
+                                  0), coarser levels are its box-filter chain */
 } adms_opt_params;
 
 /* Device pointers into a job's resident state (owned by the library, valid
@@ -207,13 +213,16 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
 
 /* Level-0 gradient of each optimized texture with the adjoint of the box-filter
  * mip chain folded in (what the optimizer step applies), written to device
- * buffers [h][w][4] (NULL entries skipped); nothing is updated or zeroed.
+ * buffers [h][w][4] (NULL entries skipped); nothing is updated or zeroed. With
+ * per-level textures, level 0's own gradient (the coarser levels' gradients
+ * stay in the chain behind adms_param_view's gradient pointers).
  * ADMS_ERR_STATE for a texture that is not optimized. */
 adms_status adms_job_fold_gradients(adms_ctx* ctx, adms_job job, float* g_kd, float* g_orm, float* g_nrm);
 /* Zero every gradient buffer of a job (positions, displacement, textures). */
 adms_status adms_job_zero_gradients(adms_ctx* ctx, adms_job job);
-/* Rebuild the mip chains from level 0 and recompute the vertex frame at the
- * next forward: call after writing latents through adms_job_params pointers. */
+/* Rebuild the mip chains from level 0 (not for per-level textures, whose levels
+ * are latents) and recompute the vertex frame at the next forward: call after
+ * writing latents through adms_job_params pointers. */
 adms_status adms_job_invalidate(adms_ctx* ctx, adms_job job);
 /* L_delta of the job's current positions (Eq. 4; delta' = 0 unless the job
  * was created with relative_laplacian) into out_loss (device scalar), and

@@ -21,6 +21,7 @@ struct TexState {
     float4* m = nullptr;     // level 0
     float4* v = nullptr;
     int* done = nullptr;     // tiles finished in the current tiled Adam launch
+    bool per_level = false;  // every level is a latent: m, v span the chain
     int w = 0, h = 0, levels = 0;
     int off[ADMS_MAX_LEVELS] = {0};
     size_t total = 0;
@@ -256,7 +257,8 @@ adms_status to_host(adms_ctx* ctx, const T* src, size_t n, std::vector<T>& dst) 
     return ADMS_OK;
 }
 
-adms_status tex_create(adms_ctx* ctx, Job& j, TexState& t, const float* src, int h, int w, bool mips, bool opt) {
+adms_status tex_create(adms_ctx* ctx, Job& j, TexState& t, const float* src, int h, int w, bool mips, bool opt,
+                       bool per_level) {
     if (!src || !pow2(h) || !pow2(w)) return fail(ctx, ADMS_ERR_ARG, "texture sizes must be powers of two");
     t.w = w;
     t.h = h;
@@ -274,10 +276,12 @@ adms_status tex_create(adms_ctx* ctx, Job& j, TexState& t, const float* src, int
     t.total = off;
     AL(t.data, t.total);
     CK(cudaMemcpyAsync(t.data, src, (size_t)w * h * sizeof(float4), cudaMemcpyDefault, ctx->stream));
+    t.per_level = opt && per_level && t.levels > 1;
     if (opt) {
+        size_t nm = t.per_level ? t.total : (size_t)w * h;
         AL(t.grad, t.total);
-        AL(t.m, (size_t)w * h);
-        AL(t.v, (size_t)w * h);
+        AL(t.m, nm);
+        AL(t.v, nm);
         AL(t.done, 1);
     }
     CK(mip_build(t.dev(), ctx->stream));
@@ -711,9 +715,11 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
     AL(j.g_pos_acc, (size_t)j.V * 3);
     AL(j.st, 1);
     bool mips = mat->mips != 0;
-    if ((s = tex_create(ctx, j, j.kd, mat->kd, mat->kd_h, mat->kd_w, mips, j.opt.optimize_kd))) return s;
-    if ((s = tex_create(ctx, j, j.orm, mat->orm, mat->orm_h, mat->orm_w, mips, j.opt.optimize_orm))) return s;
-    if ((s = tex_create(ctx, j, j.nrm, mat->nrm, mat->nrm_h, mat->nrm_w, mips, j.opt.optimize_nrm))) return s;
+    bool pl = j.opt.per_level_textures != 0;
+    if (pl && !mips) return fail(ctx, ADMS_ERR_ARG, "per-level textures need mip chains");
+    if ((s = tex_create(ctx, j, j.kd, mat->kd, mat->kd_h, mat->kd_w, mips, j.opt.optimize_kd, pl))) return s;
+    if ((s = tex_create(ctx, j, j.orm, mat->orm, mat->orm_h, mat->orm_w, mips, j.opt.optimize_orm, pl))) return s;
+    if ((s = tex_create(ctx, j, j.nrm, mat->nrm, mat->nrm_h, mat->nrm_w, mips, j.opt.optimize_nrm, pl))) return s;
     if (j.opt.relative_laplacian) {
         AL(j.delta_ref, (size_t)Vb * 3);
         LapArgs la{Vb, j.pos, j.ring_off, j.ring, nullptr, j.delta_ref, j.g_pos, j.st};
@@ -886,7 +892,7 @@ struct CkptHeader {
     int32_t LV, V, F, tess_levels, dh, dw;
     int32_t tex_w[3], tex_h[3], tex_levels[3], tex_opt[3];
     int32_t optimize[5];  // pos, kd, orm, nrm, disp
-    int32_t loss, relative_laplacian, batch_views, aa;
+    int32_t loss, relative_laplacian, batch_views, aa, per_level_textures;
     float lr0, lambda0;
     uint64_t section_bytes[16];
 };
@@ -923,6 +929,7 @@ void ckpt_describe(Job& j, CkptHeader& h, std::vector<CkptSection>& secs) {
     h.relative_laplacian = j.opt.relative_laplacian;
     h.batch_views = j.opt.batch_views;
     h.aa = j.opt.aa;
+    h.per_level_textures = j.opt.per_level_textures;
     h.lr0 = j.opt.lr0;
     h.lambda0 = j.opt.lambda0;
     secs.clear();
@@ -937,8 +944,9 @@ void ckpt_describe(Job& j, CkptHeader& h, std::vector<CkptSection>& secs) {
         TexState& t = *const_cast<TexState*>(tx[k]);
         add(t.data, t.total * sizeof(float4));  // the whole chain: resumes without a rebuild
         if (t.opt) {
-            add(t.m, (size_t)t.w * t.h * sizeof(float4));
-            add(t.v, (size_t)t.w * t.h * sizeof(float4));
+            size_t nm = (t.per_level ? t.total : (size_t)t.w * t.h) * sizeof(float4);
+            add(t.m, nm);
+            add(t.v, nm);
         }
     }
     size_t pd = (size_t)j.dh * j.dw * sizeof(float);
@@ -1349,7 +1357,9 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         for (int m = 0; m < 3; ++m) {
             if (!maps[m]->opt) continue;
             TexDev td = maps[m]->dev();
-            if (adam_tiled(td)) tiled.push_back(TexAdam{td, maps[m]->m, maps[m]->v, j.st, maps[m]->done, m, 0});
+            if (maps[m]->per_level)
+                CK(TIMED(ST_ADAM, adam_texture_levels(td, maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
+            else if (adam_tiled(td)) tiled.push_back(TexAdam{td, maps[m]->m, maps[m]->v, j.st, maps[m]->done, m, 0});
             else CK(TIMED(ST_ADAM, adam_texture_and_mips(td, maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
         }
     }
@@ -1369,7 +1379,11 @@ adms_status adms_job_fold_gradients(adms_ctx* ctx, adms_job job, float* g_kd, fl
     for (int m = 0; m < 3; ++m) {
         if (!outs[m]) continue;
         if (!maps[m]->opt) return fail(ctx, ADMS_ERR_STATE, "texture is not optimized: no gradient");
-        CK(fold_mip_gradient(maps[m]->dev(), reinterpret_cast<float4*>(outs[m]), ctx->stream));
+        if (maps[m]->per_level)
+            CK(cudaMemcpyAsync(outs[m], maps[m]->grad, sizeof(float4) * maps[m]->w * maps[m]->h,
+                               cudaMemcpyDeviceToDevice, ctx->stream));
+        else
+            CK(fold_mip_gradient(maps[m]->dev(), reinterpret_cast<float4*>(outs[m]), ctx->stream));
     }
     return ADMS_OK;
 }
@@ -1395,7 +1409,8 @@ adms_status adms_job_invalidate(adms_ctx* ctx, adms_job job) {
     Job* j = get_job(ctx, job);
     if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
     TexState* maps[3] = {&j->kd, &j->orm, &j->nrm};
-    for (int m = 0; m < 3; ++m) CK(TIMED(ST_MIP, mip_build(maps[m]->dev(), ctx->stream)));
+    for (int m = 0; m < 3; ++m)
+        if (!maps[m]->per_level) CK(TIMED(ST_MIP, mip_build(maps[m]->dev(), ctx->stream)));
     j->frame_valid = false;
     return ADMS_OK;
 }

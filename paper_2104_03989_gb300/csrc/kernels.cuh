@@ -239,6 +239,10 @@ cudaError_t schedule_step(const SchedArgs& a, cudaStream_t st);
 cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const JobState* js, cudaStream_t st);
 // Adam on a float4 texture (level 0) with the mip-chain adjoint folded in; clamp_kind 0 kd, 1 orm, 2 nrm
 cudaError_t adam_texture(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js, cudaStream_t st);
+// Adam on every level of a texture whose mip levels are independent latents (m, v
+// hold the whole chain); no mip adjoint, no rebuild
+cudaError_t adam_texture_levels(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js,
+                                cudaStream_t st);
 // rebuild levels 1.. of a mip chain from level 0 (2x2 box average)
 cudaError_t mip_build(const TexDev& t, cudaStream_t st);
 // Adam on a texture, then the rebuild of its mip chain (textures that do not tile)

@@ -92,6 +92,50 @@ cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const
 
 __device__ __forceinline__ float clampf(float x, float lo, float hi) { return fminf(fmaxf(x, lo), hi); }
 
+// range clamps after an update (Sec. 5.3 reading): kd in [0,1]; (gamma, r, m) in
+// [0,1] x [0.08,1] x [0,1]; normal xy in [-1,1], z in [0,1]
+__device__ __forceinline__ float4 clamp_texel(float4 p, int clamp_kind) {
+    if (clamp_kind == 0) {
+        p = make_float4(clampf(p.x, 0.f, 1.f), clampf(p.y, 0.f, 1.f), clampf(p.z, 0.f, 1.f), clampf(p.w, 0.f, 1.f));
+    } else if (clamp_kind == 1) {
+        p.x = clampf(p.x, 0.f, 1.f);
+        p.y = clampf(p.y, ADMS_ROUGH_MIN, 1.f);
+        p.z = clampf(p.z, 0.f, 1.f);
+    } else if (clamp_kind == 2) {
+        p.x = clampf(p.x, -1.f, 1.f);
+        p.y = clampf(p.y, -1.f, 1.f);
+        p.z = clampf(p.z, 0.f, 1.f);
+    }
+    return p;
+}
+
+// Adam on every texel of every level of a texture whose levels are independent
+// latents (Sec. 6 prefiltering): each level keeps its own gradient and moments,
+// and nothing is folded or rebuilt
+__global__ void k_adam_tex_levels(TexDev t, float4* __restrict__ m, float4* __restrict__ v, long long n,
+                                  int clamp_kind, const JobState* __restrict__ js) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float lr = js->lr, bc1 = js->bc1, bc2 = js->bc2;
+    float4 g = t.grad[i], p = t.tex[i], mm = m[i], vv = v[i];
+    p.x = adam1(p.x, g.x, mm.x, vv.x, lr, bc1, bc2);
+    p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
+    p.z = adam1(p.z, g.z, mm.z, vv.z, lr, bc1, bc2);
+    p.w = adam1(p.w, g.w, mm.w, vv.w, lr, bc1, bc2);
+    const_cast<float4*>(t.tex)[i] = clamp_texel(p, clamp_kind);
+    m[i] = mm;
+    v[i] = vv;
+    t.grad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+cudaError_t adam_texture_levels(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js,
+                                cudaStream_t st) {
+    long long n = t.off[t.levels - 1] + (long long)max(t.w0 >> (t.levels - 1), 1) * max(t.h0 >> (t.levels - 1), 1);
+    k_adam_tex_levels<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(t, m, v, n, clamp_kind, js);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 __global__ void k_adam_tex(TexDev t, float4* __restrict__ m, float4* __restrict__ v, int clamp_kind,
                            const JobState* __restrict__ js) {
     int n = t.w0 * t.h0;
@@ -114,17 +158,7 @@ __global__ void k_adam_tex(TexDev t, float4* __restrict__ m, float4* __restrict_
     p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
     p.z = adam1(p.z, g.z, mm.z, vv.z, lr, bc1, bc2);
     p.w = adam1(p.w, g.w, mm.w, vv.w, lr, bc1, bc2);
-    if (clamp_kind == 0) {
-        p = make_float4(clampf(p.x, 0.f, 1.f), clampf(p.y, 0.f, 1.f), clampf(p.z, 0.f, 1.f), clampf(p.w, 0.f, 1.f));
-    } else if (clamp_kind == 1) {
-        p.x = clampf(p.x, 0.f, 1.f);
-        p.y = clampf(p.y, ADMS_ROUGH_MIN, 1.f);
-        p.z = clampf(p.z, 0.f, 1.f);
-    } else if (clamp_kind == 2) {
-        p.x = clampf(p.x, -1.f, 1.f);
-        p.y = clampf(p.y, -1.f, 1.f);
-        p.z = clampf(p.z, 0.f, 1.f);
-    }
+    p = clamp_texel(p, clamp_kind);
     const_cast<float4*>(t.tex)[i] = p;
     m[i] = mm;
     v[i] = vv;
@@ -150,17 +184,7 @@ __device__ __forceinline__ float4 adam_texel(const TexDev& t, float4* __restrict
     p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
     p.z = adam1(p.z, g.z, mm.z, vv.z, lr, bc1, bc2);
     p.w = adam1(p.w, g.w, mm.w, vv.w, lr, bc1, bc2);
-    if (clamp_kind == 0) {
-        p = make_float4(clampf(p.x, 0.f, 1.f), clampf(p.y, 0.f, 1.f), clampf(p.z, 0.f, 1.f), clampf(p.w, 0.f, 1.f));
-    } else if (clamp_kind == 1) {
-        p.x = clampf(p.x, 0.f, 1.f);
-        p.y = clampf(p.y, ADMS_ROUGH_MIN, 1.f);
-        p.z = clampf(p.z, 0.f, 1.f);
-    } else if (clamp_kind == 2) {
-        p.x = clampf(p.x, -1.f, 1.f);
-        p.y = clampf(p.y, -1.f, 1.f);
-        p.z = clampf(p.z, 0.f, 1.f);
-    }
+    p = clamp_texel(p, clamp_kind);
     const_cast<float4*>(t.tex)[i] = p;
     m[i] = mm;
     v[i] = vv;

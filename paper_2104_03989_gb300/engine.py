@@ -53,10 +53,11 @@ class Context:
 
     # ------------------------------------------------------------------ jobs
     def create_job(self, scene, optimize=None, loss="logl1", lr0=0.01, lambda0=0.0, batch_views=0, aa=True,
-                   relative_laplacian=False, frozen=False, seed=0):
-        """scene: object with .mesh (pos, uv, tri_pos, tri_uv), .kd, .orm, .nrm, .mips (numpy)."""
+                   relative_laplacian=False, frozen=False, seed=0, per_level_textures=False):
+        """scene: object with .mesh (pos, uv, tri_pos, tri_uv), .kd, .orm, .nrm, .mips (numpy).
+        per_level_textures: every mip level of each optimized texture is its own latent."""
         mesh, mat, opt, keep = self._descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian,
-                                           frozen)
+                                           frozen, per_level_textures)
         return B.adms_job_create(self.ctx, mesh, mat, opt, seed)
 
     def export_job(self, job):
@@ -64,15 +65,15 @@ class Context:
         return B.adms_job_export(self.ctx, job)
 
     def import_job(self, blob, scene, optimize=None, loss="logl1", lr0=0.01, lambda0=0.0, batch_views=0, aa=True,
-                   relative_laplacian=False, frozen=False):
+                   relative_laplacian=False, frozen=False, per_level_textures=False):
         """A new job resumed from export_job's output; scene and options as given
         when the exported job was created."""
         mesh, mat, opt, keep = self._descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian,
-                                           frozen)
+                                           frozen, per_level_textures)
         return B.adms_job_import(self.ctx, mesh, mat, opt, np.ascontiguousarray(blob, dtype=np.uint8))
 
     @staticmethod
-    def _descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian, frozen):
+    def _descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian, frozen, per_level_textures):
         m = scene.mesh
         arrays = dict(pos=_c32(m.pos, np.float32), uv=_c32(m.uv, np.float32), tri=_c32(m.tri_pos, np.int32),
                       tri_uv=_c32(m.tri_uv, np.int32), kd=_c32(scene.kd, np.float32),
@@ -86,7 +87,7 @@ class Context:
         if not frozen or levels:
             opt = B.opt_params(optimize if optimize is not None else getattr(scene, "optimize", {}), loss=loss,
                                tess_levels=levels, batch_views=batch_views, relative_laplacian=relative_laplacian,
-                               aa=aa, lr0=lr0, lambda0=lambda0)
+                               aa=aa, lr0=lr0, lambda0=lambda0, per_level_textures=per_level_textures)
             if frozen:
                 for k in ("optimize_pos", "optimize_kd", "optimize_orm", "optimize_nrm", "optimize_disp"):
                     setattr(opt, k, 0)
@@ -112,6 +113,7 @@ class Context:
             h, w, L = getattr(pv, name + "_h"), getattr(pv, name + "_w"), getattr(pv, name + "_levels")
             total = sum(max(h >> k, 1) * max(w >> k, 1) for k in range(L))
             out[name] = device_view(getattr(pv, name), (h, w, 4))
+            out[name + "_chain"] = device_view(getattr(pv, name), (total, 4))
             out["g_" + name] = device_view(getattr(pv, "g_" + name), (h, w, 4))
             out["g_" + name + "_chain"] = device_view(getattr(pv, "g_" + name), (total, 4))
             out[name + "_levels"] = L

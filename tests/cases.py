@@ -65,6 +65,17 @@ def oracle_reference(scene, views, H, W):
     return img.numpy().astype(np.float32), keys
 
 
+def chain_levels(chain, h, w, levels):
+    """Split a texture's mip chain (total_texels, 4), level after level, into
+    per-level (h_k, w_k, 4) arrays."""
+    out, off = [], 0
+    for k in range(levels):
+        hk, wk = max(h >> k, 1), max(w >> k, 1)
+        out.append(chain[off: off + hk * wk].reshape(hk, wk, 4))
+        off += hk * wk
+    return out
+
+
 def fold_mips(g, h, w, levels):
     """Level-0 gradient of a texture from the gradients of its whole mip chain.
 
@@ -80,10 +91,10 @@ def fold_mips(g, h, w, levels):
     return out
 
 
-def oracle_grads(scene, views, refs, H, W, loss):
+def oracle_grads(scene, views, refs, H, W, loss, per_level=False):
     """Oracle image-loss gradients (lambda = 0), images, keys, loss, and the
     vertices whose gradient is not unique at float32 resolution."""
-    job = S.OracleJob(scene, loss=loss)
+    job = S.OracleJob(scene, loss=loss, per_level=per_level)
     params = {k: v.clone().requires_grad_(job.optimize[k]) for k, v in job.params.items()}
     diags = []
     obj = S.objective(job, params, views, torch.as_tensor(refs.astype(np.float64)), H, W, lam=0.0, diags=diags)
