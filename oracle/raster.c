@@ -276,3 +276,31 @@ void oracle_raster(const int32_t* XY, const float* z01, const int8_t* ok,
         }
     }
 }
+
+/* Skinned positions (Eq. 2) under the float32 contract that visibility uses:
+ *   v^s_i = sum over bones b in ascending order of w_ib * (M_b [v_i; 1])[0..2],
+ *   where row r of M_b v is ((M[r][0] x + M[r][1] y) + M[r][2] z) + M[r][3],
+ *   and the weighted sum starts at 0 and adds w_ib * t_r for b = 0, 1, ...;
+ *   every operation rounded once (no FMA; built with -ffp-contract=off).
+ * pos [V][3], w [V][B] (row per vertex), bones [B][16] row-major 4x4. */
+void oracle_skin_positions(const float* pos, int V, const float* w, int B, const float* bones, float* out)
+{
+    for (int i = 0; i < V; ++i) {
+        float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int b = 0; b < B; ++b) {
+            const float* M = bones + 16 * b;
+            float wb = w[(size_t)i * B + b];
+            for (int r = 0; r < 3; ++r) {
+                float t = M[4 * r] * x;
+                t = t + M[4 * r + 1] * y;
+                t = t + M[4 * r + 2] * z;
+                t = t + M[4 * r + 3];
+                acc[r] = acc[r] + wb * t;
+            }
+        }
+        out[3 * i] = acc[0];
+        out[3 * i + 1] = acc[1];
+        out[3 * i + 2] = acc[2];
+    }
+}

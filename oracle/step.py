@@ -13,6 +13,7 @@ import torch
 
 from . import render as R
 from . import visibility
+from . import skinning as SK
 from . import tessellate as TS
 
 F64 = torch.float64
@@ -24,7 +25,8 @@ class OracleJob:
 
     scene: synth.Scene. Textures are (h, w, 4); `disp` (h, w) when present."""
 
-    def __init__(self, scene, loss="logl1", lr0=0.01, lam0=None, relative_laplacian=False, per_level=False):
+    def __init__(self, scene, loss="logl1", lr0=0.01, lam0=None, relative_laplacian=False, per_level=False,
+                 skin_weights=None):
         m = scene.mesh
         self.tri = torch.as_tensor(m.tri_pos.astype(np.int64))
         self.tri_uv = torch.as_tensor(m.tri_uv.astype(np.int64))
@@ -45,6 +47,14 @@ class OracleJob:
         # level of an optimized texture is its own latent "name@k" (k >= 1), starting
         # from the box-filter chain of the given level 0 (reading: the paper does not
         # say how the levels start)
+        # Skinning (Eq. 2): dense weights (V, B) are a latent "w"; the bone matrices of
+        # the frame being rendered are set per step in self.bones (B, 4, 4)
+        self.bones = None
+        if skin_weights is not None:
+            w = torch.as_tensor(np.asarray(skin_weights, dtype=np.float64))
+            self.params["w"] = w
+            self.optimize["w"] = True
+            self.bones = torch.eye(4, dtype=torch.float64).repeat(w.shape[1], 1, 1)
         self.per_level = bool(per_level) and self.mips
         if self.per_level:
             for name in ("kd", "orm", "nrm"):
@@ -78,6 +88,8 @@ def geometry(job, params):
     smooth normals and tangents (Sec. 5.1)."""
     if job.tess is None:
         pos, tri, uv, tri_uv = params["pos"], job.tri, job.uv, job.tri_uv
+        if job.bones is not None:
+            pos = SK.skin(pos, params["w"], job.bones)
     else:
         base_n = R.vertex_normals(params["pos"], job.tri)
         pos = job.tess.displaced_positions(params["pos"], base_n, params["disp"])
@@ -106,7 +118,10 @@ def render(job, params, views, height, width, aa=True, vis=None, lods=None, diag
     geo = geometry(job, params)
     tex = texture_levels(job, params)
     if vis is None:
-        if job.tess is None:
+        if job.bones is not None:   # float32 contract of the skinned positions (raster.c)
+            pos32 = visibility.skin_positions_f32(params["pos"].detach().numpy(), params["w"].detach().numpy(),
+                                                  job.bones.numpy())
+        elif job.tess is None:
             pos32 = geo["pos"].detach().numpy().astype(np.float32)
         else:   # float32 contract of the displaced positions (raster.c)
             pos32 = job.tess.positions_f32(params["pos"].detach().numpy(), job.tri_np,

@@ -29,6 +29,8 @@ def _load():
         lib.oracle_tess_positions.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P,
                                               ctypes.c_int, ctypes.c_int, P, P]
         lib.oracle_tess_positions.restype = None
+        lib.oracle_skin_positions.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P, P]
+        lib.oracle_skin_positions.restype = None
         _lib = lib
     return _lib
 
@@ -74,3 +76,15 @@ def raster_views(views, pos, tri, width, height):
         keys.append(k)
         signs.append(s)
     return np.stack(keys), np.stack(signs)
+
+
+def skin_positions_f32(pos, weights, bones):
+    """Skinned positions (Eq. 2) under the float32 contract of raster.c
+    (oracle_skin_positions): pos (V, 3), weights (V, B), bones (B, 4, 4)."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    weights = np.ascontiguousarray(weights, dtype=np.float32)
+    bones = np.ascontiguousarray(np.asarray(bones, dtype=np.float32).reshape(-1, 16))
+    out = np.zeros_like(pos)
+    lib.oracle_skin_positions(_ptr(pos), pos.shape[0], _ptr(weights), bones.shape[0], _ptr(bones), _ptr(out))
+    return out

@@ -34,3 +34,7 @@ from .workloads import (  # noqa: F401
     job_mix,
     job_scenes,
 )
+from .rig import (  # noqa: F401
+    bone_weights,
+    bone_pose,
+)

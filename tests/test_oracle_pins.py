@@ -12,6 +12,7 @@ import torch
 
 import synth
 from oracle import render as R
+from oracle import skinning as SK
 from oracle import step as S
 from oracle import visibility as V
 from oracle import tessellate as TS
@@ -458,7 +459,7 @@ def test_tessellation_float32_contract_matches_float64():
 
 # ----------------------------------------------------------------------------- gradients vs central differences
 
-def _tiny_job(loss="logl1", tess=0):
+def _tiny_job(loss="logl1", tess=0, skin=0):
     p, tri = synth.icosphere(3)
     uv, tri_uv = synth.equirect_uv_corners(p, tri)
     mesh = synth.Mesh(p.astype(np.float32), uv, tri, tri_uv)
@@ -471,16 +472,20 @@ def _tiny_job(loss="logl1", tess=0):
     disp = rng.uniform(-0.02, 0.02, (8, 8)).astype(np.float32) if tess else None
     sc = synth.Scene(mesh=mesh, kd=kd, orm=orm, nrm=nrm, disp=disp, tess_levels=tess,
                      optimize={"pos": True, "kd": True, "orm": True, "nrm": True, "disp": bool(tess)})
-    return S.OracleJob(sc, loss=loss)
+    if not skin:
+        return S.OracleJob(sc, loss=loss)
+    job = S.OracleJob(sc, loss=loss, skin_weights=synth.bone_weights(p, skin, seed=2))
+    job.bones = torch.as_tensor(synth.bone_pose(skin, 2, 0).astype(np.float64))
+    return job
 
 
-@pytest.mark.parametrize("loss,tess", [("logl1", 0), ("l1", 0), ("logl1", 1)])
-def test_gradients_match_central_differences(loss, tess):
+@pytest.mark.parametrize("loss,tess,skin", [("logl1", 0, 0), ("l1", 0, 0), ("logl1", 1, 0), ("logl1", 0, 4)])
+def test_gradients_match_central_differences(loss, tess, skin):
     """Central differences on 64 random latents with visibility, LOD and the AA
     edge choice held fixed: h = 1e-3 for texels; h = 1e-5 for positions and
     displacement, whose moves of 1e-3 cross kinks of the piecewise-bilinear
     filter and of |.| in the loss."""
-    job = _tiny_job(loss, tess)
+    job = _tiny_job(loss, tess, skin)
     H = W = 40
     views = synth.sample_views(11, 0, 2, W, H, r_min=2.2, r_max=2.6)
     rng = np.random.default_rng(9)
@@ -501,7 +506,7 @@ def test_gradients_match_central_differences(loss, tess):
     assert len(picks) >= 40
     errs = []
     for k, i in picks:
-        h = 1e-5 if k in ("pos", "disp") else 1e-3
+        h = 1e-5 if k in ("pos", "disp", "w") else 1e-3
         vals = []
         for sgn in (1, -1):
             pp = {kk: vv.detach().clone() for kk, vv in params.items()}
@@ -575,3 +580,54 @@ def test_per_level_step_updates_levels_independently():
     assert not torch.allclose(chain[2], lev.params["kd@2"])
     # clamps act per level as on level 0
     assert float(lev.params["kd@2"].min()) >= 0.0 and float(lev.params["kd@2"].max()) <= 1.0
+
+
+# ---------------------------------------------------------------- skinning (Eq. 2)
+def _rig(n_bones=5, seed=3):
+    p, tri = synth.icosphere(4)
+    return p.astype(np.float32), synth.bone_weights(p, n_bones, seed), synth.bone_pose(n_bones, seed, 1)
+
+
+def test_skinning_with_identity_bones_and_convex_weights_is_the_rest_pose():
+    pos, w, _ = _rig()
+    eye = np.tile(np.eye(4, dtype=np.float32), (w.shape[1], 1, 1))
+    f64 = SK.skin(torch.as_tensor(pos.astype(np.float64)), torch.as_tensor(w.astype(np.float64)),
+                  torch.as_tensor(eye.astype(np.float64))).numpy()
+    assert np.abs(f64 - pos).max() < 1e-6          # the float32 weights sum to 1 within 1e-7
+    one_hot = np.eye(w.shape[1], dtype=np.float32)[np.argmax(w, 1)]
+    assert np.array_equal(V.skin_positions_f32(pos, one_hot, eye), pos)
+
+
+def test_skinning_one_bone_is_its_affine_map():
+    pos, _, pose = _rig(n_bones=1)
+    M = pose[0]
+    want = (pos.astype(np.float64) @ M[:3, :3].T.astype(np.float64)) + M[:3, 3]
+    got = SK.skin(torch.as_tensor(pos.astype(np.float64)), torch.ones((len(pos), 1), dtype=F64),
+                  torch.as_tensor(pose.astype(np.float64))).numpy()
+    assert np.abs(got - want).max() < 1e-12
+    # the float32 contract, restated step by step in numpy float32 (no fused operations)
+    f = np.float32
+    t = [((M[r, 0] * pos[:, 0] + M[r, 1] * pos[:, 1]) + M[r, 2] * pos[:, 2]) + M[r, 3] for r in range(3)]
+    ref32 = np.stack([f(0) + f(1) * t[r] for r in range(3)], 1).astype(np.float32)
+    assert np.array_equal(V.skin_positions_f32(pos, np.ones((len(pos), 1), np.float32), pose), ref32)
+
+
+def test_skinning_is_linear_in_the_weights():
+    pos, w, pose = _rig()
+    rng = np.random.default_rng(4)
+    w2 = rng.uniform(-0.5, 0.5, w.shape)
+    P, Bn = torch.as_tensor(pos.astype(np.float64)), torch.as_tensor(pose.astype(np.float64))
+    a = SK.skin(P, torch.as_tensor(w.astype(np.float64)), Bn)
+    b = SK.skin(P, torch.as_tensor(w2), Bn)
+    c = SK.skin(P, torch.as_tensor(w.astype(np.float64) + w2), Bn)
+    assert torch.allclose(a + b, c, atol=1e-13)
+    assert torch.allclose(SK.skin(P, 2.5 * torch.as_tensor(w2), Bn), 2.5 * b, atol=1e-13)
+
+
+def test_skinning_float32_contract_is_near_float64():
+    pos, w, pose = _rig()
+    f32 = V.skin_positions_f32(pos, w, pose)
+    f64 = SK.skin(torch.as_tensor(pos.astype(np.float64)), torch.as_tensor(w.astype(np.float64)),
+                  torch.as_tensor(pose.astype(np.float64))).numpy()
+    assert np.abs(f32 - f64).max() < 2e-6
+    assert np.abs(f32 - pos).max() > 1e-2            # the pose moved the mesh
