@@ -257,9 +257,20 @@ def run_native(args):
     n_steps = args.warmup + args.steps
     host_views = [synth.sample_views(replica_seed(rank), i, VIEWS, RES, RES) for i in range(n_steps)]
     view_np = np.stack([v.view(np.uint8) for v in host_views])                  # (steps, 8*112)
+    SKB = int(args.skinning)
+    if SKB:
+        # both meshes skinned by the same bones (Eq. 2); a new pose each step rides in
+        # the step's input record after the views
+        ctx.skinning(ref_job, synth.bone_weights(cfg["ref"].mesh.pos, SKB, seed=5), lr_scale=0.0)
+        wc = synth.bone_weights(cfg["cand"].mesh.pos, SKB, seed=5)
+        ctx.skinning(cand, wc, lr_scale=1.0 / SKB)   # weights of a vertex move together: keep the blend in step
+        ctx.skinning(plain, wc, lr_scale=1.0 / SKB)
+        pose_np = np.stack([synth.bone_pose(SKB, 5 + replica_seed(rank), i).reshape(-1).view(np.uint8)
+                            for i in range(n_steps)])
+        view_np = np.ascontiguousarray(np.concatenate([view_np, pose_np], axis=1))
     dev_views = torch.from_numpy(view_np).to(dev)
     pinned_views = torch.from_numpy(view_np).pin_memory()
-    staging = torch.empty(VIEWS * 112, dtype=torch.uint8, device=dev)            # graph's fixed view buffer
+    staging = torch.empty(view_np.shape[1], dtype=torch.uint8, device=dev)       # graph's fixed input buffer
     ref_buf = torch.empty((VIEWS, RES, RES, 3), dtype=torch.float32, device=dev)
     loss_buf = torch.zeros(n_steps + 1, dtype=torch.float32, device=dev)
     graph_loss = torch.zeros(1, dtype=torch.float32, device=dev)
@@ -278,7 +289,13 @@ def run_native(args):
         if st != 0:
             raise B.AdmsError(st, L.adms_last_error(cptr).decode())
 
+    def set_pose(vp, jobs):
+        if SKB:
+            for jb in jobs:
+                ck(L.adms_job_set_bones(cptr, jb, vp + VIEWS * 112))
+
     def step_at(vp, loss_ptr):
+        set_pose(vp, (ref_job, cand))
         ck(L.adms_render_reference(cptr, ref_job, vp, VIEWS, RES, RES, ref_buf.data_ptr()))
         ck(L.adms_forward_loss(cptr, jobs_c, 1, vp, vpj8, hw, refs8, loss_ptr, None))
         ck(L.adms_backward(cptr, jobs_c, 1, 0))
@@ -289,6 +306,7 @@ def run_native(args):
 
     def plain_step(i):
         vp = dev_views[i].data_ptr()
+        set_pose(vp, (ref_job, plain))
         for v in range(VIEWS):
             one = vp + v * view_bytes
             ck(L.adms_render_reference(cptr, ref_job, one, 1, RES, RES, ref_buf[v:v + 1].data_ptr()))
@@ -341,7 +359,7 @@ def run_native(args):
     stages = B.adms_ctx_stage_times(cptr)
     B.adms_ctx_profile(cptr, False)
     # end to end through the C ABI: host views in (pinned), graph step, loss read back, every step
-    h2d = VIEWS * view_bytes
+    h2d = view_np.shape[1]   # the step's views (and bone matrices when skinned)
     d2h = 4
     barrier()
     t0 = time.perf_counter()
@@ -411,7 +429,10 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD + ("; every mip level of each texture its own latent (Sec. 6)" if pl else ""),
+            "config": {"workload": WORKLOAD + ("; every mip level of each texture its own latent (Sec. 6)" if pl else "")
+                       + (f"; both meshes skinned by {SKB} bones (Eq. 2), dense weights optimized (learning rate / {SKB}), "
+                          "a new pose per step"
+                          if SKB else ""),
                        "global_batch": VIEWS * world, "seq_len": None,
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "launch": "one CUDA graph per step (reference render, forward+loss, backward, Adam)",
@@ -633,6 +654,8 @@ def main():
     ap.add_argument("--iterations", type=int, default=200, help="serving: iterations per job")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: HBM budget")
     ap.add_argument("--per-job-iterations", type=int, default=3, help="serving: iterations of the per-job loop")
+    ap.add_argument("--skinning", type=int, default=0, metavar="BONES",
+                    help="plain workload with both meshes skinned by BONES bones and a new pose per step (Eq. 2)")
     ap.add_argument("--per-level-textures", action="store_true",
                     help="plain workload with every mip level of each texture an independent latent (Sec. 6)")
     args = ap.parse_args()

@@ -121,6 +121,8 @@ typedef struct {
     int32_t n_verts, n_tris_render, kd_h, kd_w, orm_h, orm_w, nrm_h, nrm_w, disp_h, disp_w;
     int32_t kd_levels, orm_levels, nrm_levels; /* mip levels held per texture (1 = level 0 only) */
     int32_t t;            /* optimizer steps taken */
+    float *skin_w, *g_skin_w; /* skinning weights [n_verts][n_bones] and their gradient (NULL if none) */
+    int32_t n_bones;      /* 0 without skinning */
 } adms_param_view;
 
 /* Job state scalars, read back with adms_job_stats (synchronises the stream). */
@@ -167,6 +169,27 @@ adms_status adms_job_destroy(adms_ctx* ctx, adms_job job);
  * (a set's lists live until one of its jobs is destroyed otherwise).
  * Synchronises the stream. */
 adms_status adms_ctx_release_batches(adms_ctx* ctx);
+/* Dense linear-blend skinning (Sec. 5.1, Eq. 2): from now on the job renders
+ * v^s_i = sum_b w_ib M_b [v_i; 1] instead of its rest positions v_i, with the
+ * affine bone matrices M_b of the current frame (adms_job_set_bones; identity
+ * until set). weights: [n_verts][n_bones] float32, host or device, copied;
+ * every vertex-bone pair is its own weight (the dense operator), used as given
+ * (no normalisation). lr_scale > 0 makes the weights a latent: the backward
+ * accumulates their gradient beside the rest positions' and the optimizer
+ * step applies Adam to them with learning rate lr_t * lr_scale (no clamps);
+ * 0 keeps them fixed. Adam moves every weight by about its learning rate per
+ * step, and the weights of a vertex tend to move together, so its skinned
+ * position moves up to n_bones times faster than a rest position: 1/n_bones
+ * keeps the two in step. The skinned positions feed the
+ * bit-exact visibility through a fixed float32 evaluation (bones ascending,
+ * each row ((m0 x + m1 y) + m2 z) + m3, weighted sum from 0, no FMA).
+ * ADMS_ERR_ARG: n_bones outside [1, 1024], lr_scale < 0 or a null pointer; ADMS_ERR_STATE:
+ * a tessellated job or skinning already set. Synchronises the stream. */
+adms_status adms_job_skinning(adms_ctx* ctx, adms_job job, const float* weights, int32_t n_bones, float lr_scale);
+/* The bone matrices of the frame the next calls render: [n_bones][4][4]
+ * row-major float32 (last row 0 0 0 1), host or device; copied on the stream
+ * (from device memory it records into a graph like the views). */
+adms_status adms_job_set_bones(adms_ctx* ctx, adms_job job, const float* bones);
 /* Allocate the job's per-call render scratch for n_views views of H x W now
  * (keys, per-pixel buffers, per-view transforms, bins), so that later calls of
  * that size or smaller allocate nothing for this job. Lets a scheduler admit
@@ -247,7 +270,9 @@ adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t*
 /* Recreate a job from adms_job_export output (checkpoint/resume): mesh, mat and
  * opt must describe the job that was exported (same topology, texture sizes,
  * options); their latent values are replaced by the blob's. ADMS_ERR_ARG if
- * the blob is not a checkpoint of this version or does not match them. */
+ * the blob is not a checkpoint of this version or does not match them. A
+ * skinned job comes back skinned (weights, moments and the last bones from the
+ * blob). */
 adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adms_material_desc* mat,
                             const adms_opt_params* opt, const void* host_buf, size_t bytes, adms_job* out);
 

@@ -26,7 +26,7 @@ class OracleJob:
     scene: synth.Scene. Textures are (h, w, 4); `disp` (h, w) when present."""
 
     def __init__(self, scene, loss="logl1", lr0=0.01, lam0=None, relative_laplacian=False, per_level=False,
-                 skin_weights=None):
+                 skin_weights=None, skin_lr_scale=1.0):
         m = scene.mesh
         self.tri = torch.as_tensor(m.tri_pos.astype(np.int64))
         self.tri_uv = torch.as_tensor(m.tri_uv.astype(np.int64))
@@ -50,11 +50,16 @@ class OracleJob:
         # Skinning (Eq. 2): dense weights (V, B) are a latent "w"; the bone matrices of
         # the frame being rendered are set per step in self.bones (B, 4, 4)
         self.bones = None
+        # True: shade the float32 skinned positions that visibility (and the GPU) use,
+        # differentiated through the float64 operator; False: shade the float64 ones
+        self.shade_f32_skin = False
         if skin_weights is not None:
             w = torch.as_tensor(np.asarray(skin_weights, dtype=np.float64))
             self.params["w"] = w
-            self.optimize["w"] = True
+            self.optimize["w"] = skin_lr_scale > 0
             self.bones = torch.eye(4, dtype=torch.float64).repeat(w.shape[1], 1, 1)
+        # learning-rate factor per latent (the weights' own; the rest take lr_t)
+        self.lr_scale = {"w": float(skin_lr_scale)}
         self.per_level = bool(per_level) and self.mips
         if self.per_level:
             for name in ("kd", "orm", "nrm"):
@@ -90,6 +95,10 @@ def geometry(job, params):
         pos, tri, uv, tri_uv = params["pos"], job.tri, job.uv, job.tri_uv
         if job.bones is not None:
             pos = SK.skin(pos, params["w"], job.bones)
+            if job.shade_f32_skin:
+                p32 = visibility.skin_positions_f32(params["pos"].detach().numpy(), params["w"].detach().numpy(),
+                                                    job.bones.numpy())
+                pos = pos + (torch.as_tensor(p32.astype(np.float64)) - pos).detach()
     else:
         base_n = R.vertex_normals(params["pos"], job.tri)
         pos = job.tess.displaced_positions(params["pos"], base_n, params["disp"])
@@ -188,7 +197,8 @@ def step(job, views, refs, height, width):
     job.lam = obj["lam"]
     lr = R.learning_rate(job.lr0, job.t)
     for k in live:
-        job.params[k], job.m[k], job.v[k] = R.adam_update(job.params[k], grads[k], job.m[k], job.v[k], job.t, lr, k)
+        job.params[k], job.m[k], job.v[k] = R.adam_update(job.params[k], grads[k], job.m[k], job.v[k], job.t,
+                                                          lr * job.lr_scale.get(k, 1.0), k)
     job.t += 1
     return dict(keys=obj["out"]["keys"], asign=obj["out"]["asign"], pre=obj["out"]["pre"].detach(),
                 img=obj["out"]["img"].detach(), loss=float(obj["total"]), image_loss=float(obj["image"]),

@@ -60,7 +60,7 @@ class adms_param_view(C.Structure):
                 ("n_tris_render", C.c_int32), ("kd_h", C.c_int32), ("kd_w", C.c_int32), ("orm_h", C.c_int32),
                 ("orm_w", C.c_int32), ("nrm_h", C.c_int32), ("nrm_w", C.c_int32), ("disp_h", C.c_int32),
                 ("disp_w", C.c_int32), ("kd_levels", C.c_int32), ("orm_levels", C.c_int32),
-                ("nrm_levels", C.c_int32), ("t", C.c_int32)]
+                ("nrm_levels", C.c_int32), ("t", C.c_int32), ("skin_w", C.c_void_p), ("g_skin_w", C.c_void_p), ("n_bones", C.c_int32)]
 
 
 class adms_stats(C.Structure):
@@ -84,6 +84,8 @@ SIGNATURES = {
     "adms_job_destroy": ([P, C.c_int32], C.c_int),
     "adms_job_reserve": ([P, C.c_int32, C.c_int32, C.c_int32, C.c_int32], C.c_int),
     "adms_ctx_release_batches": ([P], C.c_int),
+    "adms_job_skinning": ([P, C.c_int32, P, C.c_int32, C.c_float], C.c_int),
+    "adms_job_set_bones": ([P, C.c_int32, P], C.c_int),
     "adms_job_params": ([P, C.c_int32, C.POINTER(adms_param_view)], C.c_int),
     "adms_job_stats": ([P, C.c_int32, C.POINTER(adms_stats)], C.c_int),
     "adms_render_reference": ([P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P], C.c_int),
@@ -208,6 +210,14 @@ def adms_job_create(ctx, mesh, mat, opt=None, seed=0):
 
 def adms_job_destroy(ctx, job):
     _check(ctx, lib().adms_job_destroy(ctx, job))
+
+
+def adms_job_skinning(ctx, job, weights, n_bones, lr_scale=1.0):
+    _check(ctx, lib().adms_job_skinning(ctx, job, ptr(weights), int(n_bones), float(lr_scale)))
+
+
+def adms_job_set_bones(ctx, job, bones):
+    _check(ctx, lib().adms_job_set_bones(ctx, job, ptr(bones)))
 
 
 def adms_ctx_release_batches(ctx):

@@ -64,6 +64,11 @@ struct Job {
     double *g_bnrm = nullptr, *g_btan0 = nullptr, *g_bpos_acc = nullptr;
     float4 *b_vpos = nullptr, *b_vnrm = nullptr, *b_vtan = nullptr, *b_tmp_n = nullptr, *b_tmp_t = nullptr;
     float *disp = nullptr, *g_disp = nullptr, *m_disp = nullptr, *v_disp = nullptr;
+    // dense skinning (Eq. 2): render positions = skinned rest positions
+    bool skin = false;
+    int SB = 0;  // bones
+    float *skin_w = nullptr, *g_skin_w = nullptr, *m_skin_w = nullptr, *v_skin_w = nullptr, *bones = nullptr;
+    float skin_lr_scale = 0.f;  // the weights' learning rate is lr_t times this (0: frozen)
     // topology
     float2* uv = nullptr;
     int* tri = nullptr;
@@ -437,9 +442,24 @@ ShadeArgs shade_args(Job& j) {
 }
 
 // frame, raster and pre-AA shading of B views already copied to j.views
+SkinArgs skin_args(Job& j) {
+    SkinArgs a;
+    a.V = j.V;
+    a.B = j.SB;
+    a.pos = j.pos;
+    a.w = j.skin_w;
+    a.bones = j.bones;
+    a.out = j.rpos;
+    a.g_out = j.g_rpos;
+    a.g_pos = j.g_pos;
+    a.g_w = j.g_skin_w;
+    return a;
+}
+
 adms_status render_core(adms_ctx* ctx, Job& j) {
     if (!j.frame_valid) {
         if (j.tess) CK(TIMED(ST_FRAME, tess_forward(tess_args(j), ctx->stream)));
+        if (j.skin) CK(TIMED(ST_FRAME, skin_forward(skin_args(j), ctx->stream)));
         CK(TIMED(ST_FRAME, frame_forward(frame_args(j), ctx->stream)));
         j.frame_valid = true;
     }
@@ -733,6 +753,7 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
 adms_status frame_and_prepare(adms_ctx* ctx, Job& j) {
     if (!j.frame_valid) {
         if (j.tess) CK(TIMED(ST_FRAME, tess_forward(tess_args(j), ctx->stream)));
+        if (j.skin) CK(TIMED(ST_FRAME, skin_forward(skin_args(j), ctx->stream)));
         CK(TIMED(ST_FRAME, frame_forward(frame_args(j), ctx->stream)));
         j.frame_valid = true;
     }
@@ -892,8 +913,8 @@ struct CkptHeader {
     int32_t LV, V, F, tess_levels, dh, dw;
     int32_t tex_w[3], tex_h[3], tex_levels[3], tex_opt[3];
     int32_t optimize[5];  // pos, kd, orm, nrm, disp
-    int32_t loss, relative_laplacian, batch_views, aa, per_level_textures;
-    float lr0, lambda0;
+    int32_t loss, relative_laplacian, batch_views, aa, per_level_textures, n_bones;
+    float lr0, lambda0, skin_lr_scale;
     uint64_t section_bytes[16];
 };
 
@@ -930,6 +951,8 @@ void ckpt_describe(Job& j, CkptHeader& h, std::vector<CkptSection>& secs) {
     h.batch_views = j.opt.batch_views;
     h.aa = j.opt.aa;
     h.per_level_textures = j.opt.per_level_textures;
+    h.n_bones = j.SB;
+    h.skin_lr_scale = j.skin_lr_scale;
     h.lr0 = j.opt.lr0;
     h.lambda0 = j.opt.lambda0;
     secs.clear();
@@ -954,6 +977,11 @@ void ckpt_describe(Job& j, CkptHeader& h, std::vector<CkptSection>& secs) {
     add(j.m_disp, pd);
     add(j.v_disp, pd);
     add(j.delta_ref, pv);
+    size_t psw = (size_t)j.LV * j.SB * sizeof(float);
+    add(j.skin_w, psw);
+    add(j.m_skin_w, psw);
+    add(j.v_skin_w, psw);
+    add(j.bones, (size_t)j.SB * 16 * sizeof(float));
     add(j.st, sizeof(JobState));
     h.n_sections = (uint32_t)secs.size();
     for (size_t k = 0; k < secs.size() && k < 16; ++k) h.section_bytes[k] = secs[k].bytes;
@@ -1167,6 +1195,48 @@ adms_status adms_job_params(adms_ctx* ctx, adms_job job, adms_param_view* out) {
     CK(cudaMemcpyAsync(&hs, j->st, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     out->t = hs.t;
+    out->skin_w = j->skin_w;
+    out->g_skin_w = j->g_skin_w;
+    out->n_bones = j->SB;
+    return ADMS_OK;
+}
+
+adms_status adms_job_skinning(adms_ctx* ctx, adms_job job, const float* weights, int32_t n_bones, float lr_scale) {
+    Job* jp = get_job(ctx, job);
+    if (!jp || !weights || n_bones < 1 || n_bones > ADMS_MAX_BONES || !(lr_scale >= 0.f))
+        return fail(ctx, ADMS_ERR_ARG, "invalid job, weights, bone count (1..1024) or learning-rate scale");
+    Job& j = *jp;
+    if (j.tess) return fail(ctx, ADMS_ERR_STATE, "skinning of a tessellated job is not supported");
+    if (j.skin) return fail(ctx, ADMS_ERR_STATE, "skinning is already set for this job");
+    size_t nw = (size_t)j.LV * n_bones;
+    AL(j.skin_w, nw);
+    CK(cudaMemcpyAsync(j.skin_w, weights, nw * sizeof(float), cudaMemcpyDefault, ctx->stream));
+    if (lr_scale > 0.f && !j.frozen) {
+        AL(j.g_skin_w, nw);
+        AL(j.m_skin_w, nw);
+        AL(j.v_skin_w, nw);
+        j.skin_lr_scale = lr_scale;
+    }
+    AL(j.bones, (size_t)n_bones * 16);
+    std::vector<float> eye((size_t)n_bones * 16, 0.f);
+    for (int b = 0; b < n_bones; ++b)
+        for (int r = 0; r < 4; ++r) eye[(size_t)b * 16 + 5 * r] = 1.f;
+    CK(cudaMemcpyAsync(j.bones, eye.data(), eye.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    AL(j.rpos, (size_t)j.V * 3);  // render positions no longer alias the rest positions
+    AL(j.g_rpos, (size_t)j.V * 3);
+    j.SB = n_bones;
+    j.skin = true;
+    j.frame_valid = false;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return ADMS_OK;
+}
+
+adms_status adms_job_set_bones(adms_ctx* ctx, adms_job job, const float* bones) {
+    Job* j = get_job(ctx, job);
+    if (!j || !bones) return fail(ctx, ADMS_ERR_ARG, "invalid job handle or bones");
+    if (!j->skin) return fail(ctx, ADMS_ERR_STATE, "the job has no skinning (adms_job_skinning)");
+    CK(cudaMemcpyAsync(j->bones, bones, sizeof(float) * 16 * j->SB, cudaMemcpyDefault, ctx->stream));
+    j->frame_valid = false;
     return ADMS_OK;
 }
 
@@ -1294,7 +1364,7 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
         }
         CK(cudaMemsetAsync(j.g_nrm, 0, sizeof(double) * 3 * j.V, ctx->stream));
         CK(cudaMemsetAsync(j.g_tan, 0, sizeof(double) * 3 * j.V, ctx->stream));
-        if (j.tess) CK(cudaMemsetAsync(j.g_rpos, 0, sizeof(float) * 3 * j.V, ctx->stream));
+        if (j.tess || j.skin) CK(cudaMemsetAsync(j.g_rpos, 0, sizeof(float) * 3 * j.V, ctx->stream));
         if (n_jobs == 1) {
             ShadeArgs a = shade_args(j);
             a.ref = j.ref;
@@ -1319,6 +1389,8 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
             CK(TIMED(ST_FRAME_BWD, tess_backward(tess_args(j), ctx->stream)));
             CK(TIMED(ST_FRAME_BWD, frame_backward(base_frame_args(j), ctx->stream)));
         }
+        // skinned positions -> rest positions and weights
+        if (j.skin) CK(TIMED(ST_FRAME_BWD, skin_backward(skin_args(j), ctx->stream)));
         j.have_fwd = false;
     }
     return ADMS_OK;
@@ -1348,6 +1420,9 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         } else {
             CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.LV, ctx->stream));
         }
+        if (j.g_skin_w)
+            CK(TIMED(ST_ADAM, adam_flat(j.skin_w, j.g_skin_w, j.m_skin_w, j.v_skin_w, (long long)j.LV * j.SB, j.st,
+                                        ctx->stream, j.skin_lr_scale)));
         if (j.tess) {
             if (j.opt.optimize_disp)
                 CK(TIMED(ST_ADAM, adam_flat(j.disp, j.g_disp, j.m_disp, j.v_disp, (long long)j.dh * j.dw, j.st,
@@ -1398,6 +1473,8 @@ adms_status adms_job_zero_gradients(adms_ctx* ctx, adms_job job) {
         CK(cudaMemsetAsync(j.g_rpos, 0, sizeof(float) * 3 * j.V, ctx->stream));
         CK(cudaMemsetAsync(j.g_bpos_acc, 0, sizeof(double) * 3 * j.LV, ctx->stream));
     }
+    if (j.skin) CK(cudaMemsetAsync(j.g_rpos, 0, sizeof(float) * 3 * j.V, ctx->stream));
+    if (j.g_skin_w) CK(cudaMemsetAsync(j.g_skin_w, 0, sizeof(float) * j.LV * j.SB, ctx->stream));
     if (j.g_disp) CK(cudaMemsetAsync(j.g_disp, 0, sizeof(float) * j.dh * j.dw, ctx->stream));
     TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
     for (int m = 0; m < 3; ++m)
@@ -1471,6 +1548,14 @@ adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
     adms_job h = -1;
     adms_status s = adms_job_create(ctx, mesh, mat, opt, want.seed, &h);
     if (s) return s;
+    if (want.n_bones > 0) {  // skinning is set after creation: set it up, the blob brings its weights
+        std::vector<float> zeros((size_t)ctx->jobs[h].LV * want.n_bones, 0.f);
+        s = adms_job_skinning(ctx, h, zeros.data(), want.n_bones, want.skin_lr_scale);
+        if (s) {
+            adms_job_destroy(ctx, h);
+            return s;
+        }
+    }
     Job& j = ctx->jobs[h];
     CkptHeader got;
     std::vector<CkptSection> secs;

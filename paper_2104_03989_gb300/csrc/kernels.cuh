@@ -175,6 +175,21 @@ cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st);
 cudaError_t frame_backward(const FrameArgs& a, cudaStream_t st);
 
 // tessellation + displacement (latent base mesh -> render mesh) and its adjoint
+// dense skinning (Eq. 2) of the rest positions by the frame's bones
+#define ADMS_MAX_BONES 1024  // 12 floats of shared memory per bone
+struct SkinArgs {
+    int V, B;
+    const float* pos;    // [V][3] rest positions (latent)
+    const float* w;      // [V][B] weights (latent)
+    const float* bones;  // [B][16] row-major affine bone matrices of the frame
+    float* out;          // [V][3] skinned (render) positions
+    const float* g_out;  // [V][3] dL/d(skinned positions)
+    float* g_pos;        // [V][3] += dL/d(rest positions)
+    float* g_w;          // [V][B] += dL/dw (null: weights not optimized)
+};
+cudaError_t skin_forward(const SkinArgs& a, cudaStream_t st);
+cudaError_t skin_backward(const SkinArgs& a, cudaStream_t st);
+
 struct TessArgs {
     int Vb, Fb, Vt, n_seg;
     const float* base_pos;   // [Vb][3] latent
@@ -236,7 +251,8 @@ struct SchedArgs {
 cudaError_t schedule_step(const SchedArgs& a, cudaStream_t st);
 
 // Adam on a flat float array (positions, displacement): no clamps
-cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const JobState* js, cudaStream_t st);
+cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const JobState* js, cudaStream_t st,
+                      float lr_scale = 1.f);
 // Adam on a float4 texture (level 0) with the mip-chain adjoint folded in; clamp_kind 0 kd, 1 orm, 2 nrm
 cudaError_t adam_texture(const TexDev& t, float4* m, float4* v, int clamp_kind, const JobState* js, cudaStream_t st);
 // Adam on every level of a texture whose mip levels are independent latents (m, v

@@ -72,10 +72,10 @@ __device__ __forceinline__ float adam1(float p, float g, float& m, float& v, flo
 }
 
 __global__ void k_adam_flat(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                            long long n, const JobState* __restrict__ js) {
+                            long long n, const JobState* __restrict__ js, float lr_scale) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float lr = js->lr, bc1 = js->bc1, bc2 = js->bc2;
+    float lr = js->lr * lr_scale, bc1 = js->bc1, bc2 = js->bc2;
     float mm = m[i], vv = v[i];
     p[i] = adam1(p[i], g[i], mm, vv, lr, bc1, bc2);
     m[i] = mm;
@@ -83,9 +83,10 @@ __global__ void k_adam_flat(float* __restrict__ p, float* __restrict__ g, float*
     g[i] = 0.f;
 }
 
-cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const JobState* js, cudaStream_t st) {
+cudaError_t adam_flat(float* p, float* g, float* m, float* v, long long n, const JobState* js, cudaStream_t st,
+                      float lr_scale) {
     if (n <= 0) return cudaSuccess;
-    k_adam_flat<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, g, m, v, n, js);
+    k_adam_flat<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, g, m, v, n, js, lr_scale);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -120,7 +120,21 @@ class Context:
         if pv.disp:
             out["disp"] = device_view(pv.disp, (pv.disp_h, pv.disp_w))
             out["g_disp"] = device_view(pv.g_disp, (pv.disp_h, pv.disp_w))
+        if pv.n_bones:
+            out["w"] = device_view(pv.skin_w, (V, pv.n_bones))
+            out["g_w"] = device_view(pv.g_skin_w, (V, pv.n_bones))
         return out
+
+    def skinning(self, job, weights, lr_scale=1.0):
+        """Dense skinning (Eq. 2) of the job's rest positions; weights (V, B),
+        optimized with learning rate lr_t * lr_scale (0: fixed)."""
+        w = _c32(weights, np.float32)
+        B.adms_job_skinning(self.ctx, job, w, w.shape[1], lr_scale)
+
+    def set_bones(self, job, bones):
+        """The frame's bone matrices (B, 4, 4): numpy (copied) or a CUDA tensor."""
+        b = bones if isinstance(bones, torch.Tensor) else _c32(bones, np.float32)
+        B.adms_job_set_bones(self.ctx, job, b)
 
     def stats(self, job):
         s = B.adms_job_stats(self.ctx, job)

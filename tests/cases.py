@@ -91,10 +91,13 @@ def fold_mips(g, h, w, levels):
     return out
 
 
-def oracle_grads(scene, views, refs, H, W, loss, per_level=False):
+def oracle_grads(scene, views, refs, H, W, loss, per_level=False, skin_weights=None, bones=None):
     """Oracle image-loss gradients (lambda = 0), images, keys, loss, and the
     vertices whose gradient is not unique at float32 resolution."""
-    job = S.OracleJob(scene, loss=loss, per_level=per_level)
+    job = S.OracleJob(scene, loss=loss, per_level=per_level, skin_weights=skin_weights)
+    if bones is not None:
+        job.bones = torch.as_tensor(np.asarray(bones, dtype=np.float64))
+        job.shade_f32_skin = True   # the GPU shades the float32 skinned positions it renders
     params = {k: v.clone().requires_grad_(job.optimize[k]) for k, v in job.params.items()}
     diags = []
     obj = S.objective(job, params, views, torch.as_tensor(refs.astype(np.float64)), H, W, lam=0.0, diags=diags)
@@ -170,12 +173,12 @@ def assert_grads_match(got, orc, label, tol=1e-3):
     for name, want in orc["grads"].items():
         g = got[name]
         assert np.linalg.norm(want) > 0, name
-        if name == "pos":
+        if name in ("pos", "w"):   # rows per vertex (skinning weights: one row per vertex too)
             amb = np.zeros(len(want), bool)
             amb[sorted(orc["ambiguous"])] = True
             assert amb.mean() < 0.3, f"{label}: {amb.sum()} ambiguous vertices"
             err = rel_l2(g[~amb], want[~amb])
-            print(f"{label} pos: {amb.sum()} of {len(amb)} vertices one-sided; rel L2 of the rest {err:.3e}, "
+            print(f"{label} {name}: {amb.sum()} of {len(amb)} vertices one-sided; rel L2 of the rest {err:.3e}, "
                   f"of all {rel_l2(g, want):.3e}")
             for v in np.nonzero(amb)[0]:
                 assert np.linalg.norm(g[v] - want[v]) <= 0.5 * np.linalg.norm(want[v]) + 1e-3 * np.abs(want).max()
