@@ -37,7 +37,7 @@ WORKLOAD = ("reference 200k-tri fBm icosphere with 2048^2 procedural maps; candi
 # DRAM bytes per launch of the dominant kernel from an ncu capture, valid only
 # for the source it was measured on (sha256 of the listed files).
 TRAFFIC = {
-    "shade_bwd": {"bytes_per_launch": 163197696 + 59788544,
+    "shade_bwd": {"bytes_per_launch": 163197696 + 59788544, "warp_instructions_per_launch": 181384842,
                   "files": ["paper_2104_03989_gb300/csrc/shade.cu", "paper_2104_03989_gb300/csrc/common.cuh",
                             "paper_2104_03989_gb300/csrc/kernels.cuh"],
                   "sha": "1dc4bc555dacdcb5",
@@ -411,12 +411,21 @@ def run_native(args):
     traffic = None
     if tr and _sha(tr["files"]) == tr["sha"]:
         traffic = tr["bytes_per_launch"]
+    # the same kernel against the instruction-issue rate (one warp instruction per
+    # scheduler per cycle: SMs x 4 x SM clock), with ncu's instruction count per launch
+    issue = None
+    if tr and _sha(tr["files"]) == tr["sha"] and tr.get("warp_instructions_per_launch") and clocks.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ach = tr["warp_instructions_per_launch"] / (d["ms_per_step"] / launches_per_step / 1e3) / 1e9
+        pk = sms * 4 * clocks["sm_mhz"] / 1e3
+        issue = {"bound": "issue", "achieved": ach, "peak": pk, "unit": "G warp instructions/s", "frac": ach / pk,
+                 "instructions_per_launch": tr["warp_instructions_per_launch"], "sms": sms}
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
                 "traffic": traffic,
                 "algorithmic_bytes_per_launch": (d["algorithmic_bytes_per_step"] / launches_per_step)
                 if d["algorithmic_bytes_per_step"] else None,
-                "ms_per_launch": d["ms_per_step"] / launches_per_step}
+                "ms_per_launch": d["ms_per_step"] / launches_per_step, "issue_roofline": issue}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

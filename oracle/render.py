@@ -315,7 +315,8 @@ def texel_margin(levels, uv, lod):
     return out
 
 
-def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True, lod_store=None, diag=None):
+def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True, lod_store=None, diag=None,
+                msaa=1):
     """Pre-AA and AA images (H, W, 3) of one view with fixed visibility keys.
 
     geo: dict pos (V,3), nrm (V,3), tan (V,3), uv (T,2), tri (F,3), tri_uv (F,3)
@@ -326,7 +327,11 @@ def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True,
     differences hold them fixed, like the visibility keys).
     diag: optional dict filled with per-pixel margins to the discrete
     decisions inside the differentiable path (texel cells, n.l = 0, AA tau
-    and crossing tests), for tests that must tell kinks apart."""
+    and crossing tests), for tests that must tell kinks apart.
+    msaa = s > 1 (the antialiasing paragraph of Sec. 5.2, reading): keys and
+    width, height are those of the s x s sample grid of each pixel; every sample
+    takes its triangle shaded once per pixel, at the pixel's centre, with the
+    LOD of the pixel's footprint; antialiasing acts on the sample grid."""
     pos, tri, tri_uv = geo["pos"], geo["tri"], geo["tri_uv"]
     M = t64(np.asarray(view["mvp"], dtype=np.float32).astype(np.float64).reshape(4, 4))
     clip = torch.cat([pos, torch.ones_like(pos[:, :1])], dim=1) @ M.T
@@ -337,8 +342,12 @@ def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True,
     pix = np.nonzero(covered)[0]
     fid = torch.as_tensor((flat[pix] & np.uint64(0xFFFFFFFF)).astype(np.int64))
     pixt = torch.as_tensor(pix.astype(np.int64))
-    qx = (pixt % width).to(F64) + 0.5
-    qy = (pixt // width).to(F64) + 0.5
+    if msaa > 1:   # the centre of the pixel that holds the sample, in sample-grid units
+        qx = ((pixt % width) // msaa).to(F64) * msaa + 0.5 * msaa
+        qy = ((pixt // width) // msaa).to(F64) * msaa + 0.5 * msaa
+    else:
+        qx = (pixt % width).to(F64) + 0.5
+        qy = (pixt // width).to(F64) + 0.5
     q = torch.stack([qx, qy], dim=1)
 
     vi = tri[fid]                       # (N, 3) position indices
@@ -354,7 +363,8 @@ def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True,
     n_i = interp(geo["nrm"], vi)
     t_i = interp(geo["tan"], vi)
     uv = interp(geo["uv"], ui)
-    duv = [sum(db[k][:, None] * geo["uv"][ui[:, k]] for k in range(3)) for db in dbeta]
+    # screen derivatives per pixel (s sample-grid steps per pixel under MSAA)
+    duv = [msaa * sum(db[k][:, None] * geo["uv"][ui[:, k]] for k in range(3)) for db in dbeta]
 
     margins = []
 
@@ -388,6 +398,14 @@ def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True,
 
 
 # ----------------------------------------------------------------------------- antialiasing
+
+def resolve(img, s):
+    """Pixel = mean of its s x s samples: (sH, sW, 3) -> (H, W, 3)."""
+    if s == 1:
+        return img
+    h, w = img.shape[0] // s, img.shape[1] // s
+    return img.reshape(h, s, w, s, img.shape[2]).mean(dim=(1, 3))
+
 
 def silhouette_flags(asign, adj):
     """reading: edge k of face f is a silhouette edge in a view when it has no

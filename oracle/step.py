@@ -26,7 +26,7 @@ class OracleJob:
     scene: synth.Scene. Textures are (h, w, 4); `disp` (h, w) when present."""
 
     def __init__(self, scene, loss="logl1", lr0=0.01, lam0=None, relative_laplacian=False, per_level=False,
-                 skin_weights=None, skin_lr_scale=1.0):
+                 skin_weights=None, skin_lr_scale=1.0, msaa=1):
         m = scene.mesh
         self.tri = torch.as_tensor(m.tri_pos.astype(np.int64))
         self.tri_uv = torch.as_tensor(m.tri_uv.astype(np.int64))
@@ -41,6 +41,7 @@ class OracleJob:
         if scene.disp is not None:
             self.params["disp"] = torch.as_tensor(scene.disp.astype(np.float64))
         self.tess_levels = int(scene.tess_levels)
+        self.msaa = int(msaa)   # s x s visibility samples per pixel, shaded once per pixel (Sec. 5.2)
         self.mips = bool(scene.mips)
         self.optimize = {k: bool(scene.optimize.get(k, False)) for k in self.params}
         # Per-level latent textures (the prefiltering variant of Sec. 6): every mip
@@ -120,10 +121,17 @@ def texture_levels(job, params):
     return out
 
 
-def render(job, params, views, height, width, aa=True, vis=None, lods=None, diags=None):
+def render(job, params, views, height, width, aa=True, vis=None, lods=None, diags=None, ssaa=1):
     """Images of a batch of views. vis = (keys, asign) holds visibility fixed;
     lods = a dict filled on first use and reused after it holds the LOD fixed;
-    diags = a list that receives each view's decision margins (render_view)."""
+    diags = a list that receives each view's decision margins (render_view).
+    With job.msaa = s > 1 visibility, pre-AA colours and antialiasing are on the
+    s x s sample grid (keys, pre and img_samples at (s height, s width)) and img
+    is their per-pixel mean; ssaa = s > 1 does the same but shades every sample
+    at its own position (a supersampled render, for references)."""
+    s = job.msaa if job.msaa > 1 else ssaa
+    if s > 1:
+        height, width = height * s, width * s
     geo = geometry(job, params)
     tex = texture_levels(job, params)
     if vis is None:
@@ -142,19 +150,22 @@ def render(job, params, views, height, width, aa=True, vis=None, lods=None, diag
         store = None if lods is None else lods.setdefault(b, {})
         dg = None if diags is None else {}
         pre, img = R.render_view(geo, tex, views[b], keys[b], asign[b], job.adj, width, height, aa=aa,
-                                 lod_store=store, diag=dg)
+                                 lod_store=store, diag=dg, msaa=job.msaa)
         if diags is not None:
             diags.append(dg)
         pres.append(pre)
         imgs.append(img)
-    return dict(pre=torch.stack(pres), img=torch.stack(imgs), keys=keys, asign=asign, geo=geo)
+    samples = torch.stack(imgs)
+    img = torch.stack([R.resolve(x, s) for x in imgs]) if s > 1 else samples
+    return dict(pre=torch.stack(pres), img=img, img_samples=samples, keys=keys, asign=asign, geo=geo)
 
 
-def render_reference(scene, views, height, width):
-    """Reference images (forward only; the reference is a black box, Sec. 3)."""
+def render_reference(scene, views, height, width, ssaa=1):
+    """Reference images (forward only; the reference is a black box, Sec. 3);
+    ssaa = s > 1 renders s x s shaded samples per pixel and averages them."""
     job = OracleJob(scene, loss="l1")
     with torch.no_grad():
-        out = render(job, job.params, views, height, width)
+        out = render(job, job.params, views, height, width, ssaa=ssaa)
     return out["img"], out["keys"]
 
 

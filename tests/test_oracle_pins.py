@@ -631,3 +631,67 @@ def test_skinning_float32_contract_is_near_float64():
                   torch.as_tensor(pose.astype(np.float64))).numpy()
     assert np.abs(f32 - f64).max() < 2e-6
     assert np.abs(f32 - pos).max() > 1e-2            # the pose moved the mesh
+
+
+# ---------------------------------------------------------------- MSAA training render (Sec. 5.2, antialiasing)
+def test_msaa_interior_pixels_equal_the_one_sample_render():
+    # a pixel whose s x s samples all see the triangle under its centre is that
+    # triangle shaded once at the centre with the pixel's LOD: the 1-spp value
+    c = synth.config_plain(tex_res=64, ref_tex_res=64, ref_freq=8, cand_freq=6, n_views=1, res=48)
+    views = synth.sample_views(3, 0, 2, 48, 48)
+    one = S.OracleJob(c["cand"], loss="l1")
+    ms = S.OracleJob(c["cand"], loss="l1", msaa=2)
+    with torch.no_grad():
+        a = S.render(one, one.params, views, 48, 48, aa=False)
+        b = S.render(ms, ms.params, views, 48, 48, aa=False)
+    tid = lambda k: np.where(k == np.uint64(R.EMPTY), -1, (k & np.uint64(0xFFFFFFFF)).astype(np.int64))
+    t1, t2 = tid(a["keys"]), tid(b["keys"]).reshape(2, 48, 2, 48, 2)
+    same = (t2 == t1[:, :, None, :, None]).all(axis=(2, 4)) & (t1 >= 0)
+    assert same.mean() > 0.2
+    x, y = a["img"].numpy()[same], b["img"].numpy()[same]
+    assert np.abs(x - y).max() <= 1e-12 * np.abs(x).max()
+    assert not np.allclose(a["img"].numpy(), b["img"].numpy())   # edges do differ: coverage is integrated
+
+
+def _lambert_quad(half):
+    pos = np.array([[-half, -half, 0], [half, -half, 0], [half, half, 0], [-half, half, 0]], np.float32)
+    uv = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], np.float32)
+    tri = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    mesh = synth.Mesh(pos, uv, tri, tri.copy())
+    return synth.Scene(mesh=mesh, kd=synth.constant_texture((0.6, 0.3, 0.9, 1.0)),
+                       orm=synth.constant_texture((1.0, 1.0, 0.0)), nrm=synth.constant_texture((0.0, 0.0, 1.0)),
+                       optimize={})
+
+
+@pytest.mark.parametrize("mode", ["msaa", "ssaa"])
+def test_supersampled_coverage_of_a_lambertian_quad(mode):
+    # gamma = 1 removes the specular lobe and a directional light on a plane gives one
+    # radiance c everywhere, so with antialiasing off each pixel is c times the share of
+    # its 2 x 2 samples inside the quad, decided here from the float64 projection
+    W = H = 40
+    sc = _lambert_quad(0.537)
+    view = synth.make_view((0.0, 0.0, 3.0), W, H, light_dir=(0.3, 0.2, 1.0), light_E=2.0)
+    views = np.zeros(1, dtype=synth.VIEW_DTYPE)
+    views[0] = view
+    job = S.OracleJob(sc, loss="l1", msaa=2 if mode == "msaa" else 1)
+    with torch.no_grad():
+        img = S.render(job, job.params, views, H, W, aa=False, ssaa=2 if mode == "ssaa" else 1)["img"][0].numpy()
+    M = view["mvp"].astype(np.float64).reshape(4, 4)
+    corner = M @ np.array([0.537, 0.537, 0.0, 1.0])
+    ex = (corner[0] / corner[3] * 0.5 + 0.5) * W          # right edge, pixels
+    ey = (0.5 - corner[1] / corner[3] * 0.5) * H          # top edge (y down)
+    lo_x, lo_y = W - ex, H - ey                           # left / bottom edges by symmetry
+    c = img[H // 2, W // 2]
+    lam = np.array([0.6, 0.3, 0.9]) / math.pi * 2.0 * (np.array([0.3, 0.2, 1.0]) / np.linalg.norm([0.3, 0.2, 1.0]))[2]
+    assert np.allclose(c, lam, rtol=1e-6)
+    checked = 0
+    for j in range(H):
+        for i in range(W):
+            xs = [i + 0.25, i + 0.75]
+            ys = [j + 0.25, j + 0.75]
+            if min(abs(x - e) for x in xs for e in (lo_x, ex)) < 1e-3 or min(abs(y - e) for y in ys for e in (ey, lo_y)) < 1e-3:
+                continue
+            cov = sum((lo_x < x < ex) and (ey < y < lo_y) for x in xs for y in ys) / 4.0
+            assert np.allclose(img[j, i], cov * lam, rtol=1e-6, atol=1e-12), (i, j, cov)
+            checked += cov not in (0.0, 1.0)
+    assert checked > 20      # partly covered edge pixels were checked
