@@ -37,10 +37,10 @@ WORKLOAD = ("reference 200k-tri fBm icosphere with 2048^2 procedural maps; candi
 # DRAM bytes per launch of the dominant kernel from an ncu capture, valid only
 # for the source it was measured on (sha256 of the listed files).
 TRAFFIC = {
-    "shade_bwd": {"bytes_per_launch": 163197696 + 59788544, "warp_instructions_per_launch": 181384842,
+    "shade_bwd": {"bytes_per_launch": 163170048 + 59651072, "warp_instructions_per_launch": 181634723,
                   "files": ["paper_2104_03989_gb300/csrc/shade.cu", "paper_2104_03989_gb300/csrc/common.cuh",
                             "paper_2104_03989_gb300/csrc/kernels.cuh"],
-                  "sha": "1dc4bc555dacdcb5",
+                  "sha": "b24a5fefa345ab78",
                   "capture": "profiles/shade_bwd_plain_workload.md"},
 }
 
@@ -142,14 +142,19 @@ class ClockSampler:
 def algorithmic_bytes(stage, w):
     """Compulsory DRAM bytes of one step's launches of `stage` (bytes model).
 
-    w: dict with P (pixels/step), C (covered candidate pixels), Cr (covered
-    reference pixels), texel counts and triangle/vertex counts."""
+    w: dict with P (pixels/step; samples/step under MSAA), C (covered candidate
+    pixels or samples), Cr (covered reference pixels or samples), Ppix (pixels
+    per step), S (samples per pixel side), texel counts and triangle/vertex counts."""
     P = w["P"]
     tex_px = 1.33 * 16 * 3          # unique texels per covered pixel per map x 16 B x 3 maps
     if stage == "shade_bwd":
         return 40 * P + (tex_px * 3) * w["C"]          # key+g'+pre per pixel; texel read + grad RMW
     if stage == "shade":
         return 2 * 24 * P + tex_px * (w["C"] + w["Cr"])  # candidate + reference launches
+    if stage == "aa_loss" and w.get("S", 1) > 1:
+        # per sample: AA reads key + pre and writes its colour, the resolve reads it
+        # back (and writes g' for the candidate); per pixel: reference in, image out
+        return (8 + 16 + 16) * 2 * P + (16 + 16) * P + 16 * P + (12 + 12) * w["Ppix"]
     if stage == "aa_loss":
         return (8 + 16 + 12 + 16) * P + (8 + 16 + 12) * P  # candidate (loss, g') + reference (image)
     if stage == "raster":
@@ -174,12 +179,13 @@ class OracleStep:
 
     Topology tables are built once, outside the timed calls."""
 
-    def __init__(self, scene_cfg):
+    def __init__(self, scene_cfg, msaa=1):
         from oracle import step as S
 
         self.S = S
+        self.msaa = msaa
         self.ref = S.OracleJob(scene_cfg["ref"], loss="l1")
-        self.cand = S.OracleJob(scene_cfg["cand"], loss="logl1")
+        self.cand = S.OracleJob(scene_cfg["cand"], loss="logl1", msaa=msaa)
 
     def seconds(self, n_views, res, seed=123):
         import torch
@@ -189,7 +195,7 @@ class OracleStep:
         views = synth.sample_views(seed, 0, n_views, res, res)
         t0 = time.perf_counter()
         with torch.no_grad():
-            ref = self.S.render(self.ref, self.ref.params, views, res, res)["img"]
+            ref = self.S.render(self.ref, self.ref.params, views, res, res, ssaa=self.msaa)["img"]
         self.S.step(self.cand, views, ref.numpy(), res, res)
         return time.perf_counter() - t0, torch.get_num_threads()
 
@@ -250,10 +256,12 @@ def run_native(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = Context(stream=stream)
-    ref_job = ctx.create_job(cfg["ref"], frozen=True)
+    MS = max(int(args.msaa), 1)
+    # under MSAA the references are supersampled renders (every sample shaded)
+    ref_job = ctx.create_job(cfg["ref"], frozen=True, samples=MS, shade_samples=True)
     pl = bool(args.per_level_textures)
-    cand = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, per_level_textures=pl)
-    plain = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, batch_views=VIEWS, per_level_textures=pl)
+    cand = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, per_level_textures=pl, samples=MS)
+    plain = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, batch_views=VIEWS, per_level_textures=pl, samples=MS)
     n_steps = args.warmup + args.steps
     host_views = [synth.sample_views(replica_seed(rank), i, VIEWS, RES, RES) for i in range(n_steps)]
     view_np = np.stack([v.view(np.uint8) for v in host_views])                  # (steps, 8*112)
@@ -374,17 +382,18 @@ def run_native(args):
     e2e_s = max_over_ranks(e2e_s, world, dev)
 
     # workload facts for the bytes model
-    keys = ctx.keys(cand, (VIEWS, RES, RES))
+    keys = ctx.keys(cand, (VIEWS, RES * MS, RES * MS))
     covered = int((keys != -1).sum())
     pv = ctx.params(cand)
     texels = sum(pv[n].shape[0] * pv[n].shape[1] for n in ("kd", "orm", "nrm"))
     # latent texels Adam updates: level 0, or every level of each chain with per-level latents
     latent_texels = sum(pv[n + "_chain"].shape[0] for n in ("kd", "orm", "nrm")) if pl else texels
     ctx.render_reference(ref_job, host_views[-1], RES, RES, out=ref_buf)
-    rkeys = ctx.keys(ref_job, (VIEWS, RES, RES))
+    rkeys = ctx.keys(ref_job, (VIEWS, RES * MS, RES * MS))
     covered_ref = int((rkeys != -1).sum())
-    wl = dict(P=VIEWS * RES * RES, C=covered, Cr=covered_ref, texels=texels, texel_floats=4 * latent_texels,
-              V=cfg["cand"].mesh.n_verts, F=cfg["cand"].mesh.n_tris, Fr=cfg["ref"].mesh.n_tris)
+    wl = dict(P=VIEWS * RES * RES * MS * MS, C=covered, Cr=covered_ref, texels=texels, texel_floats=4 * latent_texels,
+              V=cfg["cand"].mesh.n_verts, F=cfg["cand"].mesh.n_tris, Fr=cfg["ref"].mesh.n_tris,
+              Ppix=VIEWS * RES * RES, S=MS)
 
     px_step = VIEWS * RES * RES
     value = whole_job_mpix(world, px_step, args.steps, total_ms / 1e3)
@@ -407,7 +416,8 @@ def run_native(args):
     d = stage_rows[dominant]
     launches_per_step = max(d["launches_per_step"], 1e-9)
     achieved = d["gbs"]
-    tr = TRAFFIC.get(dominant)
+    # the committed DRAM counters and instruction counts are the plain workload's
+    tr = TRAFFIC.get(dominant) if not (pl or SKB or MS > 1) else None
     traffic = None
     if tr and _sha(tr["files"]) == tr["sha"]:
         traffic = tr["bytes_per_launch"]
@@ -429,9 +439,11 @@ def run_native(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, cores = OracleStep(cfg).seconds(1, RES)
-        cpu = {"value": RES * RES / dt / 1e6, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
-               "sample": f"1 of 8 views at {RES}^2: full oracle step (reference render + fwd/bwd/Adam)"}
+        cres = RES // MS    # the same samples per view as the plain sample
+        dt, cores = OracleStep(cfg, msaa=MS).seconds(1, cres)
+        cpu = {"value": cres * cres / dt / 1e6, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
+               "sample": f"1 of 8 views at {cres}^2" + (f" with {MS}x{MS} MSAA" if MS > 1 else "")
+               + ": full oracle step (reference render + fwd/bwd/Adam)"}
 
     if rank == 0:
         line = {
@@ -441,7 +453,10 @@ def run_native(args):
             "config": {"workload": WORKLOAD + ("; every mip level of each texture its own latent (Sec. 6)" if pl else "")
                        + (f"; both meshes skinned by {SKB} bones (Eq. 2), dense weights optimized (learning rate / {SKB}), "
                           "a new pose per step"
-                          if SKB else ""),
+                          if SKB else "")
+                       + (f"; {MS}x{MS} multisampling (Sec. 5.2): visibility, shading and antialiasing on the "
+                          f"{RES * MS}^2 sample grid, each sample shaded at its pixel centre, loss on the resolved "
+                          f"pixels; references supersampled {MS}x{MS}" if MS > 1 else ""),
                        "global_batch": VIEWS * world, "seq_len": None,
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "launch": "one CUDA graph per step (reference render, forward+loss, backward, Adam)",
@@ -454,7 +469,7 @@ def run_native(args):
             "gpu_launches": int(round(launches * args.steps)), "gpu_launches_per_step": launches,
             "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "roofline": roofline, "stages": stage_rows, "clocks": clocks, "cpu_baseline": cpu,
-            "coverage": covered / px_step,
+            "coverage": covered / (px_step * MS * MS),
         }
         print(json.dumps(line), flush=True)
     B.adms_graph_destroy(graph)
@@ -665,6 +680,9 @@ def main():
     ap.add_argument("--per-job-iterations", type=int, default=3, help="serving: iterations of the per-job loop")
     ap.add_argument("--skinning", type=int, default=0, metavar="BONES",
                     help="plain workload with both meshes skinned by BONES bones and a new pose per step (Eq. 2)")
+    ap.add_argument("--msaa", type=int, default=1, metavar="S",
+                    help="plain workload rendered with S x S samples per pixel (MSAA, Sec. 5.2), references "
+                         "supersampled; the metric counts pixels")
     ap.add_argument("--per-level-textures", action="store_true",
                     help="plain workload with every mip level of each texture an independent latent (Sec. 6)")
     args = ap.parse_args()

@@ -107,6 +107,16 @@ typedef struct {
                                   level takes its own gradient and Adam moments, and nothing is
                                   folded or rebuilt; needs mips. 0: one latent per texture (level
                                   0), coarser levels are its box-filter chain */
+    int32_t samples;         /* s in [2, 8]: s x s visibility samples per pixel (Sec. 5.2,
+                                antialiasing): raster, shading and silhouette antialiasing on the
+                                sample grid, each pixel the mean of its samples, the loss per
+                                pixel; 0 or 1: one sample per pixel. Such a job runs one per
+                                forward_loss / backward call (not batched); adms_job_keys returns
+                                the sample grid's keys */
+    int32_t shade_samples;   /* with samples > 1: 0 = MSAA, each sample takes its triangle shaded
+                                once per pixel at the pixel's centre with the pixel's LOD (the
+                                training render); 1 = every sample shaded at its own position (a
+                                supersampled render, e.g. for reference images) */
 } adms_opt_params;
 
 /* Device pointers into a job's resident state (owned by the library, valid

@@ -95,7 +95,13 @@ struct Job {
     RasterScratch rs{};
     // latest forward
     bool have_fwd = false;
-    int B = 0, H = 0, W = 0;
+    int B = 0, H = 0, W = 0;  // views and the grid the kernels work on (the sample grid when S > 1)
+    // supersampled rendering (Sec. 5.2): S x S samples per pixel; MSAA shades once per
+    // pixel (at its centre), ssaa shades every sample; the resolve averages them
+    int S = 1;
+    bool ssaa = false;
+    int PH = 0, PW = 0;        // pixels per view
+    float4* acol = nullptr;    // antialiased sample colours (+ blend masks) for the resolve
     const float* ref = nullptr;
     float loss_scale = 0.f;
     std::vector<void*> allocs;
@@ -303,6 +309,7 @@ adms_status ensure_scratch(adms_ctx* ctx, Job& j, int B, int H, int W) {
         AL(j.pre, px);
         AL(j.gprime, px);
         AL(j.refine, px + 1);
+        if (j.S > 1) AL(j.acol, px);
         j.px_cap = px;
     }
     if ((size_t)B > j.view_cap) {
@@ -432,6 +439,8 @@ ShadeArgs shade_args(Job& j) {
     a.pre = j.pre;
     a.gprime = j.gprime;
     a.refine = j.refine;
+    a.msaa = (j.S > 1 && !j.ssaa) ? j.S : 0;
+    a.acol = j.S > 1 ? j.acol : nullptr;
     a.loss_kind = j.opt.loss;
     a.loss_scale = j.loss_scale;
     a.aa = j.opt.aa;
@@ -440,6 +449,10 @@ ShadeArgs shade_args(Job& j) {
     a.g_tan = j.g_tan;
     return a;
 }
+
+// AA on the sample grid, then the per-pixel resolve of a supersampled job: the
+// loss and each sample's dL/d(colour) when ref is given, the image into out_img
+adms_status aa_resolve(adms_ctx* ctx, Job& j, const float* ref, double* loss_acc, float* out_img);
 
 // frame, raster and pre-AA shading of B views already copied to j.views
 SkinArgs skin_args(Job& j) {
@@ -477,6 +490,28 @@ adms_status render_core(adms_ctx* ctx, Job& j) {
     CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
     CK(TIMED(ST_RASTER, raster_tiles(in, j.rs, ctx->stream)));
     CK(TIMED(ST_SHADE, shade_forward(shade_args(j), ctx->stream)));
+    return ADMS_OK;
+}
+
+adms_status aa_resolve(adms_ctx* ctx, Job& j, const float* ref, double* loss_acc, float* out_img) {
+    ShadeArgs a = shade_args(j);
+    a.ref = nullptr;
+    a.loss_acc = nullptr;
+    a.out_img = nullptr;
+    CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
+    ResolveArgs r;
+    r.B = j.B;
+    r.H = j.PH;
+    r.W = j.PW;
+    r.S = j.S;
+    r.acol = j.acol;
+    r.ref = ref;
+    r.gprime = j.gprime;
+    r.out_img = out_img;
+    r.loss_acc = loss_acc;
+    r.loss_kind = j.opt.loss;
+    r.loss_scale = j.loss_scale;
+    CK(TIMED(ST_AA_LOSS, resolve_loss(r, ctx->stream)));
     return ADMS_OK;
 }
 
@@ -635,6 +670,9 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
         j.opt.aa = 1;
     }
     if (j.opt.tess_levels < 0 || j.opt.tess_levels > 6) return fail(ctx, ADMS_ERR_ARG, "tess_levels must be in [0, 6]");
+    if (j.opt.samples < 0 || j.opt.samples > 8) return fail(ctx, ADMS_ERR_ARG, "samples must be in [0, 8]");
+    j.S = std::max(1, (int)j.opt.samples);
+    j.ssaa = j.opt.shade_samples != 0;
     j.tess = j.opt.tess_levels > 0;
     if (j.tess && (!mat->disp || !pow2(mat->disp_h) || !pow2(mat->disp_w)))
         return fail(ctx, ADMS_ERR_ARG, "a tessellated job needs a power-of-two displacement map");
@@ -904,7 +942,7 @@ adms_status batch_upload(adms_ctx* ctx, const std::vector<Job*>& js, float* cons
 // buffers below, in this order. Gradients and per-step scratch are not kept:
 // export between optimizer steps.
 const char kCkptMagic[8] = {'A', 'D', 'M', 'S', 'C', 'K', 'P', 'T'};
-const uint32_t kCkptVersion = 1;
+const uint32_t kCkptVersion = 2;  // 2: per-level, skinning and multisampling fields
 
 struct CkptHeader {
     char magic[8];
@@ -913,7 +951,7 @@ struct CkptHeader {
     int32_t LV, V, F, tess_levels, dh, dw;
     int32_t tex_w[3], tex_h[3], tex_levels[3], tex_opt[3];
     int32_t optimize[5];  // pos, kd, orm, nrm, disp
-    int32_t loss, relative_laplacian, batch_views, aa, per_level_textures, n_bones;
+    int32_t loss, relative_laplacian, batch_views, aa, per_level_textures, n_bones, samples, shade_samples;
     float lr0, lambda0, skin_lr_scale;
     uint64_t section_bytes[16];
 };
@@ -952,6 +990,8 @@ void ckpt_describe(Job& j, CkptHeader& h, std::vector<CkptSection>& secs) {
     h.aa = j.opt.aa;
     h.per_level_textures = j.opt.per_level_textures;
     h.n_bones = j.SB;
+    h.samples = j.S;
+    h.shade_samples = j.ssaa;
     h.skin_lr_scale = j.skin_lr_scale;
     h.lr0 = j.opt.lr0;
     h.lambda0 = j.opt.lambda0;
@@ -1266,13 +1306,20 @@ adms_status adms_render_reference(adms_ctx* ctx, adms_job job, const adms_view* 
     if (!jp || !views || !out_rgb || n_views <= 0 || H <= 0 || W <= 0 || H > 16384 || W > 16384)
         return fail(ctx, ADMS_ERR_ARG, "invalid render_reference arguments");
     Job& j = *jp;
-    adms_status s = ensure_scratch(ctx, j, n_views, H, W);
+    adms_status s = ensure_scratch(ctx, j, n_views, H * j.S, W * j.S);
     if (s) return s;
     j.B = n_views;
-    j.H = H;
-    j.W = W;
+    j.H = H * j.S;
+    j.W = W * j.S;
+    j.PH = H;
+    j.PW = W;
     CK(cudaMemcpyAsync(j.views, views, sizeof(adms_view) * n_views, cudaMemcpyDefault, ctx->stream));
     if ((s = render_core(ctx, j))) return s;
+    if (j.S > 1) {
+        if ((s = aa_resolve(ctx, j, nullptr, nullptr, out_rgb))) return s;
+        j.have_fwd = false;
+        return ADMS_OK;
+    }
     ShadeArgs a = shade_args(j);
     a.ref = nullptr;
     a.loss_acc = nullptr;
@@ -1299,11 +1346,17 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
             if (o == jp) return fail(ctx, ADMS_ERR_ARG, "a job appears twice in one call");
         js.push_back(jp);
         Job& j = *jp;
-        adms_status s = ensure_scratch(ctx, j, B, H, W);
+        if (n_jobs > 1 && j.S > 1)
+            return fail(ctx, ADMS_ERR_STATE, "supersampled (MSAA) jobs run one per call, not in a batch");
+        if ((long long)H * j.S > 16384 || (long long)W * j.S > 16384)
+            return fail(ctx, ADMS_ERR_ARG, "sample grid larger than 16384 per side");
+        adms_status s = ensure_scratch(ctx, j, B, H * j.S, W * j.S);
         if (s) return s;
         j.B = B;
-        j.H = H;
-        j.W = W;
+        j.H = H * j.S;
+        j.W = W * j.S;
+        j.PH = H;
+        j.PW = W;
         j.ref = ref_rgb[k];
         int norm_views = j.opt.batch_views > 0 ? j.opt.batch_views : B;
         j.loss_scale = (float)(1.0 / (3.0 * (double)norm_views * H * W));
@@ -1312,11 +1365,15 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
         CK(cudaMemsetAsync(&j.st->call_loss, 0, sizeof(double), ctx->stream));
         if (n_jobs == 1) {
             if ((s = render_core(ctx, j))) return s;
-            ShadeArgs a = shade_args(j);
-            a.ref = j.ref;
-            a.loss_acc = &j.st->call_loss;
-            a.out_img = out_img ? out_img[k] : nullptr;
-            CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
+            if (j.S > 1) {
+                if ((s = aa_resolve(ctx, j, j.ref, &j.st->call_loss, out_img ? out_img[k] : nullptr))) return s;
+            } else {
+                ShadeArgs a = shade_args(j);
+                a.ref = j.ref;
+                a.loss_acc = &j.st->call_loss;
+                a.out_img = out_img ? out_img[k] : nullptr;
+                CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
+            }
         } else {
             if ((s = frame_and_prepare(ctx, j))) return s;
         }
@@ -1357,10 +1414,14 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
             // caller's reference images instead of reading what the forward kept
             adms_status s = render_core(ctx, j);
             if (s) return s;
-            ShadeArgs r = shade_args(j);
-            r.ref = j.ref;
-            r.loss_acc = nullptr;
-            CK(TIMED(ST_AA_LOSS, aa_loss_forward(r, ctx->stream)));
+            if (j.S > 1) {
+                if ((s = aa_resolve(ctx, j, j.ref, nullptr, nullptr))) return s;
+            } else {
+                ShadeArgs r = shade_args(j);
+                r.ref = j.ref;
+                r.loss_acc = nullptr;
+                CK(TIMED(ST_AA_LOSS, aa_loss_forward(r, ctx->stream)));
+            }
         }
         CK(cudaMemsetAsync(j.g_nrm, 0, sizeof(double) * 3 * j.V, ctx->stream));
         CK(cudaMemsetAsync(j.g_tan, 0, sizeof(double) * 3 * j.V, ctx->stream));

@@ -93,6 +93,10 @@ struct ShadeArgs {
     TexDev kd, orm, nrm;
     float4* pre;                     // [B][H][W] pre-AA colour
     const float* ref;                // [B][H][W][3]
+    int msaa;                        // s > 1: keys, pre, gprime are on an s x s sample grid per pixel
+                                     // and each sample is shaded at its pixel's centre, LOD of the pixel
+    float4* acol;                    // [B][H][W] antialiased sample colours (w: the blend mask bits) for
+                                     // the per-pixel resolve, or null
     int* refine;                     // [0]: count, then pixel indices shaded again with a refined
                                      // texture coordinate (null: none)
     float4* gprime;                  // [B][H][W] dL/d(AA colour) in xyz; w: bit n set (as raw bits)
@@ -111,14 +115,29 @@ cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st);
 cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st);
 cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st);
 
+// per-pixel resolve of a supersampled render: pixel = mean of its s x s antialiased
+// samples; with a reference, the loss per pixel and each sample's share of
+// dL/d(colour) (into gprime.xyz; gprime.w keeps the sample's blend mask)
+struct ResolveArgs {
+    int B, H, W, S;        // pixels per view H x W, samples per axis S
+    const float4* acol;    // [B][S H][S W]
+    const float* ref;      // [B][H][W][3] or null
+    float4* gprime;        // [B][S H][S W]
+    float* out_img;        // [B][H][W][3] or null
+    double* loss_acc;      // or null
+    int loss_kind;
+    float loss_scale;      // 1 / (3 P), P pixels
+};
+cudaError_t resolve_loss(const ResolveArgs& r, cudaStream_t st);
+
 // one unit of work of a batched launch: a tile of one view of one job
 struct WorkItem {
     int job, view, x0, y0;
 };
 // Jobs per batched launch: their arguments travel in the launch's parameter
-// space (64 x 496 B, under the 32 KB limit), read-only and captured with the
-// launch by a graph; larger job sets take one launch per 64 jobs.
-#define ADMS_BATCH_JOBS 64
+// space (60 x 520 B, under the 32 KB limit), read-only and captured with the
+// launch by a graph; larger job sets take one launch per 60 jobs.
+#define ADMS_BATCH_JOBS 60
 struct ShadeBatch {
     ShadeArgs a[ADMS_BATCH_JOBS];
 };

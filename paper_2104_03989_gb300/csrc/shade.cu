@@ -34,8 +34,21 @@ __device__ __forceinline__ float2 rel_screen(float4 S, float ox, float oy) {
 
 // Perspective-correct barycentrics and interpolated attributes (corner 0 plus
 // weighted differences) of pixel (px, py) inside triangle f.
+// the point a sample is shaded at: its own centre, or under MSAA the centre of
+// its pixel (s x s samples per pixel); screen units of the sample grid
+__device__ __forceinline__ void shade_point(const ShadeArgs& A, int px, int py, float& qx, float& qy) {
+    if (A.msaa > 1) {
+        qx = (float)((px / A.msaa) * A.msaa) + 0.5f * (float)A.msaa;
+        qy = (float)((py / A.msaa) * A.msaa) + 0.5f * (float)A.msaa;
+    } else {
+        qx = (float)px + 0.5f;
+        qy = (float)py + 0.5f;
+    }
+}
+
 __device__ __forceinline__ void pix_geo(const ShadeArgs& A, int b, int px, int py, int f, PixGeo& g) {
-    float qx = (float)px + 0.5f, qy = (float)py + 0.5f;
+    float qx, qy;
+    shade_point(A, px, py, qx, qy);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         g.vi[k] = A.tri[3 * f + k];
@@ -92,6 +105,11 @@ __device__ __forceinline__ void pix_geo(const ShadeArgs& A, int b, int px, int p
     float db1y = (dry[1] * g.R - g.r[1] * dRy) * iR * iR, db2y = (dry[2] * g.R - g.r[2] * dRy) * iR * iR;
     g.duv_dx = make_float2(db1x * du1.x + db2x * du2.x, db1x * du1.y + db2x * du2.y);
     g.duv_dy = make_float2(db1y * du1.x + db2y * du2.x, db1y * du1.y + db2y * du2.y);
+    if (A.msaa > 1) {  // derivatives per pixel: s sample-grid steps
+        float sc = (float)A.msaa;
+        g.duv_dx = make_float2(g.duv_dx.x * sc, g.duv_dx.y * sc);
+        g.duv_dy = make_float2(g.duv_dy.x * sc, g.duv_dy.y * sc);
+    }
 }
 
 // ------------------------------------------------------------------ shading
@@ -270,7 +288,8 @@ __device__ __forceinline__ ShadeIn shade_inputs(const ShadeArgs& A, const PixGeo
 // length in rounding; over a triangle spanning tens of texels that is ~2e-6
 // texel, which moves pixels under sharp highlights on noise textures by ~1e-5.
 __device__ __forceinline__ void refine_tc(const ShadeArgs& A, int b, int px, int py, PixGeo& g) {
-    float qx = (float)px + 0.5f, qy = (float)py + 0.5f;
+    float qx, qy;
+    shade_point(A, px, py, qx, qy);
     DF dx[3], dy[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -309,6 +328,11 @@ __device__ __forceinline__ void refine_tc(const ShadeArgs& A, int b, int px, int
     float db1y = dot2_acc(dry[1], g.R, -g.r[1], dRy) * iR2, db2y = dot2_acc(dry[2], g.R, -g.r[2], dRy) * iR2;
     g.duv_dx = make_float2(dot2_acc(db1x, du1.x, db2x, du2.x), dot2_acc(db1x, du1.y, db2x, du2.y));
     g.duv_dy = make_float2(dot2_acc(db1y, du1.x, db2y, du2.x), dot2_acc(db1y, du1.y, db2y, du2.y));
+    if (A.msaa > 1) {
+        float sc = (float)A.msaa;
+        g.duv_dx = make_float2(g.duv_dx.x * sc, g.duv_dx.y * sc);
+        g.duv_dy = make_float2(g.duv_dy.x * sc, g.duv_dy.y * sc);
+    }
 }
 
 // texels of the largest texture that the triangle's uv offsets span at the finest
@@ -514,6 +538,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
             A.out_img[pix * 3 + 1] = out.y;
             A.out_img[pix * 3 + 2] = out.z;
         }
+        if (A.acol) A.acol[pix] = make_float4(out.x, out.y, out.z, __uint_as_float(amask));
     }
     lsum = warp_sum_d(lsum);
     __syncthreads();
@@ -766,6 +791,58 @@ __global__ void __launch_bounds__(256, KIND == 2 ? 3 : (KIND == 1 ? 8 : 5))
         else if (KIND == 1) aa_loss_block(A, w.view, px, py, red);
         else shade_bwd_px(A, w.view, px, py);
     }
+}
+
+// ------------------------------------------------------------------ supersample resolve
+__global__ void __launch_bounds__(256) k_resolve(ResolveArgs r) {
+    __shared__ double red[8];
+    long long n = (long long)r.B * r.H * r.W;
+    long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double lsum = 0.0;
+    if (pix < n) {
+        int b = (int)(pix / ((long long)r.H * r.W));
+        int rem = (int)(pix - (long long)b * r.H * r.W);
+        int py = rem / r.W, px = rem - py * r.W;
+        int SW = r.S * r.W;
+        size_t base = ((size_t)b * r.S * r.H + (size_t)py * r.S) * SW + (size_t)px * r.S;
+        float3 c = zero3();
+        for (int sy = 0; sy < r.S; ++sy)
+            for (int sx = 0; sx < r.S; ++sx) c += f3of(r.acol[base + (size_t)sy * SW + sx]);
+        float inv = 1.f / (float)(r.S * r.S);
+        c = inv * c;
+        if (r.out_img) {
+            r.out_img[pix * 3] = c.x;
+            r.out_img[pix * 3 + 1] = c.y;
+            r.out_img[pix * 3 + 2] = c.z;
+        }
+        if (r.ref) {
+            const float* y = r.ref + pix * 3;
+            float g0, g1, g2;
+            lsum = (double)loss_term(r.loss_kind, c.x, y[0], &g0) + (double)loss_term(r.loss_kind, c.y, y[1], &g1) +
+                   (double)loss_term(r.loss_kind, c.z, y[2], &g2);
+            float k = r.loss_scale * inv;  // each sample carries 1 / s^2 of its pixel
+            for (int sy = 0; sy < r.S; ++sy)
+                for (int sx = 0; sx < r.S; ++sx) {
+                    size_t q = base + (size_t)sy * SW + sx;
+                    r.gprime[q] = make_float4(g0 * k, g1 * k, g2 * k, r.acol[q].w);
+                }
+        }
+    }
+    lsum = warp_sum_d(lsum);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0 && r.loss_acc) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        atomicAdd(r.loss_acc, s * (double)r.loss_scale);
+    }
+}
+
+cudaError_t resolve_loss(const ResolveArgs& r, cudaStream_t st) {
+    long long n = (long long)r.B * r.H * r.W;
+    k_resolve<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launchers

@@ -91,10 +91,11 @@ def fold_mips(g, h, w, levels):
     return out
 
 
-def oracle_grads(scene, views, refs, H, W, loss, per_level=False, skin_weights=None, bones=None):
+def oracle_grads(scene, views, refs, H, W, loss, per_level=False, skin_weights=None, bones=None, msaa=1):
     """Oracle image-loss gradients (lambda = 0), images, keys, loss, and the
-    vertices whose gradient is not unique at float32 resolution."""
-    job = S.OracleJob(scene, loss=loss, per_level=per_level, skin_weights=skin_weights)
+    vertices whose gradient is not unique at float32 resolution. msaa = s > 1:
+    keys on the s x s sample grid, images per pixel."""
+    job = S.OracleJob(scene, loss=loss, per_level=per_level, skin_weights=skin_weights, msaa=msaa)
     if bones is not None:
         job.bones = torch.as_tensor(np.asarray(bones, dtype=np.float64))
         job.shade_f32_skin = True   # the GPU shades the float32 skinned positions it renders
@@ -105,7 +106,7 @@ def oracle_grads(scene, views, refs, H, W, loss, per_level=False, skin_weights=N
     grads = dict(zip(live, [g.detach().numpy() for g in torch.autograd.grad(obj["total"], [params[k] for k in live])]))
     img = obj["out"]["img"].detach().numpy()
     if job.tess is None:
-        amb = ambiguous_vertices(diags, obj["out"]["keys"], img, refs, job.tri_np, loss)
+        amb = ambiguous_vertices(diags, obj["out"]["keys"], img, refs, job.tri_np, loss, sub=max(msaa, 1))
     else:
         # render vertices -> the base vertices they are interpolated from
         amb_r = ambiguous_vertices(diags, obj["out"]["keys"], img, refs, job.tess.tri, loss)
@@ -115,6 +116,18 @@ def oracle_grads(scene, views, refs, H, W, loss, per_level=False, skin_weights=N
         amb = base
     return dict(grads=grads, img=img, pre=obj["out"]["pre"].detach().numpy(), keys=obj["out"]["keys"],
                 loss=float(obj["image"].detach()), ambiguous=amb)
+
+
+def oracle_ambiguous(job, views, refs, H, W):
+    """The vertices whose gradient is one-sided (ambiguous_vertices) at an
+    oracle job's current parameters, for a plain (untessellated) mesh."""
+    params = {k: v.detach() for k, v in job.params.items()}
+    diags = []
+    with torch.no_grad():
+        obj = S.objective(job, params, views, torch.as_tensor(np.asarray(refs, dtype=np.float64)), H, W, lam=0.0,
+                          diags=diags)
+    return ambiguous_vertices(diags, obj["out"]["keys"], obj["out"]["img"].numpy(), refs, job.tri_np, job.loss,
+                              sub=max(job.msaa, 1))
 
 
 # Margins to the discrete decisions inside the differentiable path. The CUDA
@@ -127,13 +140,14 @@ AA_MARGIN = 1e-4      # pixels: silhouette crossing tests and tau = 1/2
 LOSS_MARGIN = 1e-5    # |f(x) - f(y)|: sign of the L1 residual
 
 
-def ambiguous_vertices(diags, keys, img, refs, tri, loss):
+def ambiguous_vertices(diags, keys, img, refs, tri, loss, sub=1):
     """Vertices touched by pixels within a margin of a kink of the forward.
 
     At such a pixel the forward is continuous but its derivative is one-sided,
     and the float32 kernel may legitimately take the other side: the gradient
     is not unique there, so parity tests compare the other vertices exactly
-    and these only for validity."""
+    and these only for validity. sub = s > 1: keys and margins on the s x s sample
+    grid, images per pixel (a pixel near an L1 kink marks all its samples)."""
     from oracle import render as R
 
     tri = np.asarray(tri)
@@ -152,6 +166,8 @@ def ambiguous_vertices(diags, keys, img, refs, tri, loss):
         if loss == "logl1":
             x, y = R.tonemap(x), R.tonemap(y)
         close = ((x - y).abs() < LOSS_MARGIN).any(dim=2).numpy() & ((x - y).abs().sum(dim=2) > 0).numpy()
+        if sub > 1:
+            close = np.repeat(np.repeat(close, sub, axis=0), sub, axis=1)
         H, W = close.shape
         for j, i in zip(*np.nonzero(close)):
             for dj, di in ((0, 0), (1, 0), (-1, 0), (0, 1), (0, -1)):
