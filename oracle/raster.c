@@ -183,10 +183,13 @@ static int64_t edge_fn(int64_t xa, int64_t ya, int64_t xb, int64_t yb, int64_t s
 
 /* Rasterize F triangles of one view into keys[H*W] (caller initialises to all
  * ones; keys already present are min-merged). area_sign[F] receives the sign
- * of the snapped signed area (0 for unusable or degenerate triangles). */
-void oracle_raster(const int32_t* XY, const float* z01, const int8_t* ok,
-                   const int32_t* tri, int F, int W, int H,
-                   uint64_t* keys, int8_t* area_sign)
+ * of the snapped signed area (0 for unusable or degenerate triangles).
+ * floor_keys (or NULL): a fragment is kept only when its key is strictly
+ * greater than floor_keys at its pixel (the two-sided depth test of a depth
+ * peeling pass, Sec. 5.2, with the previous layer's keys as the floor). */
+static void raster_into(const int32_t* XY, const float* z01, const int8_t* ok,
+                        const int32_t* tri, int F, int W, int H, const uint64_t* floor_keys,
+                        uint64_t* keys, int8_t* area_sign)
 {
     for (int f = 0; f < F; ++f) {
         const int32_t i0 = tri[3 * f], i1 = tri[3 * f + 1], i2 = tri[3 * f + 2];
@@ -271,10 +274,26 @@ void oracle_raster(const int32_t* XY, const float* z01, const int8_t* ok,
                 memcpy(&bits, &d, 4);
                 const uint64_t key = ((uint64_t)bits << 32) | (uint32_t)f;
                 uint64_t* kp = keys + j * (int64_t)W + i;
+                if (floor_keys && !(key > floor_keys[j * (int64_t)W + i])) continue;
                 if (key < *kp) *kp = key;
             }
         }
     }
+}
+
+void oracle_raster(const int32_t* XY, const float* z01, const int8_t* ok,
+                   const int32_t* tri, int F, int W, int H,
+                   uint64_t* keys, int8_t* area_sign)
+{
+    raster_into(XY, z01, ok, tri, F, W, H, NULL, keys, area_sign);
+}
+
+/* One depth-peeling pass: the nearest fragment behind floor_keys at every pixel. */
+void oracle_raster_layer(const int32_t* XY, const float* z01, const int8_t* ok,
+                         const int32_t* tri, int F, int W, int H, const uint64_t* floor_keys,
+                         uint64_t* keys, int8_t* area_sign)
+{
+    raster_into(XY, z01, ok, tri, F, W, H, floor_keys, keys, area_sign);
 }
 
 /* Skinned positions (Eq. 2) under the float32 contract that visibility uses:

@@ -332,6 +332,19 @@ def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True,
     width, height are those of the s x s sample grid of each pixel; every sample
     takes its triangle shaded once per pixel, at the pixel's centre, with the
     LOD of the pixel's footprint; antialiasing acts on the sample grid."""
+    pre, _, scr = shade_pixels(geo, tex_levels, view, keys, width, height, lod_store=lod_store, diag=diag,
+                               msaa=msaa)
+    if not aa:
+        return pre, pre
+    sil = silhouette_flags(asign, adj)
+    aa_store = None if lod_store is None else lod_store.setdefault("aa", {})
+    return pre, antialias(pre, keys, scr, geo["tri"], sil, width, height, aa_store=aa_store, diag=diag)
+
+
+def shade_pixels(geo, tex_levels, view, keys, width, height, lod_store=None, diag=None, msaa=1):
+    """Shaded colour (H, W, 3) and base-colour alpha (H, W) of the covered
+    pixels of one view (zero elsewhere), and the view's screen positions.
+    Arguments as for render_view."""
     pos, tri, tri_uv = geo["pos"], geo["tri"], geo["tri_uv"]
     M = t64(np.asarray(view["mvp"], dtype=np.float32).astype(np.float64).reshape(4, 4))
     clip = torch.cat([pos, torch.ones_like(pos[:, :1])], dim=1) @ M.T
@@ -389,12 +402,45 @@ def render_view(geo, tex_levels, view, keys, asign, adj, width, height, aa=True,
         diag.update(pix=pix, tri=fid.numpy(), texel_margin=torch.stack(margins, 1).min(1).values.numpy(),
                     nl_margin=nl.numpy())
     img = torch.zeros((height * width, 3), dtype=F64).index_copy(0, pixt, col)
-    pre = img.reshape(height, width, 3)
-    if not aa:
-        return pre, pre
-    sil = silhouette_flags(asign, adj)
-    aa_store = None if lod_store is None else lod_store.setdefault("aa", {})
-    return pre, antialias(pre, keys, scr, tri, sil, width, height, aa_store=aa_store, diag=diag)
+    alpha = torch.zeros(height * width, dtype=F64).index_copy(0, pixt, kd_s[:, 3])
+    return img.reshape(height, width, 3), alpha.reshape(height, width), scr
+
+
+def peel_view(geo, tex_levels, view, layer_keys, asign, adj, width, height, aa=True, lod_store=None, diag=None):
+    """Order-independent transparency by depth peeling (Sec. 5.2, reading).
+
+    layer_keys: (L, H, W) keys of the peeled layers, front to back
+    (visibility.raster_peeled). Each layer is shaded like an opaque render and
+    takes its opacity from the base-colour texture's fourth channel (zero where
+    the layer is empty). Blending runs back to front from a black background:
+    with A_L = 0, for l = L-1 .. 0
+        B_l = alpha_l c_l + (1 - alpha_l) A_{l+1},
+        A_l = antialias(B_l) with layer l's visibility (the identity when aa is off),
+    and the image is A_0. lod_store / diag as for render_view, kept per layer
+    (diag["layers"][l] holds layer l's margins). Returns (layer 0's shaded
+    colours, the image)."""
+    L = layer_keys.shape[0]
+    sil = silhouette_flags(asign, adj) if aa else None
+    acc = torch.zeros((height, width, 3), dtype=F64)
+    diags = [None] * L
+    pre0 = None
+    for l in reversed(range(L)):
+        st = None if lod_store is None else lod_store.setdefault(("layer", l), {})
+        dg = None if diag is None else {}
+        col, alpha, scr = shade_pixels(geo, tex_levels, view, layer_keys[l], width, height, lod_store=st, diag=dg)
+        a = alpha[..., None]
+        blended = a * col + (1 - a) * acc
+        if aa:
+            aa_store = None if st is None else st.setdefault("aa", {})
+            acc = antialias(blended, layer_keys[l], scr, geo["tri"], sil, width, height, aa_store=aa_store, diag=dg)
+        else:
+            acc = blended
+        diags[l] = dg
+        if l == 0:
+            pre0 = col
+    if diag is not None:
+        diag["layers"] = diags
+    return pre0, acc
 
 
 # ----------------------------------------------------------------------------- antialiasing

@@ -26,7 +26,7 @@ class OracleJob:
     scene: synth.Scene. Textures are (h, w, 4); `disp` (h, w) when present."""
 
     def __init__(self, scene, loss="logl1", lr0=0.01, lam0=None, relative_laplacian=False, per_level=False,
-                 skin_weights=None, skin_lr_scale=1.0, msaa=1):
+                 skin_weights=None, skin_lr_scale=1.0, msaa=1, layers=0):
         m = scene.mesh
         self.tri = torch.as_tensor(m.tri_pos.astype(np.int64))
         self.tri_uv = torch.as_tensor(m.tri_uv.astype(np.int64))
@@ -42,6 +42,11 @@ class OracleJob:
             self.params["disp"] = torch.as_tensor(scene.disp.astype(np.float64))
         self.tess_levels = int(scene.tess_levels)
         self.msaa = int(msaa)   # s x s visibility samples per pixel, shaded once per pixel (Sec. 5.2)
+        # layers = L >= 1: transparency by L depth-peeling passes, opacity from the
+        # base colour's fourth channel (Sec. 5.2, 6); 0: opaque, alpha unused
+        self.layers = int(layers)
+        if self.layers and self.msaa > 1:
+            raise ValueError("depth peeling with multisampling is not supported")
         self.mips = bool(scene.mips)
         self.optimize = {k: bool(scene.optimize.get(k, False)) for k in self.params}
         # Per-level latent textures (the prefiltering variant of Sec. 6): every mip
@@ -134,6 +139,10 @@ def render(job, params, views, height, width, aa=True, vis=None, lods=None, diag
         height, width = height * s, width * s
     geo = geometry(job, params)
     tex = texture_levels(job, params)
+    if job.layers:
+        if s > 1:
+            raise ValueError("depth peeling with supersampling is not supported")
+        return _render_peeled(job, geo, tex, views, height, width, aa, vis, lods, diags)
     if vis is None:
         if job.bones is not None:   # float32 contract of the skinned positions (raster.c)
             pos32 = visibility.skin_positions_f32(params["pos"].detach().numpy(), params["w"].detach().numpy(),
@@ -158,6 +167,28 @@ def render(job, params, views, height, width, aa=True, vis=None, lods=None, diag
     samples = torch.stack(imgs)
     img = torch.stack([R.resolve(x, s) for x in imgs]) if s > 1 else samples
     return dict(pre=torch.stack(pres), img=img, img_samples=samples, keys=keys, asign=asign, geo=geo)
+
+
+def _render_peeled(job, geo, tex, views, height, width, aa, vis, lods, diags):
+    """render() of a depth-peeled job: keys (B, L, H, W), layer 0's colours as pre."""
+    if vis is None:
+        pos32 = geo["pos"].detach().numpy().astype(np.float32)
+        if job.tess is not None or job.bones is not None:
+            raise ValueError("depth peeling runs on plain meshes")
+        vis = visibility.raster_views_peeled(views, pos32, geo["tri"].numpy(), width, height, job.layers)
+    keys, asign = vis
+    pres, imgs = [], []
+    for b in range(len(views)):
+        store = None if lods is None else lods.setdefault(b, {})
+        dg = None if diags is None else {}
+        pre, img = R.peel_view(geo, tex, views[b], keys[b], asign[b], job.adj, width, height, aa=aa,
+                               lod_store=store, diag=dg)
+        if diags is not None:
+            diags.append(dg)
+        pres.append(pre)
+        imgs.append(img)
+    img = torch.stack(imgs)
+    return dict(pre=torch.stack(pres), img=img, img_samples=img, keys=keys, asign=asign, geo=geo)
 
 
 def render_reference(scene, views, height, width, ssaa=1):

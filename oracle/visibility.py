@@ -26,6 +26,8 @@ def _load():
         lib.oracle_transform.restype = None
         lib.oracle_raster.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
         lib.oracle_raster.restype = None
+        lib.oracle_raster_layer.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]
+        lib.oracle_raster_layer.restype = None
         lib.oracle_tess_positions.argtypes = [P, P, P, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P, P,
                                               ctypes.c_int, ctypes.c_int, P, P]
         lib.oracle_tess_positions.restype = None
@@ -73,6 +75,41 @@ def raster_views(views, pos, tri, width, height):
     keys, signs = [], []
     for v in views:
         k, s, _ = raster(v["mvp"], pos, tri, width, height)
+        keys.append(k)
+        signs.append(s)
+    return np.stack(keys), np.stack(signs)
+
+
+def raster_peeled(mvp, pos, tri, width, height, layers):
+    """Depth peeling of one view (Sec. 5.2): layer 0 is the ordinary nearest-key
+    visibility; layer l keeps, per pixel, the nearest fragment whose key is
+    strictly greater than layer l-1's (EMPTY once a pixel runs out of
+    fragments). Keys order by depth first and triangle id second, so coplanar
+    fragments peel one at a time. Returns keys (layers, H, W), area_sign (F,)."""
+    lib = _load()
+    t = transform(mvp, pos, width, height)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    F = tri.shape[0]
+    keys = np.full((layers, height, width), EMPTY_KEY, dtype=np.uint64)
+    asign = np.zeros(F, np.int8)
+    for l in range(layers):
+        out = np.full((height, width), EMPTY_KEY, dtype=np.uint64)
+        if l == 0:
+            lib.oracle_raster(_ptr(t["XY"]), _ptr(t["z01"]), _ptr(t["ok"]), _ptr(tri), F, int(width), int(height),
+                              _ptr(out), _ptr(asign))
+        else:
+            fl = np.ascontiguousarray(keys[l - 1])
+            lib.oracle_raster_layer(_ptr(t["XY"]), _ptr(t["z01"]), _ptr(t["ok"]), _ptr(tri), F, int(width),
+                                    int(height), _ptr(fl), _ptr(out), _ptr(asign))
+        keys[l] = out
+    return keys, asign
+
+
+def raster_views_peeled(views, pos, tri, width, height, layers):
+    """Depth-peeled visibility for a batch of views: keys (B, L, H, W), area_sign (B, F)."""
+    keys, signs = [], []
+    for v in views:
+        k, s = raster_peeled(v["mvp"], pos, tri, width, height, layers)
         keys.append(k)
         signs.append(s)
     return np.stack(keys), np.stack(signs)

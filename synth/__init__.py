@@ -34,6 +34,10 @@ from .workloads import (  # noqa: F401
     job_mix,
     job_scenes,
 )
+from .aggregate import (  # noqa: F401
+    quad_cloud,
+    config_aggregate,
+)
 from .rig import (  # noqa: F401
     bone_weights,
     bone_pose,
