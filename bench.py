@@ -33,6 +33,10 @@ VIEWS, RES = 8, 512
 METRIC = "fwd+bwd Mpixels/s on 1 GB300 (fused vs plain, grads ≤1e-3 rel); p99 step ms"
 WORKLOAD = ("reference 200k-tri fBm icosphere with 2048^2 procedural maps; candidate 5,120 tris with 1024^2 "
             "maps + mips; 8 random views at 512x512; point + directional light; log-L1 loss")
+WORKLOAD_AGG = ("aggregate geometry (Sec. 6): reference canopy of 600k opaque leaf quads (1.2M tris) with 2048^2 "
+                "procedural maps; candidate 5,500 billboard quads (11k tris) with a 2048^2 base colour + opacity "
+                "atlas and 1024^2 (gamma, r, m) and normal maps, all optimized; 8 depth-peeling layers blended back "
+                "to front (Sec. 5.2); 8 random views at 512x512; point + directional light; squared-L2 loss")
 
 # DRAM bytes per launch of the dominant kernel from an ncu capture, valid only
 # for the source it was measured on (sha256 of the listed files).
@@ -143,10 +147,23 @@ def algorithmic_bytes(stage, w):
     """Compulsory DRAM bytes of one step's launches of `stage` (bytes model).
 
     w: dict with P (pixels/step; samples/step under MSAA), C (covered candidate
-    pixels or samples), Cr (covered reference pixels or samples), Ppix (pixels
-    per step), S (samples per pixel side), texel counts and triangle/vertex counts."""
+    pixels or samples, summed over depth-peeling layers), Cr (covered reference
+    pixels or samples), Ppix (pixels per step), S (samples per pixel side), L
+    (depth-peeling layers, 0: opaque), texel counts and triangle/vertex counts."""
     P = w["P"]
     tex_px = 1.33 * 16 * 3          # unique texels per covered pixel per map x 16 B x 3 maps
+    L = w.get("L", 0)
+    if L:
+        # per layer and pixel: key, colour + opacity, the composite behind, its
+        # gradient; the opaque reference as in the plain step
+        if stage == "shade_bwd":
+            return (8 + 16 + 16 + 16 + 16) * L * P + (tex_px * 3) * w["C"]
+        if stage == "shade":
+            return 24 * L * P + 24 * P + tex_px * (w["C"] + w["Cr"])
+        if stage == "aa_loss":
+            return (8 + 16 + 16 + 16) * L * P + 12 * P + (8 + 16 + 12) * P
+        if stage == "raster":
+            return (8 + 8) * L * P + 8 * P + 96 * VIEWS * (L * w["F"] + w["Fr"])
     if stage == "shade_bwd":
         return 40 * P + (tex_px * 3) * w["C"]          # key+g'+pre per pixel; texel read + grad RMW
     if stage == "shade":
@@ -179,13 +196,13 @@ class OracleStep:
 
     Topology tables are built once, outside the timed calls."""
 
-    def __init__(self, scene_cfg, msaa=1):
+    def __init__(self, scene_cfg, msaa=1, layers=0):
         from oracle import step as S
 
         self.S = S
         self.msaa = msaa
         self.ref = S.OracleJob(scene_cfg["ref"], loss="l1")
-        self.cand = S.OracleJob(scene_cfg["cand"], loss="logl1", msaa=msaa)
+        self.cand = S.OracleJob(scene_cfg["cand"], loss=scene_cfg["loss"], msaa=msaa, layers=layers)
 
     def seconds(self, n_views, res, seed=123):
         import torch
@@ -252,16 +269,23 @@ def run_native(args):
 
     L = B.lib()
     dev = torch.device("cuda", torch.cuda.current_device())
-    cfg = synth.config_plain()
+    agg = args.workload == "aggregate"
+    cfg = synth.config_aggregate() if agg else synth.config_plain()
+    LY = cfg["layers"] if agg else 0
+    loss = cfg["loss"]
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = Context(stream=stream)
     MS = max(int(args.msaa), 1)
     # under MSAA the references are supersampled renders (every sample shaded)
-    ref_job = ctx.create_job(cfg["ref"], frozen=True, samples=MS, shade_samples=True)
+    # the foliage reference is a dense cloud of small leaf triangles: rasterize those
+    # of up to 256 samples directly instead of binning them
+    ref_job = ctx.create_job(cfg["ref"], frozen=True, samples=MS, shade_samples=True,
+                             raster_direct_px=256 if agg else 0)
     pl = bool(args.per_level_textures)
-    cand = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, per_level_textures=pl, samples=MS)
-    plain = ctx.create_job(cfg["cand"], loss="logl1", lr0=0.01, batch_views=VIEWS, per_level_textures=pl, samples=MS)
+    cand = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, per_level_textures=pl, samples=MS, layers=LY)
+    plain = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, batch_views=VIEWS, per_level_textures=pl, samples=MS,
+                           layers=LY)
     n_steps = args.warmup + args.steps
     host_views = [synth.sample_views(replica_seed(rank), i, VIEWS, RES, RES) for i in range(n_steps)]
     view_np = np.stack([v.view(np.uint8) for v in host_views])                  # (steps, 8*112)
@@ -382,7 +406,7 @@ def run_native(args):
     e2e_s = max_over_ranks(e2e_s, world, dev)
 
     # workload facts for the bytes model
-    keys = ctx.keys(cand, (VIEWS, RES * MS, RES * MS))
+    keys = ctx.keys(cand, (max(LY, 1), VIEWS, RES * MS, RES * MS))
     covered = int((keys != -1).sum())
     pv = ctx.params(cand)
     texels = sum(pv[n].shape[0] * pv[n].shape[1] for n in ("kd", "orm", "nrm"))
@@ -393,7 +417,7 @@ def run_native(args):
     covered_ref = int((rkeys != -1).sum())
     wl = dict(P=VIEWS * RES * RES * MS * MS, C=covered, Cr=covered_ref, texels=texels, texel_floats=4 * latent_texels,
               V=cfg["cand"].mesh.n_verts, F=cfg["cand"].mesh.n_tris, Fr=cfg["ref"].mesh.n_tris,
-              Ppix=VIEWS * RES * RES, S=MS)
+              Ppix=VIEWS * RES * RES, S=MS, L=LY)
 
     px_step = VIEWS * RES * RES
     value = whole_job_mpix(world, px_step, args.steps, total_ms / 1e3)
@@ -417,7 +441,7 @@ def run_native(args):
     launches_per_step = max(d["launches_per_step"], 1e-9)
     achieved = d["gbs"]
     # the committed DRAM counters and instruction counts are the plain workload's
-    tr = TRAFFIC.get(dominant) if not (pl or SKB or MS > 1) else None
+    tr = TRAFFIC.get(dominant) if not (pl or SKB or MS > 1 or agg) else None
     traffic = None
     if tr and _sha(tr["files"]) == tr["sha"]:
         traffic = tr["bytes_per_launch"]
@@ -440,9 +464,10 @@ def run_native(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cres = RES // MS    # the same samples per view as the plain sample
-        dt, cores = OracleStep(cfg, msaa=MS).seconds(1, cres)
+        dt, cores = OracleStep(cfg, msaa=MS, layers=LY).seconds(1, cres)
         cpu = {"value": cres * cres / dt / 1e6, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
                "sample": f"1 of 8 views at {cres}^2" + (f" with {MS}x{MS} MSAA" if MS > 1 else "")
+               + (f" with {LY} peeling layers" if LY else "")
                + ": full oracle step (reference render + fwd/bwd/Adam)"}
 
     if rank == 0:
@@ -450,7 +475,8 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD + ("; every mip level of each texture its own latent (Sec. 6)" if pl else "")
+            "config": {"workload": (WORKLOAD_AGG if agg else WORKLOAD)
+                       + ("; every mip level of each texture its own latent (Sec. 6)" if pl else "")
                        + (f"; both meshes skinned by {SKB} bones (Eq. 2), dense weights optimized (learning rate / {SKB}), "
                           "a new pose per step"
                           if SKB else "")
@@ -670,8 +696,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serving"],
-                    help="plain: the headline single-job step; batched: uneven jobs in one launch per stage; "
+    ap.add_argument("--workload", default="plain", choices=["plain", "aggregate", "batched", "serving"],
+                    help="plain: the headline single-job step; aggregate: billboard quads with opacity under "
+                         "depth peeling (Sec. 6 aggregate geometry); batched: uneven jobs in one launch per stage; "
                          "serving: continuous batching of Poisson arrivals")
     ap.add_argument("--jobs", type=int, default=64, help="jobs of the batched and serving workloads")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
@@ -686,6 +713,8 @@ def main():
     ap.add_argument("--per-level-textures", action="store_true",
                     help="plain workload with every mip level of each texture an independent latent (Sec. 6)")
     args = ap.parse_args()
+    if args.workload == "aggregate" and (args.msaa > 1 or args.skinning or args.per_level_textures):
+        ap.error("the aggregate workload runs without --msaa, --skinning and --per-level-textures")
     if args.impl == "reference":
         run_reference_arm(args)
     elif args.workload == "batched":

@@ -117,6 +117,25 @@ typedef struct {
                                 once per pixel at the pixel's centre with the pixel's LOD (the
                                 training render); 1 = every sample shaded at its own position (a
                                 supersampled render, e.g. for reference images) */
+    int32_t layers;          /* L in [1, 16]: order-independent transparency by L depth-peeling
+                                passes (Sec. 5.2; the aggregate-geometry application of Sec. 6).
+                                Layer 0 is the nearest fragment per pixel, layer l the nearest
+                                one whose depth|id key is strictly greater than layer l-1's; each
+                                layer is shaded and takes its opacity from the base colour's
+                                fourth channel; blending runs back to front from a black
+                                background, each layer's composite antialiased with that layer's
+                                visibility, and the loss is taken on the front composite.
+                                Plain meshes only (no tessellation, skinning or samples > 1); runs
+                                one job per forward_loss / backward call; adms_job_keys returns
+                                the L layers' keys, layer after layer. 0: opaque rendering, the
+                                fourth channel unused */
+    int32_t raster_direct_px; /* raster tuning (no counterpart in the paper; results do not depend on
+                                it): triangles whose pixel bounding box holds at most this many
+                                samples are rasterized one thread per triangle with a 64-bit atomicMin
+                                per covered sample, larger ones binned into 16x16 tiles. 0 = 16.
+                                Dense clouds of small triangles (e.g. a 1.2M-triangle foliage
+                                reference) run faster with a few hundred. Ignored with layers > 0
+                                (every triangle is binned). In [0, 4096] */
 } adms_opt_params;
 
 /* Device pointers into a job's resident state (owned by the library, valid
@@ -263,7 +282,8 @@ adms_status adms_job_invalidate(adms_ctx* ctx, adms_job job);
 adms_status adms_laplacian(adms_ctx* ctx, adms_job job, float* out_loss, float* g_pos);
 
 /* Raw visibility of the latest forward_loss / render_reference of a job:
- * copies [B][H][W] keys into out_keys (device). */
+ * copies [B][H][W] keys into out_keys (device); a depth-peeled job's are
+ * [L][B][H][W]. ADMS_ERR_ARG when capacity (in keys) is smaller. */
 adms_status adms_job_keys(adms_ctx* ctx, adms_job job, uint64_t* out_keys, size_t capacity);
 
 /* ---- checkpoint / resume --------------------------------------------------- */

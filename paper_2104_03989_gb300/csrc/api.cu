@@ -102,6 +102,12 @@ struct Job {
     bool ssaa = false;
     int PH = 0, PW = 0;        // pixels per view
     float4* acol = nullptr;    // antialiased sample colours (+ blend masks) for the resolve
+    // depth-peeled transparency (Sec. 5.2): L layers; keys and pre hold L slices of
+    // B H W (front to back), acc the composites A_1 .. A_{L-1} of the layers behind
+    // each layer (xyz; w: blend mask bits), gprime2 the second dL/d(composite) buffer
+    int L = 0;
+    float4* acc = nullptr;
+    float4* gprime2 = nullptr;
     const float* ref = nullptr;
     float loss_scale = 0.f;
     std::vector<void*> allocs;
@@ -305,11 +311,16 @@ adms_status ensure_scratch(adms_ctx* ctx, Job& j, int B, int H, int W) {
     int tiles = ((W + ADMS_TILE - 1) / ADMS_TILE) * ((H + ADMS_TILE - 1) / ADMS_TILE);
     size_t ntiles = (size_t)B * tiles;
     if (px > j.px_cap) {
-        AL(j.keys, px);
-        AL(j.pre, px);
+        size_t nl = (size_t)std::max(j.L, 1);
+        AL(j.keys, px * nl);
+        AL(j.pre, px * nl);
         AL(j.gprime, px);
         AL(j.refine, px + 1);
         if (j.S > 1) AL(j.acol, px);
+        if (j.L > 1) {
+            AL(j.acc, px * (nl - 1));
+            AL(j.gprime2, px);
+        }
         j.px_cap = px;
     }
     if ((size_t)B > j.view_cap) {
@@ -441,6 +452,7 @@ ShadeArgs shade_args(Job& j) {
     a.refine = j.refine;
     a.msaa = (j.S > 1 && !j.ssaa) ? j.S : 0;
     a.acol = j.S > 1 ? j.acol : nullptr;
+    a.peel = j.L > 0;
     a.loss_kind = j.opt.loss;
     a.loss_scale = j.loss_scale;
     a.aa = j.opt.aa;
@@ -453,6 +465,24 @@ ShadeArgs shade_args(Job& j) {
 // AA on the sample grid, then the per-pixel resolve of a supersampled job: the
 // loss and each sample's dL/d(colour) when ref is given, the image into out_img
 adms_status aa_resolve(adms_ctx* ctx, Job& j, const float* ref, double* loss_acc, float* out_img);
+
+// arguments of layer l of a depth-peeled job: its keys and colours, the
+// composite behind it (A_{l+1}, none behind the last layer)
+ShadeArgs layer_args(Job& j, int l) {
+    ShadeArgs a = shade_args(j);
+    size_t px = (size_t)j.B * j.H * j.W;
+    a.keys = j.keys + (size_t)l * px;
+    a.pre = j.pre + (size_t)l * px;
+    a.under = l + 1 < j.L ? j.acc + (size_t)l * px : nullptr;
+    return a;
+}
+
+// back-to-front composite of a depth-peeled job, each layer antialiased with its own
+// visibility: A_l = AA_l(alpha_l c_l + (1 - alpha_l) A_{l+1}); layer 0 takes the loss
+// (and dL/dA_0 into gprime) when ref is given and writes the image into out_img
+adms_status peel_composite(adms_ctx* ctx, Job& j, const float* ref, double* loss_acc, float* out_img);
+// the adjoint of peel_composite and of every layer's shading, front to back
+adms_status peel_backward(adms_ctx* ctx, Job& j);
 
 // frame, raster and pre-AA shading of B views already copied to j.views
 SkinArgs skin_args(Job& j) {
@@ -487,9 +517,42 @@ adms_status render_core(adms_ctx* ctx, Job& j) {
     in.W = j.W;
     in.H = j.H;
     in.keys = j.keys;
+    if (j.L > 0) {
+        // all L peeling layers in one tile pass (a k-buffer per sample): every triangle binned
+        in.small_px = 0;
+        CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
+        CK(TIMED(ST_RASTER, raster_tiles_peeled(in, j.rs, j.L, ctx->stream)));
+        for (int l = 0; l < j.L; ++l) CK(TIMED(ST_SHADE, shade_forward(layer_args(j, l), ctx->stream)));
+        return ADMS_OK;
+    }
+    in.small_px = j.opt.raster_direct_px > 0 ? j.opt.raster_direct_px : ADMS_SMALL_PX;
     CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
     CK(TIMED(ST_RASTER, raster_tiles(in, j.rs, ctx->stream)));
     CK(TIMED(ST_SHADE, shade_forward(shade_args(j), ctx->stream)));
+    return ADMS_OK;
+}
+
+adms_status peel_composite(adms_ctx* ctx, Job& j, const float* ref, double* loss_acc, float* out_img) {
+    size_t px = (size_t)j.B * j.H * j.W;
+    for (int l = j.L - 1; l >= 0; --l) {
+        ShadeArgs a = layer_args(j, l);
+        a.ref = l == 0 ? ref : nullptr;
+        a.loss_acc = l == 0 ? loss_acc : nullptr;
+        a.out_img = l == 0 ? out_img : nullptr;
+        a.acol = l > 0 ? j.acc + (size_t)(l - 1) * px : nullptr;
+        CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
+    }
+    return ADMS_OK;
+}
+
+adms_status peel_backward(adms_ctx* ctx, Job& j) {
+    for (int l = 0; l < j.L; ++l) {
+        ShadeArgs a = layer_args(j, l);
+        a.ref = j.ref;
+        a.gprime = l % 2 == 0 ? j.gprime : j.gprime2;
+        a.g_under = l + 1 < j.L ? (l % 2 == 0 ? j.gprime2 : j.gprime) : nullptr;
+        CK(TIMED(ST_SHADE_BWD, shade_backward(a, ctx->stream)));
+    }
     return ADMS_OK;
 }
 
@@ -671,6 +734,12 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
     }
     if (j.opt.tess_levels < 0 || j.opt.tess_levels > 6) return fail(ctx, ADMS_ERR_ARG, "tess_levels must be in [0, 6]");
     if (j.opt.samples < 0 || j.opt.samples > 8) return fail(ctx, ADMS_ERR_ARG, "samples must be in [0, 8]");
+    if (j.opt.layers < 0 || j.opt.layers > 16) return fail(ctx, ADMS_ERR_ARG, "layers must be in [0, 16]");
+    if (j.opt.raster_direct_px < 0 || j.opt.raster_direct_px > 4096)
+        return fail(ctx, ADMS_ERR_ARG, "raster_direct_px must be in [0, 4096]");
+    if (j.opt.layers > 0 && (j.opt.samples > 1 || j.opt.tess_levels > 0))
+        return fail(ctx, ADMS_ERR_ARG, "depth peeling runs on plain meshes at one sample per pixel");
+    j.L = j.opt.layers;
     j.S = std::max(1, (int)j.opt.samples);
     j.ssaa = j.opt.shade_samples != 0;
     j.tess = j.opt.tess_levels > 0;
@@ -806,6 +875,7 @@ adms_status frame_and_prepare(adms_ctx* ctx, Job& j) {
     in.W = j.W;
     in.H = j.H;
     in.keys = j.keys;
+    in.small_px = j.opt.raster_direct_px > 0 ? j.opt.raster_direct_px : ADMS_SMALL_PX;
     CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
     return ADMS_OK;
 }
@@ -942,7 +1012,7 @@ adms_status batch_upload(adms_ctx* ctx, const std::vector<Job*>& js, float* cons
 // buffers below, in this order. Gradients and per-step scratch are not kept:
 // export between optimizer steps.
 const char kCkptMagic[8] = {'A', 'D', 'M', 'S', 'C', 'K', 'P', 'T'};
-const uint32_t kCkptVersion = 2;  // 2: per-level, skinning and multisampling fields
+const uint32_t kCkptVersion = 3;  // 2: per-level, skinning and multisampling fields; 3: layers
 
 struct CkptHeader {
     char magic[8];
@@ -951,7 +1021,7 @@ struct CkptHeader {
     int32_t LV, V, F, tess_levels, dh, dw;
     int32_t tex_w[3], tex_h[3], tex_levels[3], tex_opt[3];
     int32_t optimize[5];  // pos, kd, orm, nrm, disp
-    int32_t loss, relative_laplacian, batch_views, aa, per_level_textures, n_bones, samples, shade_samples;
+    int32_t loss, relative_laplacian, batch_views, aa, per_level_textures, n_bones, samples, shade_samples, layers;
     float lr0, lambda0, skin_lr_scale;
     uint64_t section_bytes[16];
 };
@@ -992,6 +1062,7 @@ void ckpt_describe(Job& j, CkptHeader& h, std::vector<CkptSection>& secs) {
     h.n_bones = j.SB;
     h.samples = j.S;
     h.shade_samples = j.ssaa;
+    h.layers = j.L;
     h.skin_lr_scale = j.skin_lr_scale;
     h.lr0 = j.opt.lr0;
     h.lambda0 = j.opt.lambda0;
@@ -1247,6 +1318,7 @@ adms_status adms_job_skinning(adms_ctx* ctx, adms_job job, const float* weights,
         return fail(ctx, ADMS_ERR_ARG, "invalid job, weights, bone count (1..1024) or learning-rate scale");
     Job& j = *jp;
     if (j.tess) return fail(ctx, ADMS_ERR_STATE, "skinning of a tessellated job is not supported");
+    if (j.L > 0) return fail(ctx, ADMS_ERR_STATE, "skinning of a depth-peeled job is not supported");
     if (j.skin) return fail(ctx, ADMS_ERR_STATE, "skinning is already set for this job");
     size_t nw = (size_t)j.LV * n_bones;
     AL(j.skin_w, nw);
@@ -1315,8 +1387,10 @@ adms_status adms_render_reference(adms_ctx* ctx, adms_job job, const adms_view* 
     j.PW = W;
     CK(cudaMemcpyAsync(j.views, views, sizeof(adms_view) * n_views, cudaMemcpyDefault, ctx->stream));
     if ((s = render_core(ctx, j))) return s;
-    if (j.S > 1) {
-        if ((s = aa_resolve(ctx, j, nullptr, nullptr, out_rgb))) return s;
+    if (j.S > 1 || j.L > 0) {
+        if ((s = j.L > 0 ? peel_composite(ctx, j, nullptr, nullptr, out_rgb)
+                         : aa_resolve(ctx, j, nullptr, nullptr, out_rgb)))
+            return s;
         j.have_fwd = false;
         return ADMS_OK;
     }
@@ -1346,8 +1420,9 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
             if (o == jp) return fail(ctx, ADMS_ERR_ARG, "a job appears twice in one call");
         js.push_back(jp);
         Job& j = *jp;
-        if (n_jobs > 1 && j.S > 1)
-            return fail(ctx, ADMS_ERR_STATE, "supersampled (MSAA) jobs run one per call, not in a batch");
+        if (n_jobs > 1 && (j.S > 1 || j.L > 0))
+            return fail(ctx, ADMS_ERR_STATE,
+                        "supersampled (MSAA) and depth-peeled jobs run one per call, not in a batch");
         if ((long long)H * j.S > 16384 || (long long)W * j.S > 16384)
             return fail(ctx, ADMS_ERR_ARG, "sample grid larger than 16384 per side");
         adms_status s = ensure_scratch(ctx, j, B, H * j.S, W * j.S);
@@ -1365,7 +1440,9 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
         CK(cudaMemsetAsync(&j.st->call_loss, 0, sizeof(double), ctx->stream));
         if (n_jobs == 1) {
             if ((s = render_core(ctx, j))) return s;
-            if (j.S > 1) {
+            if (j.L > 0) {
+                if ((s = peel_composite(ctx, j, j.ref, &j.st->call_loss, out_img ? out_img[k] : nullptr))) return s;
+            } else if (j.S > 1) {
                 if ((s = aa_resolve(ctx, j, j.ref, &j.st->call_loss, out_img ? out_img[k] : nullptr))) return s;
             } else {
                 ShadeArgs a = shade_args(j);
@@ -1414,7 +1491,9 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
             // caller's reference images instead of reading what the forward kept
             adms_status s = render_core(ctx, j);
             if (s) return s;
-            if (j.S > 1) {
+            if (j.L > 0) {
+                if ((s = peel_composite(ctx, j, j.ref, nullptr, nullptr))) return s;
+            } else if (j.S > 1) {
                 if ((s = aa_resolve(ctx, j, j.ref, nullptr, nullptr))) return s;
             } else {
                 ShadeArgs r = shade_args(j);
@@ -1426,7 +1505,10 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
         CK(cudaMemsetAsync(j.g_nrm, 0, sizeof(double) * 3 * j.V, ctx->stream));
         CK(cudaMemsetAsync(j.g_tan, 0, sizeof(double) * 3 * j.V, ctx->stream));
         if (j.tess || j.skin) CK(cudaMemsetAsync(j.g_rpos, 0, sizeof(float) * 3 * j.V, ctx->stream));
-        if (n_jobs == 1) {
+        if (n_jobs == 1 && j.L > 0) {
+            adms_status s = peel_backward(ctx, j);
+            if (s) return s;
+        } else if (n_jobs == 1) {
             ShadeArgs a = shade_args(j);
             a.ref = j.ref;
             CK(TIMED(ST_SHADE_BWD, shade_backward(a, ctx->stream)));
@@ -1567,7 +1649,7 @@ adms_status adms_laplacian(adms_ctx* ctx, adms_job job, float* out_loss, float* 
 adms_status adms_job_keys(adms_ctx* ctx, adms_job job, uint64_t* out_keys, size_t capacity) {
     Job* j = get_job(ctx, job);
     if (!j || !out_keys) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
-    size_t n = (size_t)j->B * j->H * j->W;
+    size_t n = (size_t)j->B * j->H * j->W * std::max(j->L, 1);
     if (capacity < n) return fail(ctx, ADMS_ERR_ARG, "key buffer too small");
     CK(cudaMemcpyAsync(out_keys, j->keys, n * sizeof(uint64_t), cudaMemcpyDefault, ctx->stream));
     return ADMS_OK;

@@ -38,7 +38,7 @@ struct TriBin {
     short bx0, bx1, by0, by1;
 };
 
-// triangles with at most this many samples in their pixel bbox skip binning
+// triangles with at most this many samples in their pixel bbox skip binning (default)
 #define ADMS_SMALL_PX 16
 
 struct RasterIn {
@@ -48,6 +48,8 @@ struct RasterIn {
     const adms_view* views;    // device, [B]
     int B, V, F, W, H;
     unsigned long long* keys;  // [B][H][W]
+    int small_px = ADMS_SMALL_PX;  // triangles with at most this many samples in their bbox are
+                                   // rasterized directly (atomicMin), the rest binned into tiles
 };
 
 // scratch of the raster (global memory beyond inputs and outputs)
@@ -73,6 +75,10 @@ cudaError_t raster_views(const RasterIn& in, RasterScratch& s, cudaStream_t st);
 cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st);
 // the per-tile z-buffer pass
 cudaError_t raster_tiles(const RasterIn& in, RasterScratch& s, cudaStream_t st);
+// depth peeling (Sec. 5.2) in one tile pass: in.keys receives L slices of [B][H][W],
+// slice l the (l+1)-th nearest fragment per sample (EMPTY beyond the last); needs
+// raster_prepare with small_px = 0 (every triangle binned); L in [1, 16]
+cudaError_t raster_tiles_peeled(const RasterIn& in, RasterScratch& s, int L, cudaStream_t st);
 
 // everything the per-pixel shading, AA, loss and backward kernels read
 struct ShadeArgs {
@@ -95,12 +101,18 @@ struct ShadeArgs {
     const float* ref;                // [B][H][W][3]
     int msaa;                        // s > 1: keys, pre, gprime are on an s x s sample grid per pixel
                                      // and each sample is shaded at its pixel's centre, LOD of the pixel
+    int peel;                        // a layer of a depth-peeled composite: pre.w is the layer's opacity
+                                     // and the colour AA acts on is opacity x pre + (1 - opacity) x under
     float4* acol;                    // [B][H][W] antialiased sample colours (w: the blend mask bits) for
                                      // the per-pixel resolve, or null
     int* refine;                     // [0]: count, then pixel indices shaded again with a refined
                                      // texture coordinate (null: none)
     float4* gprime;                  // [B][H][W] dL/d(AA colour) in xyz; w: bit n set (as raw bits)
                                      // when the pair with neighbour n (-x, +x, -y, +y) blended
+    const float4* under;             // peel: [B][H][W] the composite of the layers behind (xyz; w: its
+                                     // blend mask bits), or null for the black background
+    float4* g_under;                 // peel backward: [B][H][W] dL/d(under) with under's blend mask in
+                                     // w (the next layer's gprime), or null for the last layer
     float* out_img;                  // [B][H][W][3] or null
     int loss_kind;
     float loss_scale;                // 1 / (3 P)
@@ -135,12 +147,13 @@ struct WorkItem {
     int job, view, x0, y0;
 };
 // Jobs per batched launch: their arguments travel in the launch's parameter
-// space (60 x 520 B, under the 32 KB limit), read-only and captured with the
+// space (60 x 536 B, under the 32 KB limit), read-only and captured with the
 // launch by a graph; larger job sets take one launch per 60 jobs.
 #define ADMS_BATCH_JOBS 60
 struct ShadeBatch {
     ShadeArgs a[ADMS_BATCH_JOBS];
 };
+static_assert(sizeof(ShadeBatch) + 64 <= 32764, "batched launch parameters exceed the kernel parameter space");
 // persistent launch over work items of many jobs; kind 0 shade, 1 AA + loss, 2 backward.
 // args: host array of n_jobs arguments; items (device) are ordered by job, job k's
 // items being [item_off[k], item_off[k+1]) (item_off: host, n_jobs + 1 entries);

@@ -143,32 +143,53 @@ __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int n
 }
 
 // ---------------------------------------------------------------- coverage test
-// coverage + depth key of one triangle at one sample (keeps the minimum in best)
-__device__ __forceinline__ void test_tri(const TriRec& r, int Sx, int Sy, unsigned long long& best) {
+// coverage + depth key of one triangle at one sample, or ADMS_EMPTY_KEY
+__device__ __forceinline__ unsigned long long tri_key(const TriRec& r, int Sx, int Sy) {
     long long e0 = (long long)r.ea[0] * Sx + (long long)r.eb[0] * Sy + r.ec[0];
     long long e1 = (long long)r.ea[1] * Sx + (long long)r.eb[1] * Sy + r.ec[1];
     long long e2 = (long long)r.ea[2] * Sx + (long long)r.eb[2] * Sy + r.ec[2];
-    if (e0 < r.thr[0] || e1 < r.thr[1] || e2 < r.thr[2]) return;
+    if (e0 < r.thr[0] || e1 < r.thr[1] || e2 < r.thr[2]) return ADMS_EMPTY_KEY;
     // back to the triangle's own vertex order: E_20 = s e1, E_01 = s e2
     long long E20 = r.sg > 0 ? e1 : -e1;
     long long E01 = r.sg > 0 ? e2 : -e2;
     float b1 = __fdiv_rn(__ll2float_rn(E20), r.fA);
     float b2 = __fdiv_rn(__ll2float_rn(E01), r.fA);
     float d = __fadd_rn(__fadd_rn(r.z0, __fmul_rn(b1, r.dz1)), __fmul_rn(b2, r.dz2));
-    if (!(d >= 0.f && d <= 1.f)) return;
+    if (!(d >= 0.f && d <= 1.f)) return ADMS_EMPTY_KEY;
     if (d == 0.f) d = 0.f;
-    unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)r.id;
+    return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)r.id;
+}
+
+// keeps the minimum in best
+__device__ __forceinline__ void test_tri(const TriRec& r, int Sx, int Sy, unsigned long long& best) {
+    unsigned long long key = tri_key(r, Sx, Sy);
     if (key < best) best = key;
+}
+
+// keeps the KB smallest keys in kb[0] < kb[1] < ... (a per-sample k-buffer; the
+// keys of one sample are distinct, each triangle giving at most one): the
+// fragment sinks into place and the largest falls out
+template <int KB>
+__device__ __forceinline__ void test_tri_kbuf(const TriRec& r, int Sx, int Sy, unsigned long long (&kb)[KB]) {
+    unsigned long long key = tri_key(r, Sx, Sy);
+    if (key >= kb[KB - 1]) return;
+#pragma unroll
+    for (int i = 0; i < KB; ++i) {
+        unsigned long long lo = key < kb[i] ? key : kb[i];
+        key = key < kb[i] ? kb[i] : key;
+        kb[i] = lo;
+    }
 }
 
 // ---------------------------------------------------------------- setup, small triangles, tile counts
 // One thread per (view, triangle). Triangles whose pixel bounding box holds at
-// most ADMS_SMALL_PX samples are rasterized here directly, one 64-bit
-// atomicMin per covered sample (the minimum does not depend on the order);
-// larger ones get a setup record and are counted into the tiles they overlap.
+// most small_px samples are rasterized here directly, one 64-bit atomicMin per
+// covered sample (the minimum does not depend on the order); larger ones get a
+// setup record and are counted into the tiles they overlap.
 __global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restrict__ vs, int V, int B, int W, int H,
                         int tiles_x, int tiles_y, TriRec* __restrict__ rec, TriBin* __restrict__ bin,
-                        int8_t* __restrict__ asign, int* __restrict__ tile_count, unsigned long long* __restrict__ keys) {
+                        int8_t* __restrict__ asign, int* __restrict__ tile_count, unsigned long long* __restrict__ keys,
+                        int small_px) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B * F) return;
     int b = i / F, f = i - b * F;
@@ -218,13 +239,12 @@ __global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restri
                 r.by0 = (short)jlo;
                 r.by1 = (short)jhi;
                 long long npx = (ihi - ilo + 1) * (jhi - jlo + 1);
-                if (npx <= ADMS_SMALL_PX) {
+                if (npx <= small_px) {
                     unsigned long long* kb = keys + (size_t)b * H * W;
                     for (int y = (int)jlo; y <= (int)jhi; ++y)
                         for (int x = (int)ilo; x <= (int)ihi; ++x) {
-                            unsigned long long best = ADMS_EMPTY_KEY;
-                            test_tri(r, 256 * x + 128, 256 * y + 128, best);
-                            if (best != ADMS_EMPTY_KEY) atomicMin(kb + (size_t)y * W + x, best);
+                            unsigned long long key = tri_key(r, 256 * x + 128, 256 * y + 128);
+                            if (key != ADMS_EMPTY_KEY) atomicMin(kb + (size_t)y * W + x, key);
                         }
                 } else {
                     rec[i] = r;
@@ -345,6 +365,65 @@ __global__ void __launch_bounds__(256) k_raster(const TriRec* __restrict__ rec, 
                      blockIdx.y, blockIdx.x, sm);
 }
 
+// Depth peeling in one pass (Sec. 5.2): per sample the L nearest fragments,
+// front to back, which are exactly the layers that L peeling passes with a
+// two-sided test on the packed depth|id key would find (the keys of a sample are
+// distinct). One block per (view, 16x16 tile) as in k_raster, the tile's records
+// staged through shared memory, a KB-entry k-buffer per thread in registers
+// (KB >= L); every triangle must be binned (no small-triangle pass). keys holds
+// L slices of [B][H][W].
+template <int KB>
+__global__ void __launch_bounds__(256) k_raster_kbuf(const TriRec* __restrict__ rec, const TriBin* __restrict__ bin,
+                                                     int F, int W, int H, int tiles_x, int tiles_y,
+                                                     const int* __restrict__ tile_off,
+                                                     const int* __restrict__ tile_count, const int* __restrict__ list,
+                                                     long long capacity, unsigned long long* __restrict__ keys, int L,
+                                                     int B, unsigned long long* __restrict__ overflow_ctr) {
+    __shared__ TriRec sm[256];
+    int b = blockIdx.y, tile = blockIdx.x;
+    int tx = tile % tiles_x, ty = tile / tiles_x;
+    int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
+    int px = tx * ADMS_TILE + lx, py = ty * ADMS_TILE + ly;
+    int Sx = 256 * px + 128, Sy = 256 * py + 128;
+    bool inside = px < W && py < H;
+    unsigned long long kb[KB];
+#pragma unroll
+    for (int i = 0; i < KB; ++i) kb[i] = ADMS_EMPTY_KEY;
+    size_t t = (size_t)b * tiles_x * tiles_y + tile;
+    long long off = tile_off[t];
+    int cnt = tile_count[t];
+    const TriRec* rb = rec + (size_t)b * F;
+    const TriBin* bb = bin + (size_t)b * F;
+    bool overflow = off + cnt > capacity;
+    int n = overflow ? F : cnt;
+    if (overflow && threadIdx.x == 0) atomicAdd(overflow_ctr, 1ull);
+    for (int c0 = 0; c0 < n; c0 += 256) {
+        int m = min(256, n - c0);
+        __syncthreads();
+        if ((int)threadIdx.x < m) {
+            if (overflow) {
+                int id = c0 + threadIdx.x;
+                TriBin tb = bb[id];
+                if (tb.bx0 <= tb.bx1) sm[threadIdx.x] = rb[id];
+                else sm[threadIdx.x].valid = 0;
+            } else {
+                sm[threadIdx.x] = rb[list[off + c0 + threadIdx.x]];
+            }
+        }
+        __syncthreads();
+        for (int k = 0; k < m; ++k) {
+            const TriRec& r = sm[k];
+            if (!r.valid) continue;
+            if (px < r.bx0 || px > r.bx1 || py < r.by0 || py > r.by1) continue;
+            test_tri_kbuf<KB>(r, Sx, Sy, kb);
+        }
+    }
+    if (!inside) return;
+    size_t pix = ((size_t)b * H + py) * W + px, layer = (size_t)B * H * W;
+#pragma unroll
+    for (int i = 0; i < KB; ++i)
+        if (i < L) keys[pix + (size_t)i * layer] = kb[i];
+}
 // persistent: block k takes items k, k + gridDim.x, ... (the items are equal
 // 16x16 tiles, so a static stride balances them without a shared counter); the
 // jobs' arguments are kernel parameters (up to 64 jobs per launch)
@@ -394,7 +473,7 @@ cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st
     int bs = 256;
     k_transform<<<(B * V + bs - 1) / bs, bs, 0, st>>>(in.pos, V, in.views, B, W, H, s.clip, s.vs, s.scr);
     k_setup<<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec, s.bin,
-                                                s.asign, s.tile_count, in.keys);
+                                                s.asign, s.tile_count, in.keys, in.small_px);
     k_scan<<<1, 1024, 0, st>>>(s.tile_count, ntiles, s.tile_off, s.total_pairs);
     k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.bin, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
                                                    s.list, s.list_capacity, in.adj, s.asign, s.silmask);
@@ -407,6 +486,22 @@ cudaError_t raster_tiles(const RasterIn& in, RasterScratch& s, cudaStream_t st) 
     dim3 grid(tiles_x * tiles_y, in.B);
     k_raster<<<grid, 256, 0, st>>>(s.rec, s.bin, in.F, in.W, in.H, tiles_x, tiles_y, s.tile_off, s.tile_count, s.list,
                                    s.list_capacity, in.keys, s.overflow_ctr);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t raster_tiles_peeled(const RasterIn& in, RasterScratch& s, int L, cudaStream_t st) {
+    if (L < 1 || L > 16) return cudaErrorInvalidValue;
+    int tiles_x = (in.W + ADMS_TILE - 1) / ADMS_TILE, tiles_y = (in.H + ADMS_TILE - 1) / ADMS_TILE;
+    dim3 grid(tiles_x * tiles_y, in.B);
+#define ADMS_KBUF_LAUNCH(KB)                                                                                        \
+    k_raster_kbuf<KB><<<grid, 256, 0, st>>>(s.rec, s.bin, in.F, in.W, in.H, tiles_x, tiles_y, s.tile_off,           \
+                                            s.tile_count, s.list, s.list_capacity, in.keys, L, in.B, s.overflow_ctr)
+    if (L <= 2) ADMS_KBUF_LAUNCH(2);
+    else if (L <= 4) ADMS_KBUF_LAUNCH(4);
+    else if (L <= 8) ADMS_KBUF_LAUNCH(8);
+    else ADMS_KBUF_LAUNCH(16);
+#undef ADMS_KBUF_LAUNCH
     count_launches(1);
     return cudaGetLastError();
 }

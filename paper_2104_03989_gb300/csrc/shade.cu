@@ -360,7 +360,7 @@ __device__ __forceinline__ void shade_refine_px(const ShadeArgs& A, int pix) {
     float lod[3];
     ShadeIn in = shade_inputs(A, g, lod);
     float3 c = shade_eval<false>(A.views[b], in, zero3(), nullptr);
-    A.pre[pix] = make_float4(c.x, c.y, c.z, 1.f);
+    A.pre[pix] = make_float4(c.x, c.y, c.z, A.peel ? in.kd.w : 1.f);
 }
 
 // ------------------------------------------------------------------ shading forward
@@ -384,7 +384,7 @@ __device__ __forceinline__ void shade_fwd_px(const ShadeArgs& A, int b, int px, 
         // float32 ones.
         if (A.refine && fmaxf(c.x, fmaxf(c.y, c.z)) > 0.5f && tc_lever(A, g, lod) > 2.f)
             A.refine[1 + atomicAdd(A.refine, 1)] = (int)pix;  // for k_shade_refine
-        out = make_float4(c.x, c.y, c.z, 1.f);
+        out = make_float4(c.x, c.y, c.z, A.peel ? in.kd.w : 1.f);  // a peeled layer keeps its opacity
     }
     A.pre[pix] = out;
 }
@@ -457,6 +457,16 @@ __device__ __forceinline__ bool pair_eval(const ShadeArgs& A, int b, int px, int
 
 __device__ __forceinline__ float3 f3of(float4 a) { return f3(a.x, a.y, a.z); }
 
+// the colour antialiasing acts on: the shaded colour, or for a depth-peeled layer
+// its blend over the composite behind it, alpha c + (1 - alpha) under (black
+// background behind the last layer; alpha 0 where the layer is empty)
+__device__ __forceinline__ float3 layer_colour(const ShadeArgs& A, size_t pix) {
+    float4 p = A.pre[pix];
+    if (!A.peel) return f3of(p);
+    float3 u = A.under ? f3of(A.under[pix]) : zero3();
+    return p.w * f3of(p) + (1.f - p.w) * u;
+}
+
 // Gamma(log(max(x, 0) + 1)) with the sRGB Gamma of Sec. 5.3, and its
 // derivative. Radiance is non-negative; the antialiasing blends can undershoot
 // below zero beside a bright pixel (a pixel blended toward several darker
@@ -507,7 +517,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
     if (inside) {
         size_t pix = ((size_t)b * A.H + py) * A.W + px;
         unsigned long long kp = A.keys[pix];
-        float3 cp = f3of(A.pre[pix]);
+        float3 cp = layer_colour(A, pix);
         float3 out = cp;
         unsigned amask = 0;  // neighbours whose pair blends (tau != 1/2): the backward visits only these
         if (A.aa) {
@@ -523,7 +533,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
                 if (om != 0.f) amask |= 1u << nbi;
                 // the other pixel blends toward the owner when tau > 1/2, the owner toward it when tau < 1/2
                 bool p_target = om > 0.f ? !pi.p_owner : (om < 0.f ? pi.p_owner : false);
-                if (p_target) out += fabsf(om) * (f3of(A.pre[qpix]) - cp);
+                if (p_target) out += fabsf(om) * (layer_colour(A, qpix) - cp);
             }
         }
         if (A.ref) {
@@ -618,7 +628,7 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
         float3 gc = gp;
         unsigned amask = __float_as_uint(gp4.w);  // pairs that blended in the forward (bit per neighbour)
         if (amask) {
-            float3 cp = f3of(A.pre[pix]);
+            float3 cp = layer_colour(A, pix);
 #pragma unroll
             for (int nbi = 0; nbi < 4; ++nbi) {
                 if (!((amask >> nbi) & 1u)) continue;
@@ -638,7 +648,7 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
                 else gc += w * gq;
                 // d tau: once per pair, by its left / top pixel
                 if (nbi == 1 || nbi == 3) {
-                    float3 cq = f3of(A.pre[qpix]);
+                    float3 cq = layer_colour(A, qpix);
                     float3 gT = p_target ? gp : gq;
                     float3 cT = p_target ? cp : cq, cS = p_target ? cq : cp;
                     float g_tau = (om > 0.f ? 1.f : -1.f) * dot3(gT, cS - cT);
@@ -656,13 +666,27 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
                 }
             }
         }
-        if (f >= 0 && (gc.x != 0.f || gc.y != 0.f || gc.z != 0.f)) {
+        // a peeled layer: gc is dL/d(blend); split it into the layer's colour, its
+        // opacity and the composite behind it (the next layer's dL/d(AA colour))
+        float g_alpha = 0.f;
+        if (A.peel) {
+            float4 pr = A.pre[pix];
+            float4 un = A.under ? A.under[pix] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (A.g_under) {
+                float3 gu = (1.f - pr.w) * gc;
+                A.g_under[pix] = make_float4(gu.x, gu.y, gu.z, un.w);
+            }
+            g_alpha = dot3(gc, f3of(pr) - f3of(un));
+            gc = pr.w * gc;
+        }
+        if (f >= 0 && (gc.x != 0.f || gc.y != 0.f || gc.z != 0.f || g_alpha != 0.f)) {
             PixGeo g;
             pix_geo(A, b, px, py, f, g);
             float lod[3];
             ShadeIn in = shade_inputs(A, g, lod);
             ShadeGrad G;
             shade_eval<true>(vw, in, gc, &G);
+            G.kd.w = g_alpha;  // the opacity is the base colour's fourth channel
             float2 guv = tex_sample_bwd(A.kd, g.tc, lod[0], G.kd);
             float2 g2 = tex_sample_bwd(A.orm, g.tc, lod[1], G.orm);
             float2 g3 = tex_sample_bwd(A.nrm, g.tc, lod[2], G.nm);

@@ -91,11 +91,12 @@ def fold_mips(g, h, w, levels):
     return out
 
 
-def oracle_grads(scene, views, refs, H, W, loss, per_level=False, skin_weights=None, bones=None, msaa=1):
+def oracle_grads(scene, views, refs, H, W, loss, per_level=False, skin_weights=None, bones=None, msaa=1, layers=0):
     """Oracle image-loss gradients (lambda = 0), images, keys, loss, and the
     vertices whose gradient is not unique at float32 resolution. msaa = s > 1:
-    keys on the s x s sample grid, images per pixel."""
-    job = S.OracleJob(scene, loss=loss, per_level=per_level, skin_weights=skin_weights, msaa=msaa)
+    keys on the s x s sample grid, images per pixel. layers = L: depth-peeled,
+    keys (B, L, H, W)."""
+    job = S.OracleJob(scene, loss=loss, per_level=per_level, skin_weights=skin_weights, msaa=msaa, layers=layers)
     if bones is not None:
         job.bones = torch.as_tensor(np.asarray(bones, dtype=np.float64))
         job.shade_f32_skin = True   # the GPU shades the float32 skinned positions it renders
@@ -105,7 +106,9 @@ def oracle_grads(scene, views, refs, H, W, loss, per_level=False, skin_weights=N
     live = [k for k in params if job.optimize[k]]
     grads = dict(zip(live, [g.detach().numpy() for g in torch.autograd.grad(obj["total"], [params[k] for k in live])]))
     img = obj["out"]["img"].detach().numpy()
-    if job.tess is None:
+    if layers:
+        amb = _peeled_ambiguous(job, diags, obj["out"]["keys"], img, refs, H, W)
+    elif job.tess is None:
         amb = ambiguous_vertices(diags, obj["out"]["keys"], img, refs, job.tri_np, loss, sub=max(msaa, 1))
     else:
         # render vertices -> the base vertices they are interpolated from
@@ -118,6 +121,14 @@ def oracle_grads(scene, views, refs, H, W, loss, per_level=False, skin_weights=N
                 loss=float(obj["image"].detach()), ambiguous=amb)
 
 
+def _peeled_ambiguous(job, diags, keys, img, refs, H, W):
+    # every layer of every view is checked like a view of its own
+    L = job.layers
+    flat = [dg["layers"][l] for dg in diags for l in range(L)]
+    return ambiguous_vertices(flat, keys.reshape(-1, H, W), np.repeat(np.asarray(img), L, axis=0),
+                              np.repeat(np.asarray(refs), L, axis=0), job.tri_np, job.loss)
+
+
 def oracle_ambiguous(job, views, refs, H, W):
     """The vertices whose gradient is one-sided (ambiguous_vertices) at an
     oracle job's current parameters, for a plain (untessellated) mesh."""
@@ -126,6 +137,8 @@ def oracle_ambiguous(job, views, refs, H, W):
     with torch.no_grad():
         obj = S.objective(job, params, views, torch.as_tensor(np.asarray(refs, dtype=np.float64)), H, W, lam=0.0,
                           diags=diags)
+    if job.layers:
+        return _peeled_ambiguous(job, diags, obj["out"]["keys"], obj["out"]["img"].numpy(), refs, H, W)
     return ambiguous_vertices(diags, obj["out"]["keys"], obj["out"]["img"].numpy(), refs, job.tri_np, job.loss,
                               sub=max(job.msaa, 1))
 
@@ -166,6 +179,8 @@ def ambiguous_vertices(diags, keys, img, refs, tri, loss, sub=1):
         if loss == "logl1":
             x, y = R.tonemap(x), R.tonemap(y)
         close = ((x - y).abs() < LOSS_MARGIN).any(dim=2).numpy() & ((x - y).abs().sum(dim=2) > 0).numpy()
+        if loss == "l2":   # a smooth loss: no sign kink
+            close[:] = False
         if sub > 1:
             close = np.repeat(np.repeat(close, sub, axis=0), sub, axis=1)
         H, W = close.shape
