@@ -143,11 +143,9 @@ __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int n
 }
 
 // ---------------------------------------------------------------- coverage test
-// coverage + depth key of one triangle at one sample, or ADMS_EMPTY_KEY
-__device__ __forceinline__ unsigned long long tri_key(const TriRec& r, int Sx, int Sy) {
-    long long e0 = (long long)r.ea[0] * Sx + (long long)r.eb[0] * Sy + r.ec[0];
-    long long e1 = (long long)r.ea[1] * Sx + (long long)r.eb[1] * Sy + r.ec[1];
-    long long e2 = (long long)r.ea[2] * Sx + (long long)r.eb[2] * Sy + r.ec[2];
+// coverage + depth key of one triangle at a sample with oriented edge values
+// e0, e1, e2 there, or ADMS_EMPTY_KEY
+__device__ __forceinline__ unsigned long long key_of(const TriRec& r, long long e0, long long e1, long long e2) {
     if (e0 < r.thr[0] || e1 < r.thr[1] || e2 < r.thr[2]) return ADMS_EMPTY_KEY;
     // back to the triangle's own vertex order: E_20 = s e1, E_01 = s e2
     long long E20 = r.sg > 0 ? e1 : -e1;
@@ -158,6 +156,13 @@ __device__ __forceinline__ unsigned long long tri_key(const TriRec& r, int Sx, i
     if (!(d >= 0.f && d <= 1.f)) return ADMS_EMPTY_KEY;
     if (d == 0.f) d = 0.f;
     return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)r.id;
+}
+
+// coverage + depth key of one triangle at one sample, or ADMS_EMPTY_KEY
+__device__ __forceinline__ unsigned long long tri_key(const TriRec& r, int Sx, int Sy) {
+    return key_of(r, (long long)r.ea[0] * Sx + (long long)r.eb[0] * Sy + r.ec[0],
+                  (long long)r.ea[1] * Sx + (long long)r.eb[1] * Sy + r.ec[1],
+                  (long long)r.ea[2] * Sx + (long long)r.eb[2] * Sy + r.ec[2]);
 }
 
 // keeps the minimum in best
@@ -181,88 +186,156 @@ __device__ __forceinline__ void test_tri_kbuf(const TriRec& r, int Sx, int Sy, u
     }
 }
 
+// z-buffer update of the direct raster: the key goes in only if it is below the
+// stored one. The stored key only ever decreases, so a read that lags behind
+// other threads' updates is never below the current minimum and can only let an
+// unneeded atomicMin through; in a dense cloud of small triangles (a foliage
+// canopy puts ~160 fragments on each sample) this drops most of the atomics.
+__device__ __forceinline__ void zmin(unsigned long long* a, unsigned long long key) {
+    if (key != ADMS_EMPTY_KEY && key < __ldcg(a)) atomicMin(a, key);
+}
+
+// the setup record of lane src, for every lane of the warp
+__device__ __forceinline__ TriRec shfl_rec(const TriRec& r, int src) {
+    const unsigned full = 0xffffffffu;
+    TriRec o;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        o.ec[k] = __shfl_sync(full, r.ec[k], src);
+        o.ea[k] = __shfl_sync(full, r.ea[k], src);
+        o.eb[k] = __shfl_sync(full, r.eb[k], src);
+        o.thr[k] = __shfl_sync(full, r.thr[k], src);
+    }
+    o.fA = __shfl_sync(full, r.fA, src);
+    o.z0 = __shfl_sync(full, r.z0, src);
+    o.dz1 = __shfl_sync(full, r.dz1, src);
+    o.dz2 = __shfl_sync(full, r.dz2, src);
+    o.sg = __shfl_sync(full, r.sg, src);
+    o.id = __shfl_sync(full, r.id, src);
+    o.valid = 1;
+    int bx = __shfl_sync(full, ((int)(unsigned short)r.bx0) | ((int)r.bx1 << 16), src);
+    int by = __shfl_sync(full, ((int)(unsigned short)r.by0) | ((int)r.by1 << 16), src);
+    o.bx0 = (short)(bx & 0xffff);
+    o.bx1 = (short)(bx >> 16);
+    o.by0 = (short)(by & 0xffff);
+    o.by1 = (short)(by >> 16);
+    return o;
+}
+
 // ---------------------------------------------------------------- setup, small triangles, tile counts
 // One thread per (view, triangle). Triangles whose pixel bounding box holds at
 // most small_px samples are rasterized here directly, one 64-bit atomicMin per
 // covered sample (the minimum does not depend on the order); larger ones get a
-// setup record and are counted into the tiles they overlap.
+// setup record and are counted into the tiles they overlap. Direct triangles of
+// up to ADMS_SMALL_PX samples loop over their box in their own thread; larger
+// direct ones are rasterized by the whole warp, one triangle after another with
+// the lanes striding over its box (a thread per triangle left three quarters of
+// the lanes idle on a canopy of leaves of 20-300 samples each).
+// COOP: the instantiation with the warp-wide path and the filtered z-buffer
+// updates, launched when small_px exceeds ADMS_SMALL_PX; the other keeps the
+// common case (small_px = ADMS_SMALL_PX) to its own registers.
+template <bool COOP>
 __global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restrict__ vs, int V, int B, int W, int H,
                         int tiles_x, int tiles_y, TriRec* __restrict__ rec, TriBin* __restrict__ bin,
                         int8_t* __restrict__ asign, int* __restrict__ tile_count, unsigned long long* __restrict__ keys,
                         int small_px) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B * F) return;
-    int b = i / F, f = i - b * F;
-    int i0 = tri[3 * f], i1 = tri[3 * f + 1], i2 = tri[3 * f + 2];
-    const VtxS* vb = vs + (size_t)b * V;
-    VtxS a0 = vb[i0], a1 = vb[i1], a2 = vb[i2];
-    TriBin tb;
-    tb.bx0 = 1;
-    tb.bx1 = 0;
-    tb.by0 = 1;
-    tb.by1 = 0;
-    int8_t sgn = 0;
-    if (a0.ok && a1.ok && a2.ok) {
-        long long X0 = a0.X, Y0 = a0.Y, X1 = a1.X, Y1 = a1.Y, X2 = a2.X, Y2 = a2.Y;
-        long long A = (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0);
-        if (A != 0) {
-            int sg = A > 0 ? 1 : -1;
-            sgn = (int8_t)sg;
-            long long minX = min(X0, min(X1, X2)), maxX = max(X0, max(X1, X2));
-            long long minY = min(Y0, min(Y1, Y2)), maxY = max(Y0, max(Y1, Y2));
-            long long ilo = max(ceil_div_ll(minX - 128, 256), 0ll), ihi = min(floor_div_ll(maxX - 128, 256), (long long)W - 1);
-            long long jlo = max(ceil_div_ll(minY - 128, 256), 0ll), jhi = min(floor_div_ll(maxY - 128, 256), (long long)H - 1);
-            if (ilo <= ihi && jlo <= jhi) {
-                TriRec r;
-                // original-order edges: e0 = 1->2, e1 = 2->0, e2 = 0->1
-                long long px[3] = {X0, X1, X2}, py[3] = {Y0, Y1, Y2};
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    int a = (k + 1) % 3, c = (k + 2) % 3;
-                    long long dx = px[c] - px[a], dy = py[c] - py[a];
-                    // oriented value s E = a Sx + b Sy + cst with s = sign(A)
-                    r.ea[k] = (int)(-sg * dy);
-                    r.eb[k] = (int)(sg * dx);
-                    r.ec[k] = sg * (dy * px[a] - dx * py[a]);
-                    long long odx = sg * dx, ody = sg * dy;
-                    r.thr[k] = ((ody < 0) || (ody == 0 && odx > 0)) ? 0 : 1;
-                }
-                r.fA = __ll2float_rn(A);
-                r.sg = sg;
-                r.z0 = a0.z;
-                r.dz1 = __fsub_rn(a1.z, a0.z);
-                r.dz2 = __fsub_rn(a2.z, a0.z);
-                r.id = f;
-                r.valid = 1;
-                r.bx0 = (short)ilo;
-                r.bx1 = (short)ihi;
-                r.by0 = (short)jlo;
-                r.by1 = (short)jhi;
-                long long npx = (ihi - ilo + 1) * (jhi - jlo + 1);
-                if (npx <= small_px) {
-                    unsigned long long* kb = keys + (size_t)b * H * W;
-                    for (int y = (int)jlo; y <= (int)jhi; ++y)
-                        for (int x = (int)ilo; x <= (int)ihi; ++x) {
-                            unsigned long long key = tri_key(r, 256 * x + 128, 256 * y + 128);
-                            if (key != ADMS_EMPTY_KEY) atomicMin(kb + (size_t)y * W + x, key);
-                        }
-                } else {
-                    rec[i] = r;
-                    tb.bx0 = r.bx0;
-                    tb.bx1 = r.bx1;
-                    tb.by0 = r.by0;
-                    tb.by1 = r.by1;
-                    int tx0 = (int)ilo / ADMS_TILE, tx1 = (int)ihi / ADMS_TILE;
-                    int ty0 = (int)jlo / ADMS_TILE, ty1 = (int)jhi / ADMS_TILE;
-                    int* tc = tile_count + (size_t)b * tiles_x * tiles_y;
-                    for (int ty = ty0; ty <= ty1; ++ty)
-                        for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tc + ty * tiles_x + tx, 1);
+    bool coop = false;  // this lane's triangle goes to the warp-wide direct raster
+    TriRec r;
+    int b = 0;
+    if (i < B * F) {
+        b = i / F;
+        int f = i - b * F;
+        int i0 = tri[3 * f], i1 = tri[3 * f + 1], i2 = tri[3 * f + 2];
+        const VtxS* vb = vs + (size_t)b * V;
+        VtxS a0 = vb[i0], a1 = vb[i1], a2 = vb[i2];
+        TriBin tb;
+        tb.bx0 = 1;
+        tb.bx1 = 0;
+        tb.by0 = 1;
+        tb.by1 = 0;
+        int8_t sgn = 0;
+        if (a0.ok && a1.ok && a2.ok) {
+            long long X0 = a0.X, Y0 = a0.Y, X1 = a1.X, Y1 = a1.Y, X2 = a2.X, Y2 = a2.Y;
+            long long A = (X1 - X0) * (Y2 - Y0) - (Y1 - Y0) * (X2 - X0);
+            if (A != 0) {
+                int sg = A > 0 ? 1 : -1;
+                sgn = (int8_t)sg;
+                long long minX = min(X0, min(X1, X2)), maxX = max(X0, max(X1, X2));
+                long long minY = min(Y0, min(Y1, Y2)), maxY = max(Y0, max(Y1, Y2));
+                long long ilo = max(ceil_div_ll(minX - 128, 256), 0ll), ihi = min(floor_div_ll(maxX - 128, 256), (long long)W - 1);
+                long long jlo = max(ceil_div_ll(minY - 128, 256), 0ll), jhi = min(floor_div_ll(maxY - 128, 256), (long long)H - 1);
+                if (ilo <= ihi && jlo <= jhi) {
+                    // original-order edges: e0 = 1->2, e1 = 2->0, e2 = 0->1
+                    long long px[3] = {X0, X1, X2}, py[3] = {Y0, Y1, Y2};
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        int a = (k + 1) % 3, c = (k + 2) % 3;
+                        long long dx = px[c] - px[a], dy = py[c] - py[a];
+                        // oriented value s E = a Sx + b Sy + cst with s = sign(A)
+                        r.ea[k] = (int)(-sg * dy);
+                        r.eb[k] = (int)(sg * dx);
+                        r.ec[k] = sg * (dy * px[a] - dx * py[a]);
+                        long long odx = sg * dx, ody = sg * dy;
+                        r.thr[k] = ((ody < 0) || (ody == 0 && odx > 0)) ? 0 : 1;
+                    }
+                    r.fA = __ll2float_rn(A);
+                    r.sg = sg;
+                    r.z0 = a0.z;
+                    r.dz1 = __fsub_rn(a1.z, a0.z);
+                    r.dz2 = __fsub_rn(a2.z, a0.z);
+                    r.id = f;
+                    r.valid = 1;
+                    r.bx0 = (short)ilo;
+                    r.bx1 = (short)ihi;
+                    r.by0 = (short)jlo;
+                    r.by1 = (short)jhi;
+                    long long npx = (ihi - ilo + 1) * (jhi - jlo + 1);
+                    if (COOP && npx <= small_px && npx > ADMS_SMALL_PX) {
+                        coop = true;
+                    } else if (npx <= small_px) {
+                        unsigned long long* kb = keys + (size_t)b * H * W;
+                        for (int y = (int)jlo; y <= (int)jhi; ++y)
+                            for (int x = (int)ilo; x <= (int)ihi; ++x) {
+                                unsigned long long key = tri_key(r, 256 * x + 128, 256 * y + 128);
+                                if (COOP) zmin(kb + (size_t)y * W + x, key);
+                                else if (key != ADMS_EMPTY_KEY) atomicMin(kb + (size_t)y * W + x, key);
+                            }
+                    } else {
+                        rec[i] = r;
+                        tb.bx0 = r.bx0;
+                        tb.bx1 = r.bx1;
+                        tb.by0 = r.by0;
+                        tb.by1 = r.by1;
+                        int tx0 = (int)ilo / ADMS_TILE, tx1 = (int)ihi / ADMS_TILE;
+                        int ty0 = (int)jlo / ADMS_TILE, ty1 = (int)jhi / ADMS_TILE;
+                        int* tc = tile_count + (size_t)b * tiles_x * tiles_y;
+                        for (int ty = ty0; ty <= ty1; ++ty)
+                            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tc + ty * tiles_x + tx, 1);
+                    }
                 }
             }
         }
+        asign[i] = sgn;
+        bin[i] = tb;
     }
-    asign[i] = sgn;
-    bin[i] = tb;
+    if (!COOP) return;
+    // warp-wide direct raster of the lanes' mid-sized triangles (every lane of the
+    // warp reaches this point: none returned early)
+    unsigned todo = __ballot_sync(0xffffffffu, coop);
+    int lane = threadIdx.x & 31;
+    while (todo) {
+        int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        TriRec t = shfl_rec(r, src);
+        int tb_ = __shfl_sync(0xffffffffu, b, src);
+        int bw = t.bx1 - t.bx0 + 1, n = bw * (t.by1 - t.by0 + 1);
+        unsigned long long* kb = keys + (size_t)tb_ * H * W;
+        for (int q = lane; q < n; q += 32) {
+            int y = t.by0 + q / bw, x = t.bx0 + q - (q / bw) * bw;
+            zmin(kb + (size_t)y * W + x, tri_key(t, 256 * x + 128, 256 * y + 128));
+        }
+    }
 }
 
 // ---------------------------------------------------------------- tile lists
@@ -472,8 +545,12 @@ cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st
     if ((e = cudaMemsetAsync(s.tile_cursor, 0, sizeof(int) * ntiles, st))) return e;
     int bs = 256;
     k_transform<<<(B * V + bs - 1) / bs, bs, 0, st>>>(in.pos, V, in.views, B, W, H, s.clip, s.vs, s.scr);
-    k_setup<<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec, s.bin,
-                                                s.asign, s.tile_count, in.keys, in.small_px);
+    if (in.small_px > ADMS_SMALL_PX)
+        k_setup<true><<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec,
+                                                          s.bin, s.asign, s.tile_count, in.keys, in.small_px);
+    else
+        k_setup<false><<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec,
+                                                           s.bin, s.asign, s.tile_count, in.keys, in.small_px);
     k_scan<<<1, 1024, 0, st>>>(s.tile_count, ntiles, s.tile_off, s.total_pairs);
     k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.bin, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
                                                    s.list, s.list_capacity, in.adj, s.asign, s.silmask);

@@ -460,9 +460,10 @@ __device__ __forceinline__ float3 f3of(float4 a) { return f3(a.x, a.y, a.z); }
 // the colour antialiasing acts on: the shaded colour, or for a depth-peeled layer
 // its blend over the composite behind it, alpha c + (1 - alpha) under (black
 // background behind the last layer; alpha 0 where the layer is empty)
+template <bool PEEL>
 __device__ __forceinline__ float3 layer_colour(const ShadeArgs& A, size_t pix) {
     float4 p = A.pre[pix];
-    if (!A.peel) return f3of(p);
+    if (!PEEL) return f3of(p);
     float3 u = A.under ? f3of(A.under[pix]) : zero3();
     return p.w * f3of(p) + (1.f - p.w) * u;
 }
@@ -511,13 +512,16 @@ __device__ __forceinline__ void neighbour(int nbi, int px, int py, int& qx, int&
 
 // one block of pixels: AA, loss terms and dL/d(AA colour); the block's loss sum
 // goes to A.loss_acc (block-collective: every thread of the block calls it)
+// PEEL: A is a layer of a depth-peeled composite (A.peel set); a separate
+// instantiation keeps the opaque path's registers to its own needs
+template <bool PEEL = false>
 __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px, int py, double* red) {
     bool inside = px < A.W && py < A.H;
     double lsum = 0.0;
     if (inside) {
         size_t pix = ((size_t)b * A.H + py) * A.W + px;
         unsigned long long kp = A.keys[pix];
-        float3 cp = layer_colour(A, pix);
+        float3 cp = layer_colour<PEEL>(A, pix);
         float3 out = cp;
         unsigned amask = 0;  // neighbours whose pair blends (tau != 1/2): the backward visits only these
         if (A.aa) {
@@ -533,7 +537,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
                 if (om != 0.f) amask |= 1u << nbi;
                 // the other pixel blends toward the owner when tau > 1/2, the owner toward it when tau < 1/2
                 bool p_target = om > 0.f ? !pi.p_owner : (om < 0.f ? pi.p_owner : false);
-                if (p_target) out += fabsf(om) * (layer_colour(A, qpix) - cp);
+                if (p_target) out += fabsf(om) * (layer_colour<PEEL>(A, qpix) - cp);
             }
         }
         if (A.ref) {
@@ -610,6 +614,7 @@ __device__ __forceinline__ void atomic_add3(double* p, float3 v) {
 }
 
 // one pixel of the fused backward; warp-collective (vertex scatter)
+template <bool PEEL = false>
 __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, int py) {
     bool inside = px < A.W && py < A.H;
     const adms_view& vw = A.views[b];
@@ -628,7 +633,7 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
         float3 gc = gp;
         unsigned amask = __float_as_uint(gp4.w);  // pairs that blended in the forward (bit per neighbour)
         if (amask) {
-            float3 cp = layer_colour(A, pix);
+            float3 cp = layer_colour<PEEL>(A, pix);
 #pragma unroll
             for (int nbi = 0; nbi < 4; ++nbi) {
                 if (!((amask >> nbi) & 1u)) continue;
@@ -648,7 +653,7 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
                 else gc += w * gq;
                 // d tau: once per pair, by its left / top pixel
                 if (nbi == 1 || nbi == 3) {
-                    float3 cq = layer_colour(A, qpix);
+                    float3 cq = layer_colour<PEEL>(A, qpix);
                     float3 gT = p_target ? gp : gq;
                     float3 cT = p_target ? cp : cq, cS = p_target ? cq : cp;
                     float g_tau = (om > 0.f ? 1.f : -1.f) * dot3(gT, cS - cT);
@@ -669,7 +674,7 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
         // a peeled layer: gc is dL/d(blend); split it into the layer's colour, its
         // opacity and the composite behind it (the next layer's dL/d(AA colour))
         float g_alpha = 0.f;
-        if (A.peel) {
+        if (PEEL) {
             float4 pr = A.pre[pix];
             float4 un = A.under ? A.under[pix] : make_float4(0.f, 0.f, 0.f, 0.f);
             if (A.g_under) {
@@ -686,7 +691,7 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
             ShadeIn in = shade_inputs(A, g, lod);
             ShadeGrad G;
             shade_eval<true>(vw, in, gc, &G);
-            G.kd.w = g_alpha;  // the opacity is the base colour's fourth channel
+            if (PEEL) G.kd.w = g_alpha;  // the opacity is the base colour's fourth channel
             float2 guv = tex_sample_bwd(A.kd, g.tc, lod[0], G.kd);
             float2 g2 = tex_sample_bwd(A.orm, g.tc, lod[1], G.orm);
             float2 g3 = tex_sample_bwd(A.nrm, g.tc, lod[2], G.nm);
@@ -767,18 +772,20 @@ __global__ void __launch_bounds__(256, 5) k_shade_fwd(ShadeArgs A) {
                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
 }
 
+template <bool PEEL>
 __global__ void __launch_bounds__(256, 8) k_aa_loss(ShadeArgs A) {
     __shared__ double red[8];
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    aa_loss_block(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
+    aa_loss_block<PEEL>(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
                   (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4), red);
 }
 
 // three blocks per SM: 85 registers per thread; the spills cost less than the
 // gather latency the extra resident warps hide (0.289 -> 0.265 ms per step)
+template <bool PEEL>
 __global__ void __launch_bounds__(256, 3) k_shade_bwd(ShadeArgs A) {
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    shade_bwd_px(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
+    shade_bwd_px<PEEL>(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
 }
 
@@ -889,12 +896,14 @@ cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st) {
-    k_aa_loss<<<pix_grid(a), 256, 0, st>>>(a);
+    if (a.peel) k_aa_loss<true><<<pix_grid(a), 256, 0, st>>>(a);
+    else k_aa_loss<false><<<pix_grid(a), 256, 0, st>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st) {
-    k_shade_bwd<<<pix_grid(a), 256, 0, st>>>(a);
+    if (a.peel) k_shade_bwd<true><<<pix_grid(a), 256, 0, st>>>(a);
+    else k_shade_bwd<false><<<pix_grid(a), 256, 0, st>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
