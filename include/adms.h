@@ -174,6 +174,17 @@ typedef struct {
 adms_status adms_ctx_create(adms_ctx** out, size_t hbm_budget_bytes, void* cuda_stream);
 adms_status adms_ctx_destroy(adms_ctx* ctx);
 adms_status adms_ctx_set_stream(adms_ctx* ctx, void* cuda_stream);
+/* Overlap of reference rendering with the candidate's forward (no counterpart in
+ * the paper, which renders the reference as a black box before each comparison):
+ * cuda_event (a cudaEvent_t, or NULL for none) completes when the reference
+ * images that later forward_loss calls read are written, typically recorded
+ * after adms_render_reference on another stream (adms_ctx_set_stream switches the
+ * stream between calls). Each forward_loss, and a backward that recomputes its
+ * raster, makes the context's stream wait on it right before the first kernel
+ * that reads a reference image, so the candidate's frame, raster and shading run
+ * alongside the reference render. The event is read at those calls (and captured
+ * into a graph with them); the caller keeps it alive. */
+adms_status adms_ctx_set_ref_event(adms_ctx* ctx, void* cuda_event);
 /* Block until the context's stream is idle; surfaces latched device errors. */
 adms_status adms_sync(adms_ctx* ctx);
 const char* adms_last_error(adms_ctx* ctx);

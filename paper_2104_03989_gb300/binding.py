@@ -78,6 +78,7 @@ SIGNATURES = {
     "adms_ctx_create": ([C.POINTER(P), C.c_size_t, P], C.c_int),
     "adms_ctx_destroy": ([P], C.c_int),
     "adms_ctx_set_stream": ([P, P], C.c_int),
+    "adms_ctx_set_ref_event": ([P, P], C.c_int),
     "adms_sync": ([P], C.c_int),
     "adms_last_error": ([P], C.c_char_p),
     "adms_bytes_in_use": ([P], C.c_size_t),
@@ -170,6 +171,12 @@ def adms_ctx_destroy(ctx):
 def adms_ctx_set_stream(ctx, stream):
     st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
     _check(ctx, lib().adms_ctx_set_stream(ctx, st))
+
+
+def adms_ctx_set_ref_event(ctx, event):
+    """event: a torch.cuda.Event (or a raw cudaEvent_t handle), or None."""
+    ev = None if event is None else (event.cuda_event if hasattr(event, "cuda_event") else event)
+    _check(ctx, lib().adms_ctx_set_ref_event(ctx, ev))
 
 
 def adms_sync(ctx):

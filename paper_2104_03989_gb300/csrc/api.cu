@@ -163,6 +163,9 @@ struct BatchState {
 
 struct adms_ctx {
     cudaStream_t stream = 0;
+    // the reference images of forward_loss calls are complete once this event has
+    // completed (recorded on another stream that renders them), or null
+    cudaEvent_t ref_event = nullptr;
     size_t budget = 0;
     size_t in_use = 0;
     std::string err;
@@ -1225,6 +1228,18 @@ adms_status adms_ctx_set_stream(adms_ctx* ctx, void* cuda_stream) {
     return ADMS_OK;
 }
 
+adms_status adms_ctx_set_ref_event(adms_ctx* ctx, void* cuda_event) {
+    if (!ctx) return ADMS_ERR_ARG;
+    ctx->ref_event = (cudaEvent_t)cuda_event;
+    return ADMS_OK;
+}
+
+// the context's stream waits for the reference images, right before the first
+// kernel that reads them
+static cudaError_t wait_ref(adms_ctx* ctx) {
+    return ctx->ref_event ? cudaStreamWaitEvent(ctx->stream, ctx->ref_event, 0) : cudaSuccess;
+}
+
 adms_status adms_sync(adms_ctx* ctx) {
     if (!ctx) return ADMS_ERR_ARG;
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1440,6 +1455,7 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
         CK(cudaMemsetAsync(&j.st->call_loss, 0, sizeof(double), ctx->stream));
         if (n_jobs == 1) {
             if ((s = render_core(ctx, j))) return s;
+            CK(wait_ref(ctx));
             if (j.L > 0) {
                 if ((s = peel_composite(ctx, j, j.ref, &j.st->call_loss, out_img ? out_img[k] : nullptr))) return s;
             } else if (j.S > 1) {
@@ -1465,6 +1481,7 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
                                                  batch_grid(ctx, 3), ctx->stream)));
         CK(TIMED(ST_SHADE, pixels_batched(0, bs.h_args.data(), bs.px_off.data(), n_jobs, bs.d_px, ctx->tune_tw,
                                           batch_grid(ctx, 0), ctx->stream)));
+        CK(wait_ref(ctx));
         CK(TIMED(ST_AA_LOSS, pixels_batched(1, bs.h_args.data(), bs.px_off.data(), n_jobs, bs.d_px, ctx->tune_tw,
                                             batch_grid(ctx, 1), ctx->stream)));
     }
@@ -1491,6 +1508,7 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
             // caller's reference images instead of reading what the forward kept
             adms_status s = render_core(ctx, j);
             if (s) return s;
+            CK(wait_ref(ctx));
             if (j.L > 0) {
                 if ((s = peel_composite(ctx, j, j.ref, nullptr, nullptr))) return s;
             } else if (j.S > 1) {

@@ -189,5 +189,16 @@ class Context:
         B.adms_job_keys(self.ctx, job, out)
         return out
 
+    def set_stream(self, stream):
+        """Stream of the calls that follow (a torch.cuda.Stream)."""
+        self.stream = stream
+        B.adms_ctx_set_stream(self.ctx, stream)
+
+    def set_ref_event(self, event):
+        """forward_loss waits on this torch.cuda.Event (reference images ready) right
+        before reading the references; None: no wait."""
+        self._keep["ref_event"] = event
+        B.adms_ctx_set_ref_event(self.ctx, event)
+
     def sync(self):
         B.adms_sync(self.ctx)

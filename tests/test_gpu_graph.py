@@ -77,3 +77,64 @@ def test_capture_refuses_new_scratch(gpu_lib):
         B.adms_forward_loss(ctx.ctx, [job], dv, [1], [(64, 64)], [refs], loss)
         torch.cuda.synchronize()
         ctx.close()
+
+
+def test_reference_render_on_a_second_stream_matches_one_stream(gpu_lib):
+    """The reference rendered on its own stream, the loss waiting on its event
+    (adms_ctx_set_ref_event), directly and captured into one graph across both
+    streams, gives the step of the one-stream sequence."""
+    from paper_2104_03989_gb300 import binding as B
+    from paper_2104_03989_gb300.engine import Context
+
+    c = synth.config_small()
+    H = W = 128
+    views = synth.sample_views(6, 0, 2, W, H, r_min=2.6, r_max=3.2)
+    main, side = torch.cuda.Stream(), torch.cuda.Stream()
+    fork, ready = torch.cuda.Event(), torch.cuda.Event()
+    with torch.cuda.stream(main):
+        ctx = Context(stream=main)
+        dv = torch.from_numpy(views.view(np.uint8).copy()).cuda()
+        ref_job = ctx.create_job(c["ref"], frozen=True)
+        jobs = {k: ctx.create_job(c["cand"], loss="l1") for k in ("one", "two", "graph")}
+        refs = {k: torch.zeros((2, H, W, 3), device="cuda") for k in jobs}
+        loss = torch.zeros(3, device="cuda")
+
+        def step(k, li, overlap):
+            if overlap:
+                fork.record(main)
+                side.wait_event(fork)
+                B.adms_ctx_set_stream(ctx.ctx, side)
+            B.adms_render_reference(ctx.ctx, ref_job, dv.view(2, -1), H, W, refs[k])
+            if overlap:
+                ready.record(side)
+                B.adms_ctx_set_stream(ctx.ctx, main)
+                B.adms_ctx_set_ref_event(ctx.ctx, ready)
+            B.adms_forward_loss(ctx.ctx, [jobs[k]], dv, [2], [(H, W)], [refs[k]], loss[li:li + 1])
+            B.adms_ctx_set_ref_event(ctx.ctx, None)
+            B.adms_backward(ctx.ctx, [jobs[k]])
+            B.adms_optimizer_step(ctx.ctx, [jobs[k]])
+
+        step("one", 0, False)
+        step("two", 1, True)
+        step("graph", 2, True)     # sizes the scratch before capture
+        B.adms_graph_begin(ctx.ctx)
+        step("graph", 2, True)
+        g = B.adms_graph_end(ctx.ctx)
+        for _ in range(2):
+            step("one", 0, False)
+            step("two", 1, True)
+            B.adms_graph_launch(ctx.ctx, g)
+        torch.cuda.synchronize()
+        for k in ("two", "graph"):
+            assert torch.equal(refs[k], refs["one"])
+        p = {k: ctx.params(j) for k, j in jobs.items()}
+        assert p["one"]["t"] == p["two"]["t"] == p["graph"]["t"] == 3
+        for k in ("two", "graph"):
+            for name in ("pos", "kd", "nrm"):
+                a = p["one"][name].double().cpu().numpy()
+                b = p[k][name].double().cpu().numpy()
+                assert rel_l2(b, a) < 1e-6, (k, name)
+        l = loss.cpu().numpy()
+        assert abs(l[1] - l[0]) <= 1e-6 * abs(l[0]) and abs(l[2] - l[0]) <= 1e-6 * abs(l[0])
+        B.adms_graph_destroy(g)
+        ctx.close()
