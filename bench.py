@@ -570,14 +570,31 @@ def run_batched(args):
         if st != 0:
             raise B.AdmsError(st, L.adms_last_error(cptr).decode())
 
+    # the references render on four side streams (round robin over the jobs), beside
+    # each other and beside the candidates' forward, whose loss waits for all of them
+    sides = [torch.cuda.Stream() for _ in range(4)]
+    fork_ev, ref_ev = torch.cuda.Event(), torch.cuda.Event()
+    side_evs = [torch.cuda.Event() for _ in sides]
+
     def references(vb):
+        fork_ev.record(stream)
+        for sd in sides:
+            sd.wait_event(fork_ev)
         for k in range(n):
+            B.adms_ctx_set_stream(cptr, sides[k % len(sides)])
             ck(L.adms_render_reference(cptr, refs_j[k], vb + 112 * int(offs[k]), nv[k], res[k], res[k],
                                        ref_bufs[k].data_ptr()))
+        for sd, ev in zip(sides[1:], side_evs[1:]):
+            ev.record(sd)
+            sides[0].wait_event(ev)
+        ref_ev.record(sides[0])
+        B.adms_ctx_set_stream(cptr, stream)
+        B.adms_ctx_set_ref_event(cptr, ref_ev)
 
     def batched_at(vb):
         references(vb)
         ck(L.adms_forward_loss(cptr, jobs_c, n, vb, vpj, hw, refs_c, loss.data_ptr(), None))
+        B.adms_ctx_set_ref_event(cptr, None)
         ck(L.adms_backward(cptr, jobs_c, n, 0))
         ck(L.adms_optimizer_step(cptr, jobs_c, n))
 
@@ -588,6 +605,7 @@ def run_batched(args):
             ck(L.adms_forward_loss(cptr, j1, 1, vb + 112 * int(offs[k]), v1, hw1, r1, loss.data_ptr() + 4 * k, None))
             ck(L.adms_backward(cptr, j1, 1, 0))
             ck(L.adms_optimizer_step(cptr, j1, 1))
+        B.adms_ctx_set_ref_event(cptr, None)
 
     def timed(fn, k0, k):
         torch.cuda.synchronize()
@@ -600,6 +618,7 @@ def run_batched(args):
         return evs[0].elapsed_time(evs[-1]), sorted(evs[s].elapsed_time(evs[s + 1]) for s in range(k))
 
     references(dev_views[0].data_ptr())
+    B.adms_ctx_set_ref_event(cptr, None)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     B.adms_autotune(cptr, cands, view_np[0].view(synth.VIEW_DTYPE), nv, [(x, x) for x in res], ref_bufs)
