@@ -77,6 +77,11 @@ class SimplificationServer:
         self.loss_every = loss_every
         self.on_admit = on_admit
         self.t0 = None
+        # references render on side streams (round robin over the live jobs), beside
+        # each other and beside the candidates' forward; the loss waits for them
+        self.sides = [torch.cuda.Stream() for _ in range(4)]
+        self._fork, self._ready = torch.cuda.Event(), torch.cuda.Event()
+        self._side_evs = [torch.cuda.Event() for _ in self.sides]
 
     # ------------------------------------------------------------------ admission
     def _headroom(self, recs):
@@ -166,13 +171,24 @@ class SimplificationServer:
     def _iterate(self):
         t = time.perf_counter()
         views = []
-        for rec in self.live:
+        self._fork.record(self.stream)
+        for sd in self.sides:
+            sd.wait_event(self._fork)
+        for k, rec in enumerate(self.live):
             r = rec.req
             v = synth.sample_views(r.seed, rec.it, r.n_views, r.res, r.res)
             views.append(v)
+            self.ctx.set_stream(self.sides[k % len(self.sides)])
             self.ctx.render_reference(rec.ref, v, r.res, r.res, out=rec.ref_buf)
+        for sd, ev in zip(self.sides[1:], self._side_evs[1:]):
+            ev.record(sd)
+            self.sides[0].wait_event(ev)
+        self._ready.record(self.sides[0])
+        self.ctx.set_stream(self.stream)
+        self.ctx.set_ref_event(self._ready)
         jobs = [rec.cand for rec in self.live]
         loss = self.ctx.forward_loss(jobs, views, [rec.ref_buf for rec in self.live])
+        self.ctx.set_ref_event(None)
         self.ctx.backward(jobs)
         self.ctx.step(jobs)
         read = (self.live[0].it % self.loss_every) == 0
