@@ -138,3 +138,72 @@ def test_reference_render_on_a_second_stream_matches_one_stream(gpu_lib):
         assert abs(l[1] - l[0]) <= 1e-6 * abs(l[0]) and abs(l[2] - l[0]) <= 1e-6 * abs(l[0])
         B.adms_graph_destroy(g)
         ctx.close()
+
+
+def test_pipelined_graphs_match_sequential_steps(gpu_lib):
+    """The bench's pipelined step: two graphs alternate two view slots and two
+    reference buffers; each renders the next batch's references on a second
+    stream while the candidate steps on the current batch with the references the
+    previous launch rendered. Four steps equal four sequential steps."""
+    from paper_2104_03989_gb300 import binding as B
+    from paper_2104_03989_gb300.engine import Context
+
+    c = synth.config_small()
+    H = W = 96
+    n = 5
+    views = [torch.from_numpy(synth.sample_views(8, i, 2, W, H, r_min=2.6, r_max=3.2).view(np.uint8).copy()).cuda()
+             for i in range(n + 1)]
+    main, side = torch.cuda.Stream(), torch.cuda.Stream()
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
+    with torch.cuda.stream(main):
+        ctx = Context(stream=main)
+        ref_job = ctx.create_job(c["ref"], frozen=True)
+        seq, pipe = ctx.create_job(c["cand"], loss="l1"), ctx.create_job(c["cand"], loss="l1")
+        ref = torch.zeros((2, H, W, 3), device="cuda")
+        bufs = [torch.zeros((2, H, W, 3), device="cuda") for _ in range(2)]
+        slots = torch.zeros((2, views[0].numel()), dtype=torch.uint8, device="cuda")
+        loss = torch.zeros(2, device="cuda")
+
+        def seq_step(i, job):
+            B.adms_render_reference(ctx.ctx, ref_job, views[i].view(2, -1), H, W, ref)
+            B.adms_forward_loss(ctx.ctx, [job], views[i], [2], [(H, W)], [ref], loss[:1])
+            B.adms_backward(ctx.ctx, [job])
+            B.adms_optimizer_step(ctx.ctx, [job])
+
+        def pipelined(cur):
+            fork.record(main)
+            side.wait_event(fork)
+            B.adms_ctx_set_stream(ctx.ctx, side)
+            B.adms_render_reference(ctx.ctx, ref_job, slots[1 - cur].view(2, -1), H, W, bufs[1 - cur])
+            join.record(side)
+            B.adms_ctx_set_stream(ctx.ctx, main)
+            B.adms_forward_loss(ctx.ctx, [pipe], slots[cur], [2], [(H, W)], [bufs[cur]], loss[1:])
+            B.adms_backward(ctx.ctx, [pipe])
+            B.adms_optimizer_step(ctx.ctx, [pipe])
+            main.wait_event(join)
+
+        seq_step(0, seq)          # step 0 directly for both (sizes all scratch)
+        seq_step(0, pipe)
+        graphs = []
+        for cur in (0, 1):
+            B.adms_graph_begin(ctx.ctx)
+            pipelined(cur)
+            graphs.append(B.adms_graph_end(ctx.ctx))
+        slots[0].copy_(views[1])
+        B.adms_render_reference(ctx.ctx, ref_job, slots[0].view(2, -1), H, W, bufs[0])
+        losses = []
+        for s in range(4):
+            seq_step(1 + s, seq)
+            slots[1 - s % 2].copy_(views[2 + s])
+            B.adms_graph_launch(ctx.ctx, graphs[s % 2])
+            losses.append(loss.clone())
+        torch.cuda.synchronize()
+        for l in losses:
+            assert abs(float(l[1]) - float(l[0])) <= 1e-6 * abs(float(l[0]))
+        pa, pb = ctx.params(seq), ctx.params(pipe)
+        assert pa["t"] == pb["t"] == 5
+        for name in ("pos", "kd", "nrm"):
+            assert rel_l2(pb[name].double().cpu().numpy(), pa[name].double().cpu().numpy()) < 1e-6, name
+        for g in graphs:
+            B.adms_graph_destroy(g)
+        ctx.close()
