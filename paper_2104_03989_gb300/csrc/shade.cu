@@ -360,33 +360,63 @@ __device__ __forceinline__ void shade_refine_px(const ShadeArgs& A, int pix) {
     float lod[3];
     ShadeIn in = shade_inputs(A, g, lod);
     float3 c = shade_eval<false>(A.views[b], in, zero3(), nullptr);
-    A.pre[pix] = make_float4(c.x, c.y, c.z, A.peel ? in.kd.w : 1.f);
+    float4 v = make_float4(c.x, c.y, c.z, A.peel ? in.kd.w : 1.f);
+    if (A.msaa > 1) {
+        // every sample of the pixel that shows this triangle takes this shading
+        int sm = A.msaa, ox = (px / sm) * sm, oy = (py / sm) * sm;
+        for (int y = oy; y < min(oy + sm, A.H); ++y)
+            for (int x = ox; x < min(ox + sm, A.W); ++x) {
+                size_t q = ((size_t)b * A.H + y) * A.W + x;
+                if (key_tri(A.keys[q]) == f) A.pre[q] = v;
+            }
+    } else {
+        A.pre[pix] = v;
+    }
 }
 
 // ------------------------------------------------------------------ shading forward
+// shading of triangle f at sample (px, py), listing it for the refinement pass
+// when bright on a triangle that spans many texels
+__device__ __forceinline__ float4 shade_covered(const ShadeArgs& A, int b, int px, int py, int f, size_t pix) {
+    PixGeo g;
+    pix_geo(A, b, px, py, f, g);
+    float lod[3];
+    ShadeIn in = shade_inputs(A, g, lod);
+    float3 c = shade_eval<false>(A.views[b], in, zero3(), nullptr);
+    // Bright pixels (sharp highlights) carry almost all of the error a float32
+    // texture coordinate causes: on the noise-textured workloads the 0.35% of
+    // pixels above 0.5 carry 98% of it. Those on triangles spanning more than two
+    // texels at the sampled level are listed and shaded again by k_shade_refine
+    // with the refined coordinate and LOD (a separate pass keeps this kernel's
+    // registers to the common path). The backward, held to 1e-3, keeps the
+    // float32 ones.
+    if (A.refine && fmaxf(c.x, fmaxf(c.y, c.z)) > 0.5f && tc_lever(A, g, lod) > 2.f)
+        A.refine[1 + atomicAdd(A.refine, 1)] = (int)pix;  // for k_shade_refine
+    return make_float4(c.x, c.y, c.z, A.peel ? in.kd.w : 1.f);  // a peeled layer keeps its opacity
+}
+
 __device__ __forceinline__ void shade_fwd_px(const ShadeArgs& A, int b, int px, int py) {
     if (px >= A.W || py >= A.H) return;
     size_t pix = ((size_t)b * A.H + py) * A.W + px;
     int f = key_tri(A.keys[pix]);
-    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (f >= 0) {
-        PixGeo g;
-        pix_geo(A, b, px, py, f, g);
-        float lod[3];
-        ShadeIn in = shade_inputs(A, g, lod);
-        float3 c = shade_eval<false>(A.views[b], in, zero3(), nullptr);
-        // Bright pixels (sharp highlights) carry almost all of the error a float32
-        // texture coordinate causes: on the noise-textured workloads the 0.35% of
-        // pixels above 0.5 carry 98% of it. Those on triangles spanning more than two
-        // texels at the sampled level are listed and shaded again by k_shade_refine
-        // with the refined coordinate and LOD (a separate pass keeps this kernel's
-        // registers to the common path). The backward, held to 1e-3, keeps the
-        // float32 ones.
-        if (A.refine && fmaxf(c.x, fmaxf(c.y, c.z)) > 0.5f && tc_lever(A, g, lod) > 2.f)
-            A.refine[1 + atomicAdd(A.refine, 1)] = (int)pix;  // for k_shade_refine
-        out = make_float4(c.x, c.y, c.z, A.peel ? in.kd.w : 1.f);  // a peeled layer keeps its opacity
-    }
-    A.pre[pix] = out;
+    A.pre[pix] = f >= 0 ? shade_covered(A, b, px, py, f, pix) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// Under MSAA every sample of a pixel that shows one triangle has the same shading
+// (at the pixel's centre, with the pixel's LOD): the (pixel, triangle) groups of a
+// 16x16-sample tile are shaded once each. The group's leader is its first sample in
+// the tile (row-major); tri: the tile's triangle ids (-1: empty or outside).
+__device__ __forceinline__ int group_leader(int sm, int tx0, int ty0, int px, int py, int f, const int* tri) {
+    if (f < 0) return -1;
+    int ox = (px / sm) * sm, oy = (py / sm) * sm;
+    int x0 = max(ox, tx0), x1 = min(ox + sm, tx0 + ADMS_TILE);
+    int y0 = max(oy, ty0), y1 = min(oy + sm, ty0 + ADMS_TILE);
+    for (int y = y0; y < y1; ++y)
+        for (int x = x0; x < x1; ++x) {
+            int t = (y - ty0) * ADMS_TILE + (x - tx0);
+            if (tri[t] == f) return t;
+        }
+    return -1;
 }
 
 // ------------------------------------------------------------------ antialiasing
@@ -614,11 +644,137 @@ __device__ __forceinline__ void atomic_add3(double* p, float3 v) {
 }
 
 // one pixel of the fused backward; warp-collective (vertex scatter)
+// AA adjoint at one sample: dL/d(the colour AA acts on) there, gathered from the
+// sample's own dL/d(AA colour) and its blending neighbours'; the crossing edges'
+// vertex gradients are scattered here (warp-divergent, plain atomics)
+template <bool PEEL>
+__device__ __forceinline__ float3 aa_adjoint(const ShadeArgs& A, int b, int px, int py, size_t pix,
+                                             unsigned long long kp) {
+    const adms_view& vw = A.views[b];
+    float hW = 0.5f * (float)A.W, hH = 0.5f * (float)A.H;
+    float4 gp4 = A.gprime[pix];
+    float3 gp = f3of(gp4);
+    float3 gc = gp;
+    unsigned amask = __float_as_uint(gp4.w);  // pairs that blended in the forward (bit per neighbour)
+    if (amask) {
+        float3 cp = layer_colour<PEEL>(A, pix);
+#pragma unroll
+        for (int nbi = 0; nbi < 4; ++nbi) {
+            if (!((amask >> nbi) & 1u)) continue;
+            int qx, qy;
+            neighbour(nbi, px, py, qx, qy);
+            if (qx < 0 || qx >= A.W || qy < 0 || qy >= A.H) continue;
+            size_t qpix = ((size_t)b * A.H + qy) * A.W + qx;
+            int axis = nbi < 2 ? 0 : 1;
+            PairInfo pi;
+            if (!pair_eval(A, b, px, py, kp, qx, qy, A.keys[qpix], axis, pi)) continue;
+            float om = pi.t.tau - 0.5f;
+            if (om == 0.f) continue;
+            bool p_target = om > 0.f ? !pi.p_owner : pi.p_owner;
+            float3 gq = f3of(A.gprime[qpix]);
+            float w = fabsf(om);
+            if (p_target) gc -= w * gp;
+            else gc += w * gq;
+            // d tau: once per pair, by its left / top pixel
+            if (nbi == 1 || nbi == 3) {
+                float3 cq = layer_colour<PEEL>(A, qpix);
+                float3 gT = p_target ? gp : gq;
+                float3 cT = p_target ? cp : cq, cS = p_target ? cq : cp;
+                float g_tau = (om > 0.f ? 1.f : -1.f) * dot3(gT, cS - cT);
+                float au = axis == 0 ? pi.t.a.y : pi.t.a.x, bu = axis == 0 ? pi.t.b.y : pi.t.b.x;
+                float ax = axis == 0 ? pi.t.a.x : pi.t.a.y, bx = axis == 0 ? pi.t.b.x : pi.t.b.y;
+                float du = bu - au, dx = bx - ax, sp = pi.t.sp;
+                float k = pi.sigma * g_tau;
+                float ga_x = k * (1.f - sp), ga_u = k * dx * (sp - 1.f) / du;
+                float gb_x = k * sp, gb_u = -k * dx * sp / du;
+                float2 gsa = axis == 0 ? make_float2(ga_x, ga_u) : make_float2(ga_u, ga_x);
+                float2 gsb = axis == 0 ? make_float2(gb_x, gb_u) : make_float2(gb_u, gb_x);
+                float4 ca = A.clip[(size_t)b * A.V + pi.t.va], cb = A.clip[(size_t)b * A.V + pi.t.vb];
+                atomic_add3(A.g_pos + 3 * pi.t.va, clip_to_pos_grad(vw.mvp, screen_bwd(ca, hW, hH, gsa)));
+                atomic_add3(A.g_pos + 3 * pi.t.vb, clip_to_pos_grad(vw.mvp, screen_bwd(cb, hW, hH, gsb)));
+            }
+        }
+    }
+    return gc;
+}
+
+// shading adjoint of triangle f at sample (px, py) for dL/d(colour) gc (and, for a
+// peeled layer, dL/d(opacity) g_alpha): texel gradients scattered here, the three
+// corners' position / normal / tangent gradients returned in vi, vg
+template <bool PEEL>
+__device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int px, int py, int f, float3 gc,
+                                                float g_alpha, int vi[3], float vg[27]) {
+    const adms_view& vw = A.views[b];
+    float hW = 0.5f * (float)A.W, hH = 0.5f * (float)A.H;
+    PixGeo g;
+    pix_geo(A, b, px, py, f, g);
+    float lod[3];
+    ShadeIn in = shade_inputs(A, g, lod);
+    ShadeGrad G;
+    shade_eval<true>(vw, in, gc, &G);
+    if (PEEL) G.kd.w = g_alpha;  // the opacity is the base colour's fourth channel
+    float2 guv = tex_sample_bwd(A.kd, g.tc, lod[0], G.kd);
+    float2 g2 = tex_sample_bwd(A.orm, g.tc, lod[1], G.orm);
+    float2 g3 = tex_sample_bwd(A.nrm, g.tc, lod[2], G.nm);
+    guv.x += g2.x + g3.x;
+    guv.y += g2.y + g3.y;
+    // interpolation: attr = sum_k beta_k attr_k, beta_k = r_k / R  =>  d attr / d r_j = (attr_j - attr) / R
+    float gr[3];
+    {
+        float2 u0 = A.uv[g.ui[0]];
+        float3 p0 = f3(A.vpos[g.vi[0]]), n0 = f3(A.vnrm[g.vi[0]]), t0 = f3(A.vtan[g.vi[0]]);
+        float iR = 1.f / g.R;
+        gr[0] = -(dot3(G.p, g.dp) + dot3(G.n_i, g.dn) + dot3(G.t_i, g.dt) + guv.x * g.duv.x + guv.y * g.duv.y) * iR;
+#pragma unroll
+        for (int k = 1; k < 3; ++k) {
+            float2 uk = A.uv[g.ui[k]];
+            float3 ep = f3(A.vpos[g.vi[k]]) - p0 - g.dp;
+            float3 en = f3(A.vnrm[g.vi[k]]) - n0 - g.dn;
+            float3 et = f3(A.vtan[g.vi[k]]) - t0 - g.dt;
+            float eu = (uk.x - u0.x) - g.duv.x, ev = (uk.y - u0.y) - g.duv.y;
+            gr[k] = (dot3(G.p, ep) + dot3(G.n_i, en) + dot3(G.t_i, et) + guv.x * eu + guv.y * ev) * iR;
+        }
+    }
+    float glam[3], gw[3], sgl = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        vi[k] = g.vi[k];
+        glam[k] = gr[k] / g.c[k].w;
+        gw[k] = -gr[k] * g.r[k] / g.c[k].w;
+        sgl += glam[k] * g.lam[k];
+    }
+    float ia = 1.f / g.area;
+    float ge[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ge[k] = (glam[k] - sgl) * ia;
+    const float2* d = g.d;
+    float2 gs[3];
+    // e0 = cross(d1, d2), e1 = cross(d2, d0), e2 = cross(d0, d1)
+    gs[0] = make_float2(-ge[1] * d[2].y + ge[2] * d[1].y, ge[1] * d[2].x - ge[2] * d[1].x);
+    gs[1] = make_float2(ge[0] * d[2].y - ge[2] * d[0].y, -ge[0] * d[2].x + ge[2] * d[0].x);
+    gs[2] = make_float2(-ge[0] * d[1].y + ge[1] * d[0].y, ge[0] * d[1].x - ge[1] * d[0].x);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float4 gcl = screen_bwd(g.c[k], hW, hH, gs[k]);
+        gcl.w += gw[k];
+        float3 gpk = g.beta[k] * G.p + clip_to_pos_grad(vw.mvp, gcl);
+        float3 gnk = g.beta[k] * G.n_i, gtk = g.beta[k] * G.t_i;
+        vg[9 * k + 0] = gpk.x;
+        vg[9 * k + 1] = gpk.y;
+        vg[9 * k + 2] = gpk.z;
+        vg[9 * k + 3] = gnk.x;
+        vg[9 * k + 4] = gnk.y;
+        vg[9 * k + 5] = gnk.z;
+        vg[9 * k + 6] = gtk.x;
+        vg[9 * k + 7] = gtk.y;
+        vg[9 * k + 8] = gtk.z;
+    }
+}
+
+// one pixel of the fused backward; warp-collective (vertex scatter)
 template <bool PEEL = false>
 __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, int py) {
     bool inside = px < A.W && py < A.H;
-    const adms_view& vw = A.views[b];
-    float hW = 0.5f * (float)A.W, hH = 0.5f * (float)A.H;
     int f = -1;
     int vi[3] = {0, 0, 0};
     float vg[27];
@@ -628,49 +784,7 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
         size_t pix = ((size_t)b * A.H + py) * A.W + px;
         unsigned long long kp = A.keys[pix];
         f = key_tri(kp);
-        float4 gp4 = A.gprime[pix];
-        float3 gp = f3of(gp4);
-        float3 gc = gp;
-        unsigned amask = __float_as_uint(gp4.w);  // pairs that blended in the forward (bit per neighbour)
-        if (amask) {
-            float3 cp = layer_colour<PEEL>(A, pix);
-#pragma unroll
-            for (int nbi = 0; nbi < 4; ++nbi) {
-                if (!((amask >> nbi) & 1u)) continue;
-                int qx, qy;
-                neighbour(nbi, px, py, qx, qy);
-                if (qx < 0 || qx >= A.W || qy < 0 || qy >= A.H) continue;
-                size_t qpix = ((size_t)b * A.H + qy) * A.W + qx;
-                int axis = nbi < 2 ? 0 : 1;
-                PairInfo pi;
-                if (!pair_eval(A, b, px, py, kp, qx, qy, A.keys[qpix], axis, pi)) continue;
-                float om = pi.t.tau - 0.5f;
-                if (om == 0.f) continue;
-                bool p_target = om > 0.f ? !pi.p_owner : pi.p_owner;
-                float3 gq = f3of(A.gprime[qpix]);
-                float w = fabsf(om);
-                if (p_target) gc -= w * gp;
-                else gc += w * gq;
-                // d tau: once per pair, by its left / top pixel
-                if (nbi == 1 || nbi == 3) {
-                    float3 cq = layer_colour<PEEL>(A, qpix);
-                    float3 gT = p_target ? gp : gq;
-                    float3 cT = p_target ? cp : cq, cS = p_target ? cq : cp;
-                    float g_tau = (om > 0.f ? 1.f : -1.f) * dot3(gT, cS - cT);
-                    float au = axis == 0 ? pi.t.a.y : pi.t.a.x, bu = axis == 0 ? pi.t.b.y : pi.t.b.x;
-                    float ax = axis == 0 ? pi.t.a.x : pi.t.a.y, bx = axis == 0 ? pi.t.b.x : pi.t.b.y;
-                    float du = bu - au, dx = bx - ax, sp = pi.t.sp;
-                    float k = pi.sigma * g_tau;
-                    float ga_x = k * (1.f - sp), ga_u = k * dx * (sp - 1.f) / du;
-                    float gb_x = k * sp, gb_u = -k * dx * sp / du;
-                    float2 gsa = axis == 0 ? make_float2(ga_x, ga_u) : make_float2(ga_u, ga_x);
-                    float2 gsb = axis == 0 ? make_float2(gb_x, gb_u) : make_float2(gb_u, gb_x);
-                    float4 ca = A.clip[(size_t)b * A.V + pi.t.va], cb = A.clip[(size_t)b * A.V + pi.t.vb];
-                    atomic_add3(A.g_pos + 3 * pi.t.va, clip_to_pos_grad(vw.mvp, screen_bwd(ca, hW, hH, gsa)));
-                    atomic_add3(A.g_pos + 3 * pi.t.vb, clip_to_pos_grad(vw.mvp, screen_bwd(cb, hW, hH, gsb)));
-                }
-            }
-        }
+        float3 gc = aa_adjoint<PEEL>(A, b, px, py, pix, kp);
         // a peeled layer: gc is dL/d(blend); split it into the layer's colour, its
         // opacity and the composite behind it (the next layer's dL/d(AA colour))
         float g_alpha = 0.f;
@@ -684,73 +798,10 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
             g_alpha = dot3(gc, f3of(pr) - f3of(un));
             gc = pr.w * gc;
         }
-        if (f >= 0 && (gc.x != 0.f || gc.y != 0.f || gc.z != 0.f || g_alpha != 0.f)) {
-            PixGeo g;
-            pix_geo(A, b, px, py, f, g);
-            float lod[3];
-            ShadeIn in = shade_inputs(A, g, lod);
-            ShadeGrad G;
-            shade_eval<true>(vw, in, gc, &G);
-            if (PEEL) G.kd.w = g_alpha;  // the opacity is the base colour's fourth channel
-            float2 guv = tex_sample_bwd(A.kd, g.tc, lod[0], G.kd);
-            float2 g2 = tex_sample_bwd(A.orm, g.tc, lod[1], G.orm);
-            float2 g3 = tex_sample_bwd(A.nrm, g.tc, lod[2], G.nm);
-            guv.x += g2.x + g3.x;
-            guv.y += g2.y + g3.y;
-            // interpolation: attr = sum_k beta_k attr_k, beta_k = r_k / R  =>  d attr / d r_j = (attr_j - attr) / R
-            float gr[3];
-            {
-                float2 u0 = A.uv[g.ui[0]];
-                float3 p0 = f3(A.vpos[g.vi[0]]), n0 = f3(A.vnrm[g.vi[0]]), t0 = f3(A.vtan[g.vi[0]]);
-                float iR = 1.f / g.R;
-                gr[0] = -(dot3(G.p, g.dp) + dot3(G.n_i, g.dn) + dot3(G.t_i, g.dt) + guv.x * g.duv.x + guv.y * g.duv.y) * iR;
-#pragma unroll
-                for (int k = 1; k < 3; ++k) {
-                    float2 uk = A.uv[g.ui[k]];
-                    float3 ep = f3(A.vpos[g.vi[k]]) - p0 - g.dp;
-                    float3 en = f3(A.vnrm[g.vi[k]]) - n0 - g.dn;
-                    float3 et = f3(A.vtan[g.vi[k]]) - t0 - g.dt;
-                    float eu = (uk.x - u0.x) - g.duv.x, ev = (uk.y - u0.y) - g.duv.y;
-                    gr[k] = (dot3(G.p, ep) + dot3(G.n_i, en) + dot3(G.t_i, et) + guv.x * eu + guv.y * ev) * iR;
-                }
-            }
-            float glam[3], gw[3], sgl = 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                vi[k] = g.vi[k];
-                glam[k] = gr[k] / g.c[k].w;
-                gw[k] = -gr[k] * g.r[k] / g.c[k].w;
-                sgl += glam[k] * g.lam[k];
-            }
-            float ia = 1.f / g.area;
-            float ge[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) ge[k] = (glam[k] - sgl) * ia;
-            const float2* d = g.d;
-            float2 gs[3];
-            // e0 = cross(d1, d2), e1 = cross(d2, d0), e2 = cross(d0, d1)
-            gs[0] = make_float2(-ge[1] * d[2].y + ge[2] * d[1].y, ge[1] * d[2].x - ge[2] * d[1].x);
-            gs[1] = make_float2(ge[0] * d[2].y - ge[2] * d[0].y, -ge[0] * d[2].x + ge[2] * d[0].x);
-            gs[2] = make_float2(-ge[0] * d[1].y + ge[1] * d[0].y, ge[0] * d[1].x - ge[1] * d[0].x);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float4 gcl = screen_bwd(g.c[k], hW, hH, gs[k]);
-                gcl.w += gw[k];
-                float3 gpk = g.beta[k] * G.p + clip_to_pos_grad(vw.mvp, gcl);
-                float3 gnk = g.beta[k] * G.n_i, gtk = g.beta[k] * G.t_i;
-                vg[9 * k + 0] = gpk.x;
-                vg[9 * k + 1] = gpk.y;
-                vg[9 * k + 2] = gpk.z;
-                vg[9 * k + 3] = gnk.x;
-                vg[9 * k + 4] = gnk.y;
-                vg[9 * k + 5] = gnk.z;
-                vg[9 * k + 6] = gtk.x;
-                vg[9 * k + 7] = gtk.y;
-                vg[9 * k + 8] = gtk.z;
-            }
-        } else {
+        if (f >= 0 && (gc.x != 0.f || gc.y != 0.f || gc.z != 0.f || g_alpha != 0.f))
+            shading_adjoint<PEEL>(A, b, px, py, f, gc, g_alpha, vi, vg);
+        else
             f = -1;
-        }
     }
     scatter_vertex_grads(A, f, vi, vg);
 }
@@ -787,6 +838,96 @@ __global__ void __launch_bounds__(256, 3) k_shade_bwd(ShadeArgs A) {
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
     shade_bwd_px<PEEL>(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
+}
+
+// MSAA forward: the tile's (pixel, triangle) groups are compacted into a list and
+// each is shaded by one thread; every sample copies its group's colour
+__global__ void __launch_bounds__(256, 5) k_shade_fwd_msaa(ShadeArgs A) {
+    __shared__ int tri[256];
+    __shared__ short list[256];
+    __shared__ float4 col[256];
+    __shared__ int count;
+    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    int b = blockIdx.y, tid = threadIdx.x;
+    int tx0 = (blockIdx.x % tiles_x) * ADMS_TILE, ty0 = (blockIdx.x / tiles_x) * ADMS_TILE;
+    int px = tx0 + (tid & 15), py = ty0 + (tid >> 4);
+    bool inside = px < A.W && py < A.H;
+    size_t pix = inside ? ((size_t)b * A.H + py) * A.W + px : 0;
+    int f = inside ? key_tri(A.keys[pix]) : -1;
+    if (tid == 0) count = 0;
+    tri[tid] = f;
+    __syncthreads();
+    int lead = group_leader(A.msaa, tx0, ty0, px, py, f, tri);
+    if (f >= 0 && lead == tid) list[atomicAdd(&count, 1)] = (short)tid;
+    __syncthreads();
+    int n = count;
+    for (int i = tid; i < n; i += 256) {
+        int t = list[i];
+        int sx = tx0 + (t & 15), sy = ty0 + (t >> 4);
+        col[t] = shade_covered(A, b, sx, sy, tri[t], ((size_t)b * A.H + sy) * A.W + sx);
+    }
+    __syncthreads();
+    if (inside) A.pre[pix] = f >= 0 ? col[lead] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// MSAA backward: the AA adjoint runs per sample; the shading adjoint of a (pixel,
+// triangle) group is linear in its colour gradient and its samples share the
+// shading, so the group's leader takes the sum of its samples' gradients (in a
+// fixed order) and the compacted leaders run the adjoint once per group
+__global__ void __launch_bounds__(256, 3) k_shade_bwd_msaa(ShadeArgs A) {
+    __shared__ int tri[256];
+    __shared__ float3 gsum[256];
+    __shared__ short list[256];
+    __shared__ int count;
+    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    int b = blockIdx.y, tid = threadIdx.x;
+    int tx0 = (blockIdx.x % tiles_x) * ADMS_TILE, ty0 = (blockIdx.x / tiles_x) * ADMS_TILE;
+    int px = tx0 + (tid & 15), py = ty0 + (tid >> 4);
+    bool inside = px < A.W && py < A.H;
+    int f = -1;
+    float3 gc = zero3();
+    if (inside) {
+        size_t pix = ((size_t)b * A.H + py) * A.W + px;
+        unsigned long long kp = A.keys[pix];
+        f = key_tri(kp);
+        gc = aa_adjoint<false>(A, b, px, py, pix, kp);
+    }
+    if (tid == 0) count = 0;
+    tri[tid] = f;
+    gsum[tid] = gc;
+    __syncthreads();
+    int lead = group_leader(A.msaa, tx0, ty0, px, py, f, tri);
+    float3 g = zero3();
+    if (f >= 0 && lead == tid) {
+        int sm = A.msaa, ox = (px / sm) * sm, oy = (py / sm) * sm;
+        for (int y = max(oy, ty0); y < min(oy + sm, ty0 + ADMS_TILE); ++y)
+            for (int x = max(ox, tx0); x < min(ox + sm, tx0 + ADMS_TILE); ++x) {
+                int t = (y - ty0) * ADMS_TILE + (x - tx0);
+                if (tri[t] == f) g += gsum[t];
+            }
+    }
+    __syncthreads();
+    if (f >= 0 && lead == tid && (g.x != 0.f || g.y != 0.f || g.z != 0.f)) {
+        gsum[tid] = g;
+        list[atomicAdd(&count, 1)] = (short)tid;
+    }
+    __syncthreads();
+    int n = count;
+    // warp-uniform trips: the vertex scatter is warp-collective
+    for (int base = tid & ~31; base < n; base += 256) {
+        int i = base + (tid & 31);
+        int fl = -1;
+        int vi[3] = {0, 0, 0};
+        float vg[27];
+#pragma unroll
+        for (int j = 0; j < 27; ++j) vg[j] = 0.f;
+        if (i < n) {
+            int t = list[i];
+            fl = tri[t];
+            shading_adjoint<false>(A, b, tx0 + (t & 15), ty0 + (t >> 4), fl, gsum[t], 0.f, vi, vg);
+        }
+        scatter_vertex_grads(A, fl, vi, vg);
+    }
 }
 
 // ------------------------------------------------------------------ persistent batched kernels
@@ -887,7 +1028,8 @@ cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
         cudaError_t e = cudaMemsetAsync(a.refine, 0, sizeof(int), st);
         if (e) return e;
     }
-    k_shade_fwd<<<pix_grid(a), 256, 0, st>>>(a);
+    if (a.msaa > 1) k_shade_fwd_msaa<<<pix_grid(a), 256, 0, st>>>(a);
+    else k_shade_fwd<<<pix_grid(a), 256, 0, st>>>(a);
     count_launches(1);
     if (a.refine) {
         k_shade_refine<<<128, 256, 0, st>>>(a);
@@ -902,7 +1044,8 @@ cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st) {
-    if (a.peel) k_shade_bwd<true><<<pix_grid(a), 256, 0, st>>>(a);
+    if (a.msaa > 1) k_shade_bwd_msaa<<<pix_grid(a), 256, 0, st>>>(a);
+    else if (a.peel) k_shade_bwd<true><<<pix_grid(a), 256, 0, st>>>(a);
     else k_shade_bwd<false><<<pix_grid(a), 256, 0, st>>>(a);
     count_launches(1);
     return cudaGetLastError();
