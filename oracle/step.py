@@ -243,5 +243,5 @@ def step(job, views, refs, height, width):
                                                           lr * job.lr_scale.get(k, 1.0), k)
     job.t += 1
     return dict(keys=obj["out"]["keys"], asign=obj["out"]["asign"], pre=obj["out"]["pre"].detach(),
-                img=obj["out"]["img"].detach(), loss=float(obj["total"]), image_loss=float(obj["image"]),
+                img=obj["out"]["img"].detach(), loss=float(obj["total"].detach()), image_loss=float(obj["image"].detach()),
                 laplacian=float(obj["laplacian"]), lam=obj["lam"], grads=grads, lr=lr)
