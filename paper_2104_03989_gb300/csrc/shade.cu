@@ -840,34 +840,61 @@ __global__ void __launch_bounds__(256, 3) k_shade_bwd(ShadeArgs A) {
                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
 }
 
-// MSAA forward: the tile's (pixel, triangle) groups are compacted into a list and
-// each is shaded by one thread; every sample copies its group's colour
-__global__ void __launch_bounds__(256, 5) k_shade_fwd_msaa(ShadeArgs A) {
-    __shared__ int tri[256];
-    __shared__ short list[256];
-    __shared__ float4 col[256];
+// MSAA forward: a block takes a 32x32-sample region (four samples per thread), its
+// (pixel, triangle) groups are compacted into a shared-memory list and each group is
+// shaded by one thread; every sample copies its group's colour. (A 16x16 region holds
+// only ~70 groups at 2x2 MSAA, which left most of a block's warps waiting while three
+// shaded.)
+#define ADMS_MSAA_REGION 32
+__global__ void __launch_bounds__(256, 4) k_shade_fwd_msaa(ShadeArgs A) {
+    constexpr int R = ADMS_MSAA_REGION, N = R * R, PER = N / 256;
+    __shared__ int tri[N];
+    __shared__ short list[N];
+    __shared__ float4 col[N];
     __shared__ int count;
-    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    int rx = (A.W + R - 1) / R;
     int b = blockIdx.y, tid = threadIdx.x;
-    int tx0 = (blockIdx.x % tiles_x) * ADMS_TILE, ty0 = (blockIdx.x / tiles_x) * ADMS_TILE;
-    int px = tx0 + (tid & 15), py = ty0 + (tid >> 4);
-    bool inside = px < A.W && py < A.H;
-    size_t pix = inside ? ((size_t)b * A.H + py) * A.W + px : 0;
-    int f = inside ? key_tri(A.keys[pix]) : -1;
+    int x0 = (blockIdx.x % rx) * R, y0 = (blockIdx.x / rx) * R;
     if (tid == 0) count = 0;
-    tri[tid] = f;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int t = tid + 256 * k, px = x0 + (t % R), py = y0 + (t / R);
+        bool inside = px < A.W && py < A.H;
+        tri[t] = inside ? key_tri(A.keys[((size_t)b * A.H + py) * A.W + px]) : -1;
+    }
     __syncthreads();
-    int lead = group_leader(A.msaa, tx0, ty0, px, py, f, tri);
-    if (f >= 0 && lead == tid) list[atomicAdd(&count, 1)] = (short)tid;
+    int lead[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int t = tid + 256 * k, px = x0 + (t % R), py = y0 + (t / R);
+        int f = tri[t];
+        lead[k] = -1;
+        if (f < 0) continue;
+        int sm = A.msaa, ox = (px / sm) * sm, oy = (py / sm) * sm;
+        for (int y = max(oy, y0); y < min(oy + sm, y0 + R) && lead[k] < 0; ++y)
+            for (int x = max(ox, x0); x < min(ox + sm, x0 + R); ++x) {
+                int u = (y - y0) * R + (x - x0);
+                if (tri[u] == f) {
+                    lead[k] = u;
+                    break;
+                }
+            }
+        if (lead[k] == t) list[atomicAdd(&count, 1)] = (short)t;
+    }
     __syncthreads();
     int n = count;
     for (int i = tid; i < n; i += 256) {
         int t = list[i];
-        int sx = tx0 + (t & 15), sy = ty0 + (t >> 4);
+        int sx = x0 + (t % R), sy = y0 + (t / R);
         col[t] = shade_covered(A, b, sx, sy, tri[t], ((size_t)b * A.H + sy) * A.W + sx);
     }
     __syncthreads();
-    if (inside) A.pre[pix] = f >= 0 ? col[lead] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int t = tid + 256 * k, px = x0 + (t % R), py = y0 + (t / R);
+        if (px < A.W && py < A.H)
+            A.pre[((size_t)b * A.H + py) * A.W + px] = lead[k] >= 0 ? col[lead[k]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 }
 
 // MSAA backward: the AA adjoint runs per sample; the shading adjoint of a (pixel,
@@ -1028,8 +1055,12 @@ cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
         cudaError_t e = cudaMemsetAsync(a.refine, 0, sizeof(int), st);
         if (e) return e;
     }
-    if (a.msaa > 1) k_shade_fwd_msaa<<<pix_grid(a), 256, 0, st>>>(a);
-    else k_shade_fwd<<<pix_grid(a), 256, 0, st>>>(a);
+    if (a.msaa > 1) {
+        int R = ADMS_MSAA_REGION;
+        k_shade_fwd_msaa<<<dim3(((a.W + R - 1) / R) * ((a.H + R - 1) / R), a.B), 256, 0, st>>>(a);
+    } else {
+        k_shade_fwd<<<pix_grid(a), 256, 0, st>>>(a);
+    }
     count_launches(1);
     if (a.refine) {
         k_shade_refine<<<128, 256, 0, st>>>(a);
