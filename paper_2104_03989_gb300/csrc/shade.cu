@@ -897,46 +897,64 @@ __global__ void __launch_bounds__(256, 4) k_shade_fwd_msaa(ShadeArgs A) {
     }
 }
 
-// MSAA backward: the AA adjoint runs per sample; the shading adjoint of a (pixel,
-// triangle) group is linear in its colour gradient and its samples share the
-// shading, so the group's leader takes the sum of its samples' gradients (in a
-// fixed order) and the compacted leaders run the adjoint once per group
+// MSAA backward over a 32x32-sample region (four samples per thread): the AA
+// adjoint runs per sample; the shading adjoint of a (pixel, triangle) group is
+// linear in its colour gradient and its samples share the shading, so the group's
+// leader takes the sum of its samples' gradients (in a fixed order) and the
+// compacted leaders run the adjoint once per group
 __global__ void __launch_bounds__(256, 3) k_shade_bwd_msaa(ShadeArgs A) {
-    __shared__ int tri[256];
-    __shared__ float3 gsum[256];
-    __shared__ short list[256];
+    constexpr int R = ADMS_MSAA_REGION, N = R * R, PER = N / 256;
+    __shared__ int tri[N];
+    __shared__ float3 gsum[N];
+    __shared__ short list[N];
     __shared__ int count;
-    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
+    int rx = (A.W + R - 1) / R;
     int b = blockIdx.y, tid = threadIdx.x;
-    int tx0 = (blockIdx.x % tiles_x) * ADMS_TILE, ty0 = (blockIdx.x / tiles_x) * ADMS_TILE;
-    int px = tx0 + (tid & 15), py = ty0 + (tid >> 4);
-    bool inside = px < A.W && py < A.H;
-    int f = -1;
-    float3 gc = zero3();
-    if (inside) {
-        size_t pix = ((size_t)b * A.H + py) * A.W + px;
-        unsigned long long kp = A.keys[pix];
-        f = key_tri(kp);
-        gc = aa_adjoint<false>(A, b, px, py, pix, kp);
-    }
+    int x0 = (blockIdx.x % rx) * R, y0 = (blockIdx.x / rx) * R;
     if (tid == 0) count = 0;
-    tri[tid] = f;
-    gsum[tid] = gc;
-    __syncthreads();
-    int lead = group_leader(A.msaa, tx0, ty0, px, py, f, tri);
-    float3 g = zero3();
-    if (f >= 0 && lead == tid) {
-        int sm = A.msaa, ox = (px / sm) * sm, oy = (py / sm) * sm;
-        for (int y = max(oy, ty0); y < min(oy + sm, ty0 + ADMS_TILE); ++y)
-            for (int x = max(ox, tx0); x < min(ox + sm, tx0 + ADMS_TILE); ++x) {
-                int t = (y - ty0) * ADMS_TILE + (x - tx0);
-                if (tri[t] == f) g += gsum[t];
-            }
+    for (int k = 0; k < PER; ++k) {
+        int t = tid + 256 * k, px = x0 + (t % R), py = y0 + (t / R);
+        int f = -1;
+        float3 gc = zero3();
+        if (px < A.W && py < A.H) {
+            size_t pix = ((size_t)b * A.H + py) * A.W + px;
+            unsigned long long kp = A.keys[pix];
+            f = key_tri(kp);
+            gc = aa_adjoint<false>(A, b, px, py, pix, kp);
+        }
+        tri[t] = f;
+        gsum[t] = gc;
     }
     __syncthreads();
-    if (f >= 0 && lead == tid && (g.x != 0.f || g.y != 0.f || g.z != 0.f)) {
-        gsum[tid] = g;
-        list[atomicAdd(&count, 1)] = (short)tid;
+    // leaders sum their groups (registers first: other leaders still read gsum)
+    float3 g[PER];
+    bool leader[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int t = tid + 256 * k, px = x0 + (t % R), py = y0 + (t / R);
+        int f = tri[t];
+        g[k] = zero3();
+        leader[k] = false;
+        if (f < 0) continue;
+        int sm = A.msaa, ox = (px / sm) * sm, oy = (py / sm) * sm;
+        int first = -1;
+        for (int y = max(oy, y0); y < min(oy + sm, y0 + R); ++y)
+            for (int x = max(ox, x0); x < min(ox + sm, x0 + R); ++x) {
+                int u = (y - y0) * R + (x - x0);
+                if (tri[u] != f) continue;
+                if (first < 0) first = u;
+                g[k] += gsum[u];
+            }
+        leader[k] = first == t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        int t = tid + 256 * k;
+        if (leader[k] && (g[k].x != 0.f || g[k].y != 0.f || g[k].z != 0.f)) {
+            gsum[t] = g[k];
+            list[atomicAdd(&count, 1)] = (short)t;
+        }
     }
     __syncthreads();
     int n = count;
@@ -951,7 +969,7 @@ __global__ void __launch_bounds__(256, 3) k_shade_bwd_msaa(ShadeArgs A) {
         if (i < n) {
             int t = list[i];
             fl = tri[t];
-            shading_adjoint<false>(A, b, tx0 + (t & 15), ty0 + (t >> 4), fl, gsum[t], 0.f, vi, vg);
+            shading_adjoint<false>(A, b, x0 + (t % R), y0 + (t / R), fl, gsum[t], 0.f, vi, vg);
         }
         scatter_vertex_grads(A, fl, vi, vg);
     }
@@ -1075,9 +1093,14 @@ cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st) {
-    if (a.msaa > 1) k_shade_bwd_msaa<<<pix_grid(a), 256, 0, st>>>(a);
-    else if (a.peel) k_shade_bwd<true><<<pix_grid(a), 256, 0, st>>>(a);
-    else k_shade_bwd<false><<<pix_grid(a), 256, 0, st>>>(a);
+    if (a.msaa > 1) {
+        int R = ADMS_MSAA_REGION;
+        k_shade_bwd_msaa<<<dim3(((a.W + R - 1) / R) * ((a.H + R - 1) / R), a.B), 256, 0, st>>>(a);
+    } else if (a.peel) {
+        k_shade_bwd<true><<<pix_grid(a), 256, 0, st>>>(a);
+    } else {
+        k_shade_bwd<false><<<pix_grid(a), 256, 0, st>>>(a);
+    }
     count_launches(1);
     return cudaGetLastError();
 }
