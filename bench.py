@@ -41,10 +41,10 @@ WORKLOAD_AGG = ("aggregate geometry (Sec. 6): reference canopy of 600k opaque le
 # DRAM bytes per launch of the dominant kernel from an ncu capture, valid only
 # for the source it was measured on (sha256 of the listed files).
 TRAFFIC = {
-    "shade_bwd": {"bytes_per_launch": 163421184 + 59897344, "warp_instructions_per_launch": 181182186,
+    "shade_bwd": {"bytes_per_launch": 163115520 + 59575040, "warp_instructions_per_launch": 181182186,
                   "files": ["paper_2104_03989_gb300/csrc/shade.cu", "paper_2104_03989_gb300/csrc/common.cuh",
                             "paper_2104_03989_gb300/csrc/kernels.cuh"],
-                  "sha": "d3d2c573cdd8a692",
+                  "sha": "f6c231a7029c3ad1",
                   "capture": "profiles/shade_bwd_plain_workload.md"},
 }
 

@@ -403,17 +403,17 @@ __device__ __forceinline__ void shade_fwd_px(const ShadeArgs& A, int b, int px, 
 }
 
 // Under MSAA every sample of a pixel that shows one triangle has the same shading
-// (at the pixel's centre, with the pixel's LOD): the (pixel, triangle) groups of a
-// 16x16-sample tile are shaded once each. The group's leader is its first sample in
-// the tile (row-major); tri: the tile's triangle ids (-1: empty or outside).
-__device__ __forceinline__ int group_leader(int sm, int tx0, int ty0, int px, int py, int f, const int* tri) {
+// (at the pixel's centre, with the pixel's LOD), so the (pixel, triangle) groups of
+// an R x R-sample region at (rx0, ry0) are shaded once each. A group's leader is its
+// first sample in the region (row-major); tri: the region's triangle ids (-1: empty
+// or outside); returns the leader's index in the region, -1 for f < 0.
+__device__ __forceinline__ int group_leader(int sm, int rx0, int ry0, int R, int px, int py, int f,
+                                            const int* tri) {
     if (f < 0) return -1;
     int ox = (px / sm) * sm, oy = (py / sm) * sm;
-    int x0 = max(ox, tx0), x1 = min(ox + sm, tx0 + ADMS_TILE);
-    int y0 = max(oy, ty0), y1 = min(oy + sm, ty0 + ADMS_TILE);
-    for (int y = y0; y < y1; ++y)
-        for (int x = x0; x < x1; ++x) {
-            int t = (y - ty0) * ADMS_TILE + (x - tx0);
+    for (int y = max(oy, ry0); y < min(oy + sm, ry0 + R); ++y)
+        for (int x = max(ox, rx0); x < min(ox + sm, rx0 + R); ++x) {
+            int t = (y - ry0) * R + (x - rx0);
             if (tri[t] == f) return t;
         }
     return -1;
@@ -866,19 +866,8 @@ __global__ void __launch_bounds__(256, 4) k_shade_fwd_msaa(ShadeArgs A) {
     int lead[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        int t = tid + 256 * k, px = x0 + (t % R), py = y0 + (t / R);
-        int f = tri[t];
-        lead[k] = -1;
-        if (f < 0) continue;
-        int sm = A.msaa, ox = (px / sm) * sm, oy = (py / sm) * sm;
-        for (int y = max(oy, y0); y < min(oy + sm, y0 + R) && lead[k] < 0; ++y)
-            for (int x = max(ox, x0); x < min(ox + sm, x0 + R); ++x) {
-                int u = (y - y0) * R + (x - x0);
-                if (tri[u] == f) {
-                    lead[k] = u;
-                    break;
-                }
-            }
+        int t = tid + 256 * k;
+        lead[k] = group_leader(A.msaa, x0, y0, R, x0 + (t % R), y0 + (t / R), tri[t], tri);
         if (lead[k] == t) list[atomicAdd(&count, 1)] = (short)t;
     }
     __syncthreads();
