@@ -1139,14 +1139,27 @@ adms_status adms_autotune(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, c
     const int tws[3] = {8, 16, 32};
     float best_total = 1e30f;
     int best_tw = ctx->tune_tw, best_b[4] = {ctx->tune_bpsm[0], ctx->tune_bpsm[1], ctx->tune_bpsm[2], ctx->tune_bpsm[3]};
-    cudaEvent_t ev[2];
-    for (auto& e : ev) CK(cudaEventCreate(&e));
     std::vector<Job*> js;
     for (int k = 0; k < n_jobs; ++k) {
         Job* j = get_job(ctx, jobs[k]);
         if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
         js.push_back(j);
     }
+    // timing events, destroyed on every return path; the tile width is restored
+    // if a timing run fails
+    struct Timing {
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        adms_ctx* ctx;
+        int tw0;
+        bool done = false;
+        ~Timing() {
+            for (auto& e : ev)
+                if (e) cudaEventDestroy(e);
+            if (!done) ctx->tune_tw = tw0;
+        }
+    } timing{{nullptr, nullptr}, ctx, ctx->tune_tw};
+    cudaEvent_t* ev = timing.ev;
+    for (int k = 0; k < 2; ++k) CK(cudaEventCreate(&ev[k]));
     // a forward sizes every job's scratch; then time each kernel at each tile
     // width with one block per item and with persistent grids of occ/2 .. occ
     // resident blocks per SM (second of two runs; every kernel here is
@@ -1194,7 +1207,7 @@ adms_status adms_autotune(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, c
             for (int kk = 0; kk < 3; ++kk) best_b[kk] = b_kind[kk];
         }
     }
-    for (auto& e : ev) cudaEventDestroy(e);
+    timing.done = true;
     ctx->tune_tw = best_tw;
     for (int kk = 0; kk < 4; ++kk) ctx->tune_bpsm[kk] = best_b[kk];
     // leave the jobs as they were: no gradients, no pending forward, no loss recorded

@@ -174,21 +174,25 @@ class SimplificationServer:
         self._fork.record(self.stream)
         for sd in self.sides:
             sd.wait_event(self._fork)
-        for k, rec in enumerate(self.live):
-            r = rec.req
-            v = synth.sample_views(r.seed, rec.it, r.n_views, r.res, r.res)
-            views.append(v)
-            self.ctx.set_stream(self.sides[k % len(self.sides)])
-            self.ctx.render_reference(rec.ref, v, r.res, r.res, out=rec.ref_buf)
-        for sd, ev in zip(self.sides[1:], self._side_evs[1:]):
-            ev.record(sd)
-            self.sides[0].wait_event(ev)
-        self._ready.record(self.sides[0])
-        self.ctx.set_stream(self.stream)
+        try:
+            for k, rec in enumerate(self.live):
+                r = rec.req
+                v = synth.sample_views(r.seed, rec.it, r.n_views, r.res, r.res)
+                views.append(v)
+                self.ctx.set_stream(self.sides[k % len(self.sides)])
+                self.ctx.render_reference(rec.ref, v, r.res, r.res, out=rec.ref_buf)
+        finally:
+            for sd, ev in zip(self.sides[1:], self._side_evs[1:]):
+                ev.record(sd)
+                self.sides[0].wait_event(ev)
+            self._ready.record(self.sides[0])
+            self.ctx.set_stream(self.stream)
         self.ctx.set_ref_event(self._ready)
         jobs = [rec.cand for rec in self.live]
-        loss = self.ctx.forward_loss(jobs, views, [rec.ref_buf for rec in self.live])
-        self.ctx.set_ref_event(None)
+        try:
+            loss = self.ctx.forward_loss(jobs, views, [rec.ref_buf for rec in self.live])
+        finally:
+            self.ctx.set_ref_event(None)
         self.ctx.backward(jobs)
         self.ctx.step(jobs)
         read = (self.live[0].it % self.loss_every) == 0
