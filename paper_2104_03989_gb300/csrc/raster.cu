@@ -186,13 +186,30 @@ __device__ __forceinline__ void test_tri_kbuf(const TriRec& r, int Sx, int Sy, u
     }
 }
 
-// z-buffer update of the direct raster: the key goes in only if it is below the
-// stored one. The stored key only ever decreases, so a read that lags behind
-// other threads' updates is never below the current minimum and can only let an
-// unneeded atomicMin through; in a dense cloud of small triangles (a foliage
-// canopy puts ~160 fragments on each sample) this drops most of the atomics.
-__device__ __forceinline__ void zmin(unsigned long long* a, unsigned long long key) {
-    if (key != ADMS_EMPTY_KEY && key < __ldcg(a)) atomicMin(a, key);
+// z-buffer update of the direct raster, for dense clouds of small triangles (a
+// foliage canopy puts ~160 fragments on each sample). The stored key is read
+// first: zlo is a lower bound on every key the triangle can produce, so when it
+// is above the stored key the sample is skipped without its coverage test; else
+// the key goes in only if it is below the stored one. The stored key only ever
+// decreases, so a read that lags behind other threads' updates is never below the
+// current minimum and can only let an unneeded test or atomicMin through.
+__device__ __forceinline__ void zmin_test(unsigned long long* a, const TriRec& r, int Sx, int Sy,
+                                          unsigned long long zlo) {
+    unsigned long long cur = __ldcg(a);
+    if (zlo > cur) return;
+    unsigned long long key = tri_key(r, Sx, Sy);
+    if (key != ADMS_EMPTY_KEY && key < cur) atomicMin(a, key);
+}
+
+// A lower bound on the keys of a triangle with vertex depths z0, z1, z2: its
+// interpolated depth d = z0 + b1 (z1 - z0) + b2 (z2 - z0) (b1, b2 >= 0, b1 + b2 <= 1,
+// each operation rounded once) is at least min z less a few units of rounding of
+// the largest |z| (1e-6 x max(1, |z|) covers them with room), and a key needs d >= 0.
+__device__ __forceinline__ unsigned long long key_floor(float z0, float z1, float z2) {
+    float zmn = fminf(z0, fminf(z1, z2));
+    float zmx = fmaxf(fabsf(z0), fmaxf(fabsf(z1), fabsf(z2)));
+    float lo = fmaxf(zmn - 1e-6f * fmaxf(1.f, zmx), 0.f);
+    return (unsigned long long)__float_as_uint(lo) << 32;
 }
 
 // the setup record of lane src, for every lane of the warp
@@ -235,7 +252,7 @@ __device__ __forceinline__ TriRec shfl_rec(const TriRec& r, int src) {
 // updates, launched when small_px exceeds ADMS_SMALL_PX; the other keeps the
 // common case (small_px = ADMS_SMALL_PX) to its own registers.
 template <bool COOP>
-__global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restrict__ vs, int V, int B, int W, int H,
+__global__ void __launch_bounds__(256, COOP ? 3 : 1) k_setup(const int* __restrict__ tri, int F, const VtxS* __restrict__ vs, int V, int B, int W, int H,
                         int tiles_x, int tiles_y, TriRec* __restrict__ rec, TriBin* __restrict__ bin,
                         int8_t* __restrict__ asign, int* __restrict__ tile_count, unsigned long long* __restrict__ keys,
                         int small_px) {
@@ -243,6 +260,7 @@ __global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restri
     bool coop = false;  // this lane's triangle goes to the warp-wide direct raster
     TriRec r;
     int b = 0;
+    unsigned long long zlo = 0ull;  // lower bound on the triangle's keys (COOP)
     if (i < B * F) {
         b = i / F;
         int f = i - b * F;
@@ -291,15 +309,19 @@ __global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restri
                     r.by0 = (short)jlo;
                     r.by1 = (short)jhi;
                     long long npx = (ihi - ilo + 1) * (jhi - jlo + 1);
+                    if (COOP) zlo = key_floor(a0.z, a1.z, a2.z);
                     if (COOP && npx <= small_px && npx > ADMS_SMALL_PX) {
                         coop = true;
                     } else if (npx <= small_px) {
                         unsigned long long* kb = keys + (size_t)b * H * W;
                         for (int y = (int)jlo; y <= (int)jhi; ++y)
                             for (int x = (int)ilo; x <= (int)ihi; ++x) {
-                                unsigned long long key = tri_key(r, 256 * x + 128, 256 * y + 128);
-                                if (COOP) zmin(kb + (size_t)y * W + x, key);
-                                else if (key != ADMS_EMPTY_KEY) atomicMin(kb + (size_t)y * W + x, key);
+                                if (COOP) {
+                                    zmin_test(kb + (size_t)y * W + x, r, 256 * x + 128, 256 * y + 128, zlo);
+                                } else {
+                                    unsigned long long key = tri_key(r, 256 * x + 128, 256 * y + 128);
+                                    if (key != ADMS_EMPTY_KEY) atomicMin(kb + (size_t)y * W + x, key);
+                                }
                             }
                     } else {
                         rec[i] = r;
@@ -329,11 +351,12 @@ __global__ void k_setup(const int* __restrict__ tri, int F, const VtxS* __restri
         todo &= todo - 1;
         TriRec t = shfl_rec(r, src);
         int tb_ = __shfl_sync(0xffffffffu, b, src);
+        unsigned long long tlo = __shfl_sync(0xffffffffu, zlo, src);
         int bw = t.bx1 - t.bx0 + 1, n = bw * (t.by1 - t.by0 + 1);
         unsigned long long* kb = keys + (size_t)tb_ * H * W;
         for (int q = lane; q < n; q += 32) {
             int y = t.by0 + q / bw, x = t.bx0 + q - (q / bw) * bw;
-            zmin(kb + (size_t)y * W + x, tri_key(t, 256 * x + 128, 256 * y + 128));
+            zmin_test(kb + (size_t)y * W + x, t, 256 * x + 128, 256 * y + 128, tlo);
         }
     }
 }
