@@ -11,7 +11,8 @@ render per job, then forward + loss, backward and Adam for all live jobs in
 one batched call per stage (one persistent launch per pixel stage). Jobs that
 reach their iteration count retire and free their memory for waiting
 requests. A job whose loss turns non-finite is quarantined (retired with an
-error) without disturbing the others.
+error) without disturbing the others; a cancelled request leaves the queue, or
+retires between iterations, and frees its memory the same way.
 
 All arithmetic runs in libadms.so; this module schedules.
 """
@@ -100,6 +101,26 @@ class SimplificationServer:
 
     def submit(self, req: Request):
         self.queue.append(JobRecord(req))
+
+    def cancel(self, rid):
+        """Cancel request rid between iterations: a waiting request leaves the
+        queue, a live job retires with its latents as of its last step. Returns
+        False when rid is neither waiting nor live."""
+        for rec in list(self.queue):
+            if rec.req.rid == rid:
+                self.queue.remove(rec)
+                rec.status = "cancelled"
+                rec.finished = self._now()
+                self.done.append(rec)
+                self.blocked = False      # the head of the queue may have changed
+                return True
+        for rec in list(self.live):
+            if rec.req.rid == rid:
+                with torch.cuda.stream(self.stream):
+                    self.stream.synchronize()
+                    self._retire(rec, "cancelled")
+                return True
+        return False
 
     def _now(self):
         return time.perf_counter() - self.t0
@@ -238,6 +259,7 @@ class SimplificationServer:
             "done": len(done),
             "quarantined": sum(r.status == "quarantined" for r in self.done),
             "rejected": sum(r.status == "rejected" for r in self.done),
+            "cancelled": sum(r.status == "cancelled" for r in self.done),
             "max_live": self.max_live,
             "wall_s": wall,
         }

@@ -1,8 +1,9 @@
 """The continuous-batching server: a job's result does not depend on when it
 arrives or who shares its batches (views are keyed by the job's own seed and
 iteration; the batched launches keep jobs apart), admission waits for the HBM
-budget, and a job whose loss turns non-finite is quarantined while the others
-finish with unchanged results."""
+budget, a job whose loss turns non-finite is quarantined while the others
+finish with unchanged results, and cancelled requests (waiting or live) free
+their memory without changing the others' results."""
 
 import math
 
@@ -134,5 +135,35 @@ def test_non_finite_job_is_quarantined_and_the_others_are_unchanged(alone):
     assert status[1].status == "quarantined" and status[1].it == 1 and not math.isfinite(status[1].losses[0])
     for rid in (0, 2):
         assert status[rid].status == "done"
+        _same(srv.results[rid], alone[rid])
+    srv.close()
+
+
+def test_cancelled_requests_free_their_memory_and_the_others_are_unchanged(alone):
+    from paper_2104_03989_gb300.serving import SimplificationServer
+    reqs = _requests()
+    srv = SimplificationServer()
+    srv.start()
+    for r in reqs:
+        srv.submit(r)
+    srv.admit()
+    assert len(srv.live) == 3
+    srv.iterate()
+    before = srv.ctx.bytes_in_use()
+    assert srv.cancel(1)                      # a live job, between iterations
+    assert srv.ctx.bytes_in_use() < before
+    assert not srv.cancel(1)
+    waiting = reqs[0].__class__(**{**reqs[0].__dict__, "rid": 9})
+    srv.submit(waiting)
+    assert srv.cancel(9)                      # a request still in the queue
+    while srv.queue or srv.live:
+        srv.admit()
+        srv.iterate()
+    rep = srv.report()
+    assert rep["done"] == 2 and rep["cancelled"] == 2 and rep["quarantined"] == 0
+    status = {r.req.rid: r for r in srv.done}
+    assert status[1].status == "cancelled" and status[1].it == 1
+    assert status[9].status == "cancelled" and status[9].it == 0
+    for rid in (0, 2):
         _same(srv.results[rid], alone[rid])
     srv.close()
