@@ -232,6 +232,92 @@ def test_normal_map_tilts_shading_normal():
     assert np.allclose(col.numpy(), 0.5 / math.pi * float(np.dot(ld, l)), atol=1e-7)
 
 
+# ----------------------------------------------------------------------------- mesh frame
+
+def test_vertex_normals_of_the_icosahedron_point_outwards():
+    """By symmetry each icosahedron vertex normal is its radial direction
+    exactly; on finer geodesic spheres it stays within a fraction of a
+    degree of it. An inward (flipped) cross product gives -p instead."""
+    p, tri = synth.icosphere(1)
+    n = R.vertex_normals(torch.as_tensor(p), torch.as_tensor(tri.astype(np.int64))).numpy()
+    assert np.abs(n - p).max() < 1e-12
+    p, tri = synth.icosphere(8)
+    n = R.vertex_normals(torch.as_tensor(p), torch.as_tensor(tri.astype(np.int64))).numpy()
+    assert (n * p).sum(1).min() > 0.999
+
+
+def test_vertex_normal_weights_faces_by_area():
+    """A vertex shared by a face of area a in the plane z = 0 (normal +z) and a
+    face of area b in the plane x = 0 (normal +x) has the normal
+    normalize(b, 0, a): each unnormalised face normal is 2 x area x unit normal."""
+    a, b = 0.5 * 2.0 * 1.0, 0.5 * 1.0 * 3.0
+    pos = torch.as_tensor([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0], [0.0, 1.0, 0.0],
+                           [0.0, 0.0, -3.0]], dtype=F64)
+    # face 0: (0, 1, 2) counter-clockwise seen from +z; face 1: (0, 3, 2) from +x
+    tri = torch.as_tensor([[0, 1, 2], [0, 3, 2]])
+    n = R.vertex_normals(pos, tri).numpy()
+    want = np.array([b, 0.0, a]) / math.hypot(a, b)
+    assert np.abs(n[0] - want).max() < 1e-15
+    assert np.abs(n[1] - [0, 0, 1]).max() < 1e-15 and np.abs(n[3] - [1, 0, 0]).max() < 1e-15
+
+
+def _planar_quad(flip_u=False, flip_v=False):
+    pos = torch.as_tensor([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [1.0, 1.0, 0.0], [0.0, 1.0, 0.0]], dtype=F64)
+    uv = pos[:, :2].clone()
+    if flip_u:
+        uv[:, 0] = 1.0 - uv[:, 0]
+    if flip_v:
+        uv[:, 1] = 1.0 - uv[:, 1]
+    tri = torch.as_tensor([[0, 1, 2], [0, 2, 3]])
+    return pos, uv, tri
+
+
+@pytest.mark.parametrize("flip_u,flip_v,want", [(False, False, 1.0), (True, False, -1.0),
+                                                (False, True, 1.0), (True, True, -1.0)])
+def test_vertex_tangent_of_a_planar_quad_follows_increasing_u(flip_u, flip_v, want):
+    """u along +x gives the tangent +x exactly and u along -x gives -x; the
+    direction of v does not change it (the tangent is dp/du, not dp/dv)."""
+    pos, uv, tri = _planar_quad(flip_u, flip_v)
+    t = R.vertex_tangents(pos, uv, tri, tri).numpy()
+    assert np.abs(t - np.array([want, 0.0, 0.0])).max() < 1e-15
+
+
+def test_face_tangent_is_the_direction_of_dp_du():
+    """For an affine map of a triangle from uv to positions, the tangent is
+    the normalised dp/du, found here by solving [e1 e2] = [dp/du dp/dv] [d1 d2]
+    with a library solve, for random triangles of either uv orientation."""
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        P = rng.normal(size=(3, 3))
+        T = rng.uniform(0, 1, size=(3, 2))
+        e = np.stack([P[1] - P[0], P[2] - P[0]], 1)       # 3 x 2
+        d = np.stack([T[1] - T[0], T[2] - T[0]], 1)       # 2 x 2
+        J = np.linalg.solve(d.T, e.T).T                   # e = J d, J = [dp/du dp/dv]
+        want = J[:, 0] / np.linalg.norm(J[:, 0])
+        tri = torch.as_tensor([[0, 1, 2]])
+        got = R.vertex_tangents(torch.as_tensor(P), torch.as_tensor(T), tri, tri).numpy()
+        for k in range(3):
+            assert np.abs(got[k] - want).max() < 1e-9
+
+
+def test_vertex_tangents_of_the_equirectangular_sphere_follow_longitude():
+    """u = atan2(z, x) / 2 pi + 1/2 increases with longitude, so dp/du is along
+    (-z, 0, x): the vertex tangents of a fine geodesic sphere lie within a few
+    degrees of it away from the poles, and nearly perpendicular to the normals."""
+    p, tri = synth.icosphere(16)
+    uv, tri_uv = synth.equirect_uv_corners(p, tri)
+    pos = torch.as_tensor(p)
+    t = R.vertex_tangents(pos, torch.as_tensor(uv.astype(np.float64)), torch.as_tensor(tri.astype(np.int64)),
+                          torch.as_tensor(tri_uv.astype(np.int64))).numpy()
+    n = R.vertex_normals(pos, torch.as_tensor(tri.astype(np.int64))).numpy()
+    away = np.abs(p[:, 1]) < 0.9
+    lon = np.stack([-p[:, 2], np.zeros(len(p)), p[:, 0]], 1)
+    lon /= np.linalg.norm(lon, axis=1, keepdims=True)
+    cosang = (t * lon).sum(1)[away]
+    assert cosang.min() > math.cos(math.radians(3.0))
+    assert np.abs((t * n).sum(1)[away]).max() < 0.05
+
+
 # ----------------------------------------------------------------------------- antialiasing
 
 def _aa_setup(tau, W=8, H=4, colour=(0.2, 0.4, 0.8)):
@@ -381,16 +467,30 @@ def test_laplacian_icosahedron_closed_form():
     assert float(R.laplacian_loss(pos, ring, d)) == 0.0
 
 
-def test_lambda_and_lr_schedules():
+def test_lambda_schedule_closed_form_of_the_recursive_reading():
+    """The recursive reading of the schedule after Eq. 5 multiplies the excess
+    over lambda_min by 10^(-k s) at every step s = 1..t, so the product
+    telescopes: lambda_t - lambda_min = (lambda_0 - lambda_min) 10^(-k t (t + 1) / 2)."""
     lam0 = 2.0
     lmin = 0.02 * lam0
     lam = lam0
-    for t in range(1, 4):
-        nxt = R.lambda_schedule(lam, lam0, t)
-        assert nxt == pytest.approx((lam - lmin) * 10 ** (-1e-6 * t) + lmin)
-        assert lmin < nxt < lam
-        lam = nxt
-    assert R.learning_rate(0.01, 5000) == pytest.approx(0.001)
+    got = {}
+    for t in range(1, 3001):
+        lam = R.lambda_schedule(lam, lam0, t)
+        got[t] = lam
+    for t in (1, 2, 1000, 2000, 3000):
+        want = lmin + (lam0 - lmin) * 10.0 ** (-1e-6 * t * (t + 1) / 2)
+        assert got[t] == pytest.approx(want, rel=1e-12)
+    # about 2-3k steps to decay to lambda_min: a tenth of the excess left at t = 1000,
+    # under 1e-4 of it at t = 3000
+    assert (got[1000] - lmin) / (lam0 - lmin) == pytest.approx(10 ** -0.5005, rel=1e-9)
+    assert (got[3000] - lmin) / (lam0 - lmin) < 1e-4
+
+
+def test_learning_rate_schedule_closed_form():
+    """lr_t = lr_0 10^(-0.0002 t) (Sec. 5.3): a tenth every 5000 steps."""
+    assert R.learning_rate(0.01, 5000) == pytest.approx(0.001, rel=1e-12)
+    assert R.learning_rate(0.01, 10000) == pytest.approx(0.0001, rel=1e-12)
     assert R.learning_rate(0.01, 0) == 0.01
 
 
