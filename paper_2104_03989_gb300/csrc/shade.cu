@@ -46,6 +46,8 @@ __device__ __forceinline__ void shade_point(const ShadeArgs& A, int px, int py, 
     }
 }
 
+// LOD = false skips the screen derivatives of uv (the adjoint's second pass).
+template <bool LOD = true>
 __device__ __forceinline__ void pix_geo(const ShadeArgs& A, int b, int px, int py, int f, PixGeo& g) {
     float qx, qy;
     shade_point(A, px, py, qx, qy);
@@ -90,6 +92,7 @@ __device__ __forceinline__ void pix_geo(const ShadeArgs& A, int b, int px, int p
     g.tc.dv = g.duv.y;
     g.tc.du_lo = 0.f;
     g.tc.dv_lo = 0.f;
+    if (!LOD) return;
     // screen derivatives of the perspective-correct barycentrics (texture LOD only)
     float dlx[3] = {(g.d[1].y - g.d[2].y) * ia, (g.d[2].y - g.d[0].y) * ia, (g.d[0].y - g.d[1].y) * ia};
     float dly[3] = {(g.d[2].x - g.d[1].x) * ia, (g.d[0].x - g.d[2].x) * ia, (g.d[1].x - g.d[0].x) * ia};
@@ -246,8 +249,22 @@ __device__ __forceinline__ float3 shade_eval(const adms_view& vw, const ShadeIn&
         g_ns += g_nvr * V;
         g_V += g_nvr * ns;
         g_p -= nrm3_bwd(Vn, g_V);
+        // the frame's adjoint evaluates the frame again from (n_i, t_i, nm) rather than
+        // holding its ~25 values across the lights; the empty asm keeps the compiler
+        // from merging the two evaluations back into one
+        float3 n_i = in.n_i, t_i = in.t_i;
+        float4 nm4 = in.nm;
+        asm volatile("" : "+f"(n_i.x), "+f"(n_i.y), "+f"(n_i.z), "+f"(t_i.x), "+f"(t_i.y), "+f"(t_i.z),
+                     "+f"(nm4.x), "+f"(nm4.y), "+f"(nm4.z));
+        Nn = nrm3(n_i);
+        N = Nn.y;
+        s_tn = dot3(t_i, N);
+        Tn = nrm3(t_i - s_tn * N);
+        T = Tn.y;
+        Bt = cross3(N, T);
+        NSn = nrm3(nm4.x * T + nm4.y * Bt + nm4.z * N);
         float3 g_mm = nrm3_bwd(NSn, g_ns);
-        float3 g_T = in.nm.x * g_mm, g_Bt = in.nm.y * g_mm, g_N = in.nm.z * g_mm;
+        float3 g_T = nm4.x * g_mm, g_Bt = nm4.y * g_mm, g_N = nm4.z * g_mm;
         g_N += cross3(T, g_Bt);
         g_T += cross3(g_Bt, N);
         float3 g_tt = nrm3_bwd(Tn, g_T);
@@ -255,7 +272,7 @@ __device__ __forceinline__ float3 shade_eval(const adms_view& vw, const ShadeIn&
         float g_s = -dot3(N, g_tt);
         g_N += -s_tn * g_tt;
         g_ti += g_s * N;
-        g_N += g_s * in.t_i;
+        g_N += g_s * t_i;
         G->p = g_p;
         G->n_i = nrm3_bwd(Nn, g_N);
         G->t_i = g_ti;
@@ -596,45 +613,35 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
 }
 
 // ------------------------------------------------------------------ backward
-// Scatter 9 per-corner vertex gradients (position, unit normal, unit tangent)
-// for the triangle of each lane; lanes of a warp that share a triangle are
-// summed first, then one lane per value issues a float64 atomic. The 27 sums
-// are a butterfly transpose-reduction: at each of the 5 steps every lane keeps
-// half of its partial sums and trades the other half with its partner, so lane
-// j ends with the sum of value j after 31 shuffles (27 separate warp sums
-// would take 135).
-__device__ __forceinline__ void scatter_vertex_grads(const ShadeArgs& A, int f, const int vi[3], float v[27]) {
-    unsigned todo = __ballot_sync(0xffffffffu, f >= 0);
+// Vertex gradients of the fused backward: every lane of a warp writes the 27 values
+// of its pixel (position, unit normal and unit tangent gradients of the three
+// corners) into its row of a per-warp 32 x 27 shared-memory array; lanes that share
+// a triangle are summed column by column (lane j sums value j over the group, rows in
+// ascending lane order) and one lane per value issues a float64 atomic. The row
+// stride 27 is odd, so the 32 lanes writing one value and the 27 lanes reading one
+// row each touch distinct banks.
+#define ADMS_VROW 27
+__device__ __forceinline__ void scatter_vertex_rows(const ShadeArgs& A, int f, const float* rows) {
     int lane = threadIdx.x & 31;
+    __syncwarp();
+    unsigned todo = __ballot_sync(0xffffffffu, f >= 0);
     while (todo) {
         int lead = __ffs(todo) - 1;
         int ft = __shfl_sync(0xffffffffu, f, lead);
-        bool mine = f == ft;
-        unsigned grp = __ballot_sync(0xffffffffu, mine);
-        int v0 = __shfl_sync(0xffffffffu, vi[0], lead), v1 = __shfl_sync(0xffffffffu, vi[1], lead),
-            v2 = __shfl_sync(0xffffffffu, vi[2], lead);
-        float x[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) x[j] = (j < 27 && mine) ? v[j] : 0.f;
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            bool up = (lane & o) != 0;
-#pragma unroll
-            for (int i = 0; i < o; ++i) {
-                float send = up ? x[i] : x[i + o];
-                float keep = up ? x[i + o] : x[i];
-                x[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        unsigned grp = __ballot_sync(0xffffffffu, f == ft);
+        if (lane < ADMS_VROW) {
+            float sum = 0.f;
+            for (unsigned m = grp; m; m &= m - 1) sum += rows[(__ffs(m) - 1) * ADMS_VROW + lane];
+            if (sum != 0.f) {
+                int corner = lane / 9, comp = lane - 9 * corner;
+                int vtx = A.tri[3 * ft + corner];
+                double* dst = comp < 3 ? A.g_pos : (comp < 6 ? A.g_nrm : A.g_tan);
+                atomicAdd(dst + 3 * vtx + comp % 3, (double)sum);
             }
-        }
-        float mineval = x[0];  // the sum of value `lane`
-        if (lane < 27 && mineval != 0.f) {
-            int corner = lane / 9, comp = lane % 9;
-            int vtx = corner == 0 ? v0 : (corner == 1 ? v1 : v2);
-            double* dst = comp < 3 ? A.g_pos : (comp < 6 ? A.g_nrm : A.g_tan);
-            atomicAdd(dst + 3 * vtx + comp % 3, (double)mineval);
         }
         todo &= ~grp;
     }
+    __syncwarp();  // the rows are rewritten by the warp's next pixels
 }
 
 __device__ __forceinline__ void atomic_add3(double* p, float3 v) {
@@ -698,26 +705,131 @@ __device__ __forceinline__ float3 aa_adjoint(const ShadeArgs& A, int b, int px, 
     return gc;
 }
 
+// The three maps share their texel taps when they have the same size (one LOD and
+// one bilinear footprint per level serve all three): the usual case of equally
+// sized latent maps.
+__device__ __forceinline__ bool shared_taps(const ShadeArgs& A) {
+    return A.kd.w0 == A.orm.w0 && A.kd.w0 == A.nrm.w0 && A.kd.h0 == A.orm.h0 && A.kd.h0 == A.nrm.h0 &&
+           A.kd.levels == A.orm.levels && A.kd.levels == A.nrm.levels;
+}
+
+// tex_sample of the three maps with shared taps (the same arithmetic, map by map)
+__device__ __forceinline__ void tex_sample3(const ShadeArgs& A, const TexCoord& tc, float lod, float4 out[3]) {
+    const float4* ts[3] = {A.kd.tex, A.orm.tex, A.nrm.tex};
+    int l0 = (int)floorf(lod);
+    float fr = lod - (float)l0;
+    int l1 = min(l0 + 1, A.kd.levels - 1);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) out[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        int k = s == 0 ? l0 : l1;
+        float wl = s == 0 ? 1.f - fr : fr;
+        if (wl == 0.f) continue;
+        BilinTap b = bilin_tap(A.kd, k, tc);
+        float w00 = wl * (1.f - b.fx) * (1.f - b.fy), w10 = wl * b.fx * (1.f - b.fy);
+        float w01 = wl * (1.f - b.fx) * b.fy, w11 = wl * b.fx * b.fy;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            out[m] = f4madd(out[m], w00, __ldg(ts[m] + b.idx[0]));
+            out[m] = f4madd(out[m], w10, __ldg(ts[m] + b.idx[1]));
+            out[m] = f4madd(out[m], w01, __ldg(ts[m] + b.idx[2]));
+            out[m] = f4madd(out[m], w11, __ldg(ts[m] + b.idx[3]));
+        }
+    }
+}
+
+// adjoint of tex_sample3: the texel gradients of the optimized maps are scattered,
+// d/d(u, v) of g[0] . kd + g[1] . orm + g[2] . nm returned
+__device__ __forceinline__ float2 tex_sample3_bwd(const ShadeArgs& A, const TexCoord& tc, float lod, const float4 g[3]) {
+    const float4* ts[3] = {A.kd.tex, A.orm.tex, A.nrm.tex};
+    float4* gs[3] = {A.kd.grad, A.orm.grad, A.nrm.grad};
+    int l0 = (int)floorf(lod);
+    float fr = lod - (float)l0;
+    int l1 = min(l0 + 1, A.kd.levels - 1);
+    float2 guv = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        int k = s == 0 ? l0 : l1;
+        float wl = s == 0 ? 1.f - fr : fr;
+        if (wl == 0.f) continue;
+        BilinTap b = bilin_tap(A.kd, k, tc);
+        float w00 = wl * (1.f - b.fx) * (1.f - b.fy), w10 = wl * b.fx * (1.f - b.fy);
+        float w01 = wl * (1.f - b.fx) * b.fy, w11 = wl * b.fx * b.fy;
+        float gfx = 0.f, gfy = 0.f;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            float4 t00 = __ldg(ts[m] + b.idx[0]), t10 = __ldg(ts[m] + b.idx[1]);
+            float4 t01 = __ldg(ts[m] + b.idx[2]), t11 = __ldg(ts[m] + b.idx[3]);
+            gfx += dot4(g[m], f4madd(f4scale(f4sub(t10, t00), 1.f - b.fy), b.fy, f4sub(t11, t01)));
+            gfy += dot4(g[m], f4madd(f4scale(f4sub(t01, t00), 1.f - b.fx), b.fx, f4sub(t11, t10)));
+            if (gs[m]) {
+                atomicAdd(gs[m] + b.idx[0], f4scale(g[m], w00));
+                atomicAdd(gs[m] + b.idx[1], f4scale(g[m], w10));
+                atomicAdd(gs[m] + b.idx[2], f4scale(g[m], w01));
+                atomicAdd(gs[m] + b.idx[3], f4scale(g[m], w11));
+            }
+        }
+        guv.x += wl * gfx * b.sw;
+        guv.y += wl * gfy * b.sh;
+    }
+    return guv;
+}
+
 // shading adjoint of triangle f at sample (px, py) for dL/d(colour) gc (and, for a
 // peeled layer, dL/d(opacity) g_alpha): texel gradients scattered here, the three
-// corners' position / normal / tangent gradients returned in vi, vg
+// corners' position / normal / tangent gradients written to vrow[27] (corner k at
+// 9k: position xyz, normal xyz, tangent xyz). The geometry is evaluated twice, once
+// for the shading inputs and once after the BRDF and texture adjoints for the
+// barycentric adjoint, so that nothing of it stays live across them.
 template <bool PEEL>
 __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int px, int py, int f, float3 gc,
-                                                float g_alpha, int vi[3], float vg[27]) {
+                                                float g_alpha, float* vrow) {
     const adms_view& vw = A.views[b];
     float hW = 0.5f * (float)A.W, hH = 0.5f * (float)A.H;
-    PixGeo g;
-    pix_geo(A, b, px, py, f, g);
+    bool shared = shared_taps(A);
+    TexCoord tc;
     float lod[3];
-    ShadeIn in = shade_inputs(A, g, lod);
     ShadeGrad G;
-    shade_eval<true>(vw, in, gc, &G);
+    {
+        PixGeo g;
+        pix_geo<true>(A, b, px, py, f, g);
+        ShadeIn in;
+        in.p = g.p;
+        in.n_i = g.n;
+        in.t_i = g.t;
+        if (shared) {
+            lod[0] = lod[1] = lod[2] = tex_lod(A.kd, g.duv_dx, g.duv_dy);
+            float4 smp[3];
+            tex_sample3(A, g.tc, lod[0], smp);
+            in.kd = smp[0];
+            in.orm = smp[1];
+            in.nm = smp[2];
+        } else {
+            lod[0] = tex_lod(A.kd, g.duv_dx, g.duv_dy);
+            lod[1] = tex_lod(A.orm, g.duv_dx, g.duv_dy);
+            lod[2] = tex_lod(A.nrm, g.duv_dx, g.duv_dy);
+            in.kd = tex_sample(A.kd, g.tc, lod[0]);
+            in.orm = tex_sample(A.orm, g.tc, lod[1]);
+            in.nm = tex_sample(A.nrm, g.tc, lod[2]);
+        }
+        tc = g.tc;
+        shade_eval<true>(vw, in, gc, &G);
+    }
     if (PEEL) G.kd.w = g_alpha;  // the opacity is the base colour's fourth channel
-    float2 guv = tex_sample_bwd(A.kd, g.tc, lod[0], G.kd);
-    float2 g2 = tex_sample_bwd(A.orm, g.tc, lod[1], G.orm);
-    float2 g3 = tex_sample_bwd(A.nrm, g.tc, lod[2], G.nm);
-    guv.x += g2.x + g3.x;
-    guv.y += g2.y + g3.y;
+    float2 guv;
+    if (shared) {
+        float4 gt[3] = {G.kd, G.orm, G.nm};
+        guv = tex_sample3_bwd(A, tc, lod[0], gt);
+    } else {
+        guv = tex_sample_bwd(A.kd, tc, lod[0], G.kd);
+        float2 g2 = tex_sample_bwd(A.orm, tc, lod[1], G.orm);
+        float2 g3 = tex_sample_bwd(A.nrm, tc, lod[2], G.nm);
+        guv.x += g2.x + g3.x;
+        guv.y += g2.y + g3.y;
+    }
+    PixGeo g;
+    pix_geo<false>(A, b, px, py, f, g);
     // interpolation: attr = sum_k beta_k attr_k, beta_k = r_k / R  =>  d attr / d r_j = (attr_j - attr) / R
     float gr[3];
     {
@@ -738,7 +850,6 @@ __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int p
     float glam[3], gw[3], sgl = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        vi[k] = g.vi[k];
         glam[k] = gr[k] / g.c[k].w;
         gw[k] = -gr[k] * g.r[k] / g.c[k].w;
         sgl += glam[k] * g.lam[k];
@@ -759,27 +870,25 @@ __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int p
         gcl.w += gw[k];
         float3 gpk = g.beta[k] * G.p + clip_to_pos_grad(vw.mvp, gcl);
         float3 gnk = g.beta[k] * G.n_i, gtk = g.beta[k] * G.t_i;
-        vg[9 * k + 0] = gpk.x;
-        vg[9 * k + 1] = gpk.y;
-        vg[9 * k + 2] = gpk.z;
-        vg[9 * k + 3] = gnk.x;
-        vg[9 * k + 4] = gnk.y;
-        vg[9 * k + 5] = gnk.z;
-        vg[9 * k + 6] = gtk.x;
-        vg[9 * k + 7] = gtk.y;
-        vg[9 * k + 8] = gtk.z;
+        float* r = vrow + 9 * k;
+        r[0] = gpk.x;
+        r[1] = gpk.y;
+        r[2] = gpk.z;
+        r[3] = gnk.x;
+        r[4] = gnk.y;
+        r[5] = gnk.z;
+        r[6] = gtk.x;
+        r[7] = gtk.y;
+        r[8] = gtk.z;
     }
 }
 
-// one pixel of the fused backward; warp-collective (vertex scatter)
+// one pixel of the fused backward; warp-collective (vertex scatter). rows: the
+// warp's 32 x 27 floats of shared memory
 template <bool PEEL = false>
-__device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, int py) {
+__device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, int py, float* rows) {
     bool inside = px < A.W && py < A.H;
     int f = -1;
-    int vi[3] = {0, 0, 0};
-    float vg[27];
-#pragma unroll
-    for (int j = 0; j < 27; ++j) vg[j] = 0.f;
     if (inside) {
         size_t pix = ((size_t)b * A.H + py) * A.W + px;
         unsigned long long kp = A.keys[pix];
@@ -799,11 +908,11 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
             gc = pr.w * gc;
         }
         if (f >= 0 && (gc.x != 0.f || gc.y != 0.f || gc.z != 0.f || g_alpha != 0.f))
-            shading_adjoint<PEEL>(A, b, px, py, f, gc, g_alpha, vi, vg);
+            shading_adjoint<PEEL>(A, b, px, py, f, gc, g_alpha, rows + (threadIdx.x & 31) * ADMS_VROW);
         else
             f = -1;
     }
-    scatter_vertex_grads(A, f, vi, vg);
+    scatter_vertex_rows(A, f, rows);
 }
 
 // ------------------------------------------------------------------ single-job kernels (16x16 tiles)
@@ -831,13 +940,16 @@ __global__ void __launch_bounds__(256, 8) k_aa_loss(ShadeArgs A) {
                   (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4), red);
 }
 
-// three blocks per SM: 85 registers per thread; the spills cost less than the
-// gather latency the extra resident warps hide (0.289 -> 0.265 ms per step)
+// resident blocks per SM of the fused backward (register cap 65536 / (256 x this))
+#ifndef ADMS_BWD_BLOCKS
+#define ADMS_BWD_BLOCKS 3
+#endif
 template <bool PEEL>
-__global__ void __launch_bounds__(256, 3) k_shade_bwd(ShadeArgs A) {
+__global__ void __launch_bounds__(256, ADMS_BWD_BLOCKS) k_shade_bwd(ShadeArgs A) {
+    __shared__ float rows[8 * 32 * ADMS_VROW];
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
     shade_bwd_px<PEEL>(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
-                 (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
+                       (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4), rows + (threadIdx.x >> 5) * 32 * ADMS_VROW);
 }
 
 // MSAA forward: a block takes a 32x32-sample region (four samples per thread), its
@@ -897,6 +1009,7 @@ __global__ void __launch_bounds__(256, 3) k_shade_bwd_msaa(ShadeArgs A) {
     __shared__ float3 gsum[N];
     __shared__ short list[N];
     __shared__ int count;
+    __shared__ float rows[8 * 32 * ADMS_VROW];
     int rx = (A.W + R - 1) / R;
     int b = blockIdx.y, tid = threadIdx.x;
     int x0 = (blockIdx.x % rx) * R, y0 = (blockIdx.x / rx) * R;
@@ -951,16 +1064,13 @@ __global__ void __launch_bounds__(256, 3) k_shade_bwd_msaa(ShadeArgs A) {
     for (int base = tid & ~31; base < n; base += 256) {
         int i = base + (tid & 31);
         int fl = -1;
-        int vi[3] = {0, 0, 0};
-        float vg[27];
-#pragma unroll
-        for (int j = 0; j < 27; ++j) vg[j] = 0.f;
+        float* wrows = rows + (tid >> 5) * 32 * ADMS_VROW;
         if (i < n) {
             int t = list[i];
             fl = tri[t];
-            shading_adjoint<false>(A, b, x0 + (t % R), y0 + (t / R), fl, gsum[t], 0.f, vi, vg);
+            shading_adjoint<false>(A, b, x0 + (t % R), y0 + (t / R), fl, gsum[t], 0.f, wrows + (tid & 31) * ADMS_VROW);
         }
-        scatter_vertex_grads(A, fl, vi, vg);
+        scatter_vertex_rows(A, fl, wrows);
     }
 }
 
@@ -989,13 +1099,14 @@ template <int KIND>
 __global__ void __launch_bounds__(256, KIND == 2 ? 3 : (KIND == 1 ? 8 : 5))
     k_pixels_batch(const ShadeBatch P, const WorkItem* __restrict__ items, int n, int tw, int job0) {
     __shared__ double red[8];
+    __shared__ float rows[KIND == 2 ? 8 * 32 * ADMS_VROW : 1];
     for (int it = blockIdx.x; it < n; it += gridDim.x) {
         WorkItem w = items[it];
         const ShadeArgs& A = P.a[w.job - job0];
         int px = w.x0 + (int)threadIdx.x % tw, py = w.y0 + (int)threadIdx.x / tw;
         if (KIND == 0) shade_fwd_px(A, w.view, px, py);
         else if (KIND == 1) aa_loss_block(A, w.view, px, py, red);
-        else shade_bwd_px(A, w.view, px, py);
+        else shade_bwd_px(A, w.view, px, py, rows + (threadIdx.x >> 5) * 32 * ADMS_VROW);
     }
 }
 
