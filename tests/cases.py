@@ -65,6 +65,64 @@ def oracle_reference(scene, views, H, W):
     return img.numpy().astype(np.float32), keys
 
 
+def unambiguous_inputs(scene, views, refs, H, W, loss, texel_margin=2e-6, tries=16):
+    """The candidate scene with its UV corners shifted by (k, k) 1e-3 for the first
+    k at which no texture lookup of the oracle's render lies within `texel_margin`
+    texel of a bilinear cell boundary (u wraps; v clamps at the poles on both
+    sides alike), and the references with the L1 kinks of that render removed
+    (unkinked_reference).
+
+    A lookup that close to a cell boundary has no unique uv-derivative at float32
+    resolution (the float32 texture coordinate carries up to ~1e-6 texel of
+    rounding on these cases): the GPU and the float64 oracle may take different
+    one-sided derivatives there, both valid. On the returned inputs every such
+    decision is the same at either precision, so gradients can be compared as
+    whole vectors."""
+    import dataclasses
+
+    for k in range(tries):
+        mesh = scene.mesh
+        uv = mesh.uv.copy()
+        uv += np.float32(k * 1e-3)
+        sc = dataclasses.replace(scene, mesh=dataclasses.replace(mesh, uv=uv))
+        job = S.OracleJob(sc, loss=loss)
+        diags = []
+        with torch.no_grad():
+            S.render(job, job.params, views, H, W, diags=diags)
+        if min(float(dg["texel_margin"].min()) for dg in diags if len(dg["texel_margin"])) > texel_margin:
+            return sc, unkinked_reference(sc, views, refs, H, W, loss)
+    raise AssertionError("no u shift keeps every lookup away from the cell boundaries")
+
+
+def unkinked_reference(scene, views, refs, H, W, loss, step=1e-3):
+    """The reference images with every channel whose loss residual against the
+    oracle's candidate image x lies within LOSS_MARGIN of the L1 kink set to
+    x - step (x + step where that would be negative): `step` away from x in
+    radiance, so that the residual's sign is the same at float32 and float64.
+
+    At such a channel |f(x) - f(y)| has no unique derivative at float32
+    resolution: the GPU's float32 image and the oracle's float64 one can fall on
+    opposite sides, and a whole-vector gradient comparison would mix two valid
+    subgradients. Both sides are then run on these references. L2 has no kink:
+    refs are returned as is."""
+    from oracle import render as R
+
+    refs = np.array(refs, dtype=np.float32, copy=True)
+    if loss == "l2":
+        return refs
+    job = S.OracleJob(scene, loss=loss)
+    with torch.no_grad():
+        img = S.render(job, job.params, views, H, W)["img"].numpy()
+    x, y = torch.as_tensor(img), torch.as_tensor(refs.astype(np.float64))
+    if loss == "logl1":
+        x, y = R.tonemap(x), R.tonemap(y)
+    r = (x - y).numpy()
+    close = (np.abs(r) < LOSS_MARGIN) & (r != 0)
+    below = img - step
+    refs[close] = np.where(below[close] >= 0, below[close], img[close] + step).astype(np.float32)
+    return refs
+
+
 def chain_levels(chain, h, w, levels):
     """Split a texture's mip chain (total_texels, 4), level after level, into
     per-level (h_k, w_k, 4) arrays."""
@@ -199,8 +257,9 @@ def assert_grads_match(got, orc, label, tol=1e-3):
     """Per latent within `tol` relative L2 of the oracle. Vertex gradients touched
     by a pixel sitting on a kink of the forward (texel-cell boundary, n.l = 0, AA
     crossing thresholds, L1 sign) are one-sided and not unique: those vertices
-    are held to a validity bar (each within 50% of the oracle's one-sided value,
-    the whole vector within 1e-2) and all others to `tol`."""
+    are additionally held to a validity bar (each within 50% of the oracle's
+    one-sided value). The whole vector, those vertices included, is held to
+    `tol`, and so is the vector of all other vertices."""
     for name, want in orc["grads"].items():
         g = got[name]
         assert np.linalg.norm(want) > 0, name
@@ -213,7 +272,7 @@ def assert_grads_match(got, orc, label, tol=1e-3):
                   f"of all {rel_l2(g, want):.3e}")
             for v in np.nonzero(amb)[0]:
                 assert np.linalg.norm(g[v] - want[v]) <= 0.5 * np.linalg.norm(want[v]) + 1e-3 * np.abs(want).max()
-            assert rel_l2(g, want) < 1e-2
+            assert rel_l2(g, want) < tol, f"{label} {name}: rel L2 of all vertices {rel_l2(g, want):.3e}"
         else:
             err = rel_l2(g, want)
         assert err < tol, f"{label} {name}: rel L2 {err:.3e}"
