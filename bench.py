@@ -144,7 +144,7 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- algorithmic bytes model
 def algorithmic_bytes(stage, w):
-    """Compulsory DRAM bytes of one step's launches of `stage` (bytes model).
+    """Compulsory DRAM bytes of one step's launches of `stage` (the algorithmic bytes model).
 
     w: dict with P (pixels/step; samples/step under MSAA), C (covered candidate
     pixels or samples, summed over depth-peeling layers), Cr (covered reference

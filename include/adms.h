@@ -320,11 +320,11 @@ adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
 /* ---- batched jobs ------------------------------------------------------------- */
 
 /* adms_forward_loss and adms_backward with n_jobs > 1 run the per-pixel stages
- * (tile raster, shading, AA + loss, fused backward) as one persistent launch
- * each over (job, view, tile) work items of every job, whatever their meshes,
- * textures, view counts and resolutions. Block k of a launch takes items k,
- * k + grid, ...; the grid is SMs x blocks per SM, at most the resident count
- * (persistent), or one block per item (blocks per SM = 0). adms_autotune
+ * (tile raster, shading, AA + loss, fused backward) as one launch each over
+ * (job, view, tile) work items of every job, whatever their meshes, textures,
+ * view counts and resolutions. The default grid is one block per item; a
+ * persistent grid (block k takes items k, k + grid, ...; SMs x blocks per SM
+ * blocks, at most the resident count) is the other choice. adms_autotune
  * times those launches on the given batch for tile widths 8, 16, 32 pixels
  * (tiles of 256 pixels) with one block per item and with half the resident
  * blocks per SM up to all of them, and keeps the fastest choice. It leaves the
@@ -358,7 +358,8 @@ adms_status adms_ctx_set_tuning(adms_ctx* ctx, const int32_t* in5);
  * this library holds until the process exits. It must hold
  *   n_views * n_verts * 48 + n_views * n_tris * 106 + n_tris * 12
  *   + tiles * 28 bytes (tiles = n_views * ceil(W/16) * ceil(H/16)), plus
- * 256-byte rounding per part; larger problems return ADMS_ERR_ARG. Tile lists
+ * 256-byte rounding per part; larger problems return ADMS_ERR_ARG, decided with
+ * overflow-checked arithmetic before any CUDA call. Tile lists
  * use whatever space is left; a tile whose list does not fit scans every
  * triangle, with the same keys. The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current:

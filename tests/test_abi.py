@@ -44,3 +44,23 @@ def test_binding_covers_every_declared_symbol(libpath):
 
     assert set(declared_symbols()) <= set(binding.SIGNATURES)
     binding.lib()  # loads without touching a GPU
+
+
+@pytest.mark.parametrize("n_verts,n_tris,n_views,H,W", [
+    (2**31 - 1, 1, 2**31 - 1, 16, 16),        # views x vertices x 16 B wraps a 64-bit size
+    (3, 2**31 - 1, 2**31 - 1, 16, 16),        # views x triangles x 96 B wraps
+    (3, 1 << 20, 100, 16, 16),                 # no wrap, far beyond the 32 MiB array
+    (3, 1, 2**31 - 1, 16384, 16384),           # tiles of the views alone exceed it
+])
+def test_noalloc_refuses_oversized_requests_before_any_cuda_call(libpath, n_verts, n_tris, n_views, H, W):
+    """adms_visibility_noalloc sizes its scratch with checked arithmetic before it
+    touches CUDA, so requests whose size products overflow, or do not fit, are
+    refused with ADMS_ERR_ARG on the host (here: a machine without a GPU; the
+    pointers are never dereferenced)."""
+    lib = ctypes.CDLL(libpath)
+    f = lib.adms_visibility_noalloc
+    P = ctypes.c_void_p
+    f.argtypes = [P, ctypes.c_int32, P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P]
+    f.restype = ctypes.c_int
+    dummy = P(16)
+    assert f(dummy, n_verts, dummy, n_tris, dummy, n_views, H, W, dummy, None) == -1   # ADMS_ERR_ARG
