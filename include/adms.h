@@ -340,6 +340,161 @@ adms_status adms_ctx_tuning(adms_ctx* ctx, int32_t* out5);
  * recorded into a graph keep the choices they were recorded with. */
 adms_status adms_ctx_set_tuning(adms_ctx* ctx, const int32_t* in5);
 
+/* ---- per-stage calls -------------------------------------------------------------
+ *
+ * The renderer as separate differentiable primitives, each with its adjoint, for
+ * an autograd system that chains them (Sec. 5.2 builds the renderer from a
+ * rasterizer, attribute interpolation, filtered texture lookups and an
+ * antialiasing pass; Sec. 3 differentiates the image loss through all of them):
+ *
+ *   frame   (Sec. 5.1)      positions -> unit smooth vertex normals and tangents
+ *   setup   (Sec. 5.2)      positions -> clip coordinates (+ triangle setup, tile bins)
+ *   raster  (Sec. 5.2)      -> visibility keys, perspective-correct barycentrics
+ *   shade   (Sec. 5.2)      barycentrics, vertex attributes, textures -> colour
+ *   aa_loss (Sec. 5.2, 5.3) silhouette antialiasing and the image loss
+ *
+ * The arithmetic is the step calls' own; the one difference is that raster hands
+ * shade its barycentrics as a buffer, so that dL/d(barycentrics) -> dL/d(clip)
+ * (raster_bwd) and dL/d(colour) -> texels, vertex attributes and dL/d(barycentrics)
+ * (shade_bwd) are separate calls. One sample per pixel, opaque meshes, the same
+ * readings as the step calls. Stateless: every pointer is the caller's device
+ * memory on the current device, nothing is allocated and nothing is kept between
+ * calls; work is enqueued on cuda_stream (NULL: legacy default stream) and the
+ * calls return before it runs. Gradient outputs marked "+=" are accumulated into
+ * (the caller zeroes them); the others are overwritten. ADMS_ERR_ARG for null
+ * pointers, non-positive or > 16384 image sizes, textures that are not power-of-
+ * two mip chains, or a workspace that is too small or not 256-byte aligned;
+ * ADMS_ERR_CUDA when a launch fails.
+ *
+ * Workspace: setup_fwd writes the views' screen positions, triangle setup
+ * records, tile lists and silhouette masks into `work` (adms_stage_workspace_bytes,
+ * 256-byte aligned). raster_fwd, raster_bwd, aa_loss_fwd and aa_loss_bwd read
+ * them: pass the same workspace after a setup_fwd of the same positions, views
+ * and sizes. Tiles whose triangle list does not fit it scan every triangle of
+ * their view (same keys, slower). */
+typedef struct {
+    int32_t n_verts, n_uv, n_tris;
+    const float* pos;       /* [V][3] render positions */
+    const float* uv;        /* [T][2] UV corners */
+    const int32_t* tri;     /* [F][3] position indices */
+    const int32_t* tri_uv;  /* [F][3] UV indices */
+    const int32_t* adj;     /* [F][3] face across edge (tri[f][k], tri[f][(k+1)%3]), -1 if none (adms_mesh_topology) */
+    const int32_t* vf_off;  /* [V+1] vertex -> incident faces, CSR offsets (adms_mesh_topology) */
+    const int32_t* vf_face; /* [vf_off[V]] incident faces, ascending per vertex */
+} adms_stage_mesh;
+
+/* A texture with its whole mip chain: float32 texels of 4 channels, level k
+ * ([max(h>>k,1)][max(w>>k,1)][4]) right after level k-1; h, w powers of two,
+ * 1 <= levels <= the full chain. */
+typedef struct {
+    const float* tex;  /* device, the chain */
+    float* grad;       /* device, same layout, += in shade_bwd; NULL: no texel gradient */
+    int32_t h, w, levels;
+} adms_stage_texture;
+
+/* Host helper (Sec. 3: the topology is fixed during optimization): the edge
+ * adjacency adj [F][3] and the vertex -> face CSR (vf_off [V+1], vf_face [3F],
+ * faces ascending) of a triangle list; all host memory, caller-owned. An edge
+ * shared by more than two faces counts as open (-1). ADMS_ERR_ARG for an index
+ * outside [0, n_verts). */
+adms_status adms_mesh_topology(const int32_t* tri, int32_t n_verts, int32_t n_tris, int32_t* adj, int32_t* vf_off,
+                               int32_t* vf_face);
+/* Bytes of workspace for the setup / raster / aa_loss calls of one problem, with
+ * room for list_entries (>= 4) tile-list entries; 0 for invalid sizes. */
+size_t adms_stage_workspace_bytes(int32_t n_verts, int32_t n_tris, int32_t n_views, int32_t H, int32_t W,
+                                  int64_t list_entries);
+
+/* Sec. 5.1, smooth normals and tangents, recomputed from the positions: vertex
+ * normal = normalised sum of the unnormalised face normals, vertex tangent =
+ * normalised sum of sign(det duv) normalize(e1 dv2 - e2 dv1) over the faces.
+ * Outputs [V][4] (fourth component 0): vpos4 = the positions, vnrm4, vtan4. */
+adms_status adms_frame_fwd(const adms_stage_mesh* mesh, float* vpos4, float* vnrm4, float* vtan4, void* cuda_stream);
+/* Adjoint of adms_frame_fwd: g_pos [V][3] += dL/dpos from dL/d(vpos4 xyz)
+ * (g_vpos [V][3] float64, read and then zeroed), dL/d(vnrm4 xyz) and
+ * dL/d(vtan4 xyz) (g_vnrm, g_vtan [V][3] float64); tmp: [2V][4] float scratch. */
+adms_status adms_frame_bwd(const adms_stage_mesh* mesh, double* g_vpos, const double* g_vnrm, const double* g_vtan,
+                           float* g_pos, float* tmp, void* cuda_stream);
+
+/* Sec. 5.2, vertex transform and triangle setup of n_views views at H x W: clip
+ * [B][V][4] = mvp [x y z 1]^T in float32 (fixed operation order, no FMA: the
+ * bit-exact visibility contract), and into the workspace the snapped 8-bit
+ * sub-pixel positions, the double-float screen positions used for shading, the
+ * setup records, tile bins and the silhouette masks (an edge is a silhouette
+ * edge in a view when it has one face or its faces' snapped areas differ in
+ * sign). views: device [B]. */
+adms_status adms_setup_fwd(const adms_stage_mesh* mesh, const adms_view* views, int32_t n_views, int32_t H, int32_t W,
+                           float* clip, void* work, size_t work_bytes, void* cuda_stream);
+/* Adjoint of the transform: g_pos [V][3] += sum over views of mvp[:, :3]^T
+ * g_clip (g_clip: [B][V][4] float64). */
+adms_status adms_setup_bwd(const adms_view* views, int32_t n_views, int32_t n_verts, const double* g_clip,
+                           float* g_pos, void* cuda_stream);
+
+/* Sec. 5.2 rasterization: keys [B][H][W] (as adms_job_keys: depth bits << 32 |
+ * triangle id, minimum per pixel, all ones when empty; top-left fill rule on the
+ * snapped positions), and for each covered pixel the perspective-correct
+ * barycentrics of corners 1 and 2, rast [B][H][W][2], and their screen
+ * derivatives d/dx b1, d/dx b2, d/dy b1, d/dy b2, rast_db [B][H][W][4] (texture
+ * LOD only); zeros at empty pixels. clip: adms_setup_fwd's output. keep_keys = 1:
+ * keys and rast_db are inputs, read and not written (visibility and texture LOD
+ * held fixed while the positions move, as the adjoints assume, e.g. for finite
+ * differences); 0: both are computed. */
+adms_status adms_raster_fwd(const adms_stage_mesh* mesh, const adms_view* views, int32_t n_views, int32_t H, int32_t W,
+                            const float* clip, uint64_t* keys, int32_t keep_keys, float* rast, float* rast_db,
+                            void* work, size_t work_bytes, void* cuda_stream);
+/* Adjoint of the barycentrics (the keys are piecewise constant in the positions
+ * and have none; the visibility gradient is aa_loss_bwd's): g_clip [B][V][4]
+ * float64 += dL/d(clip) from g_rast [B][H][W][2] = dL/d(rast). */
+adms_status adms_raster_bwd(const adms_stage_mesh* mesh, const adms_view* views, int32_t n_views, int32_t H, int32_t W,
+                            const float* clip, const uint64_t* keys, const float* g_rast, double* g_clip, void* work,
+                            size_t work_bytes, void* cuda_stream);
+
+/* Sec. 5.2 shading of every covered pixel: position, normal, tangent and uv
+ * interpolated at (1 - b1 - b2, b1, b2) from vpos4 / vnrm4 / vtan4 [V][4] and the
+ * UV corners; trilinear lookups of maps[0] base colour, maps[1] (gamma, r, m),
+ * maps[2] tangent-space normal at the LOD of the uv footprint (u wraps, v
+ * clamps); normal mapping and diffuse + GGX under the view's lights (the
+ * readings of adms_forward_loss). pre [B][H][W][4]: colour, 1 (0 when empty). */
+adms_status adms_shade_fwd(const adms_stage_mesh* mesh, const adms_view* views, int32_t n_views, int32_t H, int32_t W,
+                           const uint64_t* keys, const float* rast, const float* rast_db, const float* vpos4,
+                           const float* vnrm4, const float* vtan4, const adms_stage_texture* maps, float* pre,
+                           void* cuda_stream);
+/* Adjoint of adms_shade_fwd for g_pre [B][H][W][4] = dL/d(pre) (fourth channel
+ * ignored; the LOD held fixed): maps[i].grad += the texel gradients (whole chain),
+ * g_vpos, g_vnrm, g_vtan [V][3] float64 += dL/d(vpos4, vnrm4, vtan4 xyz), and
+ * g_rast [B][H][W][2] = dL/d(rast). */
+adms_status adms_shade_bwd(const adms_stage_mesh* mesh, const adms_view* views, int32_t n_views, int32_t H, int32_t W,
+                           const uint64_t* keys, const float* rast, const float* rast_db, const float* vpos4,
+                           const float* vnrm4, const float* vtan4, const adms_stage_texture* maps, const float* g_pre,
+                           double* g_vpos, double* g_vnrm, double* g_vtan, float* g_rast, void* cuda_stream);
+
+/* Sec. 5.2 silhouette antialiasing and the Sec. 5.3 image loss (the readings of
+ * adms_forward_loss: pairs of 4-neighbours with different triangles blend by the
+ * crossing of the owner's silhouette edge; L1, log-tone-mapped L1 or L2 per
+ * channel, times loss_scale, e.g. 1 / (3 B H W)). pre: [B][H][W][4] from shade.
+ * With ref ([B][H][W][3]): *loss (float64 device scalar) += the loss and gprime
+ * [B][H][W][4] = dL/d(antialiased colour) in xyz (w: the pair bits the adjoint
+ * reads). img [B][H][W][3]: the antialiased image, or NULL (needed without ref). */
+adms_status adms_aa_loss_fwd(const adms_stage_mesh* mesh, const adms_view* views, int32_t n_views, int32_t H, int32_t W,
+                             const float* clip, const uint64_t* keys, const float* pre, const float* ref,
+                             int32_t loss_kind, float loss_scale, float* img, double* loss, float* gprime, void* work,
+                             size_t work_bytes, void* cuda_stream);
+/* Adjoint of adms_aa_loss_fwd for dL/d(loss) = *g_loss (device scalar; NULL = 1):
+ * g_pre [B][H][W][4] = dL/d(pre) (fourth channel 0), and g_clip [B][V][4]
+ * float64 += the silhouette crossings' gradient w.r.t. their edges' clip
+ * coordinates. gprime: adms_aa_loss_fwd's. */
+adms_status adms_aa_loss_bwd(const adms_stage_mesh* mesh, const adms_view* views, int32_t n_views, int32_t H, int32_t W,
+                             const float* clip, const uint64_t* keys, const float* pre, const float* gprime,
+                             const float* g_loss, float* g_pre, double* g_clip, void* work, size_t work_bytes,
+                             void* cuda_stream);
+
+/* Sec. 5.2 filtered lookups: rebuild levels 1 .. levels-1 of a chain from level 0
+ * (each texel the mean of its 2 x 2 parents), in place. */
+adms_status adms_mip_fwd(float* chain, int32_t h, int32_t w, int32_t levels, void* cuda_stream);
+/* Adjoint of adms_mip_fwd: g_level0 [h][w][4] = level 0's gradient plus every
+ * coarser level's gradient spread evenly over the level-0 texels under it. */
+adms_status adms_mip_bwd(const float* g_chain, int32_t h, int32_t w, int32_t levels, float* g_level0,
+                         void* cuda_stream);
+
 /* ---- visibility without allocation -------------------------------------------- */
 
 /* Visibility keys of n_views views, for callers that cannot call cudaMalloc

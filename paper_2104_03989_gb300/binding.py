@@ -70,6 +70,17 @@ class adms_stats(C.Structure):
                 ("t", C.c_int32), ("status", C.c_int32), ("tile_overflows", C.c_int64), ("call_loss", C.c_double)]
 
 
+class adms_stage_mesh(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_uv", C.c_int32), ("n_tris", C.c_int32), ("pos", C.c_void_p),
+                ("uv", C.c_void_p), ("tri", C.c_void_p), ("tri_uv", C.c_void_p), ("adj", C.c_void_p),
+                ("vf_off", C.c_void_p), ("vf_face", C.c_void_p)]
+
+
+class adms_stage_texture(C.Structure):
+    _fields_ = [("tex", C.c_void_p), ("grad", C.c_void_p), ("h", C.c_int32), ("w", C.c_int32),
+                ("levels", C.c_int32)]
+
+
 assert C.sizeof(adms_view) == 112
 
 # name -> (argtypes, restype)
@@ -103,6 +114,26 @@ SIGNATURES = {
     "adms_job_export": ([P, C.c_int32, P, C.POINTER(C.c_size_t)], C.c_int),
     "adms_job_import": ([P, C.POINTER(adms_mesh_desc), C.POINTER(adms_material_desc), C.POINTER(adms_opt_params),
                          P, C.c_size_t, C.POINTER(C.c_int32)], C.c_int),
+    "adms_mesh_topology": ([P, C.c_int32, C.c_int32, P, P, P], C.c_int),
+    "adms_stage_workspace_bytes": ([C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64], C.c_size_t),
+    "adms_frame_fwd": ([C.POINTER(adms_stage_mesh), P, P, P, P], C.c_int),
+    "adms_frame_bwd": ([C.POINTER(adms_stage_mesh), P, P, P, P, P, P], C.c_int),
+    "adms_setup_fwd": ([C.POINTER(adms_stage_mesh), P, C.c_int32, C.c_int32, C.c_int32, P, P, C.c_size_t, P], C.c_int),
+    "adms_setup_bwd": ([P, C.c_int32, C.c_int32, P, P, P], C.c_int),
+    "adms_raster_fwd": ([C.POINTER(adms_stage_mesh), P, C.c_int32, C.c_int32, C.c_int32, P, P, C.c_int32, P, P, P,
+                         C.c_size_t, P], C.c_int),
+    "adms_raster_bwd": ([C.POINTER(adms_stage_mesh), P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, C.c_size_t,
+                         P], C.c_int),
+    "adms_shade_fwd": ([C.POINTER(adms_stage_mesh), P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P,
+                        C.POINTER(adms_stage_texture), P, P], C.c_int),
+    "adms_shade_bwd": ([C.POINTER(adms_stage_mesh), P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P,
+                        C.POINTER(adms_stage_texture), P, P, P, P, P, P], C.c_int),
+    "adms_aa_loss_fwd": ([C.POINTER(adms_stage_mesh), P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, C.c_int32,
+                          C.c_float, P, P, P, P, C.c_size_t, P], C.c_int),
+    "adms_aa_loss_bwd": ([C.POINTER(adms_stage_mesh), P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P,
+                          C.c_size_t, P], C.c_int),
+    "adms_mip_fwd": ([P, C.c_int32, C.c_int32, C.c_int32, P], C.c_int),
+    "adms_mip_bwd": ([P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
     "adms_visibility_noalloc": ([P, C.c_int32, P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
     "adms_autotune": ([P, P, C.c_int32, P, P, P, P], C.c_int),
     "adms_ctx_tuning": ([P, P], C.c_int),
@@ -337,6 +368,112 @@ def adms_visibility_noalloc(pos, tri, views, n_views, H, W, keys, stream=None):
                                            int(n_views), int(H), int(W), ptr(keys), st)
     if status != ADMS_OK:
         raise AdmsError(status, "adms_visibility_noalloc")
+
+
+# ----------------------------------------------------------------------------- per-stage calls
+
+def _stream(stream):
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def _stage(status, name):
+    if status != ADMS_OK:
+        raise AdmsError(status, name)
+
+
+def stage_mesh(pos, uv, tri, tri_uv, adj, vf_off, vf_face):
+    """adms_stage_mesh of device tensors (kept alive by the returned struct)."""
+    m = adms_stage_mesh(int(pos.shape[0]), int(uv.shape[0]), int(tri.shape[0]), ptr(pos), ptr(uv), ptr(tri),
+                        ptr(tri_uv), ptr(adj), ptr(vf_off), ptr(vf_face))
+    m._keep = (pos, uv, tri, tri_uv, adj, vf_off, vf_face)
+    return m
+
+
+def stage_textures(maps):
+    """adms_stage_texture[3] of (chain, grad or None, h, w, levels) tuples."""
+    arr = (adms_stage_texture * 3)()
+    for i, (chain, grad, h, w, levels) in enumerate(maps):
+        arr[i] = adms_stage_texture(ptr(chain), ptr(grad), int(h), int(w), int(levels))
+    arr._keep = maps
+    return arr
+
+
+def adms_mesh_topology(tri, n_verts):
+    """Host numpy int32 tri (F, 3) -> (adj (F, 3), vf_off (V+1,), vf_face (3F,)) int32."""
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    F = tri.shape[0]
+    adj = np.empty((F, 3), np.int32)
+    vf_off = np.empty(n_verts + 1, np.int32)
+    vf_face = np.empty(3 * F, np.int32)
+    _stage(lib().adms_mesh_topology(ptr(tri), int(n_verts), F, ptr(adj), ptr(vf_off), ptr(vf_face)),
+           "adms_mesh_topology")
+    return adj, vf_off, vf_face
+
+
+def adms_stage_workspace_bytes(n_verts, n_tris, n_views, H, W, list_entries):
+    return int(lib().adms_stage_workspace_bytes(n_verts, n_tris, n_views, H, W, list_entries))
+
+
+def adms_frame_fwd(mesh, vpos4, vnrm4, vtan4, stream=None):
+    _stage(lib().adms_frame_fwd(C.byref(mesh), ptr(vpos4), ptr(vnrm4), ptr(vtan4), _stream(stream)), "adms_frame_fwd")
+
+
+def adms_frame_bwd(mesh, g_vpos, g_vnrm, g_vtan, g_pos, tmp, stream=None):
+    _stage(lib().adms_frame_bwd(C.byref(mesh), ptr(g_vpos), ptr(g_vnrm), ptr(g_vtan), ptr(g_pos), ptr(tmp),
+                                _stream(stream)), "adms_frame_bwd")
+
+
+def adms_setup_fwd(mesh, views, n_views, H, W, clip, work, stream=None):
+    _stage(lib().adms_setup_fwd(C.byref(mesh), ptr(views), n_views, H, W, ptr(clip), ptr(work), work.numel(),
+                                _stream(stream)), "adms_setup_fwd")
+
+
+def adms_setup_bwd(views, n_views, n_verts, g_clip, g_pos, stream=None):
+    _stage(lib().adms_setup_bwd(ptr(views), n_views, n_verts, ptr(g_clip), ptr(g_pos), _stream(stream)),
+           "adms_setup_bwd")
+
+
+def adms_raster_fwd(mesh, views, n_views, H, W, clip, keys, rast, rast_db, work, stream=None, keep_keys=False):
+    _stage(lib().adms_raster_fwd(C.byref(mesh), ptr(views), n_views, H, W, ptr(clip), ptr(keys), int(bool(keep_keys)),
+                                 ptr(rast), ptr(rast_db), ptr(work), work.numel(), _stream(stream)), "adms_raster_fwd")
+
+
+def adms_raster_bwd(mesh, views, n_views, H, W, clip, keys, g_rast, g_clip, work, stream=None):
+    _stage(lib().adms_raster_bwd(C.byref(mesh), ptr(views), n_views, H, W, ptr(clip), ptr(keys), ptr(g_rast),
+                                 ptr(g_clip), ptr(work), work.numel(), _stream(stream)), "adms_raster_bwd")
+
+
+def adms_shade_fwd(mesh, views, n_views, H, W, keys, rast, rast_db, vpos4, vnrm4, vtan4, maps, pre, stream=None):
+    _stage(lib().adms_shade_fwd(C.byref(mesh), ptr(views), n_views, H, W, ptr(keys), ptr(rast), ptr(rast_db),
+                                ptr(vpos4), ptr(vnrm4), ptr(vtan4), maps, ptr(pre), _stream(stream)), "adms_shade_fwd")
+
+
+def adms_shade_bwd(mesh, views, n_views, H, W, keys, rast, rast_db, vpos4, vnrm4, vtan4, maps, g_pre, g_vpos,
+                   g_vnrm, g_vtan, g_rast, stream=None):
+    _stage(lib().adms_shade_bwd(C.byref(mesh), ptr(views), n_views, H, W, ptr(keys), ptr(rast), ptr(rast_db),
+                                ptr(vpos4), ptr(vnrm4), ptr(vtan4), maps, ptr(g_pre), ptr(g_vpos), ptr(g_vnrm),
+                                ptr(g_vtan), ptr(g_rast), _stream(stream)), "adms_shade_bwd")
+
+
+def adms_aa_loss_fwd(mesh, views, n_views, H, W, clip, keys, pre, ref, loss_kind, loss_scale, img, loss, gprime,
+                     work, stream=None):
+    _stage(lib().adms_aa_loss_fwd(C.byref(mesh), ptr(views), n_views, H, W, ptr(clip), ptr(keys), ptr(pre), ptr(ref),
+                                  int(loss_kind), float(loss_scale), ptr(img), ptr(loss), ptr(gprime), ptr(work),
+                                  work.numel(), _stream(stream)), "adms_aa_loss_fwd")
+
+
+def adms_aa_loss_bwd(mesh, views, n_views, H, W, clip, keys, pre, gprime, g_loss, g_pre, g_clip, work, stream=None):
+    _stage(lib().adms_aa_loss_bwd(C.byref(mesh), ptr(views), n_views, H, W, ptr(clip), ptr(keys), ptr(pre),
+                                  ptr(gprime), ptr(g_loss), ptr(g_pre), ptr(g_clip), ptr(work), work.numel(),
+                                  _stream(stream)), "adms_aa_loss_bwd")
+
+
+def adms_mip_fwd(chain, h, w, levels, stream=None):
+    _stage(lib().adms_mip_fwd(ptr(chain), h, w, levels, _stream(stream)), "adms_mip_fwd")
+
+
+def adms_mip_bwd(g_chain, h, w, levels, g_level0, stream=None):
+    _stage(lib().adms_mip_bwd(ptr(g_chain), h, w, levels, ptr(g_level0), _stream(stream)), "adms_mip_bwd")
 
 
 def adms_graph_begin(ctx):

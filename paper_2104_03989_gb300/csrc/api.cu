@@ -1820,6 +1820,20 @@ adms_status adms_ctx_stage_times(adms_ctx* ctx, double* ms_out, int64_t* launche
     return ADMS_OK;
 }
 
+adms_status adms_mesh_topology(const int32_t* tri, int32_t n_verts, int32_t n_tris, int32_t* adj, int32_t* vf_off,
+                               int32_t* vf_face) {
+    if (!tri || !adj || !vf_off || !vf_face || n_verts <= 0 || n_tris <= 0) return ADMS_ERR_ARG;
+    std::vector<int> t(tri, tri + (size_t)3 * n_tris);
+    for (int x : t)
+        if (x < 0 || x >= n_verts) return ADMS_ERR_ARG;
+    std::vector<int> a, off, face, ring_off, ring;
+    build_topology(t, n_verts, n_tris, a, off, face, ring_off, ring);
+    std::copy(a.begin(), a.end(), adj);
+    std::copy(off.begin(), off.end(), vf_off);
+    std::copy(face.begin(), face.end(), vf_face);
+    return ADMS_OK;
+}
+
 int32_t adms_stage_count(void) { return ST_COUNT; }
 
 const char* adms_stage_name(int32_t i) { return (i >= 0 && i < ST_COUNT) ? kStageNames[i] : ""; }

@@ -71,7 +71,8 @@ struct RasterScratch {
 };
 
 cudaError_t raster_views(const RasterIn& in, RasterScratch& s, cudaStream_t st);
-// transform, setup, tile counts, scan and tile lists
+// transform, setup, tile counts, scan and tile lists (in.keys may be null when
+// in.small_px is 0: nothing is then rasterized directly and the keys are untouched)
 cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st);
 // the per-tile z-buffer pass
 cudaError_t raster_tiles(const RasterIn& in, RasterScratch& s, cudaStream_t st);
@@ -121,6 +122,7 @@ struct ShadeArgs {
     double* g_pos;                   // [V][3] accumulated in float64
     double* g_nrm;                   // [V][3] d/d(unit normal)
     double* g_tan;                   // [V][3] d/d(unit tangent)
+    double* g_clip;                  // per-stage calls: [B][V][4] d/d(clip coordinates), or null
 };
 
 cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st);
@@ -147,7 +149,7 @@ struct WorkItem {
     int job, view, x0, y0;
 };
 // Jobs per batched launch: their arguments travel in the launch's parameter
-// space (60 x 536 B, under the 32 KB limit), read-only and captured with the
+// space (60 x 544 B, under the 32 KB limit), read-only and captured with the
 // launch by a graph; larger job sets take one launch per 60 jobs.
 #define ADMS_BATCH_JOBS 60
 struct ShadeBatch {

@@ -563,7 +563,8 @@ cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st
     int tiles_x = (W + ADMS_TILE - 1) / ADMS_TILE, tiles_y = (H + ADMS_TILE - 1) / ADMS_TILE;
     int ntiles = B * tiles_x * tiles_y;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(in.keys, 0xFF, sizeof(unsigned long long) * B * H * W, st))) return e;
+    // without a key buffer (every triangle binned: small_px = 0) the keys are left to raster_tiles' caller
+    if (in.keys && (e = cudaMemsetAsync(in.keys, 0xFF, sizeof(unsigned long long) * B * H * W, st))) return e;
     if ((e = cudaMemsetAsync(s.tile_count, 0, sizeof(int) * ntiles, st))) return e;
     if ((e = cudaMemsetAsync(s.tile_cursor, 0, sizeof(int) * ntiles, st))) return e;
     int bs = 256;
