@@ -487,6 +487,47 @@ adms_status adms_aa_loss_bwd(const adms_stage_mesh* mesh, const adms_view* views
                              const float* g_loss, float* g_pre, double* g_clip, void* work, size_t work_bytes,
                              void* cuda_stream);
 
+/* Tessellation with displacement (Sec. 5.1, Eq. 3) as a stage: a base mesh split
+ * `levels` times at edge midpoints (the (2^levels)-segment lattice of every base
+ * triangle; vertices shared along base edges merged), each render vertex
+ * v = sum_k w_k p_k displaced along the normalised interpolated smooth base
+ * normal by the bilinear level-0 lookup of a scalar map at the vertex's UV. */
+typedef struct {
+    int32_t n_base_verts, n_base_tris, n_verts, n_segments; /* n_segments = 2^levels */
+    const int32_t* base_tri; /* [Fb][3] */
+    const int32_t* bvf_off;  /* [Vb+1] base vertex -> incident faces (adms_mesh_topology of the base mesh) */
+    const int32_t* bvf_face;
+    const int32_t* owner;    /* [Vt][3] the base vertices of the render vertex's owning base face */
+    const int32_t* wts;      /* [Vt][3] its integer lattice weights (summing to n_segments) */
+    const float* vert_uv;    /* [Vt][2] the UV its displacement is looked up at */
+} adms_tess_desc;
+
+/* Host helper: the tessellation tables of a base mesh (host memory, caller-
+ * owned). counts [3] = {render vertices Vt, render triangles Ft, render UV
+ * corners Tt}: with every table pointer NULL only counts is written; otherwise
+ * counts holds the capacities on entry (ADMS_ERR_ARG if too small) and rtri
+ * [Ft][3], rtri_uv [Ft][3], ruv [Tt][2] (the render mesh, sub-triangles keeping
+ * their base face's UV corners interpolated), owner, wts [Vt][3] and vert_uv
+ * [Vt][2] (a shared vertex takes the UV of its lowest-numbered owning base face)
+ * are filled. levels in [1, 8]. */
+adms_status adms_tessellation(const int32_t* tri, const int32_t* tri_uv, const float* uv, int32_t n_verts, int32_t n_uv,
+                              int32_t n_tris, int32_t levels, int32_t* counts, int32_t* rtri, int32_t* rtri_uv,
+                              float* ruv, int32_t* owner, int32_t* wts, float* vert_uv);
+/* Render positions pos [Vt][3] from base positions [Vb][3] and the displacement
+ * map disp [dh][dw] (u wraps, v clamps), and the smooth base normals base_nrm
+ * [Vb][3] they use, in the float32 contract of the step calls (visibility is
+ * decided on these positions). */
+adms_status adms_tess_fwd(const adms_tess_desc* tess, const float* base_pos, const float* disp, int32_t dh, int32_t dw,
+                          float* base_nrm, float* pos, void* cuda_stream);
+/* Adjoint for g_pos [Vt][3] = dL/d(pos): g_base_pos and g_base_nrm [Vb][3]
+ * float64 += the direct position and base-normal gradients, g_disp [dh][dw] +=
+ * the displacement texels' (NULL: skipped). The base normals' own adjoint is
+ * adms_frame_bwd on the base mesh (normal gradient g_base_nrm, no tangent
+ * gradient), which also folds g_base_pos into the base positions. */
+adms_status adms_tess_bwd(const adms_tess_desc* tess, const float* base_pos, const float* base_nrm, const float* disp,
+                          int32_t dh, int32_t dw, const float* g_pos, double* g_base_pos, double* g_base_nrm,
+                          float* g_disp, void* cuda_stream);
+
 /* Sec. 5.2 filtered lookups: rebuild levels 1 .. levels-1 of a chain from level 0
  * (each texel the mean of its 2 x 2 parents), in place. */
 adms_status adms_mip_fwd(float* chain, int32_t h, int32_t w, int32_t levels, void* cuda_stream);

@@ -81,6 +81,12 @@ class adms_stage_texture(C.Structure):
                 ("levels", C.c_int32)]
 
 
+class adms_tess_desc(C.Structure):
+    _fields_ = [("n_base_verts", C.c_int32), ("n_base_tris", C.c_int32), ("n_verts", C.c_int32),
+                ("n_segments", C.c_int32), ("base_tri", C.c_void_p), ("bvf_off", C.c_void_p), ("bvf_face", C.c_void_p),
+                ("owner", C.c_void_p), ("wts", C.c_void_p), ("vert_uv", C.c_void_p)]
+
+
 assert C.sizeof(adms_view) == 112
 
 # name -> (argtypes, restype)
@@ -132,6 +138,9 @@ SIGNATURES = {
                           C.c_float, P, P, P, P, C.c_size_t, P], C.c_int),
     "adms_aa_loss_bwd": ([C.POINTER(adms_stage_mesh), P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P, P,
                           C.c_size_t, P], C.c_int),
+    "adms_tessellation": ([P, P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P, P, P], C.c_int),
+    "adms_tess_fwd": ([C.POINTER(adms_tess_desc), P, P, C.c_int32, C.c_int32, P, P, P], C.c_int),
+    "adms_tess_bwd": ([C.POINTER(adms_tess_desc), P, P, P, C.c_int32, C.c_int32, P, P, P, P, P], C.c_int),
     "adms_mip_fwd": ([P, C.c_int32, C.c_int32, C.c_int32, P], C.c_int),
     "adms_mip_bwd": ([P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
     "adms_visibility_noalloc": ([P, C.c_int32, P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P, P], C.c_int),
@@ -466,6 +475,41 @@ def adms_aa_loss_bwd(mesh, views, n_views, H, W, clip, keys, pre, gprime, g_loss
     _stage(lib().adms_aa_loss_bwd(C.byref(mesh), ptr(views), n_views, H, W, ptr(clip), ptr(keys), ptr(pre),
                                   ptr(gprime), ptr(g_loss), ptr(g_pre), ptr(g_clip), ptr(work), work.numel(),
                                   _stream(stream)), "adms_aa_loss_bwd")
+
+
+def adms_tessellation(tri, tri_uv, uv, n_verts, levels):
+    """Host tessellation tables of a base mesh: dict of numpy arrays (rtri, rtri_uv,
+    ruv, owner, wts, vert_uv) and the counts (see include/adms.h)."""
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    tri_uv = np.ascontiguousarray(tri_uv, dtype=np.int32)
+    uv = np.ascontiguousarray(uv, dtype=np.float32)
+    counts = np.zeros(3, np.int32)
+    args = (ptr(tri), ptr(tri_uv), ptr(uv), int(n_verts), int(uv.shape[0]), int(tri.shape[0]), int(levels))
+    _stage(lib().adms_tessellation(*args, ptr(counts), None, None, None, None, None, None), "adms_tessellation")
+    Vt, Ft, Tt = (int(x) for x in counts)
+    out = dict(rtri=np.empty((Ft, 3), np.int32), rtri_uv=np.empty((Ft, 3), np.int32), ruv=np.empty((Tt, 2), np.float32),
+               owner=np.empty((Vt, 3), np.int32), wts=np.empty((Vt, 3), np.int32), vert_uv=np.empty((Vt, 2), np.float32))
+    _stage(lib().adms_tessellation(*args, ptr(counts), ptr(out["rtri"]), ptr(out["rtri_uv"]), ptr(out["ruv"]),
+                                   ptr(out["owner"]), ptr(out["wts"]), ptr(out["vert_uv"])), "adms_tessellation")
+    return out
+
+
+def tess_desc(n_base_verts, n_base_tris, n_verts, n_segments, base_tri, bvf_off, bvf_face, owner, wts, vert_uv):
+    d = adms_tess_desc(int(n_base_verts), int(n_base_tris), int(n_verts), int(n_segments), ptr(base_tri), ptr(bvf_off),
+                       ptr(bvf_face), ptr(owner), ptr(wts), ptr(vert_uv))
+    d._keep = (base_tri, bvf_off, bvf_face, owner, wts, vert_uv)
+    return d
+
+
+def adms_tess_fwd(tess, base_pos, disp, base_nrm, pos, stream=None):
+    _stage(lib().adms_tess_fwd(C.byref(tess), ptr(base_pos), ptr(disp), int(disp.shape[0]), int(disp.shape[1]),
+                               ptr(base_nrm), ptr(pos), _stream(stream)), "adms_tess_fwd")
+
+
+def adms_tess_bwd(tess, base_pos, base_nrm, disp, g_pos, g_base_pos, g_base_nrm, g_disp, stream=None):
+    _stage(lib().adms_tess_bwd(C.byref(tess), ptr(base_pos), ptr(base_nrm), ptr(disp), int(disp.shape[0]),
+                               int(disp.shape[1]), ptr(g_pos), ptr(g_base_pos), ptr(g_base_nrm), ptr(g_disp),
+                               _stream(stream)), "adms_tess_bwd")
 
 
 def adms_mip_fwd(chain, h, w, levels, stream=None):

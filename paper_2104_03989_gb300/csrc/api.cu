@@ -1834,6 +1834,36 @@ adms_status adms_mesh_topology(const int32_t* tri, int32_t n_verts, int32_t n_tr
     return ADMS_OK;
 }
 
+adms_status adms_tessellation(const int32_t* tri, const int32_t* tri_uv, const float* uv, int32_t n_verts, int32_t n_uv,
+                              int32_t n_tris, int32_t levels, int32_t* counts, int32_t* rtri, int32_t* rtri_uv,
+                              float* ruv, int32_t* owner, int32_t* wts, float* vert_uv) {
+    if (!tri || !tri_uv || !uv || !counts || n_verts <= 0 || n_uv <= 0 || n_tris <= 0 || levels < 1 || levels > 8)
+        return ADMS_ERR_ARG;
+    std::vector<int> t(tri, tri + (size_t)3 * n_tris), tu(tri_uv, tri_uv + (size_t)3 * n_tris);
+    for (int x : t)
+        if (x < 0 || x >= n_verts) return ADMS_ERR_ARG;
+    for (int x : tu)
+        if (x < 0 || x >= n_uv) return ADMS_ERR_ARG;
+    TessHost h;
+    build_tessellation(t, tu, std::vector<float>(uv, uv + (size_t)2 * n_uv), n_tris, levels, h);
+    int Ft = (int)h.rtri.size() / 3;
+    bool fill = rtri || rtri_uv || ruv || owner || wts || vert_uv;
+    if (fill) {
+        if (!rtri || !rtri_uv || !ruv || !owner || !wts || !vert_uv) return ADMS_ERR_ARG;
+        if (counts[0] < h.Vt || counts[1] < Ft || counts[2] < (int)h.corner_uv.size() / 2) return ADMS_ERR_ARG;
+        std::copy(h.rtri.begin(), h.rtri.end(), rtri);
+        std::copy(h.rtri_uv.begin(), h.rtri_uv.end(), rtri_uv);
+        std::copy(h.corner_uv.begin(), h.corner_uv.end(), ruv);
+        std::copy(h.owner.begin(), h.owner.end(), owner);
+        std::copy(h.wts.begin(), h.wts.end(), wts);
+        std::copy(h.vert_uv.begin(), h.vert_uv.end(), vert_uv);
+    }
+    counts[0] = h.Vt;
+    counts[1] = Ft;
+    counts[2] = (int)h.corner_uv.size() / 2;
+    return ADMS_OK;
+}
+
 int32_t adms_stage_count(void) { return ST_COUNT; }
 
 const char* adms_stage_name(int32_t i) { return (i >= 0 && i < ST_COUNT) ? kStageNames[i] : ""; }

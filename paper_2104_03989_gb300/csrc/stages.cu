@@ -635,6 +635,55 @@ adms_status adms_aa_loss_bwd(const adms_stage_mesh* m, const adms_view* views, i
     return ADMS_OK;
 }
 
+static bool tess_ok(const adms_tess_desc* t, const float* base_pos, const float* disp, int32_t dh, int32_t dw) {
+    return t && t->base_tri && t->bvf_off && t->bvf_face && t->owner && t->wts && t->vert_uv && base_pos && disp &&
+           t->n_base_verts > 0 && t->n_base_tris > 0 && t->n_verts > 0 && t->n_segments >= 2 && dh > 0 && dw > 0;
+}
+
+static TessArgs tess_stage_args(const adms_tess_desc* t, const float* base_pos, const float* disp, int32_t dh,
+                                int32_t dw) {
+    TessArgs a{};
+    a.Vb = t->n_base_verts;
+    a.Fb = t->n_base_tris;
+    a.Vt = t->n_verts;
+    a.n_seg = t->n_segments;
+    a.base_pos = base_pos;
+    a.base_tri = t->base_tri;
+    a.bvf_off = t->bvf_off;
+    a.bvf_face = t->bvf_face;
+    a.owner = t->owner;
+    a.wts = t->wts;
+    a.vert_uv = reinterpret_cast<const float2*>(t->vert_uv);
+    a.disp = disp;
+    a.dh = dh;
+    a.dw = dw;
+    return a;
+}
+
+adms_status adms_tess_fwd(const adms_tess_desc* t, const float* base_pos, const float* disp, int32_t dh, int32_t dw,
+                          float* base_nrm, float* pos, void* cuda_stream) {
+    if (!tess_ok(t, base_pos, disp, dh, dw) || !base_nrm || !pos) return ADMS_ERR_ARG;
+    TessArgs a = tess_stage_args(t, base_pos, disp, dh, dw);
+    a.base_nrm = base_nrm;
+    a.pos_out = pos;
+    ADMS_STAGE_CHECK(tess_forward(a, (cudaStream_t)cuda_stream));
+    return ADMS_OK;
+}
+
+adms_status adms_tess_bwd(const adms_tess_desc* t, const float* base_pos, const float* base_nrm, const float* disp,
+                          int32_t dh, int32_t dw, const float* g_pos, double* g_base_pos, double* g_base_nrm,
+                          float* g_disp, void* cuda_stream) {
+    if (!tess_ok(t, base_pos, disp, dh, dw) || !base_nrm || !g_pos || !g_base_pos || !g_base_nrm) return ADMS_ERR_ARG;
+    TessArgs a = tess_stage_args(t, base_pos, disp, dh, dw);
+    a.base_nrm = const_cast<float*>(base_nrm);
+    a.g_pos_t = g_pos;
+    a.g_base_pos = g_base_pos;
+    a.g_base_nrm = g_base_nrm;
+    a.g_disp = g_disp;
+    ADMS_STAGE_CHECK(tess_backward(a, (cudaStream_t)cuda_stream));
+    return ADMS_OK;
+}
+
 adms_status adms_mip_fwd(float* chain, int32_t h, int32_t w, int32_t levels, void* cuda_stream) {
     adms_stage_texture t{chain, nullptr, h, w, levels};
     if (!tex_ok(t)) return ADMS_ERR_ARG;

@@ -6,6 +6,7 @@ texture lookups and an antialiasing pass; Sec. 3 differentiates the image loss
 through all of them), each Function's backward one hand-written adjoint call of
 libadms.so:
 
+    Tess     base positions, displacement map -> render positions    adms_tess_fwd / _bwd (+ base frame)
     Frame    positions -> (positions, unit normals, unit tangents)   adms_frame_fwd / _bwd
     Setup    positions -> clip coordinates                           adms_setup_fwd / _bwd
     Raster   clip -> barycentrics (keys, LOD derivatives alongside)  adms_raster_fwd / _bwd
@@ -238,6 +239,58 @@ class AALoss(torch.autograd.Function):
         B.adms_aa_loss_bwd(pipe.mesh(fctx.pos), pipe.views, pipe.B, pipe.H, pipe.W, clip, pipe.keys, pre, gprime,
                            g_loss.reshape(1).float().contiguous(), g_pre, g_clip, pipe.work)
         return None, None, g_pre, g_clip.float(), None, None, None
+
+
+class TessMesh:
+    """A base mesh split `levels` times (Sec. 5.1): the render mesh's topology and
+    UVs, and the tables the displacement stage reads."""
+
+    def __init__(self, tri, tri_uv, uv, n_verts, levels, device="cuda"):
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        tab = B.adms_tessellation(tri, tri_uv, uv, n_verts, levels)
+        _, bvf_off, bvf_face = B.adms_mesh_topology(tri, n_verts)
+        dev = torch.device(device)
+        t = lambda a: torch.as_tensor(a, device=dev)   # noqa: E731
+        self.Vb, self.Fb, self.Vt, self.n_seg = int(n_verts), int(tri.shape[0]), int(tab["owner"].shape[0]), 1 << levels
+        self.rtri, self.rtri_uv, self.ruv = tab["rtri"], tab["rtri_uv"], tab["ruv"]
+        self.dev = dict(base_tri=t(tri), bvf_off=t(bvf_off), bvf_face=t(bvf_face), owner=t(tab["owner"]),
+                        wts=t(tab["wts"]), vert_uv=t(tab["vert_uv"]))
+        self.desc = B.tess_desc(self.Vb, self.Fb, self.Vt, self.n_seg, **self.dev)
+        # the base mesh as a stage mesh: its frame adjoint takes the base normals' gradient
+        self.base_uv = t(np.ascontiguousarray(uv, dtype=np.float32))
+        self.base_tri_uv = t(np.ascontiguousarray(tri_uv, dtype=np.int32))
+        self.base_adj = t(np.full((self.Fb, 3), -1, np.int32))
+
+    def base_mesh(self, base_pos):
+        return B.stage_mesh(base_pos, self.base_uv, self.dev["base_tri"], self.base_tri_uv, self.base_adj,
+                            self.dev["bvf_off"], self.dev["bvf_face"])
+
+
+class Tess(torch.autograd.Function):
+    """Sec. 5.1, Eq. 3: render positions [Vt][3] from base positions and the
+    displacement map [dh][dw]; backward through the displacement lookup, the
+    lattice interpolation and the smooth base normals."""
+
+    @staticmethod
+    def forward(fctx, tm, base_pos, disp):
+        bp, d = base_pos.detach().contiguous(), disp.detach().contiguous()
+        base_nrm = torch.empty(tm.Vb, 3, dtype=torch.float32, device=bp.device)
+        pos = torch.empty(tm.Vt, 3, dtype=torch.float32, device=bp.device)
+        B.adms_tess_fwd(tm.desc, bp, d, base_nrm, pos)
+        fctx.tm, fctx.bp, fctx.d, fctx.nrm = tm, bp, d, base_nrm
+        return pos
+
+    @staticmethod
+    def backward(fctx, g_pos):
+        tm, bp = fctx.tm, fctx.bp
+        g_bpos = torch.zeros(tm.Vb, 3, dtype=torch.float64, device=bp.device)
+        g_bnrm = torch.zeros(tm.Vb, 3, dtype=torch.float64, device=bp.device)
+        g_disp = torch.zeros_like(fctx.d)
+        B.adms_tess_bwd(tm.desc, bp, fctx.nrm, fctx.d, g_pos.contiguous(), g_bpos, g_bnrm, g_disp)
+        g_base = torch.zeros(tm.Vb, 3, dtype=torch.float32, device=bp.device)
+        B.adms_frame_bwd(tm.base_mesh(bp), g_bpos, g_bnrm, torch.zeros_like(g_bnrm), g_base,
+                         torch.empty(2 * tm.Vb, 4, device=bp.device))
+        return None, g_base, g_disp
 
 
 class MipChain(torch.autograd.Function):

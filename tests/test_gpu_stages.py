@@ -236,3 +236,56 @@ def test_stage_calls_refuse_bad_arguments(gpu_lib):
         B.adms_shade_fwd(m, pipe.views, pipe.B, H, W, torch.empty(1, device="cuda"), clip, clip, clip, clip, clip,
                          bad, clip)
     assert ST.mip_levels(256, 256) == 9
+
+
+def _tess_inputs():
+    from paper_2104_03989_gb300 import stages as ST
+    from cases import tess_case
+
+    c, views, H, W = tess_case()
+    cand = c["cand"]
+    ref_np, _ = oracle_reference(c["ref"], views, H, W)
+    m = cand.mesh
+    tm = ST.TessMesh(m.tri_pos, m.tri_uv, m.uv, m.n_verts, cand.tess_levels)
+    pipe = ST.Pipeline(tm.rtri, tm.ruv, tm.rtri_uv, tm.Vt, views, H, W)
+    lat = {"pos": torch.tensor(m.pos, device="cuda"), "disp": torch.tensor(cand.disp, device="cuda")}
+    for n in ("kd", "orm", "nrm"):
+        lat[n] = torch.tensor(getattr(cand, n), device="cuda")
+    for n, t in lat.items():
+        t.requires_grad_(bool(cand.optimize.get(n, False)))
+    return ST, cand, views, H, W, ref_np, tm, pipe, lat
+
+
+def test_tessellation_stage_chain_matches_oracle(gpu_lib):
+    """Tess (Eq. 3) -> frame -> setup -> raster -> shade -> aa_loss on the
+    displacement workload shrunk for the oracle: keys bit-exact (the float32
+    contract of the displaced positions), loss within 1e-5, gradients of base
+    positions, displacement texels and normal map within 1e-3."""
+    ST, cand, views, H, W, ref_np, tm, pipe, lat = _tess_inputs()
+    ref = torch.as_tensor(ref_np).cuda()
+    pos = ST.Tess.apply(tm, lat["pos"], lat["disp"])
+    L = ST.render_loss(pipe, pos, lat["kd"], lat["orm"], lat["nrm"], ref, "logl1", mips=cand.mips)
+    keys = pipe.keys.cpu().numpy().view(np.uint64)
+    loss_val = float(L.detach())
+    L.backward()
+    orc = oracle_grads(cand, views, ref_np, H, W, "logl1")
+    np.testing.assert_array_equal(keys, orc["keys"])
+    assert abs(loss_val - orc["loss"]) / orc["loss"] < 1e-5
+    for name, want in orc["grads"].items():
+        got = lat[name].grad.double().cpu().numpy().reshape(want.shape)
+        err = rel_l2(got, want)
+        print(f"tess stages {name}: rel L2 {err:.3e}")
+        assert err < 1e-3, name
+
+
+def test_tessellation_stage_against_central_differences(gpu_lib):
+    """Central differences (h = 1e-3) of a random projection of the displaced
+    render positions in 64 base-position coordinates and 64 displacement texels."""
+    ST, cand, views, H, W, ref_np, tm, pipe, lat = _tess_inputs()
+    rng = np.random.default_rng(4)
+    bp = lat["pos"].detach().clone().requires_grad_(True)
+    dm = lat["disp"].detach().clone().requires_grad_(True)
+    R = torch.randn(tm.Vt, 3, device="cuda", dtype=torch.float64)
+    f = lambda: (ST.Tess.apply(tm, bp, dm).double() * R).sum()   # noqa: E731
+    f().backward()
+    _fd_check("tess", f, [("pos", bp, 64, 1e-3), ("disp", dm, 64, 1e-3)], rng, min_total=128)
