@@ -151,7 +151,11 @@ def algorithmic_bytes(stage, w):
     pixels or samples), Ppix (pixels per step), S (samples per pixel side), L
     (depth-peeling layers, 0: opaque), texel counts and triangle/vertex counts."""
     P = w["P"]
-    tex_px = 1.33 * 16 * 3          # unique texels per covered pixel per map x 16 B x 3 maps
+    texel = 1.33 * 16               # unique texels per covered pixel per map x 16 B
+    maps = w.get("tex_maps", 3)     # maps larger than one texel
+    tex_px = texel * maps
+    ref_px = texel * w.get("ref_maps", 3)
+    views = w.get("views", VIEWS)
     L = w.get("L", 0)
     if L:
         # per layer and pixel: key, colour + opacity, the composite behind, its
@@ -159,23 +163,30 @@ def algorithmic_bytes(stage, w):
         if stage == "shade_bwd":
             return (8 + 16 + 16 + 16 + 16) * L * P + (tex_px * 3) * w["C"]
         if stage == "shade":
-            return 24 * L * P + 24 * P + tex_px * (w["C"] + w["Cr"])
+            return 24 * L * P + 24 * P + tex_px * w["C"] + ref_px * w["Cr"]
         if stage == "aa_loss":
             return (8 + 16 + 16 + 16) * L * P + 12 * P + (8 + 16 + 12) * P
         if stage == "raster":
-            return (8 + 8) * L * P + 8 * P + 96 * VIEWS * (L * w["F"] + w["Fr"])
+            return (8 + 8) * L * P + 8 * P + 96 * views * (L * w["F"] + w["Fr"])
     if stage == "shade_bwd":
-        return 40 * P + (tex_px * 3) * w["C"]          # key+g'+pre per pixel; texel read + grad RMW
+        # the survey's model: key 8 + dL/dx 12 per pixel; per covered pixel the texels
+        # read again plus the read-modify-write of the optimized maps' texel gradients
+        return 20 * P + texel * (maps + 2 * w.get("grad_maps", 3)) * w["C"]
+    if stage == "shade_bwd_extended":
+        # what this kernel reads per pixel beyond it: the pre-AA colour (16 B, the AA
+        # adjoint's tau term) and dL/dx padded to 16 B with the blend bits (+20 B)
+        return 40 * P + texel * (maps + 2 * w.get("grad_maps", 3)) * w["C"]
+    rc = 1 + w.get("recompute", 0)    # the backward recomputes raster, shading and AA once more
     if stage == "shade":
-        return 2 * 24 * P + tex_px * (w["C"] + w["Cr"])  # candidate + reference launches
+        return (24 * P + tex_px * w["C"]) * rc               # key read, colour write; texels of covered pixels
     if stage == "aa_loss" and w.get("S", 1) > 1:
         # per sample: AA reads key + pre and writes its colour, the resolve reads it
         # back (and writes g' for the candidate); per pixel: reference in, image out
         return (8 + 16 + 16) * 2 * P + (16 + 16) * P + 16 * P + (12 + 12) * w["Ppix"]
     if stage == "aa_loss":
-        return (8 + 16 + 12 + 16) * P + (8 + 16 + 12) * P  # candidate (loss, g') + reference (image)
+        return (8 + 16 + 12 + 16) * P * rc                 # key, colour, reference in; dL/dx out
     if stage == "raster":
-        return 2 * 8 * P + 96 * VIEWS * (w["F"] + w["Fr"])
+        return (8 * P + 96 * views * w["F"]) * rc
     if stage == "adam":
         return 32 * (w["texel_floats"] + 3 * w["V"])
     if stage == "mip_build":
@@ -192,7 +203,7 @@ def _sha(files):
 
 # ----------------------------------------------------------------------------- oracle timing
 class OracleStep:
-    """The CPU oracle's full step (reference render + candidate fwd/bwd/Adam).
+    """The CPU oracle's step (candidate fwd/bwd/Adam on pre-rendered references).
 
     Topology tables are built once, outside the timed calls."""
 
@@ -205,14 +216,17 @@ class OracleStep:
         self.cand = S.OracleJob(scene_cfg["cand"], loss=scene_cfg["loss"], msaa=msaa, layers=layers)
 
     def seconds(self, n_views, res, seed=123):
+        """Seconds of the candidate's step (forward + loss, backward, Adam) on the
+        views' reference images, rendered first and not timed (the metric's step),
+        and the threads used."""
         import torch
 
         import synth
 
         views = synth.sample_views(seed, 0, n_views, res, res)
-        t0 = time.perf_counter()
         with torch.no_grad():
             ref = self.S.render(self.ref, self.ref.params, views, res, res, ssaa=self.msaa)["img"]
+        t0 = time.perf_counter()
         self.S.step(self.cand, views, ref.numpy(), res, res)
         return time.perf_counter() - t0, torch.get_num_threads()
 
@@ -246,14 +260,36 @@ def run_reference_arm(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n_views} view of 8 at {res}^2 per step"},
         "cpu_baseline": {"value": value, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{n_views} of 8 views at {res}^2 per step, full oracle step "
-                                   "(reference render + candidate fwd/bwd/Adam)"},
+                         "sample": f"{n_views} of 8 views at {res}^2 per step: the oracle's candidate step "
+                                   "(fwd/loss, bwd, Adam) on its reference images, rendered untimed"},
         "e2e": {"value": value, "unit": "Mpixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 # ----------------------------------------------------------------------------- GPU arm
+WORKLOADS = {
+    # name: (views per step, resolution, backward recomputes the raster, description)
+    "plain": (VIEWS, RES, 0, WORKLOAD),
+    "aggregate": (VIEWS, RES, 0, WORKLOAD_AGG),
+    "tess": (16, 1024, 1, "differentiation at scale (Sec. 5.1, Eq. 3): reference 1,003,520-tri fBm icosphere; "
+                          "candidate 980-tri base mesh tessellated 3 times (62,720 tris) with a 1024^2 scalar "
+                          "displacement map and a 2048^2 normal map, constant diffuse-dominated base colour and "
+                          "(gamma, r, m); 16 random views at 1024x1024; point + directional light; log-L1 loss; "
+                          "raster buffers recomputed in the backward"),
+    "small": (1, 256, 0, "plain method, one step: reference 20,480-tri icosphere displaced by 8 sinusoids, albedo "
+                         "0.7, roughness 0.5; candidate 320-tri icosphere with 256^2 base-colour and normal noise maps; "
+                         "one fixed camera at distance 3, 256x256, one directional light; L1 loss (latency-bound)"),
+}
+
+
+def _config(wk):
+    import synth
+
+    return {"aggregate": synth.config_aggregate, "tess": synth.config_tess, "small": synth.config_small}.get(
+        wk, synth.config_plain)()
+
+
 def run_native(args):
     import torch
 
@@ -269,8 +305,10 @@ def run_native(args):
 
     L = B.lib()
     dev = torch.device("cuda", torch.cuda.current_device())
-    agg = args.workload == "aggregate"
-    cfg = synth.config_aggregate() if agg else synth.config_plain()
+    wk = args.workload
+    agg = wk == "aggregate"
+    NV, RS, RECOMPUTE, wdesc = WORKLOADS[wk]
+    cfg = _config(wk)
     LY = cfg["layers"] if agg else 0
     loss = cfg["loss"]
     stream = torch.cuda.Stream()
@@ -284,11 +322,14 @@ def run_native(args):
                              raster_direct_px=256 if agg else 0)
     pl = bool(args.per_level_textures)
     cand = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, per_level_textures=pl, samples=MS, layers=LY)
-    plain = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, batch_views=VIEWS, per_level_textures=pl, samples=MS,
+    plain = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, batch_views=NV, per_level_textures=pl, samples=MS,
                            layers=LY)
     n_steps = args.warmup + args.steps
-    host_views = [synth.sample_views(replica_seed(rank), i, VIEWS, RES, RES) for i in range(n_steps)]
-    view_np = np.stack([v.view(np.uint8) for v in host_views])                  # (steps, 8*112)
+    if wk == "small":   # one fixed camera
+        host_views = [synth.fixed_view(RS, RS) for _ in range(n_steps)]
+    else:
+        host_views = [synth.sample_views(replica_seed(rank), i, NV, RS, RS) for i in range(n_steps)]
+    view_np = np.stack([v.view(np.uint8) for v in host_views])                  # (steps, NV*112)
     SKB = int(args.skinning)
     if SKB:
         # both meshes skinned by the same bones (Eq. 2); a new pose each step rides in
@@ -301,20 +342,19 @@ def run_native(args):
                             for i in range(n_steps)])
         view_np = np.ascontiguousarray(np.concatenate([view_np, pose_np], axis=1))
     dev_views = torch.from_numpy(view_np).to(dev)
-    pinned_views = torch.from_numpy(view_np).pin_memory()
     staging = torch.empty(view_np.shape[1], dtype=torch.uint8, device=dev)       # graph's fixed input buffer
-    ref_buf = torch.empty((VIEWS, RES, RES, 3), dtype=torch.float32, device=dev)
+    ref_buf = torch.empty((NV, RS, RS, 3), dtype=torch.float32, device=dev)
     loss_buf = torch.zeros(n_steps + 1, dtype=torch.float32, device=dev)
     graph_loss = torch.zeros(1, dtype=torch.float32, device=dev)
     cptr = ctx.ctx
     i32 = C.c_int32
     jobs_c = (i32 * 1)(cand)
     plain_c = (i32 * 1)(plain)
-    vpj8 = (i32 * 1)(VIEWS)
+    vpjN = (i32 * 1)(NV)
     vpj1 = (i32 * 1)(1)
-    hw = (i32 * 2)(RES, RES)
-    refs8 = (C.c_void_p * 1)(ref_buf.data_ptr())
-    refs1 = [(C.c_void_p * 1)(ref_buf[v:v + 1].data_ptr()) for v in range(VIEWS)]
+    hw = (i32 * 2)(RS, RS)
+    refsN = (C.c_void_p * 1)(ref_buf.data_ptr())
+    refs1 = [(C.c_void_p * 1)(ref_buf[v:v + 1].data_ptr()) for v in range(NV)]
     view_bytes = 112
 
     def ck(st):
@@ -324,30 +364,34 @@ def run_native(args):
     def set_pose(vp, jobs):
         if SKB:
             for jb in jobs:
-                ck(L.adms_job_set_bones(cptr, jb, vp + VIEWS * 112))
+                ck(L.adms_job_set_bones(cptr, jb, vp + NV * 112))
 
     # the reference render runs on a stream of its own, alongside the candidate's
     # frame, raster and shading; the loss waits for it (adms_ctx_set_ref_event)
     ref_stream = torch.cuda.Stream()
     fork_ev, ref_ev = torch.cuda.Event(), torch.cuda.Event()
 
+    def cand_step(vp, refs_c, loss_ptr):
+        set_pose(vp, (cand,))
+        ck(L.adms_forward_loss(cptr, jobs_c, 1, vp, vpjN, hw, refs_c, loss_ptr, None))
+        B.adms_ctx_set_ref_event(cptr, None)
+        ck(L.adms_backward(cptr, jobs_c, 1, RECOMPUTE))
+        ck(L.adms_optimizer_step(cptr, jobs_c, 1))
+
     def step_at(vp, loss_ptr, overlap=True):
+        """The step with its reference render (on a second stream when overlap)."""
         if overlap:
             fork_ev.record(stream)
             ref_stream.wait_event(fork_ev)
             B.adms_ctx_set_stream(cptr, ref_stream)
         B.adms_ctx_set_ref_event(cptr, None)
         set_pose(vp, (ref_job,))
-        ck(L.adms_render_reference(cptr, ref_job, vp, VIEWS, RES, RES, ref_buf.data_ptr()))
+        ck(L.adms_render_reference(cptr, ref_job, vp, NV, RS, RS, ref_buf.data_ptr()))
         if overlap:
             ref_ev.record(ref_stream)
             B.adms_ctx_set_stream(cptr, stream)
             B.adms_ctx_set_ref_event(cptr, ref_ev)
-        set_pose(vp, (cand,))
-        ck(L.adms_forward_loss(cptr, jobs_c, 1, vp, vpj8, hw, refs8, loss_ptr, None))
-        B.adms_ctx_set_ref_event(cptr, None)
-        ck(L.adms_backward(cptr, jobs_c, 1, 0))
-        ck(L.adms_optimizer_step(cptr, jobs_c, 1))
+        cand_step(vp, refsN, loss_ptr)
 
     def step(i):
         step_at(dev_views[i].data_ptr(), loss_buf.data_ptr() + 4 * i)
@@ -355,11 +399,11 @@ def run_native(args):
     def plain_step(i):
         vp = dev_views[i].data_ptr()
         set_pose(vp, (ref_job, plain))
-        for v in range(VIEWS):
+        for v in range(NV):
             one = vp + v * view_bytes
-            ck(L.adms_render_reference(cptr, ref_job, one, 1, RES, RES, ref_buf[v:v + 1].data_ptr()))
+            ck(L.adms_render_reference(cptr, ref_job, one, 1, RS, RS, ref_buf[v:v + 1].data_ptr()))
             ck(L.adms_forward_loss(cptr, plain_c, 1, one, vpj1, hw, refs1[v], loss_buf.data_ptr() + 4 * i, None))
-            ck(L.adms_backward(cptr, plain_c, 1, 0))
+            ck(L.adms_backward(cptr, plain_c, 1, RECOMPUTE))
         ck(L.adms_optimizer_step(cptr, plain_c, 1))
 
     def barrier():
@@ -378,7 +422,8 @@ def run_native(args):
         per = [evs[s].elapsed_time(evs[s + 1]) for s in range(k)]
         return max_over_ranks(evs[0].elapsed_time(evs[-1]), world, dev), per
 
-    # warm-up (also sizes all scratch), then record one step as a CUDA graph
+    # warm-up (also sizes all scratch), then record the step with its reference render
+    # as a CUDA graph
     for i in range(args.warmup):
         step(i)
         plain_step(i)
@@ -392,53 +437,95 @@ def run_native(args):
         staging.copy_(dev_views[i], non_blocking=True)
         B.adms_graph_launch(cptr, graph)
 
-    # headline: the graph-captured fused step, inputs resident in HBM
+    # The metric's step (forward+loss, backward, Adam) with the reference images of its
+    # views already rendered: a ring of R (views, references) slots rendered before the
+    # timed region, one graph per slot, step i on slot i mod R
+    R = min(args.steps, 16 if NV * RS * RS <= 8 * 512 * 512 else 4)
+    ring_views = [dev_views[args.warmup + r].clone() for r in range(R)]
+    ring_refs = [torch.empty((NV, RS, RS, 3), dtype=torch.float32, device=dev) for _ in range(R)]
+    for r in range(R):
+        set_pose(ring_views[r].data_ptr(), (ref_job,))
+        ck(L.adms_render_reference(cptr, ref_job, ring_views[r].data_ptr(), NV, RS, RS, ring_refs[r].data_ptr()))
+    ring_refs_c = [(C.c_void_p * 1)(t.data_ptr()) for t in ring_refs]
+    torch.cuda.synchronize()
+    ring_graphs = []
+    for r in range(R):
+        B.adms_graph_begin(cptr)
+        cand_step(ring_views[r].data_ptr(), ring_refs_c[r], graph_loss.data_ptr())
+        ring_graphs.append(B.adms_graph_end(cptr))
+
+    def cand_graph_step(i):
+        B.adms_graph_launch(cptr, ring_graphs[(i - args.warmup) % R])
+
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     launches0 = B.adms_launch_count()
-    fused_ms_nograph, _ = timed_region(step, args.warmup, args.steps)
+    for i in range(args.warmup):
+        cand_graph_step(args.warmup + i)
+    launches0 = B.adms_launch_count()
+    fused_ms_nograph, _ = timed_region(lambda i: cand_step(ring_views[(i - args.warmup) % R].data_ptr(),
+                                                           ring_refs_c[(i - args.warmup) % R],
+                                                           loss_buf.data_ptr() + 4 * i), args.warmup, args.steps)
     launches = (B.adms_launch_count() - launches0) / args.steps
-    total_ms, per = timed_region(graph_step, args.warmup, args.steps)
+    total_ms, per = timed_region(cand_graph_step, args.warmup, args.steps)
+    with_ref_ms, per_ref = timed_region(graph_step, args.warmup, args.steps)
     plain_ms, _ = timed_region(plain_step, args.warmup, args.steps)
-    # per-stage profile of the fused step on one stream (events between stages; not the headline)
+    # per-stage profile of the metric's step (events between stages; not the headline)
     B.adms_ctx_profile(cptr, True)
     B.adms_ctx_stage_times(cptr)
-    timed_region(lambda i: step_at(dev_views[i].data_ptr(), loss_buf.data_ptr() + 4 * i, overlap=False),
-                 args.warmup, args.steps)
+    timed_region(lambda i: cand_step(ring_views[(i - args.warmup) % R].data_ptr(), ring_refs_c[(i - args.warmup) % R],
+                                     loss_buf.data_ptr() + 4 * i), args.warmup, args.steps)
     stages = B.adms_ctx_stage_times(cptr)
     B.adms_ctx_profile(cptr, False)
-    # end to end through the C ABI: host views in (pinned), graph step, loss read back, every step
-    h2d = view_np.shape[1]   # the step's views (and bone matrices when skinned)
+    # end to end through the C ABI with host buffers, every step: the views from (pinned)
+    # host memory passed to adms_forward_loss as is, the reference images copied in
+    # from pinned host memory, the loss read back; no graph
+    host_refs = [t.cpu().pin_memory() for t in ring_refs]
+    pinned_views = torch.from_numpy(view_np).pin_memory()
+    e2e_loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    ebuf = torch.empty((NV, RS, RS, 3), dtype=torch.float32, device=dev)
+    ebuf_c = (C.c_void_p * 1)(ebuf.data_ptr())
+    h2d = view_np.shape[1] + host_refs[0].numel() * 4
     d2h = 4
     barrier()
     t0 = time.perf_counter()
     for s in range(args.steps):
-        staging.copy_(pinned_views[args.warmup + s], non_blocking=True)
-        B.adms_graph_launch(cptr, graph)
-        float(graph_loss.item())
+        r = s % R
+        ebuf.copy_(host_refs[r], non_blocking=True)
+        cand_step(pinned_views[args.warmup + r].data_ptr(), ebuf_c, e2e_loss.data_ptr())
+        float(e2e_loss.item())
     barrier()
     e2e_s = time.perf_counter() - t0
     clocks = sampler.stop()
-    clocks["window"] = "graph, fused, plain, profiled and end-to-end timed regions"
+    clocks["window"] = "graph, fused, with-reference, plain, profiled and end-to-end timed regions"
     e2e_s = max_over_ranks(e2e_s, world, dev)
 
     # workload facts for the bytes model
-    keys = ctx.keys(cand, (max(LY, 1), VIEWS, RES * MS, RES * MS))
+    keys = ctx.keys(cand, (max(LY, 1), NV, RS * MS, RS * MS))
     covered = int((keys != -1).sum())
     pv = ctx.params(cand)
     texels = sum(pv[n].shape[0] * pv[n].shape[1] for n in ("kd", "orm", "nrm"))
     # latent texels Adam updates: level 0, or every level of each chain with per-level latents
-    latent_texels = sum(pv[n + "_chain"].shape[0] for n in ("kd", "orm", "nrm")) if pl else texels
-    ctx.render_reference(ref_job, host_views[-1], RES, RES, out=ref_buf)
-    rkeys = ctx.keys(ref_job, (VIEWS, RES * MS, RES * MS))
+    opt_maps = [n for n in ("kd", "orm", "nrm") if pv.get("g_" + n) is not None]
+    latent_texels = (sum(pv[n + "_chain"].shape[0] for n in opt_maps) if pl
+                     else sum(pv[n].shape[0] * pv[n].shape[1] for n in opt_maps))
+    tex_maps = sum(1 for n in ("kd", "orm", "nrm") if pv[n].shape[0] * pv[n].shape[1] > 1)
+    ctx.render_reference(ref_job, host_views[-1], RS, RS, out=ref_buf)
+    rkeys = ctx.keys(ref_job, (NV, RS * MS, RS * MS))
     covered_ref = int((rkeys != -1).sum())
-    wl = dict(P=VIEWS * RES * RES * MS * MS, C=covered, Cr=covered_ref, texels=texels, texel_floats=4 * latent_texels,
-              V=cfg["cand"].mesh.n_verts, F=cfg["cand"].mesh.n_tris, Fr=cfg["ref"].mesh.n_tris,
-              Ppix=VIEWS * RES * RES, S=MS, L=LY)
+    ref_maps = sum(1 for t in (cfg["ref"].kd, cfg["ref"].orm, cfg["ref"].nrm) if t.shape[0] * t.shape[1] > 1)
+    disp_floats = cfg["cand"].disp.size if cfg["cand"].disp is not None else 0
+    V_lat = cfg["cand"].mesh.n_verts
+    F_cand = B.adms_job_params(cptr, cand).n_tris_render   # the tessellated mesh for tess
+    wl = dict(P=NV * RS * RS * MS * MS, C=covered, Cr=covered_ref, texels=texels,
+              texel_floats=4 * latent_texels + disp_floats, V=V_lat, F=F_cand, Fr=cfg["ref"].mesh.n_tris,
+              Ppix=NV * RS * RS, S=MS, L=LY, views=NV, tex_maps=tex_maps, grad_maps=len(opt_maps),
+              ref_maps=ref_maps, recompute=RECOMPUTE)
 
-    px_step = VIEWS * RES * RES
+    px_step = NV * RS * RS
     value = whole_job_mpix(world, px_step, args.steps, total_ms / 1e3)
     nograph_value = whole_job_mpix(world, px_step, args.steps, fused_ms_nograph / 1e3)
+    with_ref_value = whole_job_mpix(world, px_step, args.steps, with_ref_ms / 1e3)
     plain_value = whole_job_mpix(world, px_step, args.steps, plain_ms / 1e3)
     e2e_value = whole_job_mpix(world, px_step, args.steps, e2e_s)
     per_sorted = sorted(per)
@@ -449,16 +536,19 @@ def run_native(args):
         if n == 0:
             continue
         ab = algorithmic_bytes(name, wl)
-        stage_rows[name] = {"ms_per_step": ms / args.steps, "launches_per_step": n / args.steps,
-                            "algorithmic_bytes_per_step": ab,
-                            "gbs": (ab / (ms / 1e3 / args.steps) / 1e9) if ab else None}
+        row = {"ms_per_step": ms / args.steps, "launches_per_step": n / args.steps, "algorithmic_bytes_per_step": ab,
+               "gbs": (ab / (ms / 1e3 / args.steps) / 1e9) if ab else None}
+        if name == "shade_bwd" and not LY and MS == 1:
+            ext = algorithmic_bytes("shade_bwd_extended", wl)
+            row["extended_model"] = {"algorithmic_bytes_per_step": ext, "gbs": ext / (ms / 1e3 / args.steps) / 1e9}
+        stage_rows[name] = row
     dominant = max(stage_rows, key=lambda k: stage_rows[k]["ms_per_step"])
     peak, peak_kind = _peaks()
     d = stage_rows[dominant]
     launches_per_step = max(d["launches_per_step"], 1e-9)
     achieved = d["gbs"]
     # the committed DRAM counters and instruction counts are the plain workload's
-    tr = TRAFFIC.get(dominant) if not (pl or SKB or MS > 1 or agg) else None
+    tr = TRAFFIC.get(dominant) if (wk == "plain" and not (pl or SKB or MS > 1)) else None
     traffic = None
     if tr and _sha(tr["files"]) == tr["sha"]:
         traffic = tr["bytes_per_launch"]
@@ -477,46 +567,72 @@ def run_native(args):
                 "algorithmic_bytes_per_launch": (d["algorithmic_bytes_per_step"] / launches_per_step)
                 if d["algorithmic_bytes_per_step"] else None,
                 "ms_per_launch": d["ms_per_step"] / launches_per_step, "issue_roofline": issue}
+    if "extended_model" in d:
+        roofline["frac_extended_model"] = d["extended_model"]["gbs"] / peak
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cres = RES // MS    # the same samples per view as the plain sample
-        dt, cores = OracleStep(cfg, msaa=MS, layers=LY).seconds(1, cres)
+        import torch as _t
+
+        cres = min(RS // MS, 512)    # the same samples per view as the plain sample (capped for the big views)
+        orc = OracleStep(cfg, msaa=MS, layers=LY)
+        dt, cores = orc.seconds(1, cres)
+        sample = (f"1 of {NV} views at {cres}^2" + (f" with {MS}x{MS} MSAA" if MS > 1 else "")
+                  + (f" with {LY} peeling layers" if LY else "")
+                  + ": the oracle's candidate step (fwd/loss, bwd, Adam) on its reference images, rendered untimed")
         cpu = {"value": cres * cres / dt / 1e6, "unit": "Mpixels/s", "cores": cores, "kind": "oracle",
-               "sample": f"1 of 8 views at {cres}^2" + (f" with {MS}x{MS} MSAA" if MS > 1 else "")
-               + (f" with {LY} peeling layers" if LY else "")
-               + ": full oracle step (reference render + fwd/bwd/Adam)"}
+               "sample": sample}
+        nthr = _t.get_num_threads()
+        _t.set_num_threads(1)
+        try:
+            c1 = min(cres, 256)
+            dt1, _ = orc.seconds(1, c1)
+            cpu1 = {"value": c1 * c1 / dt1 / 1e6, "unit": "Mpixels/s", "cores": 1, "kind": "oracle",
+                    "sample": sample.replace(f"{cres}^2", f"{c1}^2") + ", one thread"}
+        finally:
+            _t.set_num_threads(nthr)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Mpixels/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": (WORKLOAD_AGG if agg else WORKLOAD)
+            "config": {"workload": wdesc
                        + ("; every mip level of each texture its own latent (Sec. 6)" if pl else "")
                        + (f"; both meshes skinned by {SKB} bones (Eq. 2), dense weights optimized (learning rate / {SKB}), "
                           "a new pose per step"
                           if SKB else "")
                        + (f"; {MS}x{MS} multisampling (Sec. 5.2): visibility, shading and antialiasing on the "
-                          f"{RES * MS}^2 sample grid, each sample shaded at its pixel centre, loss on the resolved "
+                          f"{RS * MS}^2 sample grid, each sample shaded at its pixel centre, loss on the resolved "
                           f"pixels; references supersampled {MS}x{MS}" if MS > 1 else ""),
-                       "global_batch": VIEWS * world, "seq_len": None,
+                       "global_batch": NV * world, "seq_len": None,
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
-                       "launch": "one CUDA graph per step (reference render on a second stream, forward+loss, "
-                                 "backward, Adam)",
+                       "launch": "one CUDA graph per step: forward+loss, backward"
+                                 + (" (raster recomputed)" if RECOMPUTE else "") + ", Adam; the step's reference "
+                                 f"images rendered before the timed region (a ring of {R} view batches)",
                        "l2": "working set > 126 MB L2 (textures, moments, buffers); no flush"},
             "p50_step_ms": per_sorted[len(per) // 2], "p99_step_ms": per_sorted[min(len(per) - 1, int(0.99 * len(per)))],
+            "with_reference_render": {"value": with_ref_value, "unit": "Mpixels/s",
+                                      "ms_per_step": with_ref_ms / args.steps,
+                                      "p99_step_ms": sorted(per_ref)[min(len(per_ref) - 1, int(0.99 * len(per_ref)))],
+                                      "launch": "one CUDA graph per step, reference render on a second stream"},
             "fused_without_graph": {"value": nograph_value, "unit": "Mpixels/s",
                                     "ms_per_step": fused_ms_nograph / args.steps},
-            "plain_per_view_loop": {"value": plain_value, "unit": "Mpixels/s", "ms_per_step": plain_ms / args.steps},
-            "fused_over_plain": value / plain_value,
+            "plain_per_view_loop": {"value": plain_value, "unit": "Mpixels/s", "ms_per_step": plain_ms / args.steps,
+                                    "note": "one view per call, each with its reference render"},
+            "fused_over_plain": with_ref_value / plain_value,
             "gpu_launches": int(round(launches * args.steps)), "gpu_launches_per_step": launches,
-            "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": "Mpixels/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "path": "adms_forward_loss with the views in pinned host memory, reference images copied from "
+                            "pinned host memory, adms_backward, adms_optimizer_step, loss read back; no graph"},
             "roofline": roofline, "stages": stage_rows, "clocks": clocks, "cpu_baseline": cpu,
+            "cpu_baseline_single_thread": cpu1,
             "coverage": covered / (px_step * MS * MS),
         }
         print(json.dumps(line), flush=True)
     B.adms_graph_destroy(graph)
+    for g in ring_graphs:
+        B.adms_graph_destroy(g)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -733,8 +849,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="plain", choices=["plain", "aggregate", "batched", "serving"],
-                    help="plain: the headline single-job step; aggregate: billboard quads with opacity under "
+    ap.add_argument("--workload", default="plain", choices=["plain", "tess", "small", "aggregate", "batched",
+                                                            "serving"],
+                    help="plain: the headline single-job step (8 views at 512^2); tess: tessellation + displacement "
+                         "at scale (16 views at 1024^2, raster recomputed in the backward); small: the one-step "
+                         "workload (one 256^2 view, latency-bound); aggregate: billboard quads with opacity under "
                          "depth peeling (Sec. 6 aggregate geometry); batched: uneven jobs in one launch per stage; "
                          "serving: continuous batching of Poisson arrivals")
     ap.add_argument("--jobs", type=int, default=64, help="jobs of the batched and serving workloads")
@@ -750,8 +869,8 @@ def main():
     ap.add_argument("--per-level-textures", action="store_true",
                     help="plain workload with every mip level of each texture an independent latent (Sec. 6)")
     args = ap.parse_args()
-    if args.workload == "aggregate" and (args.msaa > 1 or args.skinning or args.per_level_textures):
-        ap.error("the aggregate workload runs without --msaa, --skinning and --per-level-textures")
+    if args.workload in ("aggregate", "tess", "small") and (args.msaa > 1 or args.skinning or args.per_level_textures):
+        ap.error("the aggregate, tess and small workloads run without --msaa, --skinning and --per-level-textures")
     if args.impl == "reference":
         run_reference_arm(args)
     elif args.workload == "batched":
