@@ -53,7 +53,8 @@ typedef enum {
     ADMS_ERR_BUDGET = -2,    /* allocation would exceed the context's HBM budget */
     ADMS_ERR_CUDA = -3,      /* a CUDA runtime call failed */
     ADMS_ERR_TIMEOUT = -4,   /* a bounded device wait gave up */
-    ADMS_ERR_NONFINITE = -5, /* a loss or gradient was NaN/Inf; the job is quarantined */
+    ADMS_ERR_NONFINITE = -5, /* a loss or gradient was NaN/Inf: latched in the job's status on the
+                                device (see adms_jobs_status), its optimizer steps are skipped */
     ADMS_ERR_STATE = -6      /* call out of order (e.g. backward before forward) */
 } adms_status;
 
@@ -238,6 +239,11 @@ adms_status adms_job_set_bones(adms_ctx* ctx, adms_job job, const float* bones);
 adms_status adms_job_reserve(adms_ctx* ctx, adms_job job, int32_t n_views, int32_t H, int32_t W);
 adms_status adms_job_params(adms_ctx* ctx, adms_job job, adms_param_view* out);
 adms_status adms_job_stats(adms_ctx* ctx, adms_job job, adms_stats* out);
+/* The latched status of each job (0, or e.g. ADMS_ERR_NONFINITE) into out
+ * (device, [n_jobs] int32), ordered on the context's stream like the step
+ * calls, without synchronising: a scheduler reads it back with the losses.
+ * n_jobs in [1, 512]. */
+adms_status adms_jobs_status(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, int32_t* out);
 
 /* ---- the step (Sec. 3, Eq. 1) --------------------------------------------- */
 
@@ -271,7 +277,14 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
  * lambda_0 heuristic at t = 0), lr_t = lr0 10^(-0.0002 t) and one Adam step
  * (beta = 0.9, 0.999, eps = 1e-8) on every optimized latent, fused with the
  * adjoint of the mip chain and followed by clamping and a mip rebuild; zeroes
- * the gradients and advances t. */
+ * the gradients and advances t.
+ * Failure detection (no counterpart in the paper): a job whose status is
+ * latched is not updated (its latents, moments and gradients are left as they
+ * are). The status latches ADMS_ERR_NONFINITE on the device when a forward's
+ * loss is NaN or infinite, when a vertex-stage gradient sum of the backward is,
+ * or (from the next step on) when this step meets a non-finite gradient
+ * element, which it leaves unapplied; no latent ever receives a NaN or an
+ * infinity from an update. The other jobs of a batched call are unaffected. */
 adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs);
 
 /* Level-0 gradient of each optimized texture with the adjoint of the box-filter

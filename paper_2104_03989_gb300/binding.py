@@ -108,6 +108,7 @@ SIGNATURES = {
     "adms_job_set_bones": ([P, C.c_int32, P], C.c_int),
     "adms_job_params": ([P, C.c_int32, C.POINTER(adms_param_view)], C.c_int),
     "adms_job_stats": ([P, C.c_int32, C.POINTER(adms_stats)], C.c_int),
+    "adms_jobs_status": ([P, P, C.c_int32, P], C.c_int),
     "adms_render_reference": ([P, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P], C.c_int),
     "adms_forward_loss": ([P, P, C.c_int32, P, P, P, P, P, P], C.c_int),
     "adms_backward": ([P, P, C.c_int32, C.c_int32], C.c_int),
@@ -289,6 +290,12 @@ def adms_job_stats(ctx, job):
     out = adms_stats()
     _check(ctx, lib().adms_job_stats(ctx, job, C.byref(out)))
     return out
+
+
+def adms_jobs_status(ctx, jobs, out):
+    """Each job's latched status into the device int32 tensor out (stream-ordered)."""
+    arr = (C.c_int32 * len(jobs))(*jobs)
+    _check(ctx, lib().adms_jobs_status(ctx, arr, len(jobs), ptr(out)))
 
 
 def adms_render_reference(ctx, job, views, H, W, out_rgb):

@@ -375,6 +375,7 @@ FrameArgs frame_args(Job& j) {
     f.tmp_t = j.tmp_t;
     f.g_pos_acc = j.g_pos_acc;
     f.g_pos = j.g_rpos;
+    f.status = &j.st->status;
     return f;
 }
 
@@ -398,6 +399,7 @@ FrameArgs base_frame_args(Job& j) {
     f.tmp_t = j.b_tmp_t;
     f.g_pos_acc = j.g_bpos_acc;
     f.g_pos = j.g_pos;
+    f.status = &j.st->status;
     return f;
 }
 
@@ -443,8 +445,7 @@ ShadeArgs shade_args(Job& j) {
     a.uv = j.uv;
     a.tri = j.tri;
     a.tri_uv = j.tri_uv;
-    a.adj = j.adj;
-    a.asign = j.rs.asign;
+    a.status = &j.st->status;
     a.silmask = j.rs.silmask;
     a.keys = j.keys;
     a.kd = j.kd.dev();
@@ -1377,6 +1378,19 @@ adms_status adms_job_set_bones(adms_ctx* ctx, adms_job job, const float* bones) 
     if (!j->skin) return fail(ctx, ADMS_ERR_STATE, "the job has no skinning (adms_job_skinning)");
     CK(cudaMemcpyAsync(j->bones, bones, sizeof(float) * 16 * j->SB, cudaMemcpyDefault, ctx->stream));
     j->frame_valid = false;
+    return ADMS_OK;
+}
+
+adms_status adms_jobs_status(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, int32_t* out) {
+    if (!ctx || !jobs || !out || n_jobs <= 0 || n_jobs > ADMS_STATUS_MAX)
+        return fail(ctx, ADMS_ERR_ARG, "invalid jobs_status arguments");
+    std::vector<JobState*> sts;
+    for (int k = 0; k < n_jobs; ++k) {
+        Job* j = get_job(ctx, jobs[k]);
+        if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+        sts.push_back(j->st);
+    }
+    CK(gather_status(sts.data(), n_jobs, out, ctx->stream));
     return ADMS_OK;
 }
 

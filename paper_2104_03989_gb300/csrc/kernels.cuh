@@ -93,8 +93,8 @@ struct ShadeArgs {
     const float2* uv;                // [T]
     const int* tri;                  // [F][3]
     const int* tri_uv;               // [F][3]
-    const int* adj;                  // [F][3] face across edge (tri[f][k], tri[f][k+1]) or -1
-    const int8_t* asign;             // [B][F]
+    int* status;                     // the job's latched status word (JobState::status), or null: set to
+                                     // ADMS_ERR_NONFINITE when a vertex gradient sum is NaN or infinite
     const uint8_t* silmask;          // [B][F]
     const unsigned long long* keys;  // [B][H][W]
     TexDev kd, orm, nrm;
@@ -149,7 +149,7 @@ struct WorkItem {
     int job, view, x0, y0;
 };
 // Jobs per batched launch: their arguments travel in the launch's parameter
-// space (60 x 544 B, under the 32 KB limit), read-only and captured with the
+// space (60 x 536 B, under the 32 KB limit), read-only and captured with the
 // launch by a graph; larger job sets take one launch per 60 jobs.
 #define ADMS_BATCH_JOBS 60
 struct ShadeBatch {
@@ -204,6 +204,7 @@ struct FrameArgs {
     float4* tmp_t;        // scratch [V]
     double* g_pos_acc;    // in  [V][3] pixel-stage position gradient; read and zeroed
     float* g_pos;         // accumulated [V][3]
+    int* status = nullptr; // latched ADMS_ERR_NONFINITE when a position gradient is NaN or infinite
 };
 cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st);
 cudaError_t frame_backward(const FrameArgs& a, cudaStream_t st);
@@ -253,8 +254,8 @@ struct JobState {
     float lam, lam0, lr, bc1, bc2;
     float last_img_loss, last_lap;
     int t;
-    int status;
-    int pad;
+    int status;        // 0 or a latched adms_status; constant during an optimizer step
+    int status_next;   // latched by the optimizer step's kernels, folded into status when t advances
 };
 
 struct LapArgs {
@@ -319,6 +320,9 @@ bool adam_tiled(const TexDev& t);
 // tile per block, one launch per ADMS_ADAM_TEX textures
 cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st);
 cudaError_t advance_step(JobState* js, cudaStream_t st);
+// out[k] = the latched status of job k (stream-ordered; out: device [n])
+#define ADMS_STATUS_MAX 512
+cudaError_t gather_status(JobState* const* js, int n, int* out, cudaStream_t st);
 // out[j] = call_loss; img_loss += call_loss
 cudaError_t finish_call_loss(JobState* js, float* out, cudaStream_t st);
 

@@ -91,9 +91,11 @@ __global__ void k_frame_bwd2(FrameArgs a) {
         if (ff.idx[2] == v) g += ge2;
     }
     double* acc = a.g_pos_acc + 3 * v;
-    a.g_pos[3 * v] += (float)(acc[0] + (double)g.x);
-    a.g_pos[3 * v + 1] += (float)(acc[1] + (double)g.y);
-    a.g_pos[3 * v + 2] += (float)(acc[2] + (double)g.z);
+    double g0 = acc[0] + (double)g.x, g1 = acc[1] + (double)g.y, g2 = acc[2] + (double)g.z;
+    if (a.status && !(isfinite(g0) && isfinite(g1) && isfinite(g2))) atomicExch(a.status, (int)ADMS_ERR_NONFINITE);
+    a.g_pos[3 * v] += (float)g0;
+    a.g_pos[3 * v + 1] += (float)g1;
+    a.g_pos[3 * v + 2] += (float)g2;
     acc[0] = 0.0;
     acc[1] = 0.0;
     acc[2] = 0.0;

@@ -47,11 +47,31 @@ cudaError_t schedule_step(const SchedArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-__global__ void k_advance(JobState* s) { s->t += 1; }
+__global__ void k_advance(JobState* s) {
+    s->t += 1;
+    if (s->status_next) s->status = s->status_next;
+}
 
 __global__ void k_finish_call(JobState* s, float* out) {
     if (out) *out = (float)s->call_loss;
     s->img_loss += s->call_loss;
+    if (!isfinite(s->call_loss)) s->status = ADMS_ERR_NONFINITE;  // latched: the optimizer skips the job
+}
+
+struct StatusPtrs {
+    JobState* p[ADMS_STATUS_MAX];
+};
+__global__ void k_gather_status(const StatusPtrs P, int n, int* out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = P.p[k]->status;
+}
+cudaError_t gather_status(JobState* const* js, int n, int* out, cudaStream_t st) {
+    if (n <= 0 || n > ADMS_STATUS_MAX) return cudaErrorInvalidValue;
+    StatusPtrs P;
+    for (int k = 0; k < n; ++k) P.p[k] = js[k];
+    k_gather_status<<<(n + 127) / 128, 128, 0, st>>>(P, n, out);
+    count_launches(1);
+    return cudaGetLastError();
 }
 cudaError_t finish_call_loss(JobState* js, float* out, cudaStream_t st) {
     k_finish_call<<<1, 1, 0, st>>>(js, out);
@@ -64,20 +84,36 @@ cudaError_t advance_step(JobState* js, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// One Adam update. A job whose status is latched (a non-finite loss or gradient
+// was seen) is skipped whole by its kernels; a non-finite gradient element met
+// here (one the earlier checks missed) leaves its latent and moments unchanged
+// and latches status_next (status itself stays constant while the step's
+// kernels run, so every tile of a texture takes the same branch), so no NaN or
+// infinity is ever written into a latent.
 __device__ __forceinline__ float adam1(float p, float g, float& m, float& v, float lr, float bc1, float bc2) {
-    m = 0.9f * m + 0.1f * g;
-    v = 0.999f * v + 0.001f * g * g;
-    float mh = m / bc1, vh = v / bc2;
-    return p - lr * mh / (sqrtf(vh) + 1e-8f);
+    bool ok = isfinite(g);
+    float m1 = 0.9f * m + 0.1f * g;
+    float v1 = 0.999f * v + 0.001f * g * g;
+    float mh = m1 / bc1, vh = v1 / bc2;
+    float p1 = p - lr * mh / (sqrtf(vh) + 1e-8f);
+    m = ok ? m1 : m;
+    v = ok ? v1 : v;
+    return ok ? p1 : p;
+}
+__device__ __forceinline__ void latch_nonfinite(const JobState* js, float a, float b = 0.f, float c = 0.f,
+                                                float d = 0.f) {
+    if (!(isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d)))
+        atomicExch(&const_cast<JobState*>(js)->status_next, (int)ADMS_ERR_NONFINITE);
 }
 
 __global__ void k_adam_flat(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                             long long n, const JobState* __restrict__ js, float lr_scale) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || js->status) return;
     float lr = js->lr * lr_scale, bc1 = js->bc1, bc2 = js->bc2;
-    float mm = m[i], vv = v[i];
-    p[i] = adam1(p[i], g[i], mm, vv, lr, bc1, bc2);
+    float mm = m[i], vv = v[i], gi = g[i];
+    latch_nonfinite(js, gi);
+    p[i] = adam1(p[i], gi, mm, vv, lr, bc1, bc2);
     m[i] = mm;
     v[i] = vv;
     g[i] = 0.f;
@@ -116,9 +152,10 @@ __device__ __forceinline__ float4 clamp_texel(float4 p, int clamp_kind) {
 __global__ void k_adam_tex_levels(TexDev t, float4* __restrict__ m, float4* __restrict__ v, long long n,
                                   int clamp_kind, const JobState* __restrict__ js) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || js->status) return;
     float lr = js->lr, bc1 = js->bc1, bc2 = js->bc2;
     float4 g = t.grad[i], p = t.tex[i], mm = m[i], vv = v[i];
+    latch_nonfinite(js, g.x, g.y, g.z, g.w);
     p.x = adam1(p.x, g.x, mm.x, vv.x, lr, bc1, bc2);
     p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
     p.z = adam1(p.z, g.z, mm.z, vv.z, lr, bc1, bc2);
@@ -141,7 +178,7 @@ __global__ void k_adam_tex(TexDev t, float4* __restrict__ m, float4* __restrict_
                            const JobState* __restrict__ js) {
     int n = t.w0 * t.h0;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || js->status) return;
     int x = i % t.w0, y = i / t.w0;
     float4 g = t.grad[i];
     // adjoint of the box-filter chain: level k texel = mean of its children
@@ -154,6 +191,7 @@ __global__ void k_adam_tex(TexDev t, float4* __restrict__ m, float4* __restrict_
         g = f4madd(g, wgt, gk);
     }
     float lr = js->lr, bc1 = js->bc1, bc2 = js->bc2;
+    latch_nonfinite(js, g.x, g.y, g.z, g.w);
     float4 p = t.tex[i], mm = m[i], vv = v[i];
     p.x = adam1(p.x, g.x, mm.x, vv.x, lr, bc1, bc2);
     p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
@@ -215,6 +253,7 @@ __global__ void __launch_bounds__(256) k_adam_tex_batch(const TexAdamBatch P) {
         else hi = mid - 1;
     }
     const TexAdam& A = P.a[lo];
+    if (A.js->status) return;  // every tile of a latched job's texture leaves (its tile counter stays 0)
     const TexDev& t = A.t;
     int tb = (int)blockIdx.x - A.tile0;
     int tiles_x = t.w0 >> 5, n_tiles = tiles_x * (t.h0 >> 5);
@@ -248,6 +287,7 @@ __global__ void __launch_bounds__(256) k_adam_tex_batch(const TexAdamBatch P) {
         int x = (bx << 5) + lx, y = (by << 5) + ly;
         int i = y * t.w0 + x;
         float4 g = f4madd(t.grad[i], 1.f, push[(ly >> 1) * 16 + (lx >> 1)]);
+        latch_nonfinite(A.js, g.x, g.y, g.z, g.w);
         tile[ly][lx] = adam_texel(t, A.m, A.v, i, g, A.clamp_kind, lr, bc1, bc2);
     }
     int top = min(5, t.levels - 1);

@@ -657,6 +657,7 @@ __device__ __forceinline__ void scatter_vertex_rows(const ShadeArgs& A, int f, c
                 int vtx = A.tri[3 * ft + corner];
                 double* dst = comp < 3 ? A.g_pos : (comp < 6 ? A.g_nrm : A.g_tan);
                 atomicAdd(dst + 3 * vtx + comp % 3, (double)sum);
+                if (!isfinite(sum) && A.status) atomicExch(A.status, (int)ADMS_ERR_NONFINITE);
             }
         }
         todo &= ~grp;

@@ -106,7 +106,6 @@ ShadeArgs stage_args(const adms_stage_mesh* m, const adms_view* views, int B, in
     a.uv = reinterpret_cast<const float2*>(m->uv);
     a.tri = m->tri;
     a.tri_uv = m->tri_uv;
-    a.adj = m->adj;
     a.aa = 1;
     return a;
 }
@@ -597,7 +596,6 @@ adms_status adms_aa_loss_fwd(const adms_stage_mesh* m, const adms_view* views, i
     ShadeArgs a = stage_args(m, views, n_views, H, W);
     a.clip = reinterpret_cast<const float4*>(clip);
     a.scr = w.s.scr;
-    a.asign = w.s.asign;
     a.silmask = w.s.silmask;
     a.keys = reinterpret_cast<const unsigned long long*>(keys);
     a.pre = reinterpret_cast<float4*>(const_cast<float*>(pre));
@@ -622,7 +620,6 @@ adms_status adms_aa_loss_bwd(const adms_stage_mesh* m, const adms_view* views, i
     ShadeArgs a = stage_args(m, views, n_views, H, W);
     a.clip = reinterpret_cast<const float4*>(clip);
     a.scr = w.s.scr;
-    a.asign = w.s.asign;
     a.silmask = w.s.silmask;
     a.keys = reinterpret_cast<const unsigned long long*>(keys);
     a.pre = reinterpret_cast<float4*>(const_cast<float*>(pre));

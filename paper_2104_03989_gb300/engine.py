@@ -146,6 +146,12 @@ class Context:
         b = bones if isinstance(bones, torch.Tensor) else _c32(bones, np.float32)
         B.adms_job_set_bones(self.ctx, job, b)
 
+    def jobs_status(self, jobs):
+        """Device int32 tensor of each job's latched status (0 or an adms status), stream-ordered."""
+        out = torch.empty(len(jobs), dtype=torch.int32, device="cuda")
+        B.adms_jobs_status(self.ctx, list(jobs), out)
+        return out
+
     def stats(self, job):
         s = B.adms_job_stats(self.ctx, job)
         return dict(image_loss=s.image_loss, laplacian=s.laplacian, lam=s.lambda_, lr=s.lr, t=s.t,

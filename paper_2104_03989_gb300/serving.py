@@ -8,10 +8,11 @@ first out. Every iteration takes one step of every live job at once: fresh
 random views per job (keyed by the job's seed and its own iteration count,
 so a job's result does not depend on who shares its batches), a reference
 render per job, then forward + loss, backward and Adam for all live jobs in
-one batched call per stage (one persistent launch per pixel stage). Jobs that
+one batched call per stage (one launch per pixel stage). Jobs that
 reach their iteration count retire and free their memory for waiting
-requests. A job whose loss turns non-finite is quarantined (retired with an
-error) without disturbing the others; a cancelled request leaves the queue, or
+requests. A job whose loss or gradients turn non-finite (latched on the device,
+where its optimizer steps are then skipped) is quarantined (retired with that
+status) without disturbing the others; a cancelled request leaves the queue, or
 retires between iterations, and frees its memory the same way.
 
 All arithmetic runs in libadms.so; this module schedules.
@@ -56,6 +57,7 @@ class JobRecord:
     admitted: float = 0.0
     finished: float = 0.0
     status: str = "waiting"   # waiting, running, done, quarantined, rejected
+    status_code: int = 0      # the latched device status of a quarantined job (e.g. ADMS_ERR_NONFINITE)
     losses: list = field(default_factory=list)
     ref_buf: torch.Tensor = None
 
@@ -217,6 +219,9 @@ class SimplificationServer:
         self.ctx.backward(jobs)
         self.ctx.step(jobs)
         read = (self.live[0].it % self.loss_every) == 0
+        # the latched device status of each job (a non-finite loss or gradient), read
+        # back with the losses: such a job was not updated and is quarantined
+        status = self.ctx.jobs_status(jobs).cpu().numpy() if read else None
         vals = loss.cpu().numpy() if read else None
         self.stream.synchronize()
         ms = (time.perf_counter() - t) * 1e3
@@ -226,7 +231,8 @@ class SimplificationServer:
             self.pixels += rec.req.n_views * rec.req.res * rec.req.res
             if vals is not None:
                 rec.losses.append(float(vals[k]))
-                if not math.isfinite(float(vals[k])):
+                if status[k] != 0 or not math.isfinite(float(vals[k])):
+                    rec.status_code = int(status[k])
                     self._retire(rec, "quarantined")
                     continue
             if rec.it >= rec.req.iterations:

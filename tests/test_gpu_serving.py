@@ -133,6 +133,7 @@ def test_non_finite_job_is_quarantined_and_the_others_are_unchanged(alone):
     assert rep["done"] == 2 and rep["quarantined"] == 1
     status = {r.req.rid: r for r in srv.done}
     assert status[1].status == "quarantined" and status[1].it == 1 and not math.isfinite(status[1].losses[0])
+    assert status[1].status_code == B.ADMS_ERR_NONFINITE   # latched on the device
     for rid in (0, 2):
         assert status[rid].status == "done"
         _same(srv.results[rid], alone[rid])
