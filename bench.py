@@ -173,9 +173,9 @@ def algorithmic_bytes(stage, w):
         # read again plus the read-modify-write of the optimized maps' texel gradients
         return 20 * P + texel * (maps + 2 * w.get("grad_maps", 3)) * w["C"]
     if stage == "shade_bwd_extended":
-        # what this kernel reads per pixel beyond it: the pre-AA colour (16 B, the AA
-        # adjoint's tau term) and dL/dx padded to 16 B with the blend bits (+20 B)
-        return 40 * P + texel * (maps + 2 * w.get("grad_maps", 3)) * w["C"]
+        # this kernel's own layout: dL/dx travels as a 16-byte record with the pair
+        # blend bits in its fourth word (key 8 + 16 per pixel instead of 8 + 12)
+        return 24 * P + texel * (maps + 2 * w.get("grad_maps", 3)) * w["C"]
     rc = 1 + w.get("recompute", 0)    # the backward recomputes raster, shading and AA once more
     if stage == "shade":
         return (24 * P + tex_px * w["C"]) * rc               # key read, colour write; texels of covered pixels
