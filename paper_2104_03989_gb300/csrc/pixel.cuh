@@ -28,6 +28,19 @@ struct PixGeo {
     float2 duv_dx, duv_dy;
 };
 
+// a / b: IEEE division, or with FAST the approximate division (2 ulp). FAST is taken
+// only where the result feeds a gradient (the backward's recomputation and
+// adjoints, held to 1e-3); images and visibility keep IEEE arithmetic.
+template <bool FAST>
+__device__ __forceinline__ float fdiv(float a, float b) {
+    return FAST ? __fdividef(a, b) : a / b;
+}
+// sqrt(x) for x > 0: IEEE, or with FAST x rsqrt(x) (approximate, as fdiv)
+template <bool FAST>
+__device__ __forceinline__ float fsqrt(float x) {
+    return FAST ? x * rsqrtf(x) : sqrtf(x);
+}
+
 __device__ __forceinline__ float2 rel_screen(float4 S, float ox, float oy) {
     return make_float2((S.x - ox) + S.y, (S.z - oy) + S.w);
 }
@@ -47,46 +60,48 @@ __device__ __forceinline__ void shade_point(const ShadeArgs& A, int px, int py, 
 // Perspective-correct barycentrics of sample (px, py) in triangle f: corner ids,
 // clip coordinates, screen offsets d_k from the shading point, e_k = cross(d_k+1,
 // d_k+2), lam_k = e_k / area, r_k = lam_k / w_k, beta_k = r_k / R.
+template <bool FAST = false>
 __device__ __forceinline__ void pix_bary(const ShadeArgs& A, int b, int px, int py, int f, PixGeo& g) {
     float qx, qy;
     shade_point(A, px, py, qx, qy);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        g.vi[k] = A.tri[3 * f + k];
-        g.ui[k] = A.tri_uv[3 * f + k];
+        g.vi[k] = __ldg(A.tri + (3 * f + k));
+        g.ui[k] = __ldg(A.tri_uv + (3 * f + k));
         size_t o = (size_t)b * A.V + g.vi[k];
-        g.c[k] = A.clip[o];
-        g.d[k] = rel_screen(A.scr[o], qx, qy);
+        g.c[k] = __ldg(A.clip + (o));
+        g.d[k] = rel_screen(__ldg(A.scr + (o)), qx, qy);
     }
     g.e[0] = cross2(g.d[1], g.d[2]);
     g.e[1] = cross2(g.d[2], g.d[0]);
     g.e[2] = cross2(g.d[0], g.d[1]);
     g.area = cross2(make_float2(g.d[1].x - g.d[0].x, g.d[1].y - g.d[0].y),
                     make_float2(g.d[2].x - g.d[0].x, g.d[2].y - g.d[0].y));
-    float ia = 1.f / g.area;
+    float ia = fdiv<FAST>(1.f, g.area);
     g.R = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         g.lam[k] = g.e[k] * ia;
-        g.r[k] = g.lam[k] / g.c[k].w;
+        g.r[k] = fdiv<FAST>(g.lam[k], g.c[k].w);
         g.R += g.r[k];
     }
-    float iR = 1.f / g.R;
+    float iR = fdiv<FAST>(1.f, g.R);
 #pragma unroll
     for (int k = 0; k < 3; ++k) g.beta[k] = g.r[k] * iR;
 }
 
 // screen derivatives of beta_1 and beta_2 per sample-grid step (texture LOD only):
 // (d beta_1 / dx, d beta_2 / dx, d beta_1 / dy, d beta_2 / dy)
+template <bool FAST = false>
 __device__ __forceinline__ float4 bary_derivs(const PixGeo& g) {
-    float ia = 1.f / g.area, iR = 1.f / g.R;
+    float ia = fdiv<FAST>(1.f, g.area), iR = fdiv<FAST>(1.f, g.R);
     float dlx[3] = {(g.d[1].y - g.d[2].y) * ia, (g.d[2].y - g.d[0].y) * ia, (g.d[0].y - g.d[1].y) * ia};
     float dly[3] = {(g.d[2].x - g.d[1].x) * ia, (g.d[0].x - g.d[2].x) * ia, (g.d[1].x - g.d[0].x) * ia};
     float drx[3], dry[3], dRx = 0.f, dRy = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        drx[k] = dlx[k] / g.c[k].w;
-        dry[k] = dly[k] / g.c[k].w;
+        drx[k] = fdiv<FAST>(dlx[k], g.c[k].w);
+        dry[k] = fdiv<FAST>(dly[k], g.c[k].w);
         dRx += drx[k];
         dRy += dry[k];
     }
@@ -129,10 +144,10 @@ __device__ __forceinline__ void pix_attr(const ShadeArgs& A, PixGeo& g, float b1
 // Perspective-correct barycentrics and interpolated attributes (corner 0 plus
 // weighted differences) of sample (px, py) inside triangle f. LOD = false skips
 // the screen derivatives of uv (the adjoint's second pass).
-template <bool LOD = true>
+template <bool LOD = true, bool FAST = false>
 __device__ __forceinline__ void pix_geo(const ShadeArgs& A, int b, int px, int py, int f, PixGeo& g) {
-    pix_bary(A, b, px, py, f, g);
-    pix_attr<LOD>(A, g, g.beta[1], g.beta[2], LOD ? bary_derivs(g) : make_float4(0.f, 0.f, 0.f, 0.f));
+    pix_bary<FAST>(A, b, px, py, f, g);
+    pix_attr<LOD>(A, g, g.beta[1], g.beta[2], LOD ? bary_derivs<FAST>(g) : make_float4(0.f, 0.f, 0.f, 0.f));
 }
 
 // ------------------------------------------------------------------ shading
@@ -170,8 +185,8 @@ __device__ __forceinline__ float3 shade_eval(const adms_view& vw, const ShadeIn&
     float3 kd = f3(in.kd.x, in.kd.y, in.kd.z);
     float3 ks = f3(0.04f, 0.04f, 0.04f) * (1.f - m) + m * kd;
     float3 diff = kd * ((1.f - m) * (1.f / ADMS_PI));
-    float sqv = sqrtf(a2 + (1.f - a2) * nv * nv);
-    float G1v = 2.f * nv / (nv + sqv);
+    float sqv = fsqrt<BWD>(a2 + (1.f - a2) * nv * nv);  // > 0: a2 >= 0.08^4
+    float G1v = fdiv<BWD>(2.f * nv, nv + sqv);
 
     float3 color = zero3();
     // backward accumulators
@@ -191,7 +206,7 @@ __device__ __forceinline__ float3 shade_eval(const adms_view& vw, const ShadeIn&
             Ln = nrm3(d);
             l = Ln.y;
             dd = dot3(d, d);
-            E = vw.light_I / dd;
+            E = fdiv<BWD>(vw.light_I, dd);
         } else {
             l = f3(vw.light_dir[0], vw.light_dir[1], vw.light_dir[2]);
             E = vw.light_E;
@@ -206,14 +221,14 @@ __device__ __forceinline__ float3 shade_eval(const adms_view& vw, const ShadeIn&
         // vectors: the cross-product form keeps float32 precision at sharp highlights
         float3 nxh = cross3(ns, h);
         float den = nh_raw > 0.f ? dot3(nxh, nxh) + a2 * nh * nh : 1.f;
-        float D = a2 / (ADMS_PI * den * den);
+        float D = fdiv<BWD>(a2, ADMS_PI * den * den);
         float om = 1.f - vh;
         float om2 = om * om;
         float om5 = om2 * om2 * om;
         float3 F = ks + (f3(1.f, 1.f, 1.f) - ks) * om5;
-        float sql = sqrtf(a2 + (1.f - a2) * nl * nl);
-        float G1l = 2.f * nl / (nl + sql);
-        float q4 = E / (4.f * nv);
+        float sql = fsqrt<BWD>(a2 + (1.f - a2) * nl * nl);
+        float G1l = fdiv<BWD>(2.f * nl, nl + sql);
+        float q4 = fdiv<BWD>(E, 4.f * nv);
         float S0 = D * G1l * G1v * q4;
         float S = (1.f - gam) * S0;
         color += (E * nl) * diff + S * F;
@@ -229,20 +244,20 @@ __device__ __forceinline__ float3 shade_eval(const adms_view& vw, const ShadeIn&
             float g_D = g_S0 * G1l * G1v * q4;
             float g_G1l = g_S0 * D * G1v * q4;
             float g_G1v = g_S0 * D * G1l * q4;
-            g_E += g_S0 * D * G1l * G1v / (4.f * nv);
-            g_nv += -g_S0 * S0 / nv;
+            g_E += fdiv<BWD>(g_S0 * D * G1l * G1v, 4.f * nv);
+            g_nv += fdiv<BWD>(-g_S0 * S0, nv);
             g_ks += g_F * (1.f - om5);
             float g_om5 = dot3(g_F, f3(1.f, 1.f, 1.f) - ks);
             float g_vh = -5.f * om2 * om2 * g_om5;
             float dl = sql * (nl + sql) * (nl + sql);
-            g_nl += g_G1l * 2.f * a2 / dl;
-            g_a2 += g_G1l * (-nl * (1.f - nl * nl) / dl);
+            g_nl += fdiv<BWD>(g_G1l * 2.f * a2, dl);
+            g_a2 += g_G1l * fdiv<BWD>(-nl * (1.f - nl * nl), dl);
             float dv = sqv * (nv + sqv) * (nv + sqv);
-            g_nv += g_G1v * 2.f * a2 / dv;
-            g_a2 += g_G1v * (-nv * (1.f - nv * nv) / dv);
+            g_nv += fdiv<BWD>(g_G1v * 2.f * a2, dv);
+            g_a2 += g_G1v * fdiv<BWD>(-nv * (1.f - nv * nv), dv);
             float pd3 = ADMS_PI * den * den * den;
-            g_a2 += g_D * (1.f / (ADMS_PI * den * den) - 2.f * a2 * nh * nh / pd3);
-            float g_nh = g_D * (-4.f * a2 * nh * (a2 - 1.f) / pd3);
+            g_a2 += g_D * (fdiv<BWD>(1.f, ADMS_PI * den * den) - fdiv<BWD>(2.f * a2 * nh * nh, pd3));
+            float g_nh = g_D * fdiv<BWD>(-4.f * a2 * nh * (a2 - 1.f), pd3);
             float g_nhr = nh_raw >= 0.f ? g_nh : 0.f;
             float g_vhr = vh_raw >= 0.f ? g_vh : 0.f;
             float3 g_h = g_nhr * ns + g_vhr * V;
@@ -254,7 +269,7 @@ __device__ __forceinline__ float3 shade_eval(const adms_view& vw, const ShadeIn&
             g_ns += g_nl * l;
             g_l += g_nl * ns;
             if (point) {
-                float3 g_d = nrm3_bwd(Ln, g_l) + (-2.f * E / dd * g_E) * d;
+                float3 g_d = nrm3_bwd(Ln, g_l) + (fdiv<BWD>(-2.f * E, dd) * g_E) * d;
                 g_p -= g_d;
             }
         }
@@ -390,7 +405,7 @@ __device__ __forceinline__ void shade_refine_px(const ShadeArgs& A, int pix) {
     int hw = A.H * A.W;
     int b = pix / hw, rem = pix - b * hw;
     int py = rem / A.W, px = rem - py * A.W;
-    int f = key_tri(A.keys[pix]);
+    int f = key_tri(__ldg(A.keys + (pix)));
     PixGeo g;
     pix_geo(A, b, px, py, f, g);
     refine_tc(A, b, px, py, g);
@@ -404,7 +419,7 @@ __device__ __forceinline__ void shade_refine_px(const ShadeArgs& A, int pix) {
         for (int y = oy; y < min(oy + sm, A.H); ++y)
             for (int x = ox; x < min(ox + sm, A.W); ++x) {
                 size_t q = ((size_t)b * A.H + y) * A.W + x;
-                if (key_tri(A.keys[q]) == f) A.pre[q] = v;
+                if (key_tri(__ldg(A.keys + (q))) == f) A.pre[q] = v;
             }
     } else {
         A.pre[pix] = v;
@@ -435,7 +450,7 @@ __device__ __forceinline__ float4 shade_covered(const ShadeArgs& A, int b, int p
 __device__ __forceinline__ void shade_fwd_px(const ShadeArgs& A, int b, int px, int py) {
     if (px >= A.W || py >= A.H) return;
     size_t pix = ((size_t)b * A.H + py) * A.W + px;
-    int f = key_tri(A.keys[pix]);
+    int f = key_tri(__ldg(A.keys + (pix)));
     A.pre[pix] = f >= 0 ? shade_covered(A, b, px, py, f, pix) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
@@ -473,14 +488,14 @@ __device__ __forceinline__ PairTau pair_tau(const ShadeArgs& A, int b, int axis,
     pt.tau = 0.5f;
     float best = 1e30f;
     float ox = (float)oi + 0.5f, oy = (float)oj + 0.5f;
-    unsigned mask = A.silmask[(size_t)b * A.F + fo];
+    unsigned mask = __ldg(A.silmask + ((size_t)b * A.F + fo));
     if (!mask) return pt;
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         if (!((mask >> e) & 1u)) continue;
-        int va = A.tri[3 * fo + e], vb = A.tri[3 * fo + (e + 1) % 3];
-        float2 sa = rel_screen(A.scr[(size_t)b * A.V + va], ox, oy);
-        float2 sb = rel_screen(A.scr[(size_t)b * A.V + vb], ox, oy);
+        int va = __ldg(A.tri + (3 * fo + e)), vb = __ldg(A.tri + (3 * fo + (e + 1) % 3));
+        float2 sa = rel_screen(__ldg(A.scr + ((size_t)b * A.V + va)), ox, oy);
+        float2 sb = rel_screen(__ldg(A.scr + ((size_t)b * A.V + vb)), ox, oy);
         float au = axis == 0 ? sa.y : sa.x, bu = axis == 0 ? sb.y : sb.x;
         float ax = axis == 0 ? sa.x : sa.y, bx = axis == 0 ? sb.x : sb.y;
         float den = bu - au;
@@ -587,7 +602,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
     double lsum = 0.0;
     if (inside) {
         size_t pix = ((size_t)b * A.H + py) * A.W + px;
-        unsigned long long kp = A.keys[pix];
+        unsigned long long kp = __ldg(A.keys + (pix));
         float3 cp = layer_colour<PEEL>(A, pix);
         float3 out = cp;
         unsigned amask = 0;  // neighbours whose pair blends (tau != 1/2): the backward visits only these
@@ -599,7 +614,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
                 if (qx < 0 || qx >= A.W || qy < 0 || qy >= A.H) continue;
                 size_t qpix = ((size_t)b * A.H + qy) * A.W + qx;
                 PairInfo pi;
-                if (!pair_eval(A, b, px, py, kp, qx, qy, A.keys[qpix], nbi < 2 ? 0 : 1, pi)) continue;
+                if (!pair_eval(A, b, px, py, kp, qx, qy, __ldg(A.keys + (qpix)), nbi < 2 ? 0 : 1, pi)) continue;
                 float om = pi.t.tau - 0.5f;
                 if (om != 0.f) amask |= 1u << nbi;
                 // the other pixel blends toward the owner when tau > 1/2, the owner toward it when tau < 1/2
@@ -654,7 +669,7 @@ __device__ __forceinline__ void scatter_vertex_rows(const ShadeArgs& A, int f, c
             for (unsigned m = grp; m; m &= m - 1) sum += rows[(__ffs(m) - 1) * ADMS_VROW + lane];
             if (sum != 0.f) {
                 int corner = lane / 9, comp = lane - 9 * corner;
-                int vtx = A.tri[3 * ft + corner];
+                int vtx = __ldg(A.tri + (3 * ft + corner));
                 double* dst = comp < 3 ? A.g_pos : (comp < 6 ? A.g_nrm : A.g_tan);
                 atomicAdd(dst + 3 * vtx + comp % 3, (double)sum);
                 if (!isfinite(sum) && A.status) atomicExch(A.status, (int)ADMS_ERR_NONFINITE);
@@ -688,7 +703,7 @@ __device__ __forceinline__ float3 aa_adjoint(const ShadeArgs& A, int b, int px, 
                                              unsigned long long kp, float scale = 1.f) {
     const adms_view& vw = A.views[b];
     float hW = 0.5f * (float)A.W, hH = 0.5f * (float)A.H;
-    float4 gp4 = A.gprime[pix];
+    float4 gp4 = __ldg(A.gprime + (pix));
     float3 gp = f3of(gp4);
     float3 gc = gp;
     unsigned amask = __float_as_uint(gp4.w);  // pairs that blended in the forward (bit per neighbour)
@@ -703,11 +718,11 @@ __device__ __forceinline__ float3 aa_adjoint(const ShadeArgs& A, int b, int px, 
             size_t qpix = ((size_t)b * A.H + qy) * A.W + qx;
             int axis = nbi < 2 ? 0 : 1;
             PairInfo pi;
-            if (!pair_eval(A, b, px, py, kp, qx, qy, A.keys[qpix], axis, pi)) continue;
+            if (!pair_eval(A, b, px, py, kp, qx, qy, __ldg(A.keys + (qpix)), axis, pi)) continue;
             float om = pi.t.tau - 0.5f;
             if (om == 0.f) continue;
             bool p_target = om > 0.f ? !pi.p_owner : pi.p_owner;
-            float3 gq = f3of(A.gprime[qpix]);
+            float3 gq = f3of(__ldg(A.gprime + (qpix)));
             float w = fabsf(om);
             if (p_target) gc -= w * gp;
             else gc += w * gq;
@@ -725,7 +740,7 @@ __device__ __forceinline__ float3 aa_adjoint(const ShadeArgs& A, int b, int px, 
                 float gb_x = k * sp, gb_u = -k * dx * sp / du;
                 float2 gsa = axis == 0 ? make_float2(ga_x, ga_u) : make_float2(ga_u, ga_x);
                 float2 gsb = axis == 0 ? make_float2(gb_x, gb_u) : make_float2(gb_u, gb_x);
-                float4 ca = A.clip[(size_t)b * A.V + pi.t.va], cb = A.clip[(size_t)b * A.V + pi.t.vb];
+                float4 ca = __ldg(A.clip + ((size_t)b * A.V + pi.t.va)), cb = __ldg(A.clip + ((size_t)b * A.V + pi.t.vb));
                 if (CLIP) {
                     atomic_add4(A.g_clip + 4 * ((size_t)b * A.V + pi.t.va), screen_bwd(ca, hW, hH, gsa));
                     atomic_add4(A.g_clip + 4 * ((size_t)b * A.V + pi.t.vb), screen_bwd(cb, hW, hH, gsb));
@@ -827,7 +842,7 @@ __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int p
     ShadeGrad G;
     {
         PixGeo g;
-        pix_geo<true>(A, b, px, py, f, g);
+        pix_geo<true, true>(A, b, px, py, f, g);
         ShadeIn in;
         in.p = g.p;
         in.n_i = g.n;
@@ -863,13 +878,13 @@ __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int p
         guv.y += g2.y + g3.y;
     }
     PixGeo g;
-    pix_geo<false>(A, b, px, py, f, g);
+    pix_geo<false, true>(A, b, px, py, f, g);
     // interpolation: attr = sum_k beta_k attr_k, beta_k = r_k / R  =>  d attr / d r_j = (attr_j - attr) / R
     float gr[3];
     {
         float2 u0 = A.uv[g.ui[0]];
         float3 p0 = f3(A.vpos[g.vi[0]]), n0 = f3(A.vnrm[g.vi[0]]), t0 = f3(A.vtan[g.vi[0]]);
-        float iR = 1.f / g.R;
+        float iR = fdiv<true>(1.f, g.R);
         gr[0] = -(dot3(G.p, g.dp) + dot3(G.n_i, g.dn) + dot3(G.t_i, g.dt) + guv.x * g.duv.x + guv.y * g.duv.y) * iR;
 #pragma unroll
         for (int k = 1; k < 3; ++k) {
@@ -884,11 +899,12 @@ __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int p
     float glam[3], gw[3], sgl = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        glam[k] = gr[k] / g.c[k].w;
-        gw[k] = -gr[k] * g.r[k] / g.c[k].w;
+        float iw = fdiv<true>(1.f, g.c[k].w);
+        glam[k] = gr[k] * iw;
+        gw[k] = -gr[k] * g.r[k] * iw;
         sgl += glam[k] * g.lam[k];
     }
-    float ia = 1.f / g.area;
+    float ia = fdiv<true>(1.f, g.area);
     float ge[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) ge[k] = (glam[k] - sgl) * ia;
@@ -925,7 +941,7 @@ __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, 
     int f = -1;
     if (inside) {
         size_t pix = ((size_t)b * A.H + py) * A.W + px;
-        unsigned long long kp = A.keys[pix];
+        unsigned long long kp = __ldg(A.keys + (pix));
         f = key_tri(kp);
         float3 gc = aa_adjoint<PEEL>(A, b, px, py, pix, kp);
         // a peeled layer: gc is dL/d(blend); split it into the layer's colour, its

@@ -26,14 +26,20 @@ __global__ void __launch_bounds__(256) k_shade_refine(ShadeArgs A) {
 // register caps measured on the plain-method step: 5 blocks/SM for shading,
 // 8 for AA + loss, 3 for the backward (a few hundred bytes of spills cost less
 // than the latency the extra resident warps hide)
-__global__ void __launch_bounds__(256, 5) k_shade_fwd(ShadeArgs A) {
+#ifndef ADMS_FWD_BLOCKS
+#define ADMS_FWD_BLOCKS 5
+#endif
+#ifndef ADMS_AA_BLOCKS
+#define ADMS_AA_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(256, ADMS_FWD_BLOCKS) k_shade_fwd(ShadeArgs A) {
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
     shade_fwd_px(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
 }
 
 template <bool PEEL>
-__global__ void __launch_bounds__(256, 8) k_aa_loss(ShadeArgs A) {
+__global__ void __launch_bounds__(256, ADMS_AA_BLOCKS) k_aa_loss(ShadeArgs A) {
     __shared__ double red[8];
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
     aa_loss_block<PEEL>(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
