@@ -527,7 +527,7 @@ adms_status adms_tessellation(const int32_t* tri, const int32_t* tri_uv, const f
                               int32_t n_tris, int32_t levels, int32_t* counts, int32_t* rtri, int32_t* rtri_uv,
                               float* ruv, int32_t* owner, int32_t* wts, float* vert_uv);
 /* Render positions pos [Vt][3] from base positions [Vb][3] and the displacement
- * map disp [dh][dw] (u wraps, v clamps), and the smooth base normals base_nrm
+ * map disp [dh][dw] (dh, dw powers of two; u wraps, v clamps), and the smooth base normals base_nrm
  * [Vb][3] they use, in the float32 contract of the step calls (visibility is
  * decided on these positions). */
 adms_status adms_tess_fwd(const adms_tess_desc* tess, const float* base_pos, const float* disp, int32_t dh, int32_t dw,

@@ -132,13 +132,15 @@ struct TexDev {
 __device__ __forceinline__ int lvl_w(const TexDev& t, int k) { return max(t.w0 >> k, 1); }
 __device__ __forceinline__ int lvl_h(const TexDev& t, int k) { return max(t.h0 >> k, 1); }
 
-// LOD: rho = max(|(du/dx w, dv/dx h)|, |(du/dy w, dv/dy h)|); lod = clamp(log2 rho, 0, levels-1)
+// LOD: rho = max(|(du/dx w, dv/dx h)|, |(du/dy w, dv/dy h)|); lod = clamp(log2 rho, 0, levels-1).
+// FAST (the backward's recomputation, whose results only feed gradients): log2 rho
+// as log2(rho^2) / 2 with the approximate log2, no square roots.
+template <bool FAST = false>
 __device__ __forceinline__ float tex_lod(const TexDev& t, float2 dx, float2 dy) {
     if (t.levels <= 1) return 0.f;
-    float ax = sqrtf((dx.x * t.w0) * (dx.x * t.w0) + (dx.y * t.h0) * (dx.y * t.h0));
-    float ay = sqrtf((dy.x * t.w0) * (dy.x * t.w0) + (dy.y * t.h0) * (dy.y * t.h0));
-    float rho = fmaxf(ax, ay);
-    float lod = log2f(rho);
+    float ax = (dx.x * t.w0) * (dx.x * t.w0) + (dx.y * t.h0) * (dx.y * t.h0);
+    float ay = (dy.x * t.w0) * (dy.x * t.w0) + (dy.y * t.h0) * (dy.y * t.h0);
+    float lod = FAST ? 0.5f * __log2f(fmaxf(ax, ay)) : log2f(fmaxf(sqrtf(ax), sqrtf(ay)));
     if (!(lod > 0.f)) lod = 0.f;  // also catches NaN and -inf
     return fminf(lod, (float)(t.levels - 1));
 }
@@ -191,9 +193,8 @@ __device__ __forceinline__ BilinTap bilin_tap(const TexDev& t, int k, const TexC
     int ix0, iy0;
     texel_coord(tc.u0, tc.du, tc.du_lo, w, ix0, b.fx);
     texel_coord(tc.v0, tc.dv, tc.dv_lo, h, iy0, b.fy);
-    int ixa = ix0 % w;
-    if (ixa < 0) ixa += w;
-    int ixb = ixa + 1 == w ? 0 : ixa + 1;
+    int ixa = ix0 & (w - 1);  // u wraps: w is a power of two (two's complement: negative ix0 wraps too)
+    int ixb = (ixa + 1) & (w - 1);
     int iya = min(max(iy0, 0), h - 1), iyb = min(max(iy0 + 1, 0), h - 1);
     int base = t.off[k];
     b.idx[0] = base + iya * w + ixa;

@@ -848,16 +848,16 @@ __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int p
         in.n_i = g.n;
         in.t_i = g.t;
         if (shared) {
-            lod[0] = lod[1] = lod[2] = tex_lod(A.kd, g.duv_dx, g.duv_dy);
+            lod[0] = lod[1] = lod[2] = tex_lod<true>(A.kd, g.duv_dx, g.duv_dy);
             float4 smp[3];
             tex_sample3(A, g.tc, lod[0], smp);
             in.kd = smp[0];
             in.orm = smp[1];
             in.nm = smp[2];
         } else {
-            lod[0] = tex_lod(A.kd, g.duv_dx, g.duv_dy);
-            lod[1] = tex_lod(A.orm, g.duv_dx, g.duv_dy);
-            lod[2] = tex_lod(A.nrm, g.duv_dx, g.duv_dy);
+            lod[0] = tex_lod<true>(A.kd, g.duv_dx, g.duv_dy);
+            lod[1] = tex_lod<true>(A.orm, g.duv_dx, g.duv_dy);
+            lod[2] = tex_lod<true>(A.nrm, g.duv_dx, g.duv_dy);
             in.kd = tex_sample(A.kd, g.tc, lod[0]);
             in.orm = tex_sample(A.orm, g.tc, lod[1]);
             in.nm = tex_sample(A.nrm, g.tc, lod[2]);

@@ -633,8 +633,9 @@ adms_status adms_aa_loss_bwd(const adms_stage_mesh* m, const adms_view* views, i
 }
 
 static bool tess_ok(const adms_tess_desc* t, const float* base_pos, const float* disp, int32_t dh, int32_t dw) {
+    auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
     return t && t->base_tri && t->bvf_off && t->bvf_face && t->owner && t->wts && t->vert_uv && base_pos && disp &&
-           t->n_base_verts > 0 && t->n_base_tris > 0 && t->n_verts > 0 && t->n_segments >= 2 && dh > 0 && dw > 0;
+           t->n_base_verts > 0 && t->n_base_tris > 0 && t->n_verts > 0 && t->n_segments >= 2 && pow2(dh) && pow2(dw);
 }
 
 static TessArgs tess_stage_args(const adms_tess_desc* t, const float* base_pos, const float* disp, int32_t dh,

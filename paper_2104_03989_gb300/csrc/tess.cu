@@ -69,9 +69,8 @@ __device__ __forceinline__ void tess_eval(const TessArgs& a, int t, TessEval& e)
     e.fx = sub(x, x0);
     e.fy = sub(y, y0);
     int ix = (int)x0, iy = (int)y0;
-    int ixa = ix % a.dw;
-    if (ixa < 0) ixa += a.dw;
-    int ixb = ixa + 1 == a.dw ? 0 : ixa + 1;
+    int ixa = ix & (a.dw - 1);  // u wraps: dw is a power of two
+    int ixb = (ixa + 1) & (a.dw - 1);
     int iya = min(max(iy, 0), a.dh - 1), iyb = min(max(iy + 1, 0), a.dh - 1);
     e.idx[0] = iya * a.dw + ixa;
     e.idx[1] = iya * a.dw + ixb;
