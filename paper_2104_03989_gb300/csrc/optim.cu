@@ -231,6 +231,22 @@ __device__ __forceinline__ float4 adam_texel(const TexDev& t, float4* __restrict
     return p;
 }
 
+// adam_texel with the texel's latent and moments already loaded
+__device__ __forceinline__ float4 adam_texel_v(const TexDev& t, float4* __restrict__ m, float4* __restrict__ v, int i,
+                                               float4 g, float4 p, float4 mm, float4 vv, int clamp_kind, float lr,
+                                               float bc1, float bc2) {
+    p.x = adam1(p.x, g.x, mm.x, vv.x, lr, bc1, bc2);
+    p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
+    p.z = adam1(p.z, g.z, mm.z, vv.z, lr, bc1, bc2);
+    p.w = adam1(p.w, g.w, mm.w, vv.w, lr, bc1, bc2);
+    p = clamp_texel(p, clamp_kind);
+    const_cast<float4*>(t.tex)[i] = p;
+    m[i] = mm;
+    v[i] = vv;
+    t.grad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return p;
+}
+
 // Adam on one 32x32 texel tile of level 0 per block, for every texture of a
 // launch (up to ADMS_ADAM_TEX textures of any jobs, block ranges from tile0),
 // then levels 1..5 of that tile built in shared memory from the updated texels
@@ -238,12 +254,21 @@ __device__ __forceinline__ float4 adam_texel(const TexDev& t, float4* __restrict
 // once for both. The mip adjoint is pushed down the tile's pyramid first; each
 // gradient texel of levels 1..5 belongs to one tile, which zeroes it with the
 // mip writes at the end (a store right after each push-down read held the
-// reads back: Adam took 0.23 instead of 0.11 ms per step). The last tile of a texture to finish (a counter per texture) builds
-// levels 6.. from level 5, zeroes their gradients and resets the counter.
-__global__ void __launch_bounds__(256) k_adam_tex_batch(const TexAdamBatch P) {
+// reads back: Adam took 0.23 instead of 0.11 ms per step). All of a tile's reads
+// are issued before its first barrier (one memory round trip instead of one per
+// pyramid level). The last tile of a texture to finish (a counter per texture)
+// builds levels 6.. from level 5, zeroes their gradients and resets the counter.
+// resident blocks per SM of the tiled Adam (register cap 65536 / (256 x this)): the
+// thread keeps its 16 level-0 loads in flight at once
+#ifndef ADMS_ADAM_BLOCKS
+#define ADMS_ADAM_BLOCKS 3
+#endif
+__global__ void __launch_bounds__(256, ADMS_ADAM_BLOCKS) k_adam_tex_batch(const TexAdamBatch P) {
     __shared__ float4 tile[32][32];
-    // push level k (k = 1..5) holds sum_{j >= k} weight_j * grad_j at the level-k texels of this tile
+    // push level k (k = 1..5): first the raw level-k gradient texels of this tile, then
+    // in place sum_{j >= k} weight_j * grad_j at those texels
     __shared__ float4 push[256 + 64 + 16 + 4 + 1];
+    __shared__ float4 anc[ADMS_MAX_LEVELS];  // gradients of the tile's ancestors at levels 6..
     __shared__ int s_last;
     const int poff[6] = {0, 0, 256, 320, 336, 340};
     int lo = 0, hi = P.n - 1;  // the texture: last entry with tile0 <= blockIdx.x
@@ -260,35 +285,52 @@ __global__ void __launch_bounds__(256) k_adam_tex_batch(const TexAdamBatch P) {
     int bx = tb % tiles_x, by = tb / tiles_x;
     int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     float lr = A.js->lr, bc1 = A.js->bc1, bc2 = A.js->bc2;
+    // every global read of the tile issued up front: the thread's four level-0 texels
+    // (gradient, latent, moments) and the raw gradients of the tile's pyramid and
+    // ancestors, so that one memory round trip covers them all
+    float4 g0[4], p0[4], m0[4], v0[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int i = ((by << 5) + ty + 8 * r) * t.w0 + (bx << 5) + tx;
+        g0[r] = t.grad[i];
+        p0[r] = t.tex[i];
+        m0[r] = A.m[i];
+        v0[r] = A.v[i];
+    }
+#pragma unroll
+    for (int k = 1; k <= 5; ++k) {
+        int n = 32 >> k, wk = t.w0 >> k;
+        for (int idx = threadIdx.x; idx < n * n; idx += 256)
+            push[poff[k] + idx] = t.grad[t.off[k] + (((by << 5) >> k) + idx / n) * wk + ((bx << 5) >> k) + idx % n];
+    }
+    {
+        int k = threadIdx.x;
+        if (k >= 6 && k < t.levels)
+            anc[k] = t.grad[t.off[k] + ((by << 5) >> k) * max(t.w0 >> k, 1) + ((bx << 5) >> k)];
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int k = 6; k < t.levels; ++k) {
-            int wk = max(t.w0 >> k, 1);
-            c = f4madd(c, level_weight(t, k), t.grad[t.off[k] + ((by << 5) >> k) * wk + ((bx << 5) >> k)]);
-        }
-        int i5 = t.off[5] + by * (t.w0 >> 5) + bx;
-        push[poff[5]] = f4madd(c, level_weight(t, 5), t.grad[i5]);
+        for (int k = 6; k < t.levels; ++k) c = f4madd(c, level_weight(t, k), anc[k]);
+        push[poff[5]] = f4madd(c, level_weight(t, 5), push[poff[5]]);
     }
     for (int k = 4; k >= 1; --k) {
         __syncthreads();
-        int n = 32 >> k, wk = t.w0 >> k;
+        int n = 32 >> k;
         float wl = level_weight(t, k);
         for (int idx = threadIdx.x; idx < n * n; idx += 256) {
             int cx = idx % n, cy = idx / n;
-            int gi = t.off[k] + (((by << 5) >> k) + cy) * wk + ((bx << 5) >> k) + cx;
-            float4 g = t.grad[gi];
-            push[poff[k] + idx] = f4madd(push[poff[k + 1] + (cy >> 1) * (n >> 1) + (cx >> 1)], wl, g);
+            push[poff[k] + idx] = f4madd(push[poff[k + 1] + (cy >> 1) * (n >> 1) + (cx >> 1)], wl, push[poff[k] + idx]);
         }
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         int lx = tx, ly = ty + 8 * r;
-        int x = (bx << 5) + lx, y = (by << 5) + ly;
-        int i = y * t.w0 + x;
-        float4 g = f4madd(t.grad[i], 1.f, push[(ly >> 1) * 16 + (lx >> 1)]);
+        int i = ((by << 5) + ly) * t.w0 + (bx << 5) + lx;
+        float4 g = f4madd(g0[r], 1.f, push[(ly >> 1) * 16 + (lx >> 1)]);
         latch_nonfinite(A.js, g.x, g.y, g.z, g.w);
-        tile[ly][lx] = adam_texel(t, A.m, A.v, i, g, A.clamp_kind, lr, bc1, bc2);
+        tile[ly][lx] = adam_texel_v(t, A.m, A.v, i, g, p0[r], m0[r], v0[r], A.clamp_kind, lr, bc1, bc2);
     }
     int top = min(5, t.levels - 1);
     float4* tex = const_cast<float4*>(t.tex);
