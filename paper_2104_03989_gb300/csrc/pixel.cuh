@@ -827,6 +827,92 @@ __device__ __forceinline__ float2 tex_sample3_bwd(const ShadeArgs& A, const TexC
     return guv;
 }
 
+// tex_sample3 that also leaves, for each map m, dS_m/du and dS_m/dv (the derivatives
+// of its trilinear sample w.r.t. the texture coordinate, float4 each) in
+// stash[8 m .. 8 m + 7] (a lane's private shared-memory row): the adjoint then needs
+// no second read of the texels
+__device__ __forceinline__ void tex_sample3_stash(const ShadeArgs& A, const TexCoord& tc, float lod, float4 out[3],
+                                                  float* stash) {
+    const float4* ts[3] = {A.kd.tex, A.orm.tex, A.nrm.tex};
+    int l0 = (int)floorf(lod);
+    float fr = lod - (float)l0;
+    int l1 = min(l0 + 1, A.kd.levels - 1);
+    float4 du[3], dv[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        out[m] = du[m] = dv[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        int k = s == 0 ? l0 : l1;
+        float wl = s == 0 ? 1.f - fr : fr;
+        if (wl == 0.f) continue;
+        BilinTap b = bilin_tap(A.kd, k, tc);
+        float w00 = wl * (1.f - b.fx) * (1.f - b.fy), w10 = wl * b.fx * (1.f - b.fy);
+        float w01 = wl * (1.f - b.fx) * b.fy, w11 = wl * b.fx * b.fy;
+        float su = wl * b.sw, sv = wl * b.sh;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            float4 t00 = __ldg(ts[m] + b.idx[0]), t10 = __ldg(ts[m] + b.idx[1]);
+            float4 t01 = __ldg(ts[m] + b.idx[2]), t11 = __ldg(ts[m] + b.idx[3]);
+            out[m] = f4madd(out[m], w00, t00);
+            out[m] = f4madd(out[m], w10, t10);
+            out[m] = f4madd(out[m], w01, t01);
+            out[m] = f4madd(out[m], w11, t11);
+            du[m] = f4madd(du[m], su, f4madd(f4scale(f4sub(t10, t00), 1.f - b.fy), b.fy, f4sub(t11, t01)));
+            dv[m] = f4madd(dv[m], sv, f4madd(f4scale(f4sub(t01, t00), 1.f - b.fx), b.fx, f4sub(t11, t10)));
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        float* q = stash + 8 * m;
+        q[0] = du[m].x;
+        q[1] = du[m].y;
+        q[2] = du[m].z;
+        q[3] = du[m].w;
+        q[4] = dv[m].x;
+        q[5] = dv[m].y;
+        q[6] = dv[m].z;
+        q[7] = dv[m].w;
+    }
+}
+
+// adjoint of tex_sample3_stash: the texel gradients of the optimized maps scattered,
+// d/d(u, v) of g[0] . kd + g[1] . orm + g[2] . nm from the stashed derivatives
+__device__ __forceinline__ float2 tex_sample3_bwd_stash(const ShadeArgs& A, const TexCoord& tc, float lod,
+                                                        const float4 g[3], const float* stash) {
+    float4* gs[3] = {A.kd.grad, A.orm.grad, A.nrm.grad};
+    float2 guv = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const float* q = stash + 8 * m;
+        guv.x += g[m].x * q[0] + g[m].y * q[1] + g[m].z * q[2] + g[m].w * q[3];
+        guv.y += g[m].x * q[4] + g[m].y * q[5] + g[m].z * q[6] + g[m].w * q[7];
+    }
+    if (!gs[0] && !gs[1] && !gs[2]) return guv;
+    int l0 = (int)floorf(lod);
+    float fr = lod - (float)l0;
+    int l1 = min(l0 + 1, A.kd.levels - 1);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        int k = s == 0 ? l0 : l1;
+        float wl = s == 0 ? 1.f - fr : fr;
+        if (wl == 0.f) continue;
+        BilinTap b = bilin_tap(A.kd, k, tc);
+        float w00 = wl * (1.f - b.fx) * (1.f - b.fy), w10 = wl * b.fx * (1.f - b.fy);
+        float w01 = wl * (1.f - b.fx) * b.fy, w11 = wl * b.fx * b.fy;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            if (!gs[m]) continue;
+            atomicAdd(gs[m] + b.idx[0], f4scale(g[m], w00));
+            atomicAdd(gs[m] + b.idx[1], f4scale(g[m], w10));
+            atomicAdd(gs[m] + b.idx[2], f4scale(g[m], w01));
+            atomicAdd(gs[m] + b.idx[3], f4scale(g[m], w11));
+        }
+    }
+    return guv;
+}
+
 // shading adjoint of triangle f at sample (px, py) for dL/d(colour) gc (and, for a
 // peeled layer, dL/d(opacity) g_alpha): texel gradients scattered here, the three
 // corners' position / normal / tangent gradients written to vrow[27] (corner k at
@@ -852,7 +938,7 @@ __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int p
         if (shared) {
             lod[0] = lod[1] = lod[2] = tex_lod<true>(A.kd, g.duv_dx, g.duv_dy);
             float4 smp[3];
-            tex_sample3(A, g.tc, lod[0], smp);
+            tex_sample3_stash(A, g.tc, lod[0], smp, vrow);  // the row holds the uv derivatives until phase 4
             in.kd = smp[0];
             in.orm = smp[1];
             in.nm = smp[2];
@@ -871,7 +957,7 @@ __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int p
     float2 guv;
     if (shared) {
         float4 gt[3] = {G.kd, G.orm, G.nm};
-        guv = tex_sample3_bwd(A, tc, lod[0], gt);
+        guv = tex_sample3_bwd_stash(A, tc, lod[0], gt, vrow);
     } else {
         guv = tex_sample_bwd(A.kd, tc, lod[0], G.kd);
         float2 g2 = tex_sample_bwd(A.orm, tc, lod[1], G.orm);
