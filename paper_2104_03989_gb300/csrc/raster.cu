@@ -426,9 +426,17 @@ __device__ __forceinline__ void raster_tile_body(const TriRec* __restrict__ rec,
     int n = overflow ? F : cnt;
     if (n == 0) return;  // no binned triangle: the small-triangle pass left the final keys
     if (overflow && threadIdx.x == 0) atomicAdd(overflow_ctr, 1ull);
+    // Each warp shades a 16 x 2 strip of the tile (rows 2w, 2w + 1): the staged records
+    // whose pixel box meets a warp's rows go to that warp's list, and each warp walks
+    // only its own. The key is a minimum over the same triangles in any order.
+    __shared__ unsigned char wlist[8][256];
+    __shared__ int wcount[8];
+    int warp = threadIdx.x >> 5;
+    int row0 = ty * ADMS_TILE;
     for (int c0 = 0; c0 < n; c0 += 256) {
         int m = min(256, n - c0);
         __syncthreads();
+        if (threadIdx.x < 8) wcount[threadIdx.x] = 0;
         if ((int)threadIdx.x < m) {
             if (overflow) {
                 int id = c0 + threadIdx.x;
@@ -440,9 +448,19 @@ __device__ __forceinline__ void raster_tile_body(const TriRec* __restrict__ rec,
             }
         }
         __syncthreads();
-        for (int k = 0; k < m; ++k) {
-            const TriRec& r = sm[k];
-            if (!r.valid) continue;
+        unsigned wmask = 0;
+        if ((int)threadIdx.x < m && sm[threadIdx.x].valid) {
+            int r0 = max((int)sm[threadIdx.x].by0 - row0, 0), r1 = min((int)sm[threadIdx.x].by1 - row0, ADMS_TILE - 1);
+            for (int w = r0 >> 1; w <= (r1 >> 1); ++w) wmask |= 1u << w;  // empty when r1 < r0
+        }
+        for (unsigned mm = wmask; mm; mm &= mm - 1) {
+            int w = __ffs(mm) - 1;
+            wlist[w][atomicAdd(&wcount[w], 1)] = (unsigned char)threadIdx.x;
+        }
+        __syncthreads();
+        int cntw = wcount[warp];
+        for (int j = 0; j < cntw; ++j) {
+            const TriRec& r = sm[wlist[warp][j]];
             if (px < r.bx0 || px > r.bx1 || py < r.by0 || py > r.by1) continue;
             test_tri(r, Sx, Sy, best);
         }
