@@ -321,9 +321,13 @@ def run_native(args):
     ref_job = ctx.create_job(cfg["ref"], frozen=True, samples=MS, shade_samples=True,
                              raster_direct_px=256 if agg else 0)
     pl = bool(args.per_level_textures)
-    cand = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, per_level_textures=pl, samples=MS, layers=LY)
+    # the tessellated candidate's ~17-pixel triangles rasterize faster directly than
+    # binned (the keys do not depend on the threshold): 256 measured best of 16..256
+    cdirect = 256 if wk == "tess" else 0
+    cand = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, per_level_textures=pl, samples=MS, layers=LY,
+                          raster_direct_px=cdirect)
     plain = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, batch_views=NV, per_level_textures=pl, samples=MS,
-                           layers=LY)
+                           layers=LY, raster_direct_px=cdirect)
     n_steps = args.warmup + args.steps
     if wk == "small":   # one fixed camera
         host_views = [synth.fixed_view(RS, RS) for _ in range(n_steps)]
@@ -411,14 +415,18 @@ def run_native(args):
         if world > 1:
             torch.distributed.barrier()
 
-    def timed_region(fn, k0, k):
+    def timed_region(fn, k0, k, name="region"):
+        # an NVTX range per region, so that a profiler can keep one region's launches
+        # (e.g. ncu --nvtx --nvtx-include "metric_step/")
         barrier()
+        torch.cuda.nvtx.range_push(name)
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
         evs[0].record(stream)
         for s in range(k):
             fn(k0 + s)
             evs[s + 1].record(stream)
         barrier()
+        torch.cuda.nvtx.range_pop()
         per = [evs[s].elapsed_time(evs[s + 1]) for s in range(k)]
         return max_over_ranks(evs[0].elapsed_time(evs[-1]), world, dev), per
 
@@ -467,9 +475,9 @@ def run_native(args):
                                                            ring_refs_c[(i - args.warmup) % R],
                                                            loss_buf.data_ptr() + 4 * i), args.warmup, args.steps)
     launches = (B.adms_launch_count() - launches0) / args.steps
-    total_ms, per = timed_region(cand_graph_step, args.warmup, args.steps)
-    with_ref_ms, per_ref = timed_region(graph_step, args.warmup, args.steps)
-    plain_ms, _ = timed_region(plain_step, args.warmup, args.steps)
+    total_ms, per = timed_region(cand_graph_step, args.warmup, args.steps, "metric_step")
+    with_ref_ms, per_ref = timed_region(graph_step, args.warmup, args.steps, "with_reference")
+    plain_ms, _ = timed_region(plain_step, args.warmup, args.steps, "plain_loop")
     # per-stage profile of the metric's step (events between stages; not the headline)
     B.adms_ctx_profile(cptr, True)
     B.adms_ctx_stage_times(cptr)
