@@ -85,6 +85,7 @@ struct Job {
     float* delta = nullptr;
     JobState* st = nullptr;
     bool frame_valid = false;
+    bool lap_valid = false;  // delta and lap_sum hold the Laplacian of the current positions
     // per-call scratch
     size_t px_cap = 0, view_cap = 0, tile_cap = 0, rec_cap = 0;
     unsigned long long* keys = nullptr;
@@ -163,6 +164,12 @@ struct BatchState {
 
 struct adms_ctx {
     cudaStream_t stream = 0;
+    // a second stream for the independent branches of a call (the vertex frame and
+    // the Laplacian beside the raster, the flat latents' Adam beside the textures'),
+    // forked from and joined back into `stream` within the call, so that a graph
+    // captured on `stream` holds both
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // the reference images of forward_loss calls are complete once this event has
     // completed (recorded on another stream that renders them), or null
     cudaEvent_t ref_event = nullptr;
@@ -228,6 +235,25 @@ cudaError_t timed(adms_ctx* ctx, int stage, F&& f) {
 }
 
 #define TIMED(stage, call) timed(ctx, stage, [&]() { return (call); })
+
+// the stream of a branch: the side stream, ordered after everything issued on the
+// context's stream so far (with per-stage profiling the branch stays on the
+// context's stream, where the stage events time it)
+cudaStream_t fork_branch(adms_ctx* ctx, cudaError_t& e) {
+    e = cudaSuccess;
+    if (ctx->profile || !ctx->side) return ctx->stream;
+    e = cudaEventRecord(ctx->ev_fork, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+    return ctx->side;
+}
+
+// the context's stream waits for everything issued on the side stream
+cudaError_t join_branch(adms_ctx* ctx) {
+    if (ctx->profile || !ctx->side) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(ctx->ev_join, ctx->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+    return e;
+}
 
 template <typename T>
 adms_status job_alloc(adms_ctx* ctx, Job& j, T** out, size_t count) {
@@ -355,6 +381,9 @@ adms_status ensure_scratch(adms_ctx* ctx, Job& j, int B, int H, int W) {
     }
     return ADMS_OK;
 }
+
+// the Laplacian of Eq. 4 over the optimized (base) positions, its gradient added into g_pos
+LapArgs lap_args(Job& j) { return LapArgs{j.LV, j.pos, j.ring_off, j.ring, j.delta_ref, j.delta, j.g_pos, j.st}; }
 
 FrameArgs frame_args(Job& j) {
     FrameArgs f;
@@ -503,13 +532,32 @@ SkinArgs skin_args(Job& j) {
     return a;
 }
 
-adms_status render_core(adms_ctx* ctx, Job& j) {
-    if (!j.frame_valid) {
-        if (j.tess) CK(TIMED(ST_FRAME, tess_forward(tess_args(j), ctx->stream)));
-        if (j.skin) CK(TIMED(ST_FRAME, skin_forward(skin_args(j), ctx->stream)));
-        CK(TIMED(ST_FRAME, frame_forward(frame_args(j), ctx->stream)));
-        j.frame_valid = true;
+// The render positions (tessellated, skinned) on the context's stream, then the
+// vertex frame and, once per set of positions, the Laplacian on a branch beside
+// the raster: both need only the positions. *forked tells the caller to join the
+// branch before the shading.
+adms_status frame_branch(adms_ctx* ctx, Job& j, bool* forked) {
+    *forked = false;
+    if (j.frame_valid) return ADMS_OK;
+    if (j.tess) CK(TIMED(ST_FRAME, tess_forward(tess_args(j), ctx->stream)));
+    if (j.skin) CK(TIMED(ST_FRAME, skin_forward(skin_args(j), ctx->stream)));
+    cudaError_t e;
+    cudaStream_t bs = fork_branch(ctx, e);
+    CK(e);
+    *forked = true;
+    CK(TIMED(ST_FRAME, frame_forward(frame_args(j), bs)));
+    if (j.opt.optimize_pos && !j.lap_valid) {
+        CK(TIMED(ST_LAPLACIAN, laplacian_forward(lap_args(j), bs)));
+        j.lap_valid = true;
     }
+    j.frame_valid = true;
+    return ADMS_OK;
+}
+
+adms_status render_core(adms_ctx* ctx, Job& j) {
+    bool forked = false;
+    adms_status fs = frame_branch(ctx, j, &forked);
+    if (fs) return fs;
     RasterIn in;
     in.pos = j.rpos;
     in.tri = j.tri;
@@ -526,12 +574,14 @@ adms_status render_core(adms_ctx* ctx, Job& j) {
         in.small_px = 0;
         CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
         CK(TIMED(ST_RASTER, raster_tiles_peeled(in, j.rs, j.L, ctx->stream)));
+        if (forked) CK(join_branch(ctx));
         for (int l = 0; l < j.L; ++l) CK(TIMED(ST_SHADE, shade_forward(layer_args(j, l), ctx->stream)));
         return ADMS_OK;
     }
     in.small_px = j.opt.raster_direct_px > 0 ? j.opt.raster_direct_px : ADMS_SMALL_PX;
     CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
     CK(TIMED(ST_RASTER, raster_tiles(in, j.rs, ctx->stream)));
+    if (forked) CK(join_branch(ctx));
     CK(TIMED(ST_SHADE, shade_forward(shade_args(j), ctx->stream)));
     return ADMS_OK;
 }
@@ -861,13 +911,13 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
 }
 
 // frame (and tessellation) plus the per-job raster preparation of a batched call
-adms_status frame_and_prepare(adms_ctx* ctx, Job& j) {
-    if (!j.frame_valid) {
-        if (j.tess) CK(TIMED(ST_FRAME, tess_forward(tess_args(j), ctx->stream)));
-        if (j.skin) CK(TIMED(ST_FRAME, skin_forward(skin_args(j), ctx->stream)));
-        CK(TIMED(ST_FRAME, frame_forward(frame_args(j), ctx->stream)));
-        j.frame_valid = true;
-    }
+// frame_branch and the raster setup of one job of a batch (*forked: join before
+// the batch's shading)
+adms_status frame_and_prepare(adms_ctx* ctx, Job& j, bool* forked) {
+    bool f = false;
+    adms_status fs = frame_branch(ctx, j, &f);
+    if (fs) return fs;
+    *forked = *forked || f;
     RasterIn in;
     in.pos = j.rpos;
     in.tri = j.tri;
@@ -1118,6 +1168,14 @@ adms_status adms_ctx_create(adms_ctx** out, size_t hbm_budget_bytes, void* cuda_
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) c->sm_count = sms;
     for (int k = 0; k < 4; ++k) c->occ[k] = adms::batched_occupancy(k);
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->side) cudaStreamDestroy(c->side);
+        delete c;
+        return ADMS_ERR_CUDA;
+    }
     *out = c;
     return ADMS_OK;
 }
@@ -1129,6 +1187,10 @@ adms_status adms_ctx_destroy(adms_ctx* ctx) {
         if (j.alive) job_free(ctx, j);
     for (BatchState& b : ctx->batches) batch_free(ctx, b);
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
+    cudaStreamSynchronize(ctx->side);
+    cudaEventDestroy(ctx->ev_fork);
+    cudaEventDestroy(ctx->ev_join);
+    cudaStreamDestroy(ctx->side);
     delete ctx;
     return ADMS_OK;
 }
@@ -1452,6 +1514,7 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
     if (!ctx || !jobs || n_jobs <= 0 || !views || !views_per_job || !hw || !ref_rgb)
         return fail(ctx, ADMS_ERR_ARG, "invalid forward_loss arguments");
     size_t vofs = 0;
+    bool forked = false;  // a batch's frame branches, joined before its shading
     std::vector<Job*> js;
     for (int k = 0; k < n_jobs; ++k) {
         Job* jp = get_job(ctx, jobs[k]);
@@ -1495,7 +1558,7 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
                 CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
             }
         } else {
-            if ((s = frame_and_prepare(ctx, j))) return s;
+            if ((s = frame_and_prepare(ctx, j, &forked))) return s;
         }
     }
     if (n_jobs > 1) {
@@ -1506,6 +1569,7 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
         BatchState& bs = *bsp;
         CK(TIMED(ST_RASTER, raster_tiles_batched(bs.h_rargs.data(), bs.rt_off.data(), n_jobs, bs.d_rt,
                                                  batch_grid(ctx, 3), ctx->stream)));
+        if (forked) CK(join_branch(ctx));
         CK(TIMED(ST_SHADE, pixels_batched(0, bs.h_args.data(), bs.px_off.data(), n_jobs, bs.d_px, ctx->tune_tw,
                                           batch_grid(ctx, 0), ctx->stream)));
         CK(wait_ref(ctx));
@@ -1593,28 +1657,34 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         if (jp->frozen) return fail(ctx, ADMS_ERR_STATE, "optimizer_step on a frozen job");
         js.push_back(jp);
     }
-    // schedules, Laplacian and the flat latents per job; then every job's tiled
-    // textures in one launch; then the step counters
+    // schedules per job (after the Laplacian when no forward computed it for these
+    // positions); then the flat latents (positions with the Laplacian term, skin
+    // weights, displacement) on a branch beside the textures: every job's tiled
+    // textures in one launch; then, joined, the step counters
+    for (Job* jp : js) {
+        Job& j = *jp;
+        if (j.opt.optimize_pos && !j.lap_valid) CK(TIMED(ST_LAPLACIAN, laplacian_forward(lap_args(j), ctx->stream)));
+        SchedArgs sa{j.st, j.opt.lr0, j.opt.lambda0, j.opt.optimize_pos, j.LV};
+        CK(TIMED(ST_SMALL, schedule_step(sa, ctx->stream)));
+    }
+    cudaError_t fe;
+    cudaStream_t bs = fork_branch(ctx, fe);
+    CK(fe);
     std::vector<TexAdam> tiled;
     for (Job* jp : js) {
         Job& j = *jp;
-        LapArgs la{j.LV, j.pos, j.ring_off, j.ring, j.delta_ref, j.delta, j.g_pos, j.st};
-        if (j.opt.optimize_pos) CK(TIMED(ST_LAPLACIAN, laplacian_forward(la, ctx->stream)));
-        SchedArgs sa{j.st, j.opt.lr0, j.opt.lambda0, j.opt.optimize_pos, j.LV};
-        CK(TIMED(ST_SMALL, schedule_step(sa, ctx->stream)));
         if (j.opt.optimize_pos) {
-            CK(TIMED(ST_LAPLACIAN, laplacian_backward(la, ctx->stream)));
-            CK(TIMED(ST_ADAM, adam_flat(j.pos, j.g_pos, j.m_pos, j.v_pos, (long long)j.LV * 3, j.st, ctx->stream)));
+            CK(TIMED(ST_LAPLACIAN, laplacian_backward(lap_args(j), bs)));
+            CK(TIMED(ST_ADAM, adam_flat(j.pos, j.g_pos, j.m_pos, j.v_pos, (long long)j.LV * 3, j.st, bs)));
         } else {
-            CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.LV, ctx->stream));
+            CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.LV, bs));
         }
         if (j.g_skin_w)
             CK(TIMED(ST_ADAM, adam_flat(j.skin_w, j.g_skin_w, j.m_skin_w, j.v_skin_w, (long long)j.LV * j.SB, j.st,
-                                        ctx->stream, j.skin_lr_scale)));
+                                        bs, j.skin_lr_scale)));
         if (j.tess) {
             if (j.opt.optimize_disp)
-                CK(TIMED(ST_ADAM, adam_flat(j.disp, j.g_disp, j.m_disp, j.v_disp, (long long)j.dh * j.dw, j.st,
-                                            ctx->stream)));
+                CK(TIMED(ST_ADAM, adam_flat(j.disp, j.g_disp, j.m_disp, j.v_disp, (long long)j.dh * j.dw, j.st, bs)));
         }
         TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
         for (int m = 0; m < 3; ++m) {
@@ -1627,9 +1697,11 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         }
     }
     if (!tiled.empty()) CK(TIMED(ST_ADAM, adam_textures_tiled(tiled, ctx->stream)));
+    CK(join_branch(ctx));
     for (Job* jp : js) {
         CK(TIMED(ST_SMALL, advance_step(jp->st, ctx->stream)));
         jp->frame_valid = false;
+        jp->lap_valid = false;
     }
     return ADMS_OK;
 }
@@ -1677,6 +1749,7 @@ adms_status adms_job_invalidate(adms_ctx* ctx, adms_job job) {
     for (int m = 0; m < 3; ++m)
         if (!maps[m]->per_level) CK(TIMED(ST_MIP, mip_build(maps[m]->dev(), ctx->stream)));
     j->frame_valid = false;
+    j->lap_valid = false;
     return ADMS_OK;
 }
 
@@ -1765,6 +1838,7 @@ adms_status adms_job_import(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
         off += c.bytes;
     }
     j.frame_valid = false;
+    j.lap_valid = false;
     j.have_fwd = false;
     *out = h;
     return ADMS_OK;

@@ -37,14 +37,29 @@ __device__ __forceinline__ FaceFrame face_frame(const FrameArgs& a, int f) {
     return r;
 }
 
+// The gathers over a vertex's faces (or one-ring) run in batches of ADMS_GATHER:
+// the batch's loads are issued together (the last entry repeated past the end)
+// and summed in list order, so each sum keeps the order of a plain loop while the
+// dependent loads of a vertex take ceil(valence / ADMS_GATHER) round trips
+// instead of one per face.
+#define ADMS_GATHER 4
+
 // unnormalised vertex normal (sum of face normals) and tangent (sum of signed unit face tangents)
 __device__ __forceinline__ void vertex_sums(const FrameArgs& a, int v, float3& n, float3& t) {
     n = zero3();
     t = zero3();
-    for (int j = a.vf_off[v]; j < a.vf_off[v + 1]; ++j) {
-        FaceFrame ff = face_frame(a, a.vf_face[j]);
-        n += ff.fn;
-        if (ff.sgn != 0) t += (float)ff.sgn * nrm3(ff.tv).y;
+    int lo = a.vf_off[v], hi = a.vf_off[v + 1];
+    for (int j0 = lo; j0 < hi; j0 += ADMS_GATHER) {
+        FaceFrame ff[ADMS_GATHER];
+#pragma unroll
+        for (int q = 0; q < ADMS_GATHER; ++q) ff[q] = face_frame(a, a.vf_face[min(j0 + q, hi - 1)]);
+#pragma unroll
+        for (int q = 0; q < ADMS_GATHER; ++q) {
+            if (j0 + q < hi) {
+                n += ff[q].fn;
+                if (ff[q].sgn != 0) t += (float)ff[q].sgn * nrm3(ff[q].tv).y;
+            }
+        }
     }
 }
 
@@ -76,19 +91,29 @@ __global__ void k_frame_bwd2(FrameArgs a) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= a.V) return;
     float3 g = zero3();
-    for (int j = a.vf_off[v]; j < a.vf_off[v + 1]; ++j) {
-        FaceFrame ff = face_frame(a, a.vf_face[j]);
-        float3 Gfn = f3(a.tmp_n[ff.idx[0]]) + f3(a.tmp_n[ff.idx[1]]) + f3(a.tmp_n[ff.idx[2]]);
-        float3 ge1 = cross3(ff.e2, Gfn), ge2 = cross3(Gfn, ff.e1);
-        if (ff.sgn != 0) {
-            float3 Gft = f3(a.tmp_t[ff.idx[0]]) + f3(a.tmp_t[ff.idx[1]]) + f3(a.tmp_t[ff.idx[2]]);
-            float3 gtv = (float)ff.sgn * nrm3_bwd(nrm3(ff.tv), Gft);
-            ge1 += ff.d2y * gtv;
-            ge2 -= ff.d1y * gtv;
+    int lo = a.vf_off[v], hi = a.vf_off[v + 1];
+    for (int j0 = lo; j0 < hi; j0 += ADMS_GATHER) {
+        FaceFrame ff[ADMS_GATHER];
+        float3 Gfn[ADMS_GATHER], Gft[ADMS_GATHER];
+#pragma unroll
+        for (int q = 0; q < ADMS_GATHER; ++q) {
+            ff[q] = face_frame(a, a.vf_face[min(j0 + q, hi - 1)]);
+            Gfn[q] = f3(a.tmp_n[ff[q].idx[0]]) + f3(a.tmp_n[ff[q].idx[1]]) + f3(a.tmp_n[ff[q].idx[2]]);
+            Gft[q] = f3(a.tmp_t[ff[q].idx[0]]) + f3(a.tmp_t[ff[q].idx[1]]) + f3(a.tmp_t[ff[q].idx[2]]);
         }
-        if (ff.idx[0] == v) g -= ge1 + ge2;
-        if (ff.idx[1] == v) g += ge1;
-        if (ff.idx[2] == v) g += ge2;
+#pragma unroll
+        for (int q = 0; q < ADMS_GATHER; ++q) {
+            if (j0 + q >= hi) continue;
+            float3 ge1 = cross3(ff[q].e2, Gfn[q]), ge2 = cross3(Gfn[q], ff[q].e1);
+            if (ff[q].sgn != 0) {
+                float3 gtv = (float)ff[q].sgn * nrm3_bwd(nrm3(ff[q].tv), Gft[q]);
+                ge1 += ff[q].d2y * gtv;
+                ge2 -= ff[q].d1y * gtv;
+            }
+            if (ff[q].idx[0] == v) g -= ge1 + ge2;
+            if (ff[q].idx[1] == v) g += ge1;
+            if (ff[q].idx[2] == v) g += ge2;
+        }
     }
     double* acc = a.g_pos_acc + 3 * v;
     double g0 = acc[0] + (double)g.x, g1 = acc[1] + (double)g.y, g2 = acc[2] + (double)g.z;
@@ -122,9 +147,16 @@ __global__ void k_lap_fwd(LapArgs a) {
     if (i < a.V) {
         int lo = a.ring_off[i], hi = a.ring_off[i + 1];
         float3 m = zero3();
-        for (int j = lo; j < hi; ++j) {
-            int k = a.ring[j];
-            m += f3(a.pos[3 * k], a.pos[3 * k + 1], a.pos[3 * k + 2]);
+        for (int j0 = lo; j0 < hi; j0 += ADMS_GATHER) {
+            float3 pk[ADMS_GATHER];
+#pragma unroll
+            for (int q = 0; q < ADMS_GATHER; ++q) {
+                int k = a.ring[min(j0 + q, hi - 1)];
+                pk[q] = f3(a.pos[3 * k], a.pos[3 * k + 1], a.pos[3 * k + 2]);
+            }
+#pragma unroll
+            for (int q = 0; q < ADMS_GATHER; ++q)
+                if (j0 + q < hi) m += pk[q];
         }
         float inv = hi > lo ? 1.f / (float)(hi - lo) : 0.f;
         float3 d = f3(a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2]) - inv * m;
@@ -140,17 +172,32 @@ __global__ void k_lap_fwd(LapArgs a) {
     if (threadIdx.x == 0) atomicAdd(&a.st->lap_sum, red[0] + red[1] + red[2] + red[3]);
 }
 
+// g -= sum over the one-ring i of vertex k of delta_i / |ring(i)| (the adjoint of
+// the one-ring means, gathered per vertex)
+__device__ __forceinline__ void ring_adjoint(const LapArgs& a, int k, float3& g) {
+    int lo = a.ring_off[k], hi = a.ring_off[k + 1];
+    for (int j0 = lo; j0 < hi; j0 += ADMS_GATHER) {
+        float inv[ADMS_GATHER];
+        float3 d[ADMS_GATHER];
+#pragma unroll
+        for (int q = 0; q < ADMS_GATHER; ++q) {
+            int i = a.ring[min(j0 + q, hi - 1)];
+            inv[q] = 1.f / (float)(a.ring_off[i + 1] - a.ring_off[i]);
+            d[q] = f3(a.delta[3 * i], a.delta[3 * i + 1], a.delta[3 * i + 2]);
+        }
+#pragma unroll
+        for (int q = 0; q < ADMS_GATHER; ++q)
+            if (j0 + q < hi) g -= inv[q] * d[q];
+    }
+}
+
 __global__ void k_lap_bwd(LapArgs a) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.V) return;
     float lam = a.st->lam;
     float scale = 2.f * lam / (float)a.V;
     float3 g = f3(a.delta[3 * k], a.delta[3 * k + 1], a.delta[3 * k + 2]);
-    for (int j = a.ring_off[k]; j < a.ring_off[k + 1]; ++j) {
-        int i = a.ring[j];
-        float inv = 1.f / (float)(a.ring_off[i + 1] - a.ring_off[i]);
-        g -= inv * f3(a.delta[3 * i], a.delta[3 * i + 1], a.delta[3 * i + 2]);
-    }
+    ring_adjoint(a, k, g);
     a.g_pos[3 * k] += scale * g.x;
     a.g_pos[3 * k + 1] += scale * g.y;
     a.g_pos[3 * k + 2] += scale * g.z;
@@ -172,11 +219,7 @@ __global__ void k_lap_grad_out(LapArgs a, float scale) {
     if (k >= a.V) return;
     float s = 2.f * scale / (float)a.V;
     float3 g = f3(a.delta[3 * k], a.delta[3 * k + 1], a.delta[3 * k + 2]);
-    for (int j = a.ring_off[k]; j < a.ring_off[k + 1]; ++j) {
-        int i = a.ring[j];
-        float inv = 1.f / (float)(a.ring_off[i + 1] - a.ring_off[i]);
-        g -= inv * f3(a.delta[3 * i], a.delta[3 * i + 1], a.delta[3 * i + 2]);
-    }
+    ring_adjoint(a, k, g);
     a.g_pos[3 * k] = s * g.x;
     a.g_pos[3 * k + 1] = s * g.y;
     a.g_pos[3 * k + 2] = s * g.z;

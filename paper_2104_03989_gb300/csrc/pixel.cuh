@@ -652,12 +652,14 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
 // ------------------------------------------------------------------ backward
 // Vertex gradients of the fused backward: every lane of a warp writes the 27 values
 // of its pixel (position, unit normal and unit tangent gradients of the three
-// corners) into its row of a per-warp 32 x 27 shared-memory array; lanes that share
-// a triangle are summed column by column (lane j sums value j over the group, rows in
-// ascending lane order) and one lane per value issues a float64 atomic. The row
-// stride 27 is odd, so the 32 lanes writing one value and the 27 lanes reading one
-// row each touch distinct banks.
-#define ADMS_VROW 27
+// corners) and its triangle's three vertex ids (columns 27-29, as int bits) into its
+// row of a per-warp 32 x 31 shared-memory array; lanes that share a triangle are
+// summed column by column (lane j sums value j over the group, rows in ascending
+// lane order) and one lane per value issues a float64 atomic at the vertex the
+// group's first row names. The row stride 31 is odd, so the 32 lanes writing one
+// value and the 27 lanes reading one row each touch distinct banks.
+#define ADMS_VROW 31
+#define ADMS_VROW_IDS 27
 __device__ __forceinline__ void scatter_vertex_rows(const ShadeArgs& A, int f, const float* rows) {
     int lane = threadIdx.x & 31;
     __syncwarp();
@@ -666,12 +668,12 @@ __device__ __forceinline__ void scatter_vertex_rows(const ShadeArgs& A, int f, c
         int lead = __ffs(todo) - 1;
         int ft = __shfl_sync(0xffffffffu, f, lead);
         unsigned grp = __ballot_sync(0xffffffffu, f == ft);
-        if (lane < ADMS_VROW) {
+        if (lane < ADMS_VROW_IDS) {
             float sum = 0.f;
             for (unsigned m = grp; m; m &= m - 1) sum += rows[(__ffs(m) - 1) * ADMS_VROW + lane];
             if (sum != 0.f) {
                 int corner = lane / 9, comp = lane - 9 * corner;
-                int vtx = __ldg(A.tri + (3 * ft + corner));
+                int vtx = __float_as_int(rows[lead * ADMS_VROW + ADMS_VROW_IDS + corner]);
                 double* dst = comp < 3 ? A.g_pos : (comp < 6 ? A.g_nrm : A.g_tan);
                 atomicAdd(dst + 3 * vtx + comp % 3, (double)sum);
                 if (!isfinite(sum) && A.status) atomicExch(A.status, (int)ADMS_ERR_NONFINITE);
@@ -1018,11 +1020,12 @@ __device__ __forceinline__ void shading_adjoint(const ShadeArgs& A, int b, int p
         r[6] = gtk.x;
         r[7] = gtk.y;
         r[8] = gtk.z;
+        vrow[ADMS_VROW_IDS + k] = __int_as_float(g.vi[k]);
     }
 }
 
 // one pixel of the fused backward; warp-collective (vertex scatter). rows: the
-// warp's 32 x 27 floats of shared memory
+// warp's 32 x ADMS_VROW floats of shared memory
 template <bool PEEL = false>
 __device__ __forceinline__ void shade_bwd_px(const ShadeArgs& A, int b, int px, int py, float* rows) {
     bool inside = px < A.W && py < A.H;

@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(256, 3) k_stage_shade_bwd(ShadeArgs A, const f
                 r[9 * k + 6] = gt.x;
                 r[9 * k + 7] = gt.y;
                 r[9 * k + 8] = gt.z;
+                r[ADMS_VROW_IDS + k] = __int_as_float(vi[k]);
             }
         } else {
             f = -1;
