@@ -81,6 +81,7 @@ struct Job {
     float* delta_ref = nullptr;
     // per-step derived state
     float4 *vpos = nullptr, *vnrm = nullptr, *vtan = nullptr, *tmp_n = nullptr, *tmp_t = nullptr;
+    float2* frame_inv = nullptr;  // the frame's normalisations (one-launch frame adjoint)
     double *g_nrm = nullptr, *g_tan = nullptr, *g_pos_acc = nullptr;
     float* delta = nullptr;
     JobState* st = nullptr;
@@ -405,6 +406,7 @@ FrameArgs frame_args(Job& j) {
     f.g_pos_acc = j.g_pos_acc;
     f.g_pos = j.g_rpos;
     f.status = &j.st->status;
+    f.inv = j.frame_inv;
     return f;
 }
 
@@ -891,6 +893,7 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
     AL(j.vtan, j.V);
     AL(j.tmp_n, j.V);
     AL(j.tmp_t, j.V);
+    AL(j.frame_inv, j.V);
     AL(j.g_nrm, (size_t)j.V * 3);
     AL(j.g_tan, (size_t)j.V * 3);
     AL(j.g_pos_acc, (size_t)j.V * 3);

@@ -205,6 +205,10 @@ struct FrameArgs {
     double* g_pos_acc;    // in  [V][3] pixel-stage position gradient; read and zeroed
     float* g_pos;         // accumulated [V][3]
     int* status = nullptr; // latched ADMS_ERR_NONFINITE when a position gradient is NaN or infinite
+    // optional [V]: 1/|sum| of each vertex's normal (x) and tangent (y) sums, negated
+    // where the squared sum is at or below the normalisation floor; written by
+    // frame_forward when set, after which frame_backward is one launch
+    float2* inv = nullptr;
 };
 cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st);
 cudaError_t frame_backward(const FrameArgs& a, cudaStream_t st);

@@ -68,10 +68,30 @@ __global__ void k_frame_fwd(FrameArgs a) {
     if (v >= a.V) return;
     float3 n, t;
     vertex_sums(a, v, n, t);
-    float3 nn = nrm3(n).y, tn = nrm3(t).y;
+    Nrm3 nn = nrm3(n), tn = nrm3(t);
     a.vpos[v] = make_float4(a.pos[3 * v], a.pos[3 * v + 1], a.pos[3 * v + 2], 0.f);
-    a.vnrm[v] = make_float4(nn.x, nn.y, nn.z, 0.f);
-    a.vtan[v] = make_float4(tn.x, tn.y, tn.z, 0.f);
+    a.vnrm[v] = make_float4(nn.y.x, nn.y.y, nn.y.z, 0.f);
+    a.vtan[v] = make_float4(tn.y.x, tn.y.y, tn.y.z, 0.f);
+    if (a.inv) a.inv[v] = make_float2(nn.big ? nn.inv : -nn.inv, tn.big ? tn.inv : -tn.inv);
+}
+
+// the normalisation of vertex c's normal (k = 0) or tangent (k = 1) sum as the
+// forward left it: the unit vector and the signed inverse length
+__device__ __forceinline__ Nrm3 stored_nrm3(const FrameArgs& a, int c, int k) {
+    float4 y = k == 0 ? a.vnrm[c] : a.vtan[c];
+    float2 iv = a.inv[c];
+    float s = k == 0 ? iv.x : iv.y;
+    Nrm3 r;
+    r.y = f3(y.x, y.y, y.z);
+    r.inv = fabsf(s);
+    r.big = s > 0.f;
+    return r;
+}
+
+// dL/d(normal sum) of vertex c: the adjoint of its normalisation (k_frame_bwd1's tmp_n)
+__device__ __forceinline__ float3 sum_grad(const FrameArgs& a, int c, int k) {
+    const double* g = (k == 0 ? a.g_nrm : a.g_tan) + 3 * c;
+    return nrm3_bwd(stored_nrm3(a, c, k), f3((float)g[0], (float)g[1], (float)g[2]));
 }
 
 // phase 1: gradients w.r.t. the unnormalised sums
@@ -84,6 +104,20 @@ __global__ void k_frame_bwd1(FrameArgs a) {
     float3 gt = nrm3_bwd(nrm3(t), f3((float)a.g_tan[3 * v], (float)a.g_tan[3 * v + 1], (float)a.g_tan[3 * v + 2]));
     a.tmp_n[v] = make_float4(gn.x, gn.y, gn.z, 0.f);
     a.tmp_t[v] = make_float4(gt.x, gt.y, gt.z, 0.f);
+}
+
+// g_pos[v] += the pixel stage's float64 position gradient + g (the frame adjoint);
+// the float64 accumulator is zeroed for the next backward
+__device__ __forceinline__ void fold_position_grad(const FrameArgs& a, int v, float3 g) {
+    double* acc = a.g_pos_acc + 3 * v;
+    double g0 = acc[0] + (double)g.x, g1 = acc[1] + (double)g.y, g2 = acc[2] + (double)g.z;
+    if (a.status && !(isfinite(g0) && isfinite(g1) && isfinite(g2))) atomicExch(a.status, (int)ADMS_ERR_NONFINITE);
+    a.g_pos[3 * v] += (float)g0;
+    a.g_pos[3 * v + 1] += (float)g1;
+    a.g_pos[3 * v + 2] += (float)g2;
+    acc[0] = 0.0;
+    acc[1] = 0.0;
+    acc[2] = 0.0;
 }
 
 // phase 2: each vertex gathers its share of every incident face's adjoint
@@ -115,15 +149,38 @@ __global__ void k_frame_bwd2(FrameArgs a) {
             if (ff[q].idx[2] == v) g += ge2;
         }
     }
-    double* acc = a.g_pos_acc + 3 * v;
-    double g0 = acc[0] + (double)g.x, g1 = acc[1] + (double)g.y, g2 = acc[2] + (double)g.z;
-    if (a.status && !(isfinite(g0) && isfinite(g1) && isfinite(g2))) atomicExch(a.status, (int)ADMS_ERR_NONFINITE);
-    a.g_pos[3 * v] += (float)g0;
-    a.g_pos[3 * v + 1] += (float)g1;
-    a.g_pos[3 * v + 2] += (float)g2;
-    acc[0] = 0.0;
-    acc[1] = 0.0;
-    acc[2] = 0.0;
+    fold_position_grad(a, v, g);
+}
+
+// k_frame_bwd1 and k_frame_bwd2 in one launch, after a frame_forward that kept the
+// normalisations (a.inv): each vertex forms the normalisation adjoints of its
+// faces' corners itself (the same values, summed in the same order)
+__global__ void k_frame_bwd_fused(FrameArgs a) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.V) return;
+    float3 g = zero3();
+    int lo = a.vf_off[v], hi = a.vf_off[v + 1];
+    for (int j0 = lo; j0 < hi; j0 += ADMS_GATHER) {
+        FaceFrame ff[ADMS_GATHER];
+#pragma unroll
+        for (int q = 0; q < ADMS_GATHER; ++q) ff[q] = face_frame(a, a.vf_face[min(j0 + q, hi - 1)]);
+#pragma unroll
+        for (int q = 0; q < ADMS_GATHER; ++q) {
+            if (j0 + q >= hi) continue;
+            float3 Gfn = sum_grad(a, ff[q].idx[0], 0) + sum_grad(a, ff[q].idx[1], 0) + sum_grad(a, ff[q].idx[2], 0);
+            float3 ge1 = cross3(ff[q].e2, Gfn), ge2 = cross3(Gfn, ff[q].e1);
+            if (ff[q].sgn != 0) {
+                float3 Gft = sum_grad(a, ff[q].idx[0], 1) + sum_grad(a, ff[q].idx[1], 1) + sum_grad(a, ff[q].idx[2], 1);
+                float3 gtv = (float)ff[q].sgn * nrm3_bwd(nrm3(ff[q].tv), Gft);
+                ge1 += ff[q].d2y * gtv;
+                ge2 -= ff[q].d1y * gtv;
+            }
+            if (ff[q].idx[0] == v) g -= ge1 + ge2;
+            if (ff[q].idx[1] == v) g += ge1;
+            if (ff[q].idx[2] == v) g += ge2;
+        }
+    }
+    fold_position_grad(a, v, g);
 }
 
 cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st) {
@@ -133,6 +190,11 @@ cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st) {
 }
 
 cudaError_t frame_backward(const FrameArgs& a, cudaStream_t st) {
+    if (a.inv) {
+        k_frame_bwd_fused<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     k_frame_bwd1<<<(a.V + 127) / 128, 128, 0, st>>>(a);
     k_frame_bwd2<<<(a.V + 127) / 128, 128, 0, st>>>(a);
     count_launches(2);

@@ -427,8 +427,9 @@ __device__ __forceinline__ void shade_refine_px(const ShadeArgs& A, int pix) {
 }
 
 // ------------------------------------------------------------------ shading forward
-// shading of triangle f at sample (px, py), listing it for the refinement pass
-// when bright on a triangle that spans many texels
+// shading of triangle f at sample (px, py), refining it (INLINE) or listing it for
+// the refinement pass when bright on a triangle that spans many texels
+template <bool INLINE = false>
 __device__ __forceinline__ float4 shade_covered(const ShadeArgs& A, int b, int px, int py, int f, size_t pix) {
     PixGeo g;
     pix_geo(A, b, px, py, f, g);
@@ -438,20 +439,29 @@ __device__ __forceinline__ float4 shade_covered(const ShadeArgs& A, int b, int p
     // Bright pixels (sharp highlights) carry almost all of the error a float32
     // texture coordinate causes: on the noise-textured workloads the 0.35% of
     // pixels above 0.5 carry 98% of it. Those on triangles spanning more than two
-    // texels at the sampled level are listed and shaded again by k_shade_refine
-    // with the refined coordinate and LOD (a separate pass keeps this kernel's
-    // registers to the common path). The backward, held to 1e-3, keeps the
-    // float32 ones.
-    if (A.refine && fmaxf(c.x, fmaxf(c.y, c.z)) > 0.5f && tc_lever(A, g, lod) > 2.f)
-        A.refine[1 + atomicAdd(A.refine, 1)] = (int)pix;  // for k_shade_refine
+    // texels at the sampled level are shaded again with the refined coordinate and
+    // LOD: here (INLINE, for small grids, where a second launch costs more than
+    // the branch) or by k_shade_refine from a list (a separate pass keeps the
+    // shading kernel's registers to the common path). The backward, held to 1e-3,
+    // keeps the float32 ones.
+    if (A.refine && fmaxf(c.x, fmaxf(c.y, c.z)) > 0.5f && tc_lever(A, g, lod) > 2.f) {
+        if (INLINE) {
+            refine_tc(A, b, px, py, g);
+            in = shade_inputs(A, g, lod);
+            c = shade_eval<false>(A.views[b], in, zero3(), nullptr);
+        } else {
+            A.refine[1 + atomicAdd(A.refine, 1)] = (int)pix;  // for k_shade_refine
+        }
+    }
     return make_float4(c.x, c.y, c.z, A.peel ? in.kd.w : 1.f);  // a peeled layer keeps its opacity
 }
 
+template <bool INLINE = false>
 __device__ __forceinline__ void shade_fwd_px(const ShadeArgs& A, int b, int px, int py) {
     if (px >= A.W || py >= A.H) return;
     size_t pix = ((size_t)b * A.H + py) * A.W + px;
     int f = key_tri(__ldg(A.keys + (pix)));
-    A.pre[pix] = f >= 0 ? shade_covered(A, b, px, py, f, pix) : make_float4(0.f, 0.f, 0.f, 0.f);
+    A.pre[pix] = f >= 0 ? shade_covered<INLINE>(A, b, px, py, f, pix) : make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Under MSAA every sample of a pixel that shows one triangle has the same shading

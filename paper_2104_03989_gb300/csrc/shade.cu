@@ -32,9 +32,10 @@ __global__ void __launch_bounds__(256) k_shade_refine(ShadeArgs A) {
 #ifndef ADMS_AA_BLOCKS
 #define ADMS_AA_BLOCKS 8
 #endif
+template <bool INLINE>
 __global__ void __launch_bounds__(256, ADMS_FWD_BLOCKS) k_shade_fwd(ShadeArgs A) {
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    shade_fwd_px(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
+    shade_fwd_px<INLINE>(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
 }
 
@@ -274,19 +275,27 @@ static dim3 pix_grid(const ShadeArgs& a) {
     return dim3(tx * ty, a.B);
 }
 
+// grids of up to this many samples refine their bright pixels in the shading
+// kernel itself (no list, no second launch)
+#define ADMS_INLINE_REFINE_PX (1 << 20)
+
 cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
-    if (a.refine) {
+    bool inline_refine = a.msaa <= 1 && (size_t)a.B * a.H * a.W <= ADMS_INLINE_REFINE_PX;
+    bool list = a.refine && !inline_refine;
+    if (list) {
         cudaError_t e = cudaMemsetAsync(a.refine, 0, sizeof(int), st);
         if (e) return e;
     }
     if (a.msaa > 1) {
         int R = ADMS_MSAA_REGION;
         k_shade_fwd_msaa<<<dim3(((a.W + R - 1) / R) * ((a.H + R - 1) / R), a.B), 256, 0, st>>>(a);
+    } else if (inline_refine) {
+        k_shade_fwd<true><<<pix_grid(a), 256, 0, st>>>(a);
     } else {
-        k_shade_fwd<<<pix_grid(a), 256, 0, st>>>(a);
+        k_shade_fwd<false><<<pix_grid(a), 256, 0, st>>>(a);
     }
     count_launches(1);
-    if (a.refine) {
+    if (list) {
         k_shade_refine<<<128, 256, 0, st>>>(a);
         count_launches(1);
     }
