@@ -102,13 +102,19 @@ def test_recompute_mode_gives_the_same_gradients(gpu_lib):
 
 def _fd_check(label, f, params, rng, min_total=64):
     """Central differences of the scalar f() in the picked entries of each
-    parameter (entries whose analytic gradient is not tiny) against the analytic
-    gradient already in .grad; median relative error < 1e-3, 90% under 1e-2."""
+    parameter (entries whose analytic gradient is above a fraction of the
+    largest, 1e-3 unless the parameter tuple gives a fifth element) against the
+    analytic gradient already in .grad; median relative error < 1e-3, 90% under
+    1e-2. f() sums float32 stage outputs, so its rounding noise is about constant
+    in absolute terms: on an entry with a tiny gradient it is a large relative
+    error that says nothing about the backward."""
     errs, groups = [], []
     with torch.no_grad():
-        for name, t, k, h in params:
+        for p in params:
+            name, t, k, h = p[:4]
+            floor = p[4] if len(p) > 4 else 1e-3
             g = t.grad.reshape(-1)
-            nz = torch.nonzero(g.abs() > 1e-3 * g.abs().max()).squeeze(1).cpu().numpy()
+            nz = torch.nonzero(g.abs() > floor * g.abs().max()).squeeze(1).cpu().numpy()
             for i in rng.choice(nz, size=min(len(nz), k), replace=False):
                 flat = t.data.view(-1)
                 x0 = float(flat[i])
@@ -148,12 +154,14 @@ def test_each_stage_backward_against_central_differences(gpu_lib):
     ST, cand, views, H, W, ref_np, loss, pipe, lat = _inputs("small")
     ref = torch.as_tensor(ref_np).cuda()
     rng = np.random.default_rng(1)
+    gen = torch.Generator().manual_seed(1)   # the random projections, drawn on the host
+    randn = lambda *shape: torch.randn(*shape, generator=gen).cuda()   # noqa: E731
     lat["kd"], lat["nrm"] = _smooth_maps(lat["kd"].shape[0])
     pos = lat["pos"].detach().clone().requires_grad_(True)
     dbl = lambda x: x.double()   # noqa: E731
 
     # frame: a random projection of (normals, tangents) w.r.t. positions
-    R = torch.randn(2, pipe.V, 4, device="cuda")
+    R = randn(2, pipe.V, 4)
     def frame():
         _, n4, t4 = ST.Frame.apply(pipe, pos)
         return (dbl(n4) * R[0]).sum() + (dbl(t4) * R[1]).sum()
@@ -165,7 +173,7 @@ def test_each_stage_backward_against_central_differences(gpu_lib):
     clip0 = ST.Setup.apply(pipe, pos.detach())
     ST.Raster.apply(pipe, pos.detach(), clip0)            # keys and LOD derivatives of the unperturbed mesh
     covered = (pipe.keys != -1).unsqueeze(-1).float()
-    Rr = torch.randn(pipe.B, pipe.H, pipe.W, 2, device="cuda") * covered
+    Rr = randn(pipe.B, pipe.H, pipe.W, 2) * covered
     def raster():
         clip = ST.Setup.apply(pipe, pos)
         return (dbl(ST.Raster.apply(pipe, pos, clip, True)) * Rr).sum()
@@ -177,7 +185,7 @@ def test_each_stage_backward_against_central_differences(gpu_lib):
     pos.grad = None
     kd = lat["kd"].detach().clone().requires_grad_(True)
     nrm = lat["nrm"].detach().clone().requires_grad_(True)
-    Rs = torch.randn(pipe.B, pipe.H, pipe.W, 4, device="cuda") * covered
+    Rs = randn(pipe.B, pipe.H, pipe.W, 4) * covered
     Rs[..., 3] = 0
     def shade():
         chains = [ST.MipChain.apply(t) for t in (kd, lat["orm"].detach(), nrm)]
@@ -187,7 +195,9 @@ def test_each_stage_backward_against_central_differences(gpu_lib):
         rast = ST.Raster.apply(pipe, pos, clip, True)
         return (dbl(ST.Shade.apply(pipe, pos, rast, v4, n4, t4, d, *chains)) * Rs).sum()
     shade().backward()
-    _fd_check("shade", shade, [("kd", kd, 32, 1e-2), ("nrm", nrm, 32, 1e-2), ("pos", pos, 64, 1e-4)], rng,
+    # positions: entries above 1e-2 of the largest (the noise floor of a 1e-4 step
+    # through the float32 shading is about 1e-3 of a typical entry)
+    _fd_check("shade", shade, [("kd", kd, 32, 1e-2), ("nrm", nrm, 32, 1e-2), ("pos", pos, 64, 1e-4, 1e-2)], rng,
               min_total=128)
 
     # aa_loss: the loss w.r.t. the pre-AA colours and (through the silhouette
@@ -213,7 +223,7 @@ def test_each_stage_backward_against_central_differences(gpu_lib):
         nonlocal Rm
         ch = ST.MipChain.apply(t0)
         if Rm is None:
-            Rm = torch.randn_like(ch)
+            Rm = randn(*ch.shape)
         return (dbl(ch) * Rm).sum()
     mip().backward()
     _fd_check("mip", mip, [("kd", t0, 64, 1e-2)], rng)
@@ -285,7 +295,7 @@ def test_tessellation_stage_against_central_differences(gpu_lib):
     rng = np.random.default_rng(4)
     bp = lat["pos"].detach().clone().requires_grad_(True)
     dm = lat["disp"].detach().clone().requires_grad_(True)
-    R = torch.randn(tm.Vt, 3, device="cuda", dtype=torch.float64)
+    R = torch.randn(tm.Vt, 3, generator=torch.Generator().manual_seed(4), dtype=torch.float64).cuda()
     f = lambda: (ST.Tess.apply(tm, bp, dm).double() * R).sum()   # noqa: E731
     f().backward()
     _fd_check("tess", f, [("pos", bp, 64, 1e-3), ("disp", dm, 64, 1e-3)], rng, min_total=128)
