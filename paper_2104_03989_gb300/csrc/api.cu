@@ -20,7 +20,7 @@ struct TexState {
     float4* grad = nullptr;  // mip chain (when optimized)
     float4* m = nullptr;     // level 0
     float4* v = nullptr;
-    int* done = nullptr;     // tiles finished in the current tiled Adam launch
+    CUtensorMap tmaps[4];  // tensor maps of level 0 for the tiled Adam (grad, tex, m, v)
     bool per_level = false;  // every level is a latent: m, v span the chain
     int w = 0, h = 0, levels = 0;
     int off[ADMS_MAX_LEVELS] = {0};
@@ -329,7 +329,7 @@ adms_status tex_create(adms_ctx* ctx, Job& j, TexState& t, const float* src, int
         AL(t.grad, t.total);
         AL(t.m, nm);
         AL(t.v, nm);
-        AL(t.done, 1);
+        if (!t.per_level && adam_tiled(t.dev())) CK(adam_encode_maps(t.dev(), t.m, t.v, t.tmaps));
     }
     CK(mip_build(t.dev(), ctx->stream));
     return ADMS_OK;
@@ -1171,6 +1171,10 @@ adms_status adms_ctx_create(adms_ctx** out, size_t hbm_budget_bytes, void* cuda_
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0) c->sm_count = sms;
     for (int k = 0; k < 4; ++k) c->occ[k] = adms::batched_occupancy(k);
+    if (adms::adam_prepare() != cudaSuccess) {
+        delete c;
+        return ADMS_ERR_CUDA;
+    }
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -1695,7 +1699,11 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
             TexDev td = maps[m]->dev();
             if (maps[m]->per_level)
                 CK(TIMED(ST_ADAM, adam_texture_levels(td, maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
-            else if (adam_tiled(td)) tiled.push_back(TexAdam{td, maps[m]->m, maps[m]->v, j.st, maps[m]->done, m, 0});
+            else if (adam_tiled(td)) {
+                TexAdam ta{td, maps[m]->m, maps[m]->v, j.st, m, 0};
+                ta.tmaps = maps[m]->tmaps;
+                tiled.push_back(ta);
+            }
             else CK(TIMED(ST_ADAM, adam_texture_and_mips(td, maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
         }
     }

@@ -6,6 +6,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap
+
 #include "common.cuh"
 
 namespace adms {
@@ -309,17 +311,24 @@ struct TexAdam {
     float4* m;
     float4* v;
     const JobState* js;
-    int* done;       // device counter of finished tiles: zero between launches (the last tile resets it)
     int clamp_kind;  // 0 kd, 1 orm, 2 nrm
     int tile0;       // set by the launcher
+    const CUtensorMap* tmaps = nullptr;  // host CUtensorMap[4]: level 0 of grad, tex, m, v (adam_encode_maps)
 };
-#define ADMS_ADAM_TEX 160  // textures per launch: their arguments are kernel parameters (< 32 KB)
+// textures per launch: their arguments and tensor maps are kernel parameters (< 32 KB)
+#define ADMS_ADAM_TEX 40
 struct TexAdamBatch {
+    CUtensorMap maps[ADMS_ADAM_TEX][4];  // grad, tex, m, v of texture k
     TexAdam a[ADMS_ADAM_TEX];
     int n;
 };
 // whether a texture takes the tiled path (both sides multiples of 32, at least 6 levels)
 bool adam_tiled(const TexDev& t);
+// the streamed Adam's shared-memory limit (called once per process before its first launch)
+cudaError_t adam_prepare();
+// host: the tensor maps of level 0 of a tiled texture's gradient, latents and
+// moments (float4 texels as float32 x 4, boxes of 32 texels x 32 rows)
+cudaError_t adam_encode_maps(const TexDev& t, const float4* m, const float4* v, CUtensorMap out[4]);
 // Adam + mip rebuild of every listed texture (all adam_tiled, any jobs), one 32x32-texel
 // tile per block, one launch per ADMS_ADAM_TEX textures
 cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st);

@@ -1,7 +1,11 @@
 // Optimizer step (Sec. 5.3): lambda and learning-rate schedules, Adam with
 // default parameters fused with the adjoint of the mip chain and the range
 // clamps, and the mip rebuild of the updated textures.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "kernels.cuh"
+#include "bulk.cuh"
 
 namespace adms {
 
@@ -215,190 +219,361 @@ __device__ __forceinline__ float level_weight(const TexDev& t, int k) {
     return w;
 }
 
-// Adam + clamps on one level-0 texel whose gradient g already includes the mip adjoint
-__device__ __forceinline__ float4 adam_texel(const TexDev& t, float4* __restrict__ m, float4* __restrict__ v, int i,
-                                             float4 g, int clamp_kind, float lr, float bc1, float bc2) {
-    float4 p = t.tex[i], mm = m[i], vv = v[i];
-    p.x = adam1(p.x, g.x, mm.x, vv.x, lr, bc1, bc2);
-    p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
-    p.z = adam1(p.z, g.z, mm.z, vv.z, lr, bc1, bc2);
-    p.w = adam1(p.w, g.w, mm.w, vv.w, lr, bc1, bc2);
-    p = clamp_texel(p, clamp_kind);
-    const_cast<float4*>(t.tex)[i] = p;
-    m[i] = mm;
-    v[i] = vv;
-    t.grad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    return p;
-}
+// Adam on the 32x32 texel tiles of level 0 of every texture of a launch (up to
+// ADMS_ADAM_TEX textures of any jobs, tile ranges from tile0), each followed by
+// levels 1..5 of its tile from the updated texels (2x2 box average, same order of
+// summation as k_mip_level), so level 0 is read once for both.
+//
+// Streaming: one persistent block per SM walks tiles blockIdx.x, + gridDim.x, ...
+// Thread 0 moves a tile's four level-0 arrays (gradient, latent, moments: one
+// 32 x 32-texel box of each texture's tensor maps, 16 KB) into one of three
+// shared-memory stages with TMA copies completing on that stage's mbarrier, two
+// tiles ahead of the arithmetic, and writes the cleared gradient, the updated
+// latent and the moments back with TMA stores from shared memory.
+//
+// Thread t owns the 2x2 level-0 quad under level-1 texel (cx, cy) of the tile,
+// t interleaving the bits of cx (even bits) and cy (odd bits): the four children
+// of a level-2 texel are lanes 4j..4j+3, those of a level-3 texel lanes 16j + {0,
+// 4, 8, 12}, those of a level-4 texel threads 64j + {0, 16, 32, 48}, each time in
+// the order (0,0), (1,0), (0,1), (1,1). Levels 1-3 are formed in registers and by
+// shuffles, level 4 through shared memory after the tile's one block barrier,
+// level 5 by shuffles in warp 0.
+//
+// The mip adjoint: each level-0 texel receives sum_k w_k g_k over its ancestors
+// (w_k = 1/4^k up to level 5, the product of the box factors beyond), formed by
+// each thread from its own loads (issued a tile ahead into registers) as
+// g0 + ((((c + w5 g5) + w4 g4) + w3 g3) + w2 g2) + w1 g1, c the sum over levels
+// 6.. . A gradient texel of levels 1..5 is cleared by its owner after every reader
+// in the block has consumed it; k_adam_mip_top, launched after, builds levels 6..
+// and clears their gradients.
+struct AdamStage {
+    float4 g[32][32], p[32][32], m[32][32], v[32][32];
+};
+#define ADMS_ADAM_STAGES 3
+#define ADMS_ADAM_THREADS 256
+struct AdamSmem {
+    AdamStage st[ADMS_ADAM_STAGES];
+    float4 s3[2][16];  // a tile's level-3 texels in thread (interleaved-bit) order, by tile parity
+    uint64_t bar[ADMS_ADAM_STAGES];
+};
+#define ADMS_ADAM_WAIT_NS 2000000000ull  // a tile's wait gives up after 2 s
 
-// adam_texel with the texel's latent and moments already loaded
-__device__ __forceinline__ float4 adam_texel_v(const TexDev& t, float4* __restrict__ m, float4* __restrict__ v, int i,
-                                               float4 g, float4 p, float4 mm, float4 vv, int clamp_kind, float lr,
-                                               float bc1, float bc2) {
-    p.x = adam1(p.x, g.x, mm.x, vv.x, lr, bc1, bc2);
-    p.y = adam1(p.y, g.y, mm.y, vv.y, lr, bc1, bc2);
-    p.z = adam1(p.z, g.z, mm.z, vv.z, lr, bc1, bc2);
-    p.w = adam1(p.w, g.w, mm.w, vv.w, lr, bc1, bc2);
-    p = clamp_texel(p, clamp_kind);
-    const_cast<float4*>(t.tex)[i] = p;
-    m[i] = mm;
-    v[i] = vv;
-    t.grad[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    return p;
+__device__ __forceinline__ int even_bits(int t) {  // bits 0, 2, 4, 6 of t, packed
+    return (t & 1) | ((t >> 1) & 2) | ((t >> 2) & 4) | ((t >> 3) & 8);
 }
-
-// Adam on one 32x32 texel tile of level 0 per block, for every texture of a
-// launch (up to ADMS_ADAM_TEX textures of any jobs, block ranges from tile0),
-// then levels 1..5 of that tile built in shared memory from the updated texels
-// (2x2 box average, same order of summation as k_mip_level), so level 0 is read
-// once for both. The mip adjoint is pushed down the tile's pyramid first; each
-// gradient texel of levels 1..5 belongs to one tile, which zeroes it with the
-// mip writes at the end (a store right after each push-down read held the
-// reads back: Adam took 0.23 instead of 0.11 ms per step). All of a tile's reads
-// are issued before its first barrier (one memory round trip instead of one per
-// pyramid level). The last tile of a texture to finish (a counter per texture)
-// builds levels 6.. from level 5, zeroes their gradients and resets the counter.
-// resident blocks per SM of the tiled Adam (register cap 65536 / (256 x this)): the
-// thread keeps its 16 level-0 loads in flight at once
-#ifndef ADMS_ADAM_BLOCKS
-#define ADMS_ADAM_BLOCKS 3
-#endif
-__global__ void __launch_bounds__(256, ADMS_ADAM_BLOCKS) k_adam_tex_batch(const TexAdamBatch P) {
-    __shared__ float4 tile[32][32];
-    // push level k (k = 1..5): first the raw level-k gradient texels of this tile, then
-    // in place sum_{j >= k} weight_j * grad_j at those texels
-    __shared__ float4 push[256 + 64 + 16 + 4 + 1];
-    __shared__ float4 anc[ADMS_MAX_LEVELS];  // gradients of the tile's ancestors at levels 6..
-    __shared__ int s_last;
-    const int poff[6] = {0, 0, 256, 320, 336, 340};
-    int lo = 0, hi = P.n - 1;  // the texture: last entry with tile0 <= blockIdx.x
+__device__ __forceinline__ float4 quad_mean(float4 a, float4 b, float4 c, float4 d) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc = f4madd(acc, 1.f, a);
+    acc = f4madd(acc, 1.f, b);
+    acc = f4madd(acc, 1.f, c);
+    acc = f4madd(acc, 1.f, d);
+    return f4scale(acc, 0.25f);
+}
+__device__ __forceinline__ float4 shfl_down4(float4 v, int d, unsigned mask = 0xffffffffu) {
+    return make_float4(__shfl_down_sync(mask, v.x, d), __shfl_down_sync(mask, v.y, d), __shfl_down_sync(mask, v.z, d),
+                       __shfl_down_sync(mask, v.w, d));
+}
+// Adam on four components with the bias corrections as reciprocals and the step's
+// division approximate (2 ulp)
+__device__ __forceinline__ float4 adam4(float4 p, float4 g, float4& m, float4& v, float lr, float ibc1, float ibc2) {
+    float pv[4] = {p.x, p.y, p.z, p.w}, gv[4] = {g.x, g.y, g.z, g.w};
+    float mv[4] = {m.x, m.y, m.z, m.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        bool ok = isfinite(gv[c]);
+        float m1 = 0.9f * mv[c] + 0.1f * gv[c];
+        float v1 = 0.999f * vv[c] + 0.001f * gv[c] * gv[c];
+        float p1 = pv[c] - __fdividef(lr * (m1 * ibc1), sqrtf(v1 * ibc2) + 1e-8f);
+        mv[c] = ok ? m1 : mv[c];
+        vv[c] = ok ? v1 : vv[c];
+        pv[c] = ok ? p1 : pv[c];
+    }
+    m = make_float4(mv[0], mv[1], mv[2], mv[3]);
+    v = make_float4(vv[0], vv[1], vv[2], vv[3]);
+    return make_float4(pv[0], pv[1], pv[2], pv[3]);
+}
+// the texture entry of flattened tile index `tile`: last entry with tile0 <= tile
+__device__ __forceinline__ int adam_entry(const TexAdamBatch& P, int tile) {
+    int lo = 0, hi = P.n - 1;
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
-        if (P.a[mid].tile0 <= (int)blockIdx.x) lo = mid;
+        if (P.a[mid].tile0 <= tile) lo = mid;
         else hi = mid - 1;
     }
-    const TexAdam& A = P.a[lo];
-    if (A.js->status) return;  // every tile of a latched job's texture leaves (its tile counter stays 0)
+    return lo;
+}
+__device__ __forceinline__ void adam_tile_xy(const TexAdam& A, int tile, int& bx, int& by) {
+    int tb = tile - A.tile0, tiles_x = A.t.w0 >> 5;
+    bx = tb % tiles_x;
+    by = tb / tiles_x;
+}
+// one thread: the tile's four level-0 arrays into stage S (four boxes of the
+// texture's tensor maps), completing on bar
+__device__ __forceinline__ void adam_fetch(const TexAdamBatch& P, int tile, AdamStage& S, uint64_t* bar) {
+    int e = adam_entry(P, tile);
+    int bx, by;
+    adam_tile_xy(P.a[e], tile, bx, by);
+    const CUtensorMap* tm = P.maps[e];
+    if (bx < 0 || by < 0 || 32 * bx >= P.a[e].t.w0 || 32 * by >= P.a[e].t.h0) {
+        // never taken for a launcher-built batch: record it and complete the phase without copies
+        atomicExch(&const_cast<JobState*>(P.a[e].js)->status_next, (int)ADMS_ERR_STATE);
+        mbar_arrive_expect_tx(bar, 0);
+        return;
+    }
+    mbar_arrive_expect_tx(bar, (uint32_t)sizeof(AdamStage));
+    tile2d_g2s(&S.g[0][0], &tm[0], bx * 128, by * 32, bar);
+    tile2d_g2s(&S.p[0][0], &tm[1], bx * 128, by * 32, bar);
+    tile2d_g2s(&S.m[0][0], &tm[2], bx * 128, by * 32, bar);
+    tile2d_g2s(&S.v[0][0], &tm[3], bx * 128, by * 32, bar);
+}
+
+// the pyramid gradients of levels 1..5 above level-0 texel (x, y) of `tile` (and
+// its quad) into
+// g[1..5] and the tile's ancestors' gradients (levels 6..) into anc[0..]: a tile's
+// loads, issued a tile ahead into registers (the ancestors are the same address
+// for every thread of the block: broadcast loads)
+#define ADMS_ADAM_ANC (ADMS_MAX_LEVELS - 6)
+__device__ __forceinline__ void adam_pyramid(const TexAdamBatch& P, int tile, int x, int y, float4 g[6],
+                                             float4 anc[ADMS_ADAM_ANC]) {
+    const TexAdam& A = P.a[adam_entry(P, tile)];
+    if (A.js->status) return;
     const TexDev& t = A.t;
-    int tb = (int)blockIdx.x - A.tile0;
-    int tiles_x = t.w0 >> 5, n_tiles = tiles_x * (t.h0 >> 5);
-    int bx = tb % tiles_x, by = tb / tiles_x;
-    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    float lr = A.js->lr, bc1 = A.js->bc1, bc2 = A.js->bc2;
-    // every global read of the tile issued up front: the thread's four level-0 texels
-    // (gradient, latent, moments) and the raw gradients of the tile's pyramid and
-    // ancestors, so that one memory round trip covers them all
-    float4 g0[4], p0[4], m0[4], v0[4];
+    int bx, by;
+    adam_tile_xy(A, tile, bx, by);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        int i = ((by << 5) + ty + 8 * r) * t.w0 + (bx << 5) + tx;
-        g0[r] = t.grad[i];
-        p0[r] = t.tex[i];
-        m0[r] = A.m[i];
-        v0[r] = A.v[i];
-    }
+    for (int l = 1; l <= 5; ++l)
+        g[l] = t.grad[t.off[l] + (((by << 5) + y) >> l) * (t.w0 >> l) + (((bx << 5) + x) >> l)];
 #pragma unroll
-    for (int k = 1; k <= 5; ++k) {
-        int n = 32 >> k, wk = t.w0 >> k;
-        for (int idx = threadIdx.x; idx < n * n; idx += 256)
-            push[poff[k] + idx] = t.grad[t.off[k] + (((by << 5) >> k) + idx / n) * wk + ((bx << 5) >> k) + idx % n];
+    for (int i = 0; i < ADMS_ADAM_ANC; ++i) {
+        int l = 6 + i;
+        if (l < t.levels) anc[i] = t.grad[t.off[l] + ((by << 5) >> l) * max(t.w0 >> l, 1) + ((bx << 5) >> l)];
     }
-    {
-        int k = threadIdx.x;
-        if (k >= 6 && k < t.levels)
-            anc[k] = t.grad[t.off[k] + ((by << 5) >> k) * max(t.w0 >> k, 1) + ((bx << 5) >> k)];
+}
+
+__global__ void __launch_bounds__(ADMS_ADAM_THREADS, 1)
+    k_adam_tex_stream(const __grid_constant__ TexAdamBatch P, int total) {
+    extern __shared__ __align__(128) unsigned char adam_raw[];
+    AdamSmem& S = *reinterpret_cast<AdamSmem*>(adam_raw);
+    int tid = threadIdx.x, lane = tid & 31;
+    if (smem_u32(adam_raw) & 127u) {  // the TMA boxes need 128-byte-aligned stages
+        if (tid == 0) atomicExch(&const_cast<JobState*>(P.a[0].js)->status_next, (int)ADMS_ERR_STATE);
+        return;
+    }
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (tid == 0) {
+        for (int q = 0; q < ADMS_ADAM_STAGES; ++q) mbar_init(&S.bar[q], 1);
+        fence_barrier_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int k = 6; k < t.levels; ++k) c = f4madd(c, level_weight(t, k), anc[k]);
-        push[poff[5]] = f4madd(c, level_weight(t, 5), push[poff[5]]);
-    }
-    for (int k = 4; k >= 1; --k) {
-        __syncthreads();
-        int n = 32 >> k;
-        float wl = level_weight(t, k);
-        for (int idx = threadIdx.x; idx < n * n; idx += 256) {
-            int cx = idx % n, cy = idx / n;
-            push[poff[k] + idx] = f4madd(push[poff[k + 1] + (cy >> 1) * (n >> 1) + (cx >> 1)], wl, push[poff[k] + idx]);
+    // tile j of this block (tile blockIdx.x + j gridDim.x) goes through stage j % 3, whose
+    // (j / 3)-th phase its copies complete; tiles 0 and 1 are fetched here, tile j + 2
+    // during tile j, once tile j - 1's stores (same stage) have read it
+    int tile = blockIdx.x;
+    if (tid == 0)
+        for (int j = 0; j < 2; ++j)
+            if (tile + j * (int)gridDim.x < total) adam_fetch(P, tile + j * gridDim.x, S.st[j], &S.bar[j]);
+    // the thread's quad: level-0 texels (x, y) .. (x + 1, y + 1) of the tile
+    int cx = even_bits(tid), cy = even_bits(tid >> 1);  // its level-1 texel
+    int x = 2 * cx, y = 2 * cy;
+    float4 gk[6], anc[ADMS_ADAM_ANC];
+    if (tile < total) adam_pyramid(P, tile, x, y, gk, anc);
+    int k = 0;
+    for (; tile < total; tile += gridDim.x, ++k) {
+        int s = k % ADMS_ADAM_STAGES;
+        int ent = adam_entry(P, tile);
+        const TexAdam& A = P.a[ent];
+        const TexDev& t = A.t;
+        int bx, by;
+        adam_tile_xy(A, tile, bx, by);
+        bool live = A.js->status == 0;  // a latched job's tiles change nothing
+        float4* grad = t.grad;
+        float4* tex = const_cast<float4*>(t.tex);
+        // one block barrier per tile: each thread waits for the stage itself; the
+        // barrier after the arithmetic orders its shared-memory writes before the
+        // stores, and the shared array a tile writes alternates with the tile's parity
+        // (agreed per warp: the shuffles below need every lane)
+        bool ok = __all_sync(0xffffffffu, mbar_wait(&S.bar[s], (uint32_t)(k / ADMS_ADAM_STAGES) & 1u, ADMS_ADAM_WAIT_NS));
+        AdamStage& T = S.st[s];
+        if (live && ok) {
+            float4 c = zero;
+            float w = 1.f / 1024.f;  // 1/4^5
+#pragma unroll
+            for (int i = 0; i < ADMS_ADAM_ANC; ++i) {
+                int l = 6 + i;
+                if (l < t.levels) {
+                    int wp = max(t.w0 >> (l - 1), 1), hp = max(t.h0 >> (l - 1), 1);
+                    w *= 1.f / (float)((wp > 1 ? 2 : 1) * (hp > 1 ? 2 : 1));
+                    c = f4madd(c, w, anc[i]);
+                }
+            }
+            float4 push = f4madd(c, 1.f / 1024.f, gk[5]);
+            push = f4madd(push, 1.f / 256.f, gk[4]);
+            push = f4madd(push, 1.f / 64.f, gk[3]);
+            push = f4madd(push, 1.f / 16.f, gk[2]);
+            push = f4madd(push, 0.25f, gk[1]);
+            float lr = A.js->lr, ibc1 = 1.f / A.js->bc1, ibc2 = 1.f / A.js->bc2;
+            float4 pq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int qx = x + (q & 1), qy = y + (q >> 1);
+                float4 g = f4madd(T.g[qy][qx], 1.f, push);
+                latch_nonfinite(A.js, g.x, g.y, g.z, g.w);
+                float4 mm = T.m[qy][qx], vv = T.v[qy][qx];
+                pq[q] = clamp_texel(adam4(T.p[qy][qx], g, mm, vv, lr, ibc1, ibc2), A.clamp_kind);
+                T.p[qy][qx] = pq[q];
+                T.m[qy][qx] = mm;
+                T.v[qy][qx] = vv;
+                T.g[qy][qx] = zero;  // stored back: the cleared gradient
+            }
+            // level 1: the thread's own quad; levels 2 and 3: lanes 4j and 16j gather by shuffles
+            float4 l = quad_mean(pq[0], pq[1], pq[2], pq[3]);
+            {
+                int o = t.off[1] + ((by << 4) + cy) * (t.w0 >> 1) + (bx << 4) + cx;
+                tex[o] = l;
+                grad[o] = zero;
+            }
+#pragma unroll
+            for (int lv = 2; lv <= 3; ++lv) {
+                int d = lv == 2 ? 1 : 4;  // lane distance of the x neighbour
+                float4 a1 = shfl_down4(l, d), a2 = shfl_down4(l, 2 * d), a3 = shfl_down4(l, 3 * d);
+                l = quad_mean(l, a1, a2, a3);
+                if ((lane & (4 * d - 1)) == 0) {
+                    int n = 32 >> lv;
+                    int o = t.off[lv] + (by * n + (y >> lv)) * (t.w0 >> lv) + bx * n + (x >> lv);
+                    tex[o] = l;
+                    grad[o] = zero;
+                }
+            }
+            if ((lane & 15) == 0) S.s3[k & 1][tid >> 4] = l;
+        }
+        if (tile + (int)gridDim.x < total) adam_pyramid(P, tile + gridDim.x, x, y, gk, anc);
+        fence_proxy_async();  // the stage's updated rows, before the stores read them
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(&const_cast<JobState*>(A.js)->status_next, (int)ADMS_ERR_TIMEOUT);
+            break;
+        }
+        if (tid == 0) {
+            int ahead = tile + 2 * (int)gridDim.x;
+            if (ahead < total) {
+                int sa = (k + 2) % ADMS_ADAM_STAGES;
+                bulk_wait_read0();  // tile k - 1's stores (stage sa) have read their rows
+                adam_fetch(P, ahead, S.st[sa], &S.bar[sa]);
+            }
+        }
+        if (live) {
+            if (tid == 0) {
+                const CUtensorMap* tm = P.maps[ent];
+                tile2d_s2g(&tm[0], bx * 128, by * 32, &T.g[0][0]);
+                tile2d_s2g(&tm[1], bx * 128, by * 32, &T.p[0][0]);
+                tile2d_s2g(&tm[2], bx * 128, by * 32, &T.m[0][0]);
+                tile2d_s2g(&tm[3], bx * 128, by * 32, &T.v[0][0]);
+                bulk_commit();
+            }
+            // level 4 in threads 0..3 (texel (q & 1, q >> 1)), level 5 in thread 0
+            if (tid < 4) {
+                const float4* s3 = S.s3[k & 1];
+                float4 l4 = quad_mean(s3[4 * tid], s3[4 * tid + 1], s3[4 * tid + 2], s3[4 * tid + 3]);
+                int o = t.off[4] + (by * 2 + (tid >> 1)) * (t.w0 >> 4) + bx * 2 + (tid & 1);
+                tex[o] = l4;
+                grad[o] = zero;
+                float4 a1 = shfl_down4(l4, 1, 0xfu), a2 = shfl_down4(l4, 2, 0xfu), a3 = shfl_down4(l4, 3, 0xfu);
+                if (tid == 0) {
+                    int o5 = t.off[5] + by * (t.w0 >> 5) + bx;
+                    tex[o5] = quad_mean(l4, a1, a2, a3);
+                    grad[o5] = zero;
+                }
+            }
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        int lx = tx, ly = ty + 8 * r;
-        int i = ((by << 5) + ly) * t.w0 + (bx << 5) + lx;
-        float4 g = f4madd(g0[r], 1.f, push[(ly >> 1) * 16 + (lx >> 1)]);
-        latch_nonfinite(A.js, g.x, g.y, g.z, g.w);
-        tile[ly][lx] = adam_texel_v(t, A.m, A.v, i, g, p0[r], m0[r], v0[r], A.clamp_kind, lr, bc1, bc2);
+    if (tile < total && tile + (int)gridDim.x < total) {
+        // gave up on tile k's wait: let tile k + 1's copies (issued a tile earlier) land
+        // before the block's memory is released
+        mbar_wait(&S.bar[(k + 1) % ADMS_ADAM_STAGES], (uint32_t)((k + 1) / ADMS_ADAM_STAGES) & 1u, ADMS_ADAM_WAIT_NS);
     }
-    int top = min(5, t.levels - 1);
+    if (tid == 0) bulk_wait0();
+}
+
+// Levels 6.. of every texture of a streamed-Adam launch, one block per texture,
+// from the level 5 that the tiles wrote (2x2 box average, same order as
+// k_mip_level); their gradients, read by every tile above, are cleared here.
+__global__ void k_adam_mip_top(const __grid_constant__ TexAdamBatch P) {
+    const TexAdam& A = P.a[blockIdx.x];
+    if (A.js->status) return;
+    const TexDev& t = A.t;
     float4* tex = const_cast<float4*>(t.tex);
-    for (int k = 1; k <= top; ++k) {
-        int n = 32 >> k;
-        __syncthreads();
-        float4 acc;
-        int cx = 0, cy = 0;
-        bool act = (int)threadIdx.x < n * n;
-        if (act) {
-            cx = threadIdx.x % n;
-            cy = threadIdx.x / n;
-            acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) acc = f4madd(acc, 1.f, tile[2 * cy + dy][2 * cx + dx]);
-            acc = f4scale(acc, 0.25f);
-        }
-        __syncthreads();
-        if (act) {
-            tile[cy][cx] = acc;
-            int o = t.off[k] + (by * n + cy) * (t.w0 >> k) + bx * n + cx;
-            tex[o] = acc;
-            t.grad[o] = make_float4(0.f, 0.f, 0.f, 0.f);  // read in the push-down above
-        }
-    }
-    if (t.levels <= 6) return;
-    // the last tile of this texture builds levels 6..
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(A.done, 1) == n_tiles - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    for (int k = 6; k < t.levels; ++k) {
-        int ws = max(t.w0 >> (k - 1), 1), hs = max(t.h0 >> (k - 1), 1);
-        int wd = max(t.w0 >> k, 1), hd = max(t.h0 >> k, 1);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int lv = 6; lv < t.levels; ++lv) {
+        int ws = max(t.w0 >> (lv - 1), 1), hs = max(t.h0 >> (lv - 1), 1);
+        int wd = max(t.w0 >> lv, 1), hd = max(t.h0 >> lv, 1);
         int sx = ws > 1 ? 2 : 1, sy = hs > 1 ? 2 : 1;
         for (int i = threadIdx.x; i < wd * hd; i += blockDim.x) {
             int x = i % wd, y = i / wd;
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 acc = zero;
             for (int dy = 0; dy < sy; ++dy)
-                for (int dx = 0; dx < sx; ++dx)
-                    acc = f4madd(acc, 1.f, __ldcg(tex + t.off[k - 1] + (y * sy + dy) * ws + (x * sx + dx)));
-            tex[t.off[k] + i] = f4scale(acc, 1.f / (float)(sx * sy));
-            t.grad[t.off[k] + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int dx = 0; dx < sx; ++dx) acc = f4madd(acc, 1.f, tex[t.off[lv - 1] + (y * sy + dy) * ws + (x * sx + dx)]);
+            tex[t.off[lv] + i] = f4scale(acc, 1.f / (float)(sx * sy));
+            t.grad[t.off[lv] + i] = zero;
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *A.done = 0;
 }
 
 bool adam_tiled(const TexDev& t) { return t.levels > 5 && (t.w0 % 32) == 0 && (t.h0 % 32) == 0; }
 
+cudaError_t adam_prepare() {
+    return cudaFuncSetAttribute(k_adam_tex_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(AdamSmem));
+}
+
+cudaError_t adam_encode_maps(const TexDev& t, const float4* m, const float4* v, CUtensorMap out[4]) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const void* base[4] = {t.grad, t.tex, m, v};
+    cuuint64_t dim[2] = {(cuuint64_t)4 * t.w0, (cuuint64_t)t.h0};
+    cuuint64_t stride[1] = {(cuuint64_t)t.w0 * sizeof(float4)};
+    cuuint32_t box[2] = {128, 32}, estride[2] = {1, 1};
+    for (int k = 0; k < 4; ++k) {
+        CUresult r = encode(&out[k],
+                            CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base[k]), dim, stride, box, estride,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st) {
-    TexAdamBatch P;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (!e) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (!e) e = adam_prepare();
+        if (e) {
+            sms = 0;
+            return e;
+        }
+    }
+    thread_local TexAdamBatch P;  // 26 KB of kernel parameters: not on the host stack
     for (size_t e0 = 0; e0 < list.size(); e0 += ADMS_ADAM_TEX) {
         size_t e1 = std::min(list.size(), e0 + ADMS_ADAM_TEX);
-        int blocks = 0;
+        int tiles = 0;
         for (size_t e = e0; e < e1; ++e) {
             P.a[e - e0] = list[e];
-            P.a[e - e0].tile0 = blocks;
-            blocks += (list[e].t.w0 >> 5) * (list[e].t.h0 >> 5);
+            P.a[e - e0].tile0 = tiles;
+            for (int k = 0; k < 4; ++k) P.maps[e - e0][k] = list[e].tmaps[k];
+            tiles += (list[e].t.w0 >> 5) * (list[e].t.h0 >> 5);
         }
         P.n = (int)(e1 - e0);
-        k_adam_tex_batch<<<blocks, 256, 0, st>>>(P);
-        count_launches(1);
+        k_adam_tex_stream<<<std::min(tiles, sms), ADMS_ADAM_THREADS, sizeof(AdamSmem), st>>>(P, tiles);
+        k_adam_mip_top<<<P.n, 256, 0, st>>>(P);
+        count_launches(2);
         cudaError_t e = cudaGetLastError();
         if (e) return e;
     }
