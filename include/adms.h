@@ -613,6 +613,17 @@ const char* adms_stage_name(int32_t i);
 /* Kernels this library has launched in this process (host-side count). */
 int64_t adms_launch_count(void);
 
+/* ---- failure-detection test hook ----------------------------------------- */
+
+/* The one wait on the device, the texture Adam's wait for each tile's TMA copies
+ * (adms_optimizer_step), gives up after 2 s of the GPU's global timer, latches
+ * ADMS_ERR_TIMEOUT in the job's status (read by adms_jobs_status / adms_job_stats
+ * after the step) and leaves that texture's latents unchanged. With enable = 1
+ * every such wait of this context's later optimizer steps expects 16 bytes more
+ * than its copies deliver, so that it runs out (each launch then takes about
+ * 4 s); 0 restores normal steps. For tests only; no paper counterpart. */
+adms_status adms_ctx_test_wait_timeout(adms_ctx* ctx, int32_t enable);
+
 #ifdef __cplusplus
 }
 #endif

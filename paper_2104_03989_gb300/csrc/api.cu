@@ -171,6 +171,9 @@ struct adms_ctx {
     // captured on `stream` holds both
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // failure-detection test hook: bytes added to each Adam tile's expected copy
+    // count, so that its bounded waits run out (adms_ctx_test_wait_timeout)
+    uint32_t adam_extra_tx = 0;
     // the reference images of forward_loss calls are complete once this event has
     // completed (recorded on another stream that renders them), or null
     cudaEvent_t ref_event = nullptr;
@@ -1707,7 +1710,7 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
             else CK(TIMED(ST_ADAM, adam_texture_and_mips(td, maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
         }
     }
-    if (!tiled.empty()) CK(TIMED(ST_ADAM, adam_textures_tiled(tiled, ctx->stream)));
+    if (!tiled.empty()) CK(TIMED(ST_ADAM, adam_textures_tiled(tiled, ctx->stream, ctx->adam_extra_tx)));
     CK(join_branch(ctx));
     for (Job* jp : js) {
         CK(TIMED(ST_SMALL, advance_step(jp->st, ctx->stream)));
@@ -1890,6 +1893,12 @@ adms_status adms_graph_destroy(adms_graph* g) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     delete g;
+    return ADMS_OK;
+}
+
+adms_status adms_ctx_test_wait_timeout(adms_ctx* ctx, int32_t enable) {
+    if (!ctx) return ADMS_ERR_ARG;
+    ctx->adam_extra_tx = enable ? 16u : 0u;
     return ADMS_OK;
 }
 

@@ -321,6 +321,7 @@ struct TexAdamBatch {
     CUtensorMap maps[ADMS_ADAM_TEX][4];  // grad, tex, m, v of texture k
     TexAdam a[ADMS_ADAM_TEX];
     int n;
+    uint32_t extra_tx;  // test hook: bytes each tile's wait expects beyond its copies (0)
 };
 // whether a texture takes the tiled path (both sides multiples of 32, at least 6 levels)
 bool adam_tiled(const TexDev& t);
@@ -331,7 +332,7 @@ cudaError_t adam_prepare();
 cudaError_t adam_encode_maps(const TexDev& t, const float4* m, const float4* v, CUtensorMap out[4]);
 // Adam + mip rebuild of every listed texture (all adam_tiled, any jobs), one 32x32-texel
 // tile per block, one launch per ADMS_ADAM_TEX textures
-cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st);
+cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st, uint32_t extra_tx = 0);
 cudaError_t advance_step(JobState* js, cudaStream_t st);
 // out[k] = the latched status of job k (stream-ordered; out: device [n])
 #define ADMS_STATUS_MAX 512

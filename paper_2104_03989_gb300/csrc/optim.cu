@@ -320,7 +320,7 @@ __device__ __forceinline__ void adam_fetch(const TexAdamBatch& P, int tile, Adam
         mbar_arrive_expect_tx(bar, 0);
         return;
     }
-    mbar_arrive_expect_tx(bar, (uint32_t)sizeof(AdamStage));
+    mbar_arrive_expect_tx(bar, (uint32_t)sizeof(AdamStage) + P.extra_tx);
     tile2d_g2s(&S.g[0][0], &tm[0], bx * 128, by * 32, bar);
     tile2d_g2s(&S.p[0][0], &tm[1], bx * 128, by * 32, bar);
     tile2d_g2s(&S.m[0][0], &tm[2], bx * 128, by * 32, bar);
@@ -548,7 +548,7 @@ cudaError_t adam_encode_maps(const TexDev& t, const float4* m, const float4* v, 
     return cudaSuccess;
 }
 
-cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st) {
+cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st, uint32_t extra_tx) {
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -571,6 +571,7 @@ cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st) {
             tiles += (list[e].t.w0 >> 5) * (list[e].t.h0 >> 5);
         }
         P.n = (int)(e1 - e0);
+        P.extra_tx = extra_tx;
         k_adam_tex_stream<<<std::min(tiles, sms), ADMS_ADAM_THREADS, sizeof(AdamSmem), st>>>(P, tiles);
         k_adam_mip_top<<<P.n, 256, 0, st>>>(P);
         count_launches(2);

@@ -100,3 +100,45 @@ def test_single_job_with_a_nan_texture_is_latched_and_not_updated(gpu_lib):
     after = _latents(ctx, job)
     assert bool((after["pos"] == before["pos"]).all()) and bool(torch.isfinite(after["pos"]).all())
     ctx.close()
+
+
+def test_adam_wait_that_runs_out_latches_a_timeout_and_the_context_stays_usable(gpu_lib):
+    """The streamed texture Adam waits on the device for each tile's TMA copies,
+    bounded by 2 s of the GPU's global timer. The test hook makes every such wait
+    expect 16 bytes more than its copies deliver (a phase that never completes):
+    the waits run out, the job latches ADMS_ERR_TIMEOUT and its textures are not
+    updated; with the hook off, the same context steps another job normally.
+    Nothing faults: every copy lands, only the barrier's byte count stays short."""
+    from paper_2104_03989_gb300 import binding as B
+    from paper_2104_03989_gb300.engine import Context
+
+    TIMEOUT = -4
+    c, views = _scene()
+    ctx = Context()
+    ref_job = ctx.create_job(c["ref"], frozen=True)
+    ref = ctx.render_reference(ref_job, views, H, W)
+    job = ctx.create_job(c["cand"], loss="l1")
+    before = _latents(ctx, job)
+    ctx.forward_loss([job], [views], [ref])
+    ctx.backward([job])
+    B.adms_ctx_test_wait_timeout(ctx.ctx, True)
+    ctx.step([job])
+    B.adms_ctx_test_wait_timeout(ctx.ctx, False)
+    torch.cuda.synchronize()
+    assert int(ctx.jobs_status([job]).cpu()[0]) == TIMEOUT
+    assert ctx.stats(job)["status"] == TIMEOUT
+    now = _latents(ctx, job)
+    for n in ("kd", "nrm"):
+        assert torch.equal(now[n], before[n]), n
+    # the context still runs a normal step
+    other = ctx.create_job(c["cand"], loss="l1")
+    start = _latents(ctx, other)
+    ctx.forward_loss([other], [views], [ref])
+    ctx.backward([other])
+    ctx.step([other])
+    torch.cuda.synchronize()
+    assert int(ctx.jobs_status([other]).cpu()[0]) == 0
+    moved = _latents(ctx, other)
+    assert not torch.equal(moved["kd"], start["kd"])
+    assert bool(torch.isfinite(moved["kd"]).all())
+    ctx.close()
