@@ -317,12 +317,14 @@ def run_native(args):
     MS = max(int(args.msaa), 1)
     # under MSAA the references are supersampled renders (every sample shaded)
     # the foliage reference is a dense cloud of small leaf triangles: rasterize those
-    # of up to 256 samples directly instead of binning them
+    # of up to 256 samples directly instead of binning them, reading each sample's key
+    # before its test (~160 fragments per sample)
     ref_job = ctx.create_job(cfg["ref"], frozen=True, samples=MS, shade_samples=True,
-                             raster_direct_px=256 if agg else 0)
+                             raster_direct_px=256 if agg else 0, raster_depth_filter=agg)
     pl = bool(args.per_level_textures)
     # the tessellated candidate's ~17-pixel triangles rasterize faster directly than
-    # binned (the keys do not depend on the threshold): 256 measured best of 16..256
+    # binned (the keys do not depend on the threshold): 256 measured best of 16..256,
+    # with plain atomicMin (about two fragments per sample: the key read costs more)
     cdirect = 256 if wk == "tess" else 0
     cand = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, per_level_textures=pl, samples=MS, layers=LY,
                           raster_direct_px=cdirect)

@@ -137,6 +137,12 @@ typedef struct {
                                 Dense clouds of small triangles (e.g. a 1.2M-triangle foliage
                                 reference) run faster with a few hundred. Ignored with layers > 0
                                 (every triangle is binned). In [0, 4096] */
+    int32_t raster_depth_filter; /* raster tuning with raster_direct_px > 16 (results do not depend on
+                                it): 1 = the direct raster reads each sample's stored key first and
+                                skips the coverage test when the triangle's depth floor cannot beat
+                                it (pays where many fragments land on each sample, e.g. foliage);
+                                0 = every covered sample goes straight to atomicMin (closed
+                                surfaces, about two fragments per sample). 0 or 1 */
 } adms_opt_params;
 
 /* Device pointers into a job's resident state (owned by the library, valid

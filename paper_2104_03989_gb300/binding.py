@@ -52,7 +52,7 @@ class adms_opt_params(C.Structure):
                 ("tess_levels", C.c_int32), ("batch_views", C.c_int32), ("relative_laplacian", C.c_int32),
                 ("aa", C.c_int32), ("lr0", C.c_float), ("lambda0", C.c_float), ("per_level_textures", C.c_int32),
                 ("samples", C.c_int32), ("shade_samples", C.c_int32), ("layers", C.c_int32),
-                ("raster_direct_px", C.c_int32)]
+                ("raster_direct_px", C.c_int32), ("raster_depth_filter", C.c_int32)]
 
 
 class adms_param_view(C.Structure):
@@ -246,12 +246,12 @@ def material_desc(kd, orm, nrm, disp=None, mips=True):
 
 def opt_params(optimize=None, loss="logl1", tess_levels=0, batch_views=0, relative_laplacian=False, aa=True,
                lr0=0.01, lambda0=0.0, per_level_textures=False, samples=1, shade_samples=False, layers=0,
-               raster_direct_px=0):
+               raster_direct_px=0, raster_depth_filter=False):
     o = optimize or {}
     return adms_opt_params(int(o.get("pos", 0)), int(o.get("kd", 0)), int(o.get("orm", 0)), int(o.get("nrm", 0)),
                            int(o.get("disp", 0)), LOSS[loss], tess_levels, batch_views, int(relative_laplacian),
                            int(aa), lr0, lambda0, int(per_level_textures), int(samples), int(shade_samples),
-                           int(layers), int(raster_direct_px))
+                           int(layers), int(raster_direct_px), int(raster_depth_filter))
 
 
 def adms_job_create(ctx, mesh, mat, opt=None, seed=0):

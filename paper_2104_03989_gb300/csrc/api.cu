@@ -584,6 +584,7 @@ adms_status render_core(adms_ctx* ctx, Job& j) {
         return ADMS_OK;
     }
     in.small_px = j.opt.raster_direct_px > 0 ? j.opt.raster_direct_px : ADMS_SMALL_PX;
+    in.zfilter = j.opt.raster_depth_filter;
     CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
     CK(TIMED(ST_RASTER, raster_tiles(in, j.rs, ctx->stream)));
     if (forked) CK(join_branch(ctx));
@@ -796,6 +797,8 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
     if (j.opt.layers < 0 || j.opt.layers > 16) return fail(ctx, ADMS_ERR_ARG, "layers must be in [0, 16]");
     if (j.opt.raster_direct_px < 0 || j.opt.raster_direct_px > 4096)
         return fail(ctx, ADMS_ERR_ARG, "raster_direct_px must be in [0, 4096]");
+    if (j.opt.raster_depth_filter != 0 && j.opt.raster_depth_filter != 1)
+        return fail(ctx, ADMS_ERR_ARG, "raster_depth_filter must be 0 or 1");
     if (j.opt.layers > 0 && (j.opt.samples > 1 || j.opt.tess_levels > 0))
         return fail(ctx, ADMS_ERR_ARG, "depth peeling runs on plain meshes at one sample per pixel");
     j.L = j.opt.layers;
@@ -936,6 +939,7 @@ adms_status frame_and_prepare(adms_ctx* ctx, Job& j, bool* forked) {
     in.H = j.H;
     in.keys = j.keys;
     in.small_px = j.opt.raster_direct_px > 0 ? j.opt.raster_direct_px : ADMS_SMALL_PX;
+    in.zfilter = j.opt.raster_depth_filter;
     CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
     return ADMS_OK;
 }

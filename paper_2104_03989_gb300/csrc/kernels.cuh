@@ -52,6 +52,7 @@ struct RasterIn {
     unsigned long long* keys;  // [B][H][W]
     int small_px = ADMS_SMALL_PX;  // triangles with at most this many samples in their bbox are
                                    // rasterized directly (atomicMin), the rest binned into tiles
+    int zfilter = 0;  // small_px > ADMS_SMALL_PX: read each sample's stored key before its test
 };
 
 // scratch of the raster (global memory beyond inputs and outputs)

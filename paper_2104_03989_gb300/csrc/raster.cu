@@ -193,8 +193,15 @@ __device__ __forceinline__ void test_tri_kbuf(const TriRec& r, int Sx, int Sy, u
 // the key goes in only if it is below the stored one. The stored key only ever
 // decreases, so a read that lags behind other threads' updates is never below the
 // current minimum and can only let an unneeded test or atomicMin through.
+// Without the filter (zfilter = 0: closed surfaces, about two fragments per sample)
+// the read would only add a dependent round trip: the key goes straight to atomicMin.
 __device__ __forceinline__ void zmin_test(unsigned long long* a, const TriRec& r, int Sx, int Sy,
-                                          unsigned long long zlo) {
+                                          unsigned long long zlo, int zfilter) {
+    if (!zfilter) {
+        unsigned long long key = tri_key(r, Sx, Sy);
+        if (key != ADMS_EMPTY_KEY) atomicMin(a, key);
+        return;
+    }
     unsigned long long cur = __ldcg(a);
     if (zlo > cur) return;
     unsigned long long key = tri_key(r, Sx, Sy);
@@ -255,7 +262,7 @@ template <bool COOP>
 __global__ void __launch_bounds__(256, COOP ? 3 : 1) k_setup(const int* __restrict__ tri, int F, const VtxS* __restrict__ vs, int V, int B, int W, int H,
                         int tiles_x, int tiles_y, TriRec* __restrict__ rec, TriBin* __restrict__ bin,
                         int8_t* __restrict__ asign, int* __restrict__ tile_count, unsigned long long* __restrict__ keys,
-                        int small_px) {
+                        int small_px, int zfilter) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool coop = false;  // this lane's triangle goes to the warp-wide direct raster
     TriRec r;
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 1) k_setup(const int* __restri
                         for (int y = (int)jlo; y <= (int)jhi; ++y)
                             for (int x = (int)ilo; x <= (int)ihi; ++x) {
                                 if (COOP) {
-                                    zmin_test(kb + (size_t)y * W + x, r, 256 * x + 128, 256 * y + 128, zlo);
+                                    zmin_test(kb + (size_t)y * W + x, r, 256 * x + 128, 256 * y + 128, zlo, zfilter);
                                 } else {
                                     unsigned long long key = tri_key(r, 256 * x + 128, 256 * y + 128);
                                     if (key != ADMS_EMPTY_KEY) atomicMin(kb + (size_t)y * W + x, key);
@@ -356,7 +363,7 @@ __global__ void __launch_bounds__(256, COOP ? 3 : 1) k_setup(const int* __restri
         unsigned long long* kb = keys + (size_t)tb_ * H * W;
         for (int q = lane; q < n; q += 32) {
             int y = t.by0 + q / bw, x = t.bx0 + q - (q / bw) * bw;
-            zmin_test(kb + (size_t)y * W + x, t, 256 * x + 128, 256 * y + 128, tlo);
+            zmin_test(kb + (size_t)y * W + x, t, 256 * x + 128, 256 * y + 128, tlo, zfilter);
         }
     }
 }
@@ -589,10 +596,10 @@ cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st
     k_transform<<<(B * V + bs - 1) / bs, bs, 0, st>>>(in.pos, V, in.views, B, W, H, s.clip, s.vs, s.scr);
     if (in.small_px > ADMS_SMALL_PX)
         k_setup<true><<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec,
-                                                          s.bin, s.asign, s.tile_count, in.keys, in.small_px);
+                                                          s.bin, s.asign, s.tile_count, in.keys, in.small_px, in.zfilter);
     else
         k_setup<false><<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec,
-                                                           s.bin, s.asign, s.tile_count, in.keys, in.small_px);
+                                                           s.bin, s.asign, s.tile_count, in.keys, in.small_px, 0);
     k_scan<<<1, 1024, 0, st>>>(s.tile_count, ntiles, s.tile_off, s.total_pairs);
     k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.bin, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
                                                    s.list, s.list_capacity, in.adj, s.asign, s.silmask);

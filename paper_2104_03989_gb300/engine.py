@@ -54,15 +54,16 @@ class Context:
     # ------------------------------------------------------------------ jobs
     def create_job(self, scene, optimize=None, loss="logl1", lr0=0.01, lambda0=0.0, batch_views=0, aa=True,
                    relative_laplacian=False, frozen=False, seed=0, per_level_textures=False, samples=1,
-                   shade_samples=False, layers=0, raster_direct_px=0):
+                   shade_samples=False, layers=0, raster_direct_px=0, raster_depth_filter=False):
         """scene: object with .mesh (pos, uv, tri_pos, tri_uv), .kd, .orm, .nrm, .mips (numpy).
         per_level_textures: every mip level of each optimized texture is its own latent.
         samples: s x s samples per pixel (MSAA; shade_samples=True: supersampling).
         layers: depth-peeling passes of a transparent render (0: opaque).
-        raster_direct_px: raster tuning, bbox samples up to which a triangle skips binning (0: 16)."""
+        raster_direct_px: raster tuning, bbox samples up to which a triangle skips binning (0: 16).
+        raster_depth_filter: raster tuning for dense clouds of small triangles (read before atomicMin)."""
         mesh, mat, opt, keep = self._descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian,
                                            frozen, per_level_textures, samples, shade_samples, layers,
-                                           raster_direct_px)
+                                           raster_direct_px, raster_depth_filter)
         return B.adms_job_create(self.ctx, mesh, mat, opt, seed)
 
     def export_job(self, job):
@@ -71,17 +72,17 @@ class Context:
 
     def import_job(self, blob, scene, optimize=None, loss="logl1", lr0=0.01, lambda0=0.0, batch_views=0, aa=True,
                    relative_laplacian=False, frozen=False, per_level_textures=False, samples=1, shade_samples=False,
-                   layers=0, raster_direct_px=0):
+                   layers=0, raster_direct_px=0, raster_depth_filter=False):
         """A new job resumed from export_job's output; scene and options as given
         when the exported job was created."""
         mesh, mat, opt, keep = self._descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian,
                                            frozen, per_level_textures, samples, shade_samples, layers,
-                                           raster_direct_px)
+                                           raster_direct_px, raster_depth_filter)
         return B.adms_job_import(self.ctx, mesh, mat, opt, np.ascontiguousarray(blob, dtype=np.uint8))
 
     @staticmethod
     def _descs(scene, optimize, loss, lr0, lambda0, batch_views, aa, relative_laplacian, frozen, per_level_textures,
-               samples=1, shade_samples=False, layers=0, raster_direct_px=0):
+               samples=1, shade_samples=False, layers=0, raster_direct_px=0, raster_depth_filter=False):
         m = scene.mesh
         arrays = dict(pos=_c32(m.pos, np.float32), uv=_c32(m.uv, np.float32), tri=_c32(m.tri_pos, np.int32),
                       tri_uv=_c32(m.tri_uv, np.int32), kd=_c32(scene.kd, np.float32),
@@ -92,12 +93,12 @@ class Context:
         mesh = B.mesh_desc(arrays["pos"], arrays["uv"], arrays["tri"], arrays["tri_uv"])
         mat = B.material_desc(arrays["kd"], arrays["orm"], arrays["nrm"], arrays["disp"], getattr(scene, "mips", True))
         opt = None
-        if not frozen or levels or samples > 1 or layers or raster_direct_px:
+        if not frozen or levels or samples > 1 or layers or raster_direct_px or raster_depth_filter:
             opt = B.opt_params(optimize if optimize is not None else getattr(scene, "optimize", {}), loss=loss,
                                tess_levels=levels, batch_views=batch_views, relative_laplacian=relative_laplacian,
                                aa=aa, lr0=lr0, lambda0=lambda0, per_level_textures=per_level_textures,
                                samples=samples, shade_samples=shade_samples, layers=layers,
-                               raster_direct_px=raster_direct_px)
+                               raster_direct_px=raster_direct_px, raster_depth_filter=raster_depth_filter)
             if frozen:
                 for k in ("optimize_pos", "optimize_kd", "optimize_orm", "optimize_nrm", "optimize_disp"):
                     setattr(opt, k, 0)

@@ -107,3 +107,25 @@ def test_coplanar_tie_lower_id_wins_on_the_gpu(gpu_lib):
         # the overlap shows id 0: the depth halves of the keys are equal there, the id decides
         depth = (got >> np.uint64(32))
         assert len(np.unique(depth[both])) >= 1
+
+
+@pytest.mark.parametrize("direct,zfilter", [(64, False), (256, False), (256, True)])
+def test_direct_raster_thresholds_and_depth_filter_keep_the_oracle_keys(gpu_lib, direct, zfilter):
+    """Raster tuning does not change visibility: the batched-view workload's
+    candidate and reference shrunk to 128^2 views (triangles of a few to a few
+    dozen samples on both faces of closed surfaces) rasterized with larger direct
+    thresholds, through the warp-wide direct raster, with the key-read filter on
+    or off, give the oracle's keys bit for bit."""
+    from cases import plain_case
+    from paper_2104_03989_gb300.engine import Context
+
+    c, views, h, w = plain_case()
+    ctx = Context()
+    for scene in (c["cand"], c["ref"]):
+        want, _ = OV.raster_views(views, scene.mesh.pos, scene.mesh.tri_pos, w, h)
+        job = ctx.create_job(scene, frozen=True, raster_direct_px=direct, raster_depth_filter=zfilter)
+        ctx.render_reference(job, views, h, w)
+        got = ctx.keys(job, (len(views), h, w)).cpu().numpy().view(np.uint64)
+        np.testing.assert_array_equal(got, want)
+        ctx.destroy_job(job)
+    ctx.close()

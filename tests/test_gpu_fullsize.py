@@ -157,7 +157,7 @@ def agg_full(gpu_lib):
     c = synth.config_aggregate()
     views = synth.sample_views(9, 0, 8, 512, 512)
     ctx = Context()
-    ref = ctx.create_job(c["ref"], frozen=True, raster_direct_px=256)
+    ref = ctx.create_job(c["ref"], frozen=True, raster_direct_px=256, raster_depth_filter=True)
     cand = ctx.create_job(c["cand"], loss="l2", layers=8)
     yield c, views, ctx, ref, cand
     ctx.close()
