@@ -153,34 +153,40 @@ __global__ void k_frame_bwd2(FrameArgs a) {
 }
 
 // k_frame_bwd1 and k_frame_bwd2 in one launch, after a frame_forward that kept the
-// normalisations (a.inv): each vertex forms the normalisation adjoints of its
-// faces' corners itself (the same values, summed in the same order)
+// normalisations (a.inv): eight threads per vertex, slot s taking the vertex's
+// incident faces s, s + 8, ... and forming their corners' normalisation adjoints
+// itself; the slots' sums are combined by shuffles in a fixed order
+#define ADMS_FRAME_SLOTS 8
 __global__ void k_frame_bwd_fused(FrameArgs a) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= a.V) return;
+    int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    int v = gid / ADMS_FRAME_SLOTS, slot = gid % ADMS_FRAME_SLOTS;
+    bool valid = v < a.V;
     float3 g = zero3();
-    int lo = a.vf_off[v], hi = a.vf_off[v + 1];
-    for (int j0 = lo; j0 < hi; j0 += ADMS_GATHER) {
-        FaceFrame ff[ADMS_GATHER];
-#pragma unroll
-        for (int q = 0; q < ADMS_GATHER; ++q) ff[q] = face_frame(a, a.vf_face[min(j0 + q, hi - 1)]);
-#pragma unroll
-        for (int q = 0; q < ADMS_GATHER; ++q) {
-            if (j0 + q >= hi) continue;
-            float3 Gfn = sum_grad(a, ff[q].idx[0], 0) + sum_grad(a, ff[q].idx[1], 0) + sum_grad(a, ff[q].idx[2], 0);
-            float3 ge1 = cross3(ff[q].e2, Gfn), ge2 = cross3(Gfn, ff[q].e1);
-            if (ff[q].sgn != 0) {
-                float3 Gft = sum_grad(a, ff[q].idx[0], 1) + sum_grad(a, ff[q].idx[1], 1) + sum_grad(a, ff[q].idx[2], 1);
-                float3 gtv = (float)ff[q].sgn * nrm3_bwd(nrm3(ff[q].tv), Gft);
-                ge1 += ff[q].d2y * gtv;
-                ge2 -= ff[q].d1y * gtv;
+    if (valid) {
+        int lo = a.vf_off[v], hi = a.vf_off[v + 1];
+        for (int j = lo + slot; j < hi; j += ADMS_FRAME_SLOTS) {
+            FaceFrame ff = face_frame(a, a.vf_face[j]);
+            float3 Gfn = sum_grad(a, ff.idx[0], 0) + sum_grad(a, ff.idx[1], 0) + sum_grad(a, ff.idx[2], 0);
+            float3 ge1 = cross3(ff.e2, Gfn), ge2 = cross3(Gfn, ff.e1);
+            if (ff.sgn != 0) {
+                float3 Gft = sum_grad(a, ff.idx[0], 1) + sum_grad(a, ff.idx[1], 1) + sum_grad(a, ff.idx[2], 1);
+                float3 gtv = (float)ff.sgn * nrm3_bwd(nrm3(ff.tv), Gft);
+                ge1 += ff.d2y * gtv;
+                ge2 -= ff.d1y * gtv;
             }
-            if (ff[q].idx[0] == v) g -= ge1 + ge2;
-            if (ff[q].idx[1] == v) g += ge1;
-            if (ff[q].idx[2] == v) g += ge2;
+            if (ff.idx[0] == v) g -= ge1 + ge2;
+            if (ff.idx[1] == v) g += ge1;
+            if (ff.idx[2] == v) g += ge2;
         }
     }
-    fold_position_grad(a, v, g);
+    // the eight slots of a vertex are consecutive lanes of one warp
+#pragma unroll
+    for (int o = ADMS_FRAME_SLOTS / 2; o > 0; o >>= 1) {
+        g.x += __shfl_down_sync(0xffffffffu, g.x, o, ADMS_FRAME_SLOTS);
+        g.y += __shfl_down_sync(0xffffffffu, g.y, o, ADMS_FRAME_SLOTS);
+        g.z += __shfl_down_sync(0xffffffffu, g.z, o, ADMS_FRAME_SLOTS);
+    }
+    if (valid && slot == 0) fold_position_grad(a, v, g);
 }
 
 cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st) {
@@ -191,7 +197,7 @@ cudaError_t frame_forward(const FrameArgs& a, cudaStream_t st) {
 
 cudaError_t frame_backward(const FrameArgs& a, cudaStream_t st) {
     if (a.inv) {
-        k_frame_bwd_fused<<<(a.V + 127) / 128, 128, 0, st>>>(a);
+        k_frame_bwd_fused<<<(a.V * ADMS_FRAME_SLOTS + 127) / 128, 128, 0, st>>>(a);
         count_launches(1);
         return cudaGetLastError();
     }

@@ -423,7 +423,6 @@ __device__ __forceinline__ void raster_tile_body(const TriRec* __restrict__ rec,
     int Sx = 256 * px + 128, Sy = 256 * py + 128;
     bool inside = px < W && py < H;
     size_t pix = ((size_t)b * H + py) * W + px;
-    unsigned long long best = inside ? keys[pix] : ADMS_EMPTY_KEY;
     size_t t = (size_t)b * tiles_x * tiles_y + tile;
     long long off = tile_off[t];
     int cnt = tile_count[t];
@@ -432,6 +431,7 @@ __device__ __forceinline__ void raster_tile_body(const TriRec* __restrict__ rec,
     bool overflow = off + cnt > capacity;
     int n = overflow ? F : cnt;
     if (n == 0) return;  // no binned triangle: the small-triangle pass left the final keys
+    unsigned long long best = inside ? keys[pix] : ADMS_EMPTY_KEY;
     if (overflow && threadIdx.x == 0) atomicAdd(overflow_ctr, 1ull);
     // Each warp shades a 16 x 2 strip of the tile (rows 2w, 2w + 1): the staged records
     // whose pixel box meets a warp's rows go to that warp's list, and each warp walks
