@@ -368,9 +368,9 @@ adms_status ensure_scratch(adms_ctx* ctx, Job& j, int B, int H, int W) {
         j.view_cap = B;
     }
     if (ntiles > j.tile_cap) {
-        AL(j.rs.tile_count, ntiles);
+        AL(j.rs.tile_count, 2 * ntiles);  // the fill cursors follow: one clear per raster pass
         AL(j.rs.tile_off, ntiles);
-        AL(j.rs.tile_cursor, ntiles);
+        j.rs.tile_cursor = j.rs.tile_count + ntiles;
         j.tile_cap = ntiles;
     }
     // tile-list capacity: 8 entries per triangle and view, at least 4 per tile
@@ -900,8 +900,8 @@ adms_status job_create_impl(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
     AL(j.tmp_n, j.V);
     AL(j.tmp_t, j.V);
     AL(j.frame_inv, j.V);
-    AL(j.g_nrm, (size_t)j.V * 3);
-    AL(j.g_tan, (size_t)j.V * 3);
+    AL(j.g_nrm, (size_t)j.V * 6);  // the tangents' gradient follows: one clear per backward
+    j.g_tan = j.g_nrm + (size_t)j.V * 3;
     AL(j.g_pos_acc, (size_t)j.V * 3);
     AL(j.st, 1);
     bool mips = mat->mips != 0;
@@ -1625,8 +1625,7 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
                 CK(TIMED(ST_AA_LOSS, aa_loss_forward(r, ctx->stream)));
             }
         }
-        CK(cudaMemsetAsync(j.g_nrm, 0, sizeof(double) * 3 * j.V, ctx->stream));
-        CK(cudaMemsetAsync(j.g_tan, 0, sizeof(double) * 3 * j.V, ctx->stream));
+        CK(cudaMemsetAsync(j.g_nrm, 0, sizeof(double) * 6 * j.V, ctx->stream));  // g_nrm and g_tan
         if (j.tess || j.skin) CK(cudaMemsetAsync(j.g_rpos, 0, sizeof(float) * 3 * j.V, ctx->stream));
         if (n_jobs == 1 && j.L > 0) {
             adms_status s = peel_backward(ctx, j);

@@ -590,8 +590,12 @@ cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st
     cudaError_t e;
     // without a key buffer (every triangle binned: small_px = 0) the keys are left to raster_tiles' caller
     if (in.keys && (e = cudaMemsetAsync(in.keys, 0xFF, sizeof(unsigned long long) * B * H * W, st))) return e;
-    if ((e = cudaMemsetAsync(s.tile_count, 0, sizeof(int) * ntiles, st))) return e;
-    if ((e = cudaMemsetAsync(s.tile_cursor, 0, sizeof(int) * ntiles, st))) return e;
+    if (s.tile_cursor == s.tile_count + ntiles) {  // one buffer: counts, then cursors
+        if ((e = cudaMemsetAsync(s.tile_count, 0, sizeof(int) * 2 * ntiles, st))) return e;
+    } else {
+        if ((e = cudaMemsetAsync(s.tile_count, 0, sizeof(int) * ntiles, st))) return e;
+        if ((e = cudaMemsetAsync(s.tile_cursor, 0, sizeof(int) * ntiles, st))) return e;
+    }
     int bs = 256;
     k_transform<<<(B * V + bs - 1) / bs, bs, 0, st>>>(in.pos, V, in.views, B, W, H, s.clip, s.vs, s.scr);
     if (in.small_px > ADMS_SMALL_PX)
