@@ -323,9 +323,10 @@ def run_native(args):
                              raster_direct_px=256 if agg else 0, raster_depth_filter=agg)
     pl = bool(args.per_level_textures)
     # the tessellated candidate's ~17-pixel triangles rasterize faster directly than
-    # binned (the keys do not depend on the threshold): 256 measured best of 16..256,
-    # with plain atomicMin (about two fragments per sample: the key read costs more)
-    cdirect = 256 if wk == "tess" else 0
+    # binned (the keys do not depend on the threshold), with plain atomicMin (about two
+    # fragments per sample: the key read costs more); step ms for thresholds 64 / 128 /
+    # 256 / 512 / 1024 / 2048 samples: 6.36 / 6.15 / 5.96 / 5.87 / 5.93 / 5.98
+    cdirect = 512 if wk == "tess" else 0
     cand = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, per_level_textures=pl, samples=MS, layers=LY,
                           raster_direct_px=cdirect)
     plain = ctx.create_job(cfg["cand"], loss=loss, lr0=0.01, batch_views=NV, per_level_textures=pl, samples=MS,
