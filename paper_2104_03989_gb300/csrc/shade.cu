@@ -47,16 +47,24 @@ __global__ void __launch_bounds__(256, ADMS_AA_BLOCKS) k_aa_loss(ShadeArgs A) {
                   (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4), red);
 }
 
-// resident blocks per SM of the fused backward (register cap 65536 / (256 x this))
+// resident blocks per SM of the fused backward (register cap 65536 / (threads x this))
+// (the plain-method step: 256 threads x 3 blocks 0.174 ms; 128 x 5: 0.175; 128 x 6:
+// 0.171; 128 x 7: 0.171)
 #ifndef ADMS_BWD_BLOCKS
-#define ADMS_BWD_BLOCKS 3
+#define ADMS_BWD_BLOCKS 6
+#endif
+#ifndef ADMS_BWD_THREADS
+#define ADMS_BWD_THREADS 128  // 256: a block per 16x16 tile; 128: two blocks of 16x8 pixels
 #endif
 template <bool PEEL>
-__global__ void __launch_bounds__(256, ADMS_BWD_BLOCKS) k_shade_bwd(ShadeArgs A) {
-    __shared__ float rows[8 * 32 * ADMS_VROW];
+__global__ void __launch_bounds__(ADMS_BWD_THREADS, ADMS_BWD_BLOCKS) k_shade_bwd(ShadeArgs A) {
+    __shared__ float rows[(ADMS_BWD_THREADS / 32) * 32 * ADMS_VROW];
+    constexpr int PARTS = 256 / ADMS_BWD_THREADS;  // blocks per 16x16 tile, each a band of rows
     int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    shade_bwd_px<PEEL>(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
-                       (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4), rows + (threadIdx.x >> 5) * 32 * ADMS_VROW);
+    int tile = blockIdx.x / PARTS, part = blockIdx.x % PARTS;
+    shade_bwd_px<PEEL>(A, blockIdx.y, (tile % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
+                       (tile / tiles_x) * ADMS_TILE + part * (ADMS_TILE / PARTS) + (threadIdx.x >> 4),
+                       rows + (threadIdx.x >> 5) * 32 * ADMS_VROW);
 }
 
 // MSAA forward: a block takes a 32x32-sample region (four samples per thread), its
@@ -270,6 +278,12 @@ cudaError_t resolve_loss(const ResolveArgs& r, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ launchers
+static dim3 pix_grid(const ShadeArgs& a);
+static dim3 bwd_grid(const ShadeArgs& a) {
+    dim3 g = pix_grid(a);
+    g.x *= 256 / ADMS_BWD_THREADS;
+    return g;
+}
 static dim3 pix_grid(const ShadeArgs& a) {
     int tx = (a.W + ADMS_TILE - 1) / ADMS_TILE, ty = (a.H + ADMS_TILE - 1) / ADMS_TILE;
     return dim3(tx * ty, a.B);
@@ -312,9 +326,9 @@ cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st) {
         int R = ADMS_MSAA_REGION;
         k_shade_bwd_msaa<<<dim3(((a.W + R - 1) / R) * ((a.H + R - 1) / R), a.B), 256, 0, st>>>(a);
     } else if (a.peel) {
-        k_shade_bwd<true><<<pix_grid(a), 256, 0, st>>>(a);
+        k_shade_bwd<true><<<bwd_grid(a), ADMS_BWD_THREADS, 0, st>>>(a);
     } else {
-        k_shade_bwd<false><<<pix_grid(a), 256, 0, st>>>(a);
+        k_shade_bwd<false><<<bwd_grid(a), ADMS_BWD_THREADS, 0, st>>>(a);
     }
     count_launches(1);
     return cudaGetLastError();
