@@ -354,6 +354,9 @@ def run_native(args):
     loss_buf = torch.zeros(n_steps + 1, dtype=torch.float32, device=dev)
     graph_loss = torch.zeros(1, dtype=torch.float32, device=dev)
     cptr = ctx.ctx
+    if args.pipeline:
+        # each step's texture Adam runs beside the next step's frame and raster
+        B.adms_ctx_set_pipelining(cptr, True)
     i32 = C.c_int32
     jobs_c = (i32 * 1)(cand)
     plain_c = (i32 * 1)(plain)
@@ -636,7 +639,10 @@ def run_native(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "launch": "one CUDA graph per step: forward+loss, backward"
                                  + (" (raster recomputed)" if RECOMPUTE else "") + ", Adam; the step's reference "
-                                 f"images rendered before the timed region (a ring of {R} view batches)",
+                                 f"images rendered before the timed region (a ring of {R} view batches)"
+                                 + ("; pipelined steps: each step's texture Adam runs beside the next step's frame "
+                                    "and raster (every timed step runs one, the first the step's before the region)"
+                                    if args.pipeline else ""),
                        "l2": "working set > 126 MB L2 (textures, moments, buffers); no flush"},
             "p50_step_ms": per_sorted[len(per) // 2], "p99_step_ms": per_sorted[min(len(per) - 1, int(0.99 * len(per)))],
             "with_reference_render": {"value": with_ref_value, "unit": "Mpixels/s",
@@ -900,6 +906,9 @@ def main():
     ap.add_argument("--msaa", type=int, default=1, metavar="S",
                     help="plain workload rendered with S x S samples per pixel (MSAA, Sec. 5.2), references "
                          "supersampled; the metric counts pixels")
+    ap.add_argument("--pipeline", type=int, default=0, choices=[0, 1],
+                    help="plain-family workloads: defer each step's texture Adam to the next step's forward, "
+                         "beside its frame and raster (adms_ctx_set_pipelining; results unchanged)")
     ap.add_argument("--per-level-textures", action="store_true",
                     help="plain workload with every mip level of each texture an independent latent (Sec. 6)")
     args = ap.parse_args()

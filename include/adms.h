@@ -192,7 +192,25 @@ adms_status adms_ctx_set_stream(adms_ctx* ctx, void* cuda_stream);
  * alongside the reference render. The event is read at those calls (and captured
  * into a graph with them); the caller keeps it alive. */
 adms_status adms_ctx_set_ref_event(adms_ctx* ctx, void* cuda_event);
-/* Block until the context's stream is idle; surfaces latched device errors. */
+/* Pipelined optimizer steps (enable = 1; 0, the default, turns them off and
+ * issues what is deferred). No counterpart in the paper; the results are those of
+ * unpipelined steps. adms_optimizer_step then issues the schedules and the flat
+ * latents' updates (positions, skin weights, displacement) and defers the job's
+ * texture step (the texture latents' Adam updates with their mip chains, and the
+ * advance of t). The job's next adms_forward_loss (one job per call) issues it on
+ * a third stream of the context beside its vertex frame and raster, which read
+ * only the positions, and makes the context's stream wait for it before the
+ * shading, the first kernel that reads a texture. Any other call naming the job
+ * (render_reference, backward, a second optimizer_step, job_params, job_stats,
+ * export, gradient access, a batched forward_loss, ...) and adms_sync issue it
+ * first, in line, so every call sees the latents of the sequential schedule;
+ * memory read directly through adms_job_params pointers is current only after
+ * such a call. A graph records which jobs held a deferred step when its capture
+ * began and ended; adms_graph_launch refuses (ADMS_ERR_STATE) to replay it unless
+ * the same jobs hold one now. Not during a capture (ADMS_ERR_STATE). */
+adms_status adms_ctx_set_pipelining(adms_ctx* ctx, int32_t enable);
+/* Issue every deferred texture step, then block until the context's stream is
+ * idle; surfaces latched device errors. */
 adms_status adms_sync(adms_ctx* ctx);
 const char* adms_last_error(adms_ctx* ctx);
 /* Bytes of HBM currently held by the context's jobs and scratch. */
@@ -600,7 +618,10 @@ typedef struct adms_graph adms_graph;
  * contents the caller refreshes between launches. */
 adms_status adms_graph_begin(adms_ctx* ctx);
 adms_status adms_graph_end(adms_ctx* ctx, adms_graph** out);
-/* Enqueue one replay of a recorded graph on the context's stream. */
+/* Enqueue one replay of a recorded graph on the context's stream. With pipelined
+ * steps (adms_ctx_set_pipelining) the jobs holding a deferred texture step must be
+ * those at the capture's start (else ADMS_ERR_STATE, nothing enqueued); after the
+ * launch they are those at its end. */
 adms_status adms_graph_launch(adms_ctx* ctx, adms_graph* graph);
 adms_status adms_graph_destroy(adms_graph* graph);
 

@@ -154,6 +154,7 @@ SIGNATURES = {
     "adms_graph_destroy": ([P], C.c_int),
     "adms_ctx_profile": ([P, C.c_int32], C.c_int),
     "adms_ctx_test_wait_timeout": ([P, C.c_int32], C.c_int),
+    "adms_ctx_set_pipelining": ([P, C.c_int32], C.c_int),
     "adms_ctx_stage_times": ([P, P, P, C.c_int32], C.c_int),
     "adms_stage_count": ([], C.c_int32),
     "adms_stage_name": ([C.c_int32], C.c_char_p),
@@ -552,6 +553,10 @@ def adms_ctx_profile(ctx, enable=True):
 
 def adms_ctx_test_wait_timeout(ctx, enable=True):
     _check(ctx, lib().adms_ctx_test_wait_timeout(ctx, int(enable)))
+
+
+def adms_ctx_set_pipelining(ctx, enable=True):
+    _check(ctx, lib().adms_ctx_set_pipelining(ctx, int(enable)))
 
 
 def adms_ctx_stage_times(ctx):

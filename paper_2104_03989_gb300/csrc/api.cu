@@ -87,6 +87,9 @@ struct Job {
     JobState* st = nullptr;
     bool frame_valid = false;
     bool lap_valid = false;  // delta and lap_sum hold the Laplacian of the current positions
+    // a pipelined context's deferred texture step (the texture latents' Adam updates
+    // and the step counter of the last optimizer_step), not yet issued
+    bool tex_pending = false;
     // per-call scratch
     size_t px_cap = 0, view_cap = 0, tile_cap = 0, rec_cap = 0;
     unsigned long long* keys = nullptr;
@@ -143,6 +146,9 @@ struct StageRec {
 struct adms_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // jobs with a deferred texture step when the capture began / ended (sorted): a
+    // replay issues the steps of the first set and leaves those of the second
+    std::vector<adms_job> pend_begin, pend_end;
 };
 
 // device-side arguments and work items of the batched (many-job) launches
@@ -171,6 +177,13 @@ struct adms_ctx {
     // captured on `stream` holds both
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // pipelined optimizer steps (adms_ctx_set_pipelining): a job's texture step is
+    // deferred to its next forward_loss, which issues it on `late` beside its frame
+    // and raster and waits for it before the shading; any other call naming the job
+    // issues it first, in line
+    bool pipeline = false;
+    cudaStream_t late = nullptr;
+    cudaEvent_t ev_late_fork = nullptr, ev_late_join = nullptr;
     // failure-detection test hook: bytes added to each Adam tile's expected copy
     // count, so that its bounded waits run out (adms_ctx_test_wait_timeout)
     uint32_t adam_extra_tx = 0;
@@ -182,6 +195,7 @@ struct adms_ctx {
     std::string err;
     std::vector<Job> jobs;
     bool capturing = false;
+    std::vector<adms_job> cap_pending;  // jobs with a deferred texture step when the capture began
     // one argument / work-item state per job set (and tile width): a graph recorded
     // for one batch keeps valid device arguments while other batches run
     std::vector<BatchState> batches;
@@ -559,7 +573,9 @@ adms_status frame_branch(adms_ctx* ctx, Job& j, bool* forked) {
     return ADMS_OK;
 }
 
-adms_status render_core(adms_ctx* ctx, Job& j) {
+// join_late: the context's stream waits for the late stream (the job's deferred
+// texture step) before the shading, the first kernel that reads the textures
+adms_status render_core(adms_ctx* ctx, Job& j, bool join_late = false) {
     bool forked = false;
     adms_status fs = frame_branch(ctx, j, &forked);
     if (fs) return fs;
@@ -580,6 +596,7 @@ adms_status render_core(adms_ctx* ctx, Job& j) {
         CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
         CK(TIMED(ST_RASTER, raster_tiles_peeled(in, j.rs, j.L, ctx->stream)));
         if (forked) CK(join_branch(ctx));
+        if (join_late) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_late_join, 0));
         for (int l = 0; l < j.L; ++l) CK(TIMED(ST_SHADE, shade_forward(layer_args(j, l), ctx->stream)));
         return ADMS_OK;
     }
@@ -588,6 +605,7 @@ adms_status render_core(adms_ctx* ctx, Job& j) {
     CK(TIMED(ST_RASTER_SETUP, raster_prepare(in, j.rs, ctx->stream)));
     CK(TIMED(ST_RASTER, raster_tiles(in, j.rs, ctx->stream)));
     if (forked) CK(join_branch(ctx));
+    if (join_late) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_late_join, 0));
     CK(TIMED(ST_SHADE, shade_forward(shade_args(j), ctx->stream)));
     return ADMS_OK;
 }
@@ -1168,6 +1186,76 @@ void ckpt_describe(Job& j, CkptHeader& h, std::vector<CkptSection>& secs) {
 
 extern "C" {
 
+// ------------------------------------------------------------------ texture steps
+// the Adam updates of the texture latents of jobs js (Eq. 4 moments, clamps, the mip
+// chain rebuilt) on stream st: every job's tiled textures in one launch
+static adms_status texture_adams(adms_ctx* ctx, const std::vector<Job*>& js, cudaStream_t st) {
+    std::vector<TexAdam> tiled;
+    for (Job* jp : js) {
+        Job& j = *jp;
+        TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
+        for (int m = 0; m < 3; ++m) {
+            if (!maps[m]->opt) continue;
+            TexDev td = maps[m]->dev();
+            if (maps[m]->per_level) {
+                CK(TIMED(ST_ADAM, adam_texture_levels(td, maps[m]->m, maps[m]->v, m, j.st, st)));
+            } else if (adam_tiled(td)) {
+                TexAdam ta{td, maps[m]->m, maps[m]->v, j.st, m, 0};
+                ta.tmaps = maps[m]->tmaps;
+                tiled.push_back(ta);
+            } else {
+                CK(TIMED(ST_ADAM, adam_texture_and_mips(td, maps[m]->m, maps[m]->v, m, j.st, st)));
+            }
+        }
+    }
+    if (!tiled.empty()) CK(TIMED(ST_ADAM, adam_textures_tiled(tiled, st, ctx->adam_extra_tx)));
+    return ADMS_OK;
+}
+
+// a job's deferred texture step and step counter, in line on the context's stream
+static adms_status flush_job(adms_ctx* ctx, Job& j) {
+    if (!j.tex_pending) return ADMS_OK;
+    j.tex_pending = false;
+    adms_status s = texture_adams(ctx, {&j}, ctx->stream);
+    if (s) return s;
+    CK(TIMED(ST_SMALL, advance_step(j.st, ctx->stream)));
+    return ADMS_OK;
+}
+static adms_status flush_all(adms_ctx* ctx) {
+    for (auto& j : ctx->jobs)
+        if (j.alive) {
+            adms_status s = flush_job(ctx, j);
+            if (s) return s;
+        }
+    return ADMS_OK;
+}
+
+// forward_loss of one job: its deferred texture step on the late stream, ordered
+// after everything issued on the context's stream so far; *forked tells the caller
+// to wait for it before the shading (in line when profiling: the stage events time
+// it on the context's stream)
+static adms_status fork_texture_step(adms_ctx* ctx, Job& j, bool* forked) {
+    *forked = false;
+    if (!j.tex_pending) return ADMS_OK;
+    if (ctx->profile) return flush_job(ctx, j);
+    j.tex_pending = false;
+    CK(cudaEventRecord(ctx->ev_late_fork, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->late, ctx->ev_late_fork, 0));
+    adms_status s = texture_adams(ctx, {&j}, ctx->late);
+    if (s) return s;
+    CK(advance_step(j.st, ctx->late));
+    CK(cudaEventRecord(ctx->ev_late_join, ctx->late));
+    *forked = true;
+    return ADMS_OK;
+}
+
+static std::vector<adms_job> pending_jobs(adms_ctx* ctx) {
+    std::vector<adms_job> out;
+    for (size_t h = 0; h < ctx->jobs.size(); ++h)
+        if (ctx->jobs[h].alive && ctx->jobs[h].tex_pending) out.push_back((adms_job)h);
+    return out;
+}
+
 adms_status adms_ctx_create(adms_ctx** out, size_t hbm_budget_bytes, void* cuda_stream) {
     if (!out) return ADMS_ERR_ARG;
     int dev = 0;
@@ -1184,7 +1272,13 @@ adms_status adms_ctx_create(adms_ctx** out, size_t hbm_budget_bytes, void* cuda_
     }
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->late, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_late_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_late_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (c->ev_late_fork) cudaEventDestroy(c->ev_late_fork);
+        if (c->late) cudaStreamDestroy(c->late);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
         if (c->ev_fork) cudaEventDestroy(c->ev_fork);
         if (c->side) cudaStreamDestroy(c->side);
         delete c;
@@ -1202,9 +1296,13 @@ adms_status adms_ctx_destroy(adms_ctx* ctx) {
     for (BatchState& b : ctx->batches) batch_free(ctx, b);
     for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
     cudaStreamSynchronize(ctx->side);
+    cudaStreamSynchronize(ctx->late);
     cudaEventDestroy(ctx->ev_fork);
     cudaEventDestroy(ctx->ev_join);
+    cudaEventDestroy(ctx->ev_late_fork);
+    cudaEventDestroy(ctx->ev_late_join);
     cudaStreamDestroy(ctx->side);
+    cudaStreamDestroy(ctx->late);
     delete ctx;
     return ADMS_OK;
 }
@@ -1220,6 +1318,7 @@ adms_status adms_autotune(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, c
     for (int k = 0; k < n_jobs; ++k) {
         Job* j = get_job(ctx, jobs[k]);
         if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+        if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
         js.push_back(j);
     }
     // timing events, destroyed on every return path; the tile width is restored
@@ -1332,6 +1431,7 @@ static cudaError_t wait_ref(adms_ctx* ctx) {
 
 adms_status adms_sync(adms_ctx* ctx) {
     if (!ctx) return ADMS_ERR_ARG;
+    if (adms_status fs = flush_all(ctx)) return fs;
     CK(cudaStreamSynchronize(ctx->stream));
     return ADMS_OK;
 }
@@ -1358,6 +1458,7 @@ adms_status adms_job_create(adms_ctx* ctx, const adms_mesh_desc* mesh, const adm
 adms_status adms_job_destroy(adms_ctx* ctx, adms_job job) {
     Job* j = get_job(ctx, job);
     if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    j->tex_pending = false;  // a destroyed job's deferred texture step is dropped
     CK(cudaStreamSynchronize(ctx->stream));
     job_free(ctx, *j);
     batch_release(ctx, job);
@@ -1377,12 +1478,14 @@ adms_status adms_job_reserve(adms_ctx* ctx, adms_job job, int32_t n_views, int32
     Job* j = get_job(ctx, job);
     if (!j || n_views <= 0 || H <= 0 || W <= 0 || H > 16384 || W > 16384)
         return fail(ctx, ADMS_ERR_ARG, "invalid job handle or size");
+    if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
     return ensure_scratch(ctx, *j, n_views, H, W);
 }
 
 adms_status adms_job_params(adms_ctx* ctx, adms_job job, adms_param_view* out) {
     Job* j = get_job(ctx, job);
     if (!j || !out) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
     memset(out, 0, sizeof(*out));
     out->pos = j->pos;
     out->kd = (float*)j->kd.data;
@@ -1421,6 +1524,7 @@ adms_status adms_job_skinning(adms_ctx* ctx, adms_job job, const float* weights,
     Job* jp = get_job(ctx, job);
     if (!jp || !weights || n_bones < 1 || n_bones > ADMS_MAX_BONES || !(lr_scale >= 0.f))
         return fail(ctx, ADMS_ERR_ARG, "invalid job, weights, bone count (1..1024) or learning-rate scale");
+    if (adms_status fs = flush_job(ctx, *jp)) return fs;  // its deferred texture step first
     Job& j = *jp;
     if (j.tess) return fail(ctx, ADMS_ERR_STATE, "skinning of a tessellated job is not supported");
     if (j.L > 0) return fail(ctx, ADMS_ERR_STATE, "skinning of a depth-peeled job is not supported");
@@ -1451,6 +1555,7 @@ adms_status adms_job_skinning(adms_ctx* ctx, adms_job job, const float* weights,
 adms_status adms_job_set_bones(adms_ctx* ctx, adms_job job, const float* bones) {
     Job* j = get_job(ctx, job);
     if (!j || !bones) return fail(ctx, ADMS_ERR_ARG, "invalid job handle or bones");
+    if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
     if (!j->skin) return fail(ctx, ADMS_ERR_STATE, "the job has no skinning (adms_job_skinning)");
     CK(cudaMemcpyAsync(j->bones, bones, sizeof(float) * 16 * j->SB, cudaMemcpyDefault, ctx->stream));
     j->frame_valid = false;
@@ -1464,6 +1569,7 @@ adms_status adms_jobs_status(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs
     for (int k = 0; k < n_jobs; ++k) {
         Job* j = get_job(ctx, jobs[k]);
         if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+        if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
         sts.push_back(j->st);
     }
     CK(gather_status(sts.data(), n_jobs, out, ctx->stream));
@@ -1473,6 +1579,7 @@ adms_status adms_jobs_status(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs
 adms_status adms_job_stats(adms_ctx* ctx, adms_job job, adms_stats* out) {
     Job* j = get_job(ctx, job);
     if (!j || !out) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
     JobState hs;
     unsigned long long ovf = 0;
     CK(cudaMemcpyAsync(&hs, j->st, sizeof(hs), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1495,6 +1602,7 @@ adms_status adms_render_reference(adms_ctx* ctx, adms_job job, const adms_view* 
     Job* jp = get_job(ctx, job);
     if (!jp || !views || !out_rgb || n_views <= 0 || H <= 0 || W <= 0 || H > 16384 || W > 16384)
         return fail(ctx, ADMS_ERR_ARG, "invalid render_reference arguments");
+    if (adms_status fs = flush_job(ctx, *jp)) return fs;  // its deferred texture step first
     Job& j = *jp;
     adms_status s = ensure_scratch(ctx, j, n_views, H * j.S, W * j.S);
     if (s) return s;
@@ -1558,7 +1666,9 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
         vofs += B;
         CK(cudaMemsetAsync(&j.st->call_loss, 0, sizeof(double), ctx->stream));
         if (n_jobs == 1) {
-            if ((s = render_core(ctx, j))) return s;
+            bool late = false;  // the job's deferred texture step runs beside its frame and raster
+            if ((s = fork_texture_step(ctx, j, &late))) return s;
+            if ((s = render_core(ctx, j, late))) return s;
             CK(wait_ref(ctx));
             if (j.L > 0) {
                 if ((s = peel_composite(ctx, j, j.ref, &j.st->call_loss, out_img ? out_img[k] : nullptr))) return s;
@@ -1572,6 +1682,7 @@ adms_status adms_forward_loss(adms_ctx* ctx, const adms_job* jobs, int32_t n_job
                 CK(TIMED(ST_AA_LOSS, aa_loss_forward(a, ctx->stream)));
             }
         } else {
+            if ((s = flush_job(ctx, j))) return s;
             if ((s = frame_and_prepare(ctx, j, &forked))) return s;
         }
     }
@@ -1603,6 +1714,7 @@ adms_status adms_backward(adms_ctx* ctx, const adms_job* jobs, int32_t n_jobs, i
     for (int k = 0; k < n_jobs; ++k) {
         Job* jp = get_job(ctx, jobs[k]);
         if (!jp) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+        if (adms_status fs = flush_job(ctx, *jp)) return fs;  // its deferred texture step first
         for (Job* o : js)
             if (o == jp) return fail(ctx, ADMS_ERR_ARG, "a job appears twice in one call");
         js.push_back(jp);
@@ -1670,20 +1782,27 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
         if (jp->frozen) return fail(ctx, ADMS_ERR_STATE, "optimizer_step on a frozen job");
         js.push_back(jp);
     }
+    for (Job* jp : js) {
+        adms_status s = flush_job(ctx, *jp);  // a step not yet consumed by a forward_loss
+        if (s) return s;
+    }
     // schedules per job (after the Laplacian when no forward computed it for these
     // positions); then the flat latents (positions with the Laplacian term, skin
     // weights, displacement) on a branch beside the textures: every job's tiled
-    // textures in one launch; then, joined, the step counters
+    // textures in one launch; then, joined, the step counters. A pipelined context
+    // issues the flat latents' updates here and defers the texture step.
     for (Job* jp : js) {
         Job& j = *jp;
         if (j.opt.optimize_pos && !j.lap_valid) CK(TIMED(ST_LAPLACIAN, laplacian_forward(lap_args(j), ctx->stream)));
         SchedArgs sa{j.st, j.opt.lr0, j.opt.lambda0, j.opt.optimize_pos, j.LV};
         CK(TIMED(ST_SMALL, schedule_step(sa, ctx->stream)));
     }
-    cudaError_t fe;
-    cudaStream_t bs = fork_branch(ctx, fe);
-    CK(fe);
-    std::vector<TexAdam> tiled;
+    cudaStream_t bs = ctx->stream;
+    if (!ctx->pipeline) {
+        cudaError_t fe;
+        bs = fork_branch(ctx, fe);
+        CK(fe);
+    }
     for (Job* jp : js) {
         Job& j = *jp;
         if (j.opt.optimize_pos) {
@@ -1699,33 +1818,26 @@ adms_status adms_optimizer_step(adms_ctx* ctx, const adms_job* jobs, int32_t n_j
             if (j.opt.optimize_disp)
                 CK(TIMED(ST_ADAM, adam_flat(j.disp, j.g_disp, j.m_disp, j.v_disp, (long long)j.dh * j.dw, j.st, bs)));
         }
-        TexState* maps[3] = {&j.kd, &j.orm, &j.nrm};
-        for (int m = 0; m < 3; ++m) {
-            if (!maps[m]->opt) continue;
-            TexDev td = maps[m]->dev();
-            if (maps[m]->per_level)
-                CK(TIMED(ST_ADAM, adam_texture_levels(td, maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
-            else if (adam_tiled(td)) {
-                TexAdam ta{td, maps[m]->m, maps[m]->v, j.st, m, 0};
-                ta.tmaps = maps[m]->tmaps;
-                tiled.push_back(ta);
-            }
-            else CK(TIMED(ST_ADAM, adam_texture_and_mips(td, maps[m]->m, maps[m]->v, m, j.st, ctx->stream)));
-        }
     }
-    if (!tiled.empty()) CK(TIMED(ST_ADAM, adam_textures_tiled(tiled, ctx->stream, ctx->adam_extra_tx)));
-    CK(join_branch(ctx));
     for (Job* jp : js) {
-        CK(TIMED(ST_SMALL, advance_step(jp->st, ctx->stream)));
         jp->frame_valid = false;
         jp->lap_valid = false;
     }
+    if (ctx->pipeline) {
+        for (Job* jp : js) jp->tex_pending = true;
+        return ADMS_OK;
+    }
+    adms_status s = texture_adams(ctx, js, ctx->stream);
+    if (s) return s;
+    CK(join_branch(ctx));
+    for (Job* jp : js) CK(TIMED(ST_SMALL, advance_step(jp->st, ctx->stream)));
     return ADMS_OK;
 }
 
 adms_status adms_job_fold_gradients(adms_ctx* ctx, adms_job job, float* g_kd, float* g_orm, float* g_nrm) {
     Job* j = get_job(ctx, job);
     if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
     TexState* maps[3] = {&j->kd, &j->orm, &j->nrm};
     float* outs[3] = {g_kd, g_orm, g_nrm};
     for (int m = 0; m < 3; ++m) {
@@ -1743,6 +1855,7 @@ adms_status adms_job_fold_gradients(adms_ctx* ctx, adms_job job, float* g_kd, fl
 adms_status adms_job_zero_gradients(adms_ctx* ctx, adms_job job) {
     Job* jp = get_job(ctx, job);
     if (!jp) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    if (adms_status fs = flush_job(ctx, *jp)) return fs;  // its deferred texture step first
     Job& j = *jp;
     CK(cudaMemsetAsync(j.g_pos, 0, sizeof(float) * 3 * j.LV, ctx->stream));
     CK(cudaMemsetAsync(j.g_pos_acc, 0, sizeof(double) * 3 * j.V, ctx->stream));
@@ -1762,6 +1875,7 @@ adms_status adms_job_zero_gradients(adms_ctx* ctx, adms_job job) {
 adms_status adms_job_invalidate(adms_ctx* ctx, adms_job job) {
     Job* j = get_job(ctx, job);
     if (!j) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
     TexState* maps[3] = {&j->kd, &j->orm, &j->nrm};
     for (int m = 0; m < 3; ++m)
         if (!maps[m]->per_level) CK(TIMED(ST_MIP, mip_build(maps[m]->dev(), ctx->stream)));
@@ -1773,6 +1887,7 @@ adms_status adms_job_invalidate(adms_ctx* ctx, adms_job job) {
 adms_status adms_laplacian(adms_ctx* ctx, adms_job job, float* out_loss, float* g_pos) {
     Job* jp = get_job(ctx, job);
     if (!jp || !out_loss) return fail(ctx, ADMS_ERR_ARG, "invalid laplacian arguments");
+    if (adms_status fs = flush_job(ctx, *jp)) return fs;  // its deferred texture step first
     Job& j = *jp;
     LapArgs la{j.LV, j.pos, j.ring_off, j.ring, j.delta_ref, j.delta, g_pos, j.st};
     CK(TIMED(ST_LAPLACIAN, laplacian_forward(la, ctx->stream)));
@@ -1784,6 +1899,7 @@ adms_status adms_laplacian(adms_ctx* ctx, adms_job job, float* out_loss, float* 
 adms_status adms_job_keys(adms_ctx* ctx, adms_job job, uint64_t* out_keys, size_t capacity) {
     Job* j = get_job(ctx, job);
     if (!j || !out_keys) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
     size_t n = (size_t)j->B * j->H * j->W * std::max(j->L, 1);
     if (capacity < n) return fail(ctx, ADMS_ERR_ARG, "key buffer too small");
     CK(cudaMemcpyAsync(out_keys, j->keys, n * sizeof(uint64_t), cudaMemcpyDefault, ctx->stream));
@@ -1793,6 +1909,7 @@ adms_status adms_job_keys(adms_ctx* ctx, adms_job job, uint64_t* out_keys, size_
 adms_status adms_job_export(adms_ctx* ctx, adms_job job, void* host_buf, size_t* bytes) {
     Job* j = get_job(ctx, job);
     if (!j || !bytes) return fail(ctx, ADMS_ERR_ARG, "invalid job handle");
+    if (adms_status fs = flush_job(ctx, *j)) return fs;  // its deferred texture step first
     CkptHeader h;
     std::vector<CkptSection> secs;
     ckpt_describe(*j, h, secs);
@@ -1867,6 +1984,7 @@ adms_status adms_graph_begin(adms_ctx* ctx) {
     if (ctx->profile) return fail(ctx, ADMS_ERR_STATE, "disable stage profiling before capturing");
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     ctx->capturing = true;
+    ctx->cap_pending = pending_jobs(ctx);
     return ADMS_OK;
 }
 
@@ -1881,13 +1999,29 @@ adms_status adms_graph_end(adms_ctx* ctx, adms_graph** out) {
         delete g;
         return fail(ctx, ADMS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     }
+    g->pend_begin = ctx->cap_pending;
+    g->pend_end = pending_jobs(ctx);
     *out = g;
     return ADMS_OK;
 }
 
 adms_status adms_graph_launch(adms_ctx* ctx, adms_graph* g) {
     if (!ctx || !g) return fail(ctx, ADMS_ERR_ARG, "null graph");
+    if (pending_jobs(ctx) != g->pend_begin)
+        return fail(ctx, ADMS_ERR_STATE,
+                    "the graph was captured with another set of jobs holding a deferred texture step");
     CK(cudaGraphLaunch(g->exec, ctx->stream));
+    for (adms_job h : g->pend_begin) ctx->jobs[h].tex_pending = false;
+    for (adms_job h : g->pend_end) ctx->jobs[h].tex_pending = true;
+    return ADMS_OK;
+}
+
+adms_status adms_ctx_set_pipelining(adms_ctx* ctx, int32_t enable) {
+    if (!ctx) return ADMS_ERR_ARG;
+    if (ctx->capturing) return fail(ctx, ADMS_ERR_STATE, "cannot change pipelining during capture");
+    if (!enable)
+        if (adms_status fs = flush_all(ctx)) return fs;
+    ctx->pipeline = enable != 0;
     return ADMS_OK;
 }
 

@@ -654,7 +654,7 @@ __device__ __forceinline__ void aa_loss_block(const ShadeArgs& A, int b, int px,
     __syncthreads();
     if (threadIdx.x == 0 && A.loss_acc) {
         double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += red[w];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
         atomicAdd(A.loss_acc, s * (double)A.loss_scale);
     }
 }

@@ -23,28 +23,48 @@ __global__ void __launch_bounds__(256) k_shade_refine(ShadeArgs A) {
         shade_refine_px(A, A.refine[1 + i]);
 }
 
-// register caps measured on the plain-method step: 5 blocks/SM for shading,
-// 8 for AA + loss, 3 for the backward (a few hundred bytes of spills cost less
-// than the latency the extra resident warps hide)
+// A 16x16 tile of pixels is shaded by 256 / THREADS blocks, each a band of
+// 16 x (THREADS / 16) rows; thread t takes column t % 16 of row t / 16 of its band.
+template <int THREADS>
+__device__ __forceinline__ void band_pixel(int W, int& px, int& py) {
+    constexpr int PARTS = 256 / THREADS;
+    int tiles_x = (W + ADMS_TILE - 1) / ADMS_TILE;
+    int tile = blockIdx.x / PARTS, part = blockIdx.x % PARTS;
+    px = (tile % tiles_x) * ADMS_TILE + (threadIdx.x & 15);
+    py = (tile / tiles_x) * ADMS_TILE + part * (ADMS_TILE / PARTS) + (threadIdx.x >> 4);
+}
+
+// block shapes measured on the plain-method step (threads per block x resident
+// blocks per SM, i.e. the register cap 65536 / (threads x blocks)); shading: 256 x 5
+// 0.0928 ms, 256 x 4 0.0919, 256 x 6 0.0902, 128 x 10 0.0903, 128 x 8 0.0882, 128 x 12
+// 0.0882; AA + loss: 256 x 8 0.0612, 256 x 6 0.0672, 128 x 12 0.0631, 128 x 16 0.0593;
+// the backward's below (a few hundred bytes of spills cost less than the latency the
+// extra resident warps hide)
+#ifndef ADMS_FWD_THREADS
+#define ADMS_FWD_THREADS 128
+#endif
 #ifndef ADMS_FWD_BLOCKS
-#define ADMS_FWD_BLOCKS 5
+#define ADMS_FWD_BLOCKS 8
+#endif
+#ifndef ADMS_AA_THREADS
+#define ADMS_AA_THREADS 128
 #endif
 #ifndef ADMS_AA_BLOCKS
-#define ADMS_AA_BLOCKS 8
+#define ADMS_AA_BLOCKS 16
 #endif
 template <bool INLINE>
-__global__ void __launch_bounds__(256, ADMS_FWD_BLOCKS) k_shade_fwd(ShadeArgs A) {
-    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    shade_fwd_px<INLINE>(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
-                 (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4));
+__global__ void __launch_bounds__(ADMS_FWD_THREADS, ADMS_FWD_BLOCKS) k_shade_fwd(ShadeArgs A) {
+    int px, py;
+    band_pixel<ADMS_FWD_THREADS>(A.W, px, py);
+    shade_fwd_px<INLINE>(A, blockIdx.y, px, py);
 }
 
 template <bool PEEL>
-__global__ void __launch_bounds__(256, ADMS_AA_BLOCKS) k_aa_loss(ShadeArgs A) {
-    __shared__ double red[8];
-    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    aa_loss_block<PEEL>(A, blockIdx.y, (blockIdx.x % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
-                  (blockIdx.x / tiles_x) * ADMS_TILE + (threadIdx.x >> 4), red);
+__global__ void __launch_bounds__(ADMS_AA_THREADS, ADMS_AA_BLOCKS) k_aa_loss(ShadeArgs A) {
+    __shared__ double red[ADMS_AA_THREADS / 32];
+    int px, py;
+    band_pixel<ADMS_AA_THREADS>(A.W, px, py);
+    aa_loss_block<PEEL>(A, blockIdx.y, px, py, red);
 }
 
 // resident blocks per SM of the fused backward (register cap 65536 / (threads x this))
@@ -59,12 +79,9 @@ __global__ void __launch_bounds__(256, ADMS_AA_BLOCKS) k_aa_loss(ShadeArgs A) {
 template <bool PEEL>
 __global__ void __launch_bounds__(ADMS_BWD_THREADS, ADMS_BWD_BLOCKS) k_shade_bwd(ShadeArgs A) {
     __shared__ float rows[(ADMS_BWD_THREADS / 32) * 32 * ADMS_VROW];
-    constexpr int PARTS = 256 / ADMS_BWD_THREADS;  // blocks per 16x16 tile, each a band of rows
-    int tiles_x = (A.W + ADMS_TILE - 1) / ADMS_TILE;
-    int tile = blockIdx.x / PARTS, part = blockIdx.x % PARTS;
-    shade_bwd_px<PEEL>(A, blockIdx.y, (tile % tiles_x) * ADMS_TILE + (threadIdx.x & 15),
-                       (tile / tiles_x) * ADMS_TILE + part * (ADMS_TILE / PARTS) + (threadIdx.x >> 4),
-                       rows + (threadIdx.x >> 5) * 32 * ADMS_VROW);
+    int px, py;
+    band_pixel<ADMS_BWD_THREADS>(A.W, px, py);
+    shade_bwd_px<PEEL>(A, blockIdx.y, px, py, rows + (threadIdx.x >> 5) * 32 * ADMS_VROW);
 }
 
 // MSAA forward: a block takes a 32x32-sample region (four samples per thread), its
@@ -278,15 +295,15 @@ cudaError_t resolve_loss(const ResolveArgs& r, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------ launchers
-static dim3 pix_grid(const ShadeArgs& a);
-static dim3 bwd_grid(const ShadeArgs& a) {
-    dim3 g = pix_grid(a);
-    g.x *= 256 / ADMS_BWD_THREADS;
-    return g;
-}
 static dim3 pix_grid(const ShadeArgs& a) {
     int tx = (a.W + ADMS_TILE - 1) / ADMS_TILE, ty = (a.H + ADMS_TILE - 1) / ADMS_TILE;
     return dim3(tx * ty, a.B);
+}
+// the grid of band_pixel<threads>: 256 / threads blocks per tile
+static dim3 band_grid(const ShadeArgs& a, int threads) {
+    dim3 g = pix_grid(a);
+    g.x *= 256 / threads;
+    return g;
 }
 
 // grids of up to this many samples refine their bright pixels in the shading
@@ -304,9 +321,9 @@ cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
         int R = ADMS_MSAA_REGION;
         k_shade_fwd_msaa<<<dim3(((a.W + R - 1) / R) * ((a.H + R - 1) / R), a.B), 256, 0, st>>>(a);
     } else if (inline_refine) {
-        k_shade_fwd<true><<<pix_grid(a), 256, 0, st>>>(a);
+        k_shade_fwd<true><<<band_grid(a, ADMS_FWD_THREADS), ADMS_FWD_THREADS, 0, st>>>(a);
     } else {
-        k_shade_fwd<false><<<pix_grid(a), 256, 0, st>>>(a);
+        k_shade_fwd<false><<<band_grid(a, ADMS_FWD_THREADS), ADMS_FWD_THREADS, 0, st>>>(a);
     }
     count_launches(1);
     if (list) {
@@ -316,8 +333,8 @@ cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 cudaError_t aa_loss_forward(const ShadeArgs& a, cudaStream_t st) {
-    if (a.peel) k_aa_loss<true><<<pix_grid(a), 256, 0, st>>>(a);
-    else k_aa_loss<false><<<pix_grid(a), 256, 0, st>>>(a);
+    if (a.peel) k_aa_loss<true><<<band_grid(a, ADMS_AA_THREADS), ADMS_AA_THREADS, 0, st>>>(a);
+    else k_aa_loss<false><<<band_grid(a, ADMS_AA_THREADS), ADMS_AA_THREADS, 0, st>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -326,9 +343,9 @@ cudaError_t shade_backward(const ShadeArgs& a, cudaStream_t st) {
         int R = ADMS_MSAA_REGION;
         k_shade_bwd_msaa<<<dim3(((a.W + R - 1) / R) * ((a.H + R - 1) / R), a.B), 256, 0, st>>>(a);
     } else if (a.peel) {
-        k_shade_bwd<true><<<bwd_grid(a), ADMS_BWD_THREADS, 0, st>>>(a);
+        k_shade_bwd<true><<<band_grid(a, ADMS_BWD_THREADS), ADMS_BWD_THREADS, 0, st>>>(a);
     } else {
-        k_shade_bwd<false><<<bwd_grid(a), ADMS_BWD_THREADS, 0, st>>>(a);
+        k_shade_bwd<false><<<band_grid(a, ADMS_BWD_THREADS), ADMS_BWD_THREADS, 0, st>>>(a);
     }
     count_launches(1);
     return cudaGetLastError();

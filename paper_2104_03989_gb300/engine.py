@@ -207,5 +207,10 @@ class Context:
         self._keep["ref_event"] = event
         B.adms_ctx_set_ref_event(self.ctx, event)
 
+    def set_pipelining(self, enable=True):
+        """Defer each optimizer step's texture update to the job's next forward_loss,
+        where it runs beside the raster; results unchanged (adms_ctx_set_pipelining)."""
+        B.adms_ctx_set_pipelining(self.ctx, enable)
+
     def sync(self):
         B.adms_sync(self.ctx)
