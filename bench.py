@@ -643,7 +643,8 @@ def run_native(args):
                                  + ("; pipelined steps: each step's texture Adam runs beside the next step's frame "
                                     "and raster (every timed step runs one, the first the step's before the region)"
                                     if args.pipeline else ""),
-                       "l2": "working set > 126 MB L2 (textures, moments, buffers); no flush"},
+                       "l2": "working set > 126 MB L2 (textures, moments, buffers); no flush",
+                       "pipelined": bool(args.pipeline)},
             "p50_step_ms": per_sorted[len(per) // 2], "p99_step_ms": per_sorted[min(len(per) - 1, int(0.99 * len(per)))],
             "with_reference_render": {"value": with_ref_value, "unit": "Mpixels/s",
                                       "ms_per_step": with_ref_ms / args.steps,
@@ -906,9 +907,9 @@ def main():
     ap.add_argument("--msaa", type=int, default=1, metavar="S",
                     help="plain workload rendered with S x S samples per pixel (MSAA, Sec. 5.2), references "
                          "supersampled; the metric counts pixels")
-    ap.add_argument("--pipeline", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--pipeline", type=int, default=1, choices=[0, 1],
                     help="plain-family workloads: defer each step's texture Adam to the next step's forward, "
-                         "beside its frame and raster (adms_ctx_set_pipelining; results unchanged)")
+                         "beside its frame and raster (adms_ctx_set_pipelining; results unchanged); 0: sequential")
     ap.add_argument("--per-level-textures", action="store_true",
                     help="plain workload with every mip level of each texture an independent latent (Sec. 6)")
     args = ap.parse_args()

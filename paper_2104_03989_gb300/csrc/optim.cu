@@ -249,7 +249,20 @@ __device__ __forceinline__ float level_weight(const TexDev& t, int k) {
 struct AdamStage {
     float4 g[32][32], p[32][32], m[32][32], v[32][32];
 };
+// shared-memory stages of the streamed Adam (tiles in flight: the one being updated and
+// STAGES - 1 fetched ahead), whether a tile's fetch is issued before (EARLY) or after the
+// arithmetic of the tile STAGES - 1 ahead of it, and the resident blocks per SM the
+// register allocation must allow
+#ifndef ADMS_ADAM_STAGES
 #define ADMS_ADAM_STAGES 3
+#endif
+#ifndef ADMS_ADAM_EARLY_FETCH
+#define ADMS_ADAM_EARLY_FETCH 0
+#endif
+#ifndef ADMS_ADAM_MIN_BLOCKS
+#define ADMS_ADAM_MIN_BLOCKS 1
+#endif
+static_assert(ADMS_ADAM_STAGES == 2 || ADMS_ADAM_STAGES == 3, "two or three Adam stages");
 #define ADMS_ADAM_THREADS 256
 struct AdamSmem {
     AdamStage st[ADMS_ADAM_STAGES];
@@ -257,6 +270,10 @@ struct AdamSmem {
     uint64_t bar[ADMS_ADAM_STAGES];
 };
 #define ADMS_ADAM_WAIT_NS 2000000000ull  // a tile's wait gives up after 2 s
+// persistent blocks of the streamed Adam, in percent of the SMs (one block per SM at 100)
+#ifndef ADMS_ADAM_GRID_PCT
+#define ADMS_ADAM_GRID_PCT 100
+#endif
 
 __device__ __forceinline__ int even_bits(int t) {  // bits 0, 2, 4, 6 of t, packed
     return (t & 1) | ((t >> 1) & 2) | ((t >> 2) & 4) | ((t >> 3) & 8);
@@ -350,7 +367,20 @@ __device__ __forceinline__ void adam_pyramid(const TexAdamBatch& P, int tile, in
     }
 }
 
-__global__ void __launch_bounds__(ADMS_ADAM_THREADS, 1)
+// tid 0, during tile k (index `tile`): fetch the tile STAGES - 1 ahead into the stage
+// that tile k - 1 used, once tile k - 1's stores have read it; *fetched: the highest
+// tile ordinal fetched so far
+__device__ __forceinline__ void adam_fetch_ahead(const TexAdamBatch& P, AdamSmem& S, int tile, int k, int total,
+                                                 int* fetched) {
+    int ahead = tile + (ADMS_ADAM_STAGES - 1) * (int)gridDim.x;
+    if (ahead >= total) return;
+    int sa = (k + ADMS_ADAM_STAGES - 1) % ADMS_ADAM_STAGES;
+    bulk_wait_read0();
+    adam_fetch(P, ahead, S.st[sa], &S.bar[sa]);
+    *fetched = k + ADMS_ADAM_STAGES - 1;
+}
+
+__global__ void __launch_bounds__(ADMS_ADAM_THREADS, ADMS_ADAM_MIN_BLOCKS)
     k_adam_tex_stream(const __grid_constant__ TexAdamBatch P, int total) {
     extern __shared__ __align__(128) unsigned char adam_raw[];
     AdamSmem& S = *reinterpret_cast<AdamSmem*>(adam_raw);
@@ -365,13 +395,18 @@ __global__ void __launch_bounds__(ADMS_ADAM_THREADS, 1)
         fence_barrier_init();
     }
     __syncthreads();
-    // tile j of this block (tile blockIdx.x + j gridDim.x) goes through stage j % 3, whose
-    // (j / 3)-th phase its copies complete; tiles 0 and 1 are fetched here, tile j + 2
-    // during tile j, once tile j - 1's stores (same stage) have read it
+    // tile j of this block (tile blockIdx.x + j gridDim.x) goes through stage j % STAGES,
+    // whose (j / STAGES)-th phase its copies complete; tiles 0 .. STAGES - 2 are fetched
+    // here, tile j + STAGES - 1 during tile j, once tile j - 1's stores (same stage) have
+    // read it
     int tile = blockIdx.x;
+    int fetched = -1;  // tid 0: the highest tile ordinal whose copies were issued
     if (tid == 0)
-        for (int j = 0; j < 2; ++j)
-            if (tile + j * (int)gridDim.x < total) adam_fetch(P, tile + j * gridDim.x, S.st[j], &S.bar[j]);
+        for (int j = 0; j < ADMS_ADAM_STAGES - 1; ++j)
+            if (tile + j * (int)gridDim.x < total) {
+                adam_fetch(P, tile + j * gridDim.x, S.st[j], &S.bar[j]);
+                fetched = j;
+            }
     // the thread's quad: level-0 texels (x, y) .. (x + 1, y + 1) of the tile
     int cx = even_bits(tid), cy = even_bits(tid >> 1);  // its level-1 texel
     int x = 2 * cx, y = 2 * cy;
@@ -394,6 +429,9 @@ __global__ void __launch_bounds__(ADMS_ADAM_THREADS, 1)
         // (agreed per warp: the shuffles below need every lane)
         bool ok = __all_sync(0xffffffffu, mbar_wait(&S.bar[s], (uint32_t)(k / ADMS_ADAM_STAGES) & 1u, ADMS_ADAM_WAIT_NS));
         AdamStage& T = S.st[s];
+#if ADMS_ADAM_EARLY_FETCH
+        if (tid == 0 && ok) adam_fetch_ahead(P, S, tile, k, total, &fetched);
+#endif
         if (live && ok) {
             float4 c = zero;
             float w = 1.f / 1024.f;  // 1/4^5
@@ -452,14 +490,9 @@ __global__ void __launch_bounds__(ADMS_ADAM_THREADS, 1)
             if (tid == 0) atomicExch(&const_cast<JobState*>(A.js)->status_next, (int)ADMS_ERR_TIMEOUT);
             break;
         }
-        if (tid == 0) {
-            int ahead = tile + 2 * (int)gridDim.x;
-            if (ahead < total) {
-                int sa = (k + 2) % ADMS_ADAM_STAGES;
-                bulk_wait_read0();  // tile k - 1's stores (stage sa) have read their rows
-                adam_fetch(P, ahead, S.st[sa], &S.bar[sa]);
-            }
-        }
+#if !ADMS_ADAM_EARLY_FETCH
+        if (tid == 0) adam_fetch_ahead(P, S, tile, k, total, &fetched);
+#endif
         if (live) {
             if (tid == 0) {
                 const CUtensorMap* tm = P.maps[ent];
@@ -485,10 +518,11 @@ __global__ void __launch_bounds__(ADMS_ADAM_THREADS, 1)
             }
         }
     }
-    if (tile < total && tile + (int)gridDim.x < total) {
-        // gave up on tile k's wait: let tile k + 1's copies (issued a tile earlier) land
-        // before the block's memory is released
-        mbar_wait(&S.bar[(k + 1) % ADMS_ADAM_STAGES], (uint32_t)((k + 1) / ADMS_ADAM_STAGES) & 1u, ADMS_ADAM_WAIT_NS);
+    if (tid == 0 && tile < total) {
+        // gave up on tile k's wait: let the copies issued for later tiles land before the
+        // block's memory is released
+        for (int q = k + 1; q <= fetched; ++q)
+            mbar_wait(&S.bar[q % ADMS_ADAM_STAGES], (uint32_t)(q / ADMS_ADAM_STAGES) & 1u, ADMS_ADAM_WAIT_NS);
     }
     if (tid == 0) bulk_wait0();
 }
@@ -572,7 +606,8 @@ cudaError_t adam_textures_tiled(std::vector<TexAdam>& list, cudaStream_t st, uin
         }
         P.n = (int)(e1 - e0);
         P.extra_tx = extra_tx;
-        k_adam_tex_stream<<<std::min(tiles, sms), ADMS_ADAM_THREADS, sizeof(AdamSmem), st>>>(P, tiles);
+        int blocks = std::min(tiles, std::max(1, sms * ADMS_ADAM_GRID_PCT / 100));
+        k_adam_tex_stream<<<blocks, ADMS_ADAM_THREADS, sizeof(AdamSmem), st>>>(P, tiles);
         k_adam_mip_top<<<P.n, 256, 0, st>>>(P);
         count_launches(2);
         cudaError_t e = cudaGetLastError();

@@ -48,8 +48,10 @@ __device__ __forceinline__ DF df_affine(float c0, float s, DF q) {
 
 // ---------------------------------------------------------------- transform
 __global__ void k_transform(const float* __restrict__ pos, int V, const adms_view* __restrict__ views, int B, int W,
-                            int H, float4* __restrict__ clip, VtxS* __restrict__ vs, float4* __restrict__ scr) {
+                            int H, float4* __restrict__ clip, VtxS* __restrict__ vs, float4* __restrict__ scr,
+                            long long* __restrict__ zero_total) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && zero_total) *zero_total = 0;  // the tile-list allocation's counter (k_list_alloc)
     if (i >= B * V) return;
     int b = i / V, v = i - b * V;
     const float* M = views[b].mvp;
@@ -92,54 +94,29 @@ __global__ void k_transform(const float* __restrict__ pos, int V, const adms_vie
     vs[i] = o;
 }
 
-// ---------------------------------------------------------------- exclusive scan (one block)
-// exclusive scan of the per-tile counts in one block of 1024 threads: rounds of
-// 8192 entries, 8 consecutive entries per thread, warp scans by shuffles and
-// one scan of the 32 warp sums; out saturates at INT_MAX (the list-capacity
-// check catches an overflow), *total is exact
-__global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ in, int n, int* __restrict__ out,
-                                               long long* __restrict__ total) {
-    __shared__ long long wsum[32];
-    int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    long long carry = 0;
-    for (int base = 0; base < n; base += 8192) {
-        int v[8];
-        long long s = 0;
+// ---------------------------------------------------------------- tile-list allocation
+// Each tile's list segment [off, off + count) in the list buffer: a warp scans its 32
+// tiles' counts by shuffles and reserves their segments together with one 64-bit
+// atomicAdd on *total (zeroed by k_transform), so the segments lie in no particular
+// order, as the entries inside a segment already do (the raster's per-pixel minimum
+// does not depend on either). Offsets saturate at INT_MAX (the list-capacity check
+// catches an overflow); *total ends exact. Many small blocks rather than one large
+// scan block: a 1024-thread block does not fit on an SM beside a resident
+// streamed-Adam block, which a pipelined step runs at the same time.
+__global__ void __launch_bounds__(256) k_list_alloc(const int* __restrict__ count, int n, int* __restrict__ off,
+                                                    unsigned long long* __restrict__ total) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x, lane = threadIdx.x & 31;
+    long long c = i < n ? count[i] : 0;
+    long long x = c;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            int i = base + tid * 8 + k;
-            v[k] = i < n ? in[i] : 0;
-            s += v[k];
-        }
-        long long x = s;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[wid] = x;
-        __syncthreads();
-        if (wid == 0) {
-            long long w = wsum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                long long y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            wsum[lane] = w;
-        }
-        __syncthreads();
-        long long run = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - s;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            int i = base + tid * 8 + k;
-            if (i < n) out[i] = (int)min(run, (long long)0x7fffffff);
-            run += v[k];
-        }
-        carry += wsum[31];
-        __syncthreads();
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
     }
-    if (tid == 0) *total = carry;
+    unsigned long long base = 0;
+    if (lane == 31 && x > 0) base = atomicAdd(total, (unsigned long long)x);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (i < n) off[i] = (int)min((long long)base + x - c, (long long)0x7fffffff);
 }
 
 // ---------------------------------------------------------------- coverage test
@@ -597,14 +574,16 @@ cudaError_t raster_prepare(const RasterIn& in, RasterScratch& s, cudaStream_t st
         if ((e = cudaMemsetAsync(s.tile_cursor, 0, sizeof(int) * ntiles, st))) return e;
     }
     int bs = 256;
-    k_transform<<<(B * V + bs - 1) / bs, bs, 0, st>>>(in.pos, V, in.views, B, W, H, s.clip, s.vs, s.scr);
+    k_transform<<<(B * V + bs - 1) / bs, bs, 0, st>>>(in.pos, V, in.views, B, W, H, s.clip, s.vs, s.scr,
+                                                    s.total_pairs);
     if (in.small_px > ADMS_SMALL_PX)
         k_setup<true><<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec,
                                                           s.bin, s.asign, s.tile_count, in.keys, in.small_px, in.zfilter);
     else
         k_setup<false><<<(B * F + bs - 1) / bs, bs, 0, st>>>(in.tri, F, s.vs, V, B, W, H, tiles_x, tiles_y, s.rec,
                                                            s.bin, s.asign, s.tile_count, in.keys, in.small_px, 0);
-    k_scan<<<1, 1024, 0, st>>>(s.tile_count, ntiles, s.tile_off, s.total_pairs);
+    k_list_alloc<<<(ntiles + bs - 1) / bs, bs, 0, st>>>(s.tile_count, ntiles, s.tile_off,
+                                                       reinterpret_cast<unsigned long long*>(s.total_pairs));
     k_bin_fill<<<(B * F + bs - 1) / bs, bs, 0, st>>>(s.bin, F, B, tiles_x, tiles_y, s.tile_off, s.tile_cursor,
                                                    s.list, s.list_capacity, in.adj, s.asign, s.silmask);
     count_launches(4);
