@@ -41,10 +41,10 @@ WORKLOAD_AGG = ("aggregate geometry (Sec. 6): reference canopy of 600k opaque le
 # DRAM bytes per launch of the dominant kernel from an ncu capture, valid only
 # for the source it was measured on (sha256 of the listed files).
 TRAFFIC = {
-    "shade_bwd": {"bytes_per_launch": 150931200 + 27303936, "warp_instructions_per_launch": 119476965,
+    "shade_bwd": {"bytes_per_launch": 151613440 + 28056576, "warp_instructions_per_launch": 119476965,
                   "files": ["paper_2104_03989_gb300/csrc/shade.cu", "paper_2104_03989_gb300/csrc/pixel.cuh",
                             "paper_2104_03989_gb300/csrc/common.cuh", "paper_2104_03989_gb300/csrc/kernels.cuh"],
-                  "sha": "51d30f996af5e580",
+                  "sha": "a11f51614ea0cd54",
                   "capture": "profiles/shade_bwd_plain_workload.md"},
 }
 
