@@ -308,7 +308,9 @@ static dim3 band_grid(const ShadeArgs& a, int threads) {
 
 // grids of up to this many samples refine their bright pixels in the shading
 // kernel itself (no list, no second launch)
+#ifndef ADMS_INLINE_REFINE_PX
 #define ADMS_INLINE_REFINE_PX (1 << 20)
+#endif
 
 cudaError_t shade_forward(const ShadeArgs& a, cudaStream_t st) {
     bool inline_refine = a.msaa <= 1 && (size_t)a.B * a.H * a.W <= ADMS_INLINE_REFINE_PX;
