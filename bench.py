@@ -44,7 +44,7 @@ TRAFFIC = {
     "shade_bwd": {"bytes_per_launch": 151613440 + 28056576, "warp_instructions_per_launch": 119476965,
                   "files": ["paper_2104_03989_gb300/csrc/shade.cu", "paper_2104_03989_gb300/csrc/pixel.cuh",
                             "paper_2104_03989_gb300/csrc/common.cuh", "paper_2104_03989_gb300/csrc/kernels.cuh"],
-                  "sha": "a11f51614ea0cd54",
+                  "sha": "fd068b253bfdce39",
                   "capture": "profiles/shade_bwd_plain_workload.md"},
 }
 
