@@ -244,4 +244,4 @@ def step(job, views, refs, height, width):
     job.t += 1
     return dict(keys=obj["out"]["keys"], asign=obj["out"]["asign"], pre=obj["out"]["pre"].detach(),
                 img=obj["out"]["img"].detach(), loss=float(obj["total"].detach()), image_loss=float(obj["image"].detach()),
-                laplacian=float(obj["laplacian"]), lam=obj["lam"], grads=grads, lr=lr)
+                laplacian=float(obj["laplacian"].detach() if torch.is_tensor(obj["laplacian"]) else obj["laplacian"]), lam=obj["lam"], grads=grads, lr=lr)
