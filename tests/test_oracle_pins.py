@@ -411,7 +411,7 @@ def test_tonemap_counts_negative_radiance_as_black():
     # flat at Gamma(log 1) = 0 with zero slope; NaN is kept so a broken job shows
     x = torch.tensor([-3.0, -1.0, -0.25, 0.0, 0.5], dtype=F64, requires_grad=True)
     y = R.tonemap(x)
-    assert torch.all(y[:4] == 0.0) and float(y[4]) > 0.0
+    assert torch.all(y[:4] == 0.0) and float(y[4].detach()) > 0.0
     (g,) = torch.autograd.grad(y.sum(), x)
     assert torch.all(g[:3] == 0.0) and float(g[4]) > 0.0
     assert math.isnan(float(R.tonemap(torch.as_tensor([float("nan")], dtype=F64))[0]))
