@@ -427,7 +427,7 @@ def test_loss_zero_at_equality_with_zero_gradient(kind):
     x = torch.as_tensor(rng.uniform(0, 3, (2, 4, 4, 3)), dtype=F64).requires_grad_(True)
     L = R.image_loss(x, x.detach().clone(), kind)
     (g,) = torch.autograd.grad(L, x)
-    assert float(L) == 0.0 and torch.all(g == 0)
+    assert float(L.detach()) == 0.0 and torch.all(g == 0)
 
 
 def test_l1_loss_is_mean_abs():
